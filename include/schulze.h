@@ -1,0 +1,156 @@
+/*
+ * schulze.h -- C ABI of the GB300 (sm_103a) Schulze hot path.
+ *
+ * The Schulze method (Csar, Lackner, Pichler, "Computing the Schulze Method
+ * for Large-Scale Preference Data Sets", arXiv 2505.12976, Sect. 2.1) ranks
+ * candidates by widest paths in the weighted majority graph. The calls below
+ * cover its data-parallel path: the pairwise tally, the all-pairs widest-path
+ * closure in the (max, min) semiring (the classical Floyd-Warshall route of
+ * Sect. 1 and Sect. 4), and winner and ranking extraction.
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers (cudaMalloc / torch CUDA memory)
+ *    owned by the caller, unless a call says "host". The library never frees
+ *    them and keeps no reference after the call returns.
+ *  - Matrices are dense, row-major, leading dimension m, int32.
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream). Outputs are valid once the stream reaches
+ *    the end of the call's work.
+ *  - Return value: SCHULZE_OK or a negative code detected on the host
+ *    (bad argument, launch failure, allocation failure). Problems found by
+ *    the kernels in the data itself (an out-of-range or repeated id in a
+ *    ballot, a negative count) are recorded in the context's device status
+ *    word and read back by schulze_get_status(); outputs are then unspecified.
+ *  - A context owns its workspace and status word. Calls that share a
+ *    context must be ordered on one stream (they reuse the workspace);
+ *    create one context per concurrent stream.
+ *  - A call grows the workspace with cudaMalloc when it is too small. During
+ *    CUDA stream capture it does not allocate and returns SCHULZE_ERANGE
+ *    instead; call schulze_reserve() with the largest sizes first.
+ */
+#ifndef SCHULZE_H
+#define SCHULZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* schulze_stream_t; /* same type as cudaStream_t */
+typedef struct schulze_ctx schulze_ctx;
+
+enum schulze_status {
+  SCHULZE_OK = 0,
+  SCHULZE_EINVAL = -1,   /* null pointer, size out of range, bad flag combination */
+  SCHULZE_ENOMEM = -2,   /* workspace allocation failed */
+  SCHULZE_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  SCHULZE_EDATA = -4,    /* (device status) bad ballot id, repeated id, negative or too large count */
+  SCHULZE_ETIMEOUT = -5, /* (device status) a bounded device wait gave up */
+  SCHULZE_ERANGE = -6    /* workspace too small while the stream is being captured */
+};
+
+/* Closure flags (schulze_strongest_paths, schulze_run). */
+#define SCHULZE_F_AUTO 0u         /* 16-bit packed closure when bound <= 32767, else int32 */
+#define SCHULZE_F_FORCE_S32 1u    /* always the int32 closure */
+#define SCHULZE_F_FORCE_S16 2u    /* always the 16-bit closure; EINVAL if bound > 32767 */
+/* Tally flags (schulze_tally, schulze_run). */
+#define SCHULZE_F_TALLY_DENSE 4u  /* position-compare tally, O(n m^2) */
+#define SCHULZE_F_TALLY_SPARSE 8u /* pair-count tally, O(n k^2) */
+
+/* Human-readable text for a status code (static storage). */
+const char* schulze_strerror(int code);
+
+/* Create a context on `device` (made current for the call). *out receives it. */
+int schulze_ctx_create(int device, schulze_ctx** out);
+
+/* Free the workspace and the context. Waits for the device first. */
+int schulze_ctx_destroy(schulze_ctx* ctx);
+
+/* Size the workspace for elections up to m_max candidates and n_max ballots
+ * of at most k_max entries, so that later calls (and stream capture) do not
+ * allocate. Synchronous. */
+int schulze_reserve(schulze_ctx* ctx, int32_t m_max, int64_t n_max, int32_t k_max);
+
+/* Bytes of workspace currently held by the context. */
+size_t schulze_workspace_bytes(const schulze_ctx* ctx);
+
+/* Wait for `stream`, then copy the device status word to *status (host) and
+ * reset it to SCHULZE_OK. */
+int schulze_get_status(schulze_ctx* ctx, int32_t* status, schulze_stream_t stream);
+
+/*
+ * Pairwise tally (Sect. 2.1: the counts behind the majority margin
+ * mu(a,b) = d[a][b] - d[b][a]).
+ *   ranks  [n, k] int32 device, row v lists candidate ids best first; every
+ *          id in [0, m) and distinct within its row; k == m is a full
+ *          ranking, and with k < m the unlisted candidates are tied below
+ *          all listed ones.
+ *   d      [m, m] int32 device output: d[i][j] = #voters preferring i to j,
+ *          d[i][i] = 0. Overwritten completely.
+ *   flags  0 (choose by cost), SCHULZE_F_TALLY_DENSE or SCHULZE_F_TALLY_SPARSE.
+ * Sizes: 1 <= m <= 65535, 0 <= k <= m, 0 <= n < 2^31, n*k < 2^32.
+ * Bad ids are reported as SCHULZE_EDATA through schulze_get_status().
+ */
+int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
+                  uint32_t flags, schulze_stream_t stream);
+
+/*
+ * Widest paths (Sect. 2.1: p(a,b) = the largest width min over the edges of
+ * a path from a to b; Sect. 4: all pairs by Floyd-Warshall). Edge weights
+ * are winning votes: w[i][j] = d[i][j] if d[i][j] > d[j][i], else 0.
+ *   d      [m, m] int32 device input (e.g. from schulze_tally); read only.
+ *   bound  an upper bound on every entry of d (n for a tally of n ballots);
+ *          it selects the 16-bit packed closure when <= 32767. A d entry
+ *          above it, or below 0, is reported as SCHULZE_EDATA.
+ *   p      [m, m] int32 device output: p[i][j] = widest-path width from i to
+ *          j, 0 if j is unreachable, p[i][i] = 0. May not alias d.
+ *   flags  SCHULZE_F_AUTO, SCHULZE_F_FORCE_S32 or SCHULZE_F_FORCE_S16.
+ */
+int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                            uint32_t flags, schulze_stream_t stream);
+
+/*
+ * Winners (Sect. 2.1): i is a winner iff no j beats it, i.e. p[i][j] >=
+ * p[j][i] for all j.
+ *   p        [m, m] int32 device input.
+ *   winners  [m] int32 device output, 1 for a winner, 0 otherwise. At least
+ *            one entry is 1 when p comes from schulze_strongest_paths.
+ */
+int schulze_winners(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, schulze_stream_t stream);
+
+/*
+ * Ranking (Sect. 2.1, the relation p(a,b) >= p(b,a)). With ties that
+ * relation need not be transitive, so the output is the linear order of ids
+ * sorted by (beaten_by, id), where beaten_by[i] = #{j : p[j][i] > p[i][j]};
+ * it extends the strict relation "a beats b".
+ *   order      [m] int32 device output: candidate ids, best first.
+ *   beaten_by  [m] int32 device output, or NULL.
+ */
+int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* order, int32_t* beaten_by,
+                    schulze_stream_t stream);
+
+/*
+ * The whole path for one election: tally, widest paths, winners and ranking
+ * in one call (device buffers). d and p are written as by the calls above;
+ * winners, order and beaten_by may each be NULL. `flags` combines the tally
+ * and closure flags. The closure bound is n.
+ */
+int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d, int32_t* p,
+                int32_t* winners, int32_t* order, int32_t* beaten_by, uint32_t flags, schulze_stream_t stream);
+
+/*
+ * Same as schulze_run with HOST buffers: copies ranks to the device, runs the
+ * path on workspace memory and copies winners and order (each may be NULL)
+ * back to the host. Synchronous on `stream`. Device d and p stay inside the
+ * context. Returns SCHULZE_EDATA directly when the ballots are invalid.
+ */
+int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
+                     int32_t* winners_host, int32_t* order_host, uint32_t flags, schulze_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCHULZE_H */

@@ -1,0 +1,55 @@
+/*
+ * schulze_profile.h -- measurement hooks of the GB300 Schulze library.
+ *
+ * Not part of the method: these calls let a benchmark time the library's own
+ * kernels on the stream they run on, count launches, and measure the integer
+ * min/max issue rate the widest-path closure is bound by.
+ */
+#ifndef SCHULZE_PROFILE_H
+#define SCHULZE_PROFILE_H
+
+#include <stdint.h>
+
+#include "schulze.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per kernel class: launches, summed device time, summed algorithmic work
+ * (the class's own unit: min/max updates for the closure, bytes for the
+ * tally and extraction stages). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double work;
+} schulze_kernel_stats;
+
+/* enable != 0: from now on every kernel launch of this context records a CUDA
+ * event pair on its stream (cleared statistics); enable == 0: stop. */
+int schulze_profile_enable(schulze_ctx* ctx, int enable);
+
+/* Synchronizes the device, then writes up to `max` classes to out[] and
+ * their number to *count. Statistics keep accumulating until re-enabled. */
+int schulze_profile_read(schulze_ctx* ctx, schulze_kernel_stats* out, int max, int* count);
+
+/* Kernel launches issued by this context since it was created. */
+int64_t schulze_launch_count(const schulze_ctx* ctx);
+
+/*
+ * Integer min/max issue-rate probe: a grid of `blocks` x 256 threads runs
+ * `iters` iterations of 8 independent (max, min) chains per thread in the
+ * given lane format (kind 0: int32, 2 instructions per update; kind 1: packed
+ * int16x2, 2 instructions per 2 updates; kind 2: packed int16x2 with a
+ * three-input max folding two updates). *seconds receives the kernel time
+ * (CUDA events) and *updates the number of (max, min) lane updates done.
+ * Synchronous.
+ */
+int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCHULZE_PROFILE_H */

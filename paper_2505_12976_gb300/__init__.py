@@ -1,0 +1,270 @@
+"""Python binding of the GB300 Schulze library (libschulze.so).
+
+Argument marshalling only: every step of the Schulze path runs in the CUDA
+kernels behind the C ABI of ``include/schulze.h``. PyTorch supplies device
+memory and the current CUDA stream. The functions carry the C names:
+
+    schulze_tally(ranks, m)            -> d        int32 [m, m]
+    schulze_strongest_paths(d, bound)  -> p        int32 [m, m]
+    schulze_winners(p)                 -> winners  int32 [m] (0/1)
+    schulze_ranking(p)                 -> (order, beaten_by)
+    schulze_run(ranks, m)              -> dict with all of the above
+    schulze_run_host(ranks_np, m)      -> (winners, order) as numpy, host buffers in and out
+
+There is no CPU fallback: importing works without a GPU, but every call
+needs the compiled library and a CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libschulze.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EDATA, ETIMEOUT, ERANGE = 0, -1, -2, -3, -4, -5, -6
+F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE = 0, 1, 2, 4, 8
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+_c = ctypes
+_i32, _i64, _u32, _vp = _c.c_int32, _c.c_int64, _c.c_uint32, _c.c_void_p
+
+# (name, restype, argtypes) of every entry point declared in include/schulze.h
+SIGNATURES = [
+    ("schulze_strerror", _c.c_char_p, [_c.c_int]),
+    ("schulze_ctx_create", _c.c_int, [_c.c_int, _c.POINTER(_vp)]),
+    ("schulze_ctx_destroy", _c.c_int, [_vp]),
+    ("schulze_reserve", _c.c_int, [_vp, _i32, _i64, _i32]),
+    ("schulze_workspace_bytes", _c.c_size_t, [_vp]),
+    ("schulze_get_status", _c.c_int, [_vp, _c.POINTER(_i32), _vp]),
+    ("schulze_tally", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _u32, _vp]),
+    ("schulze_strongest_paths", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _u32, _vp]),
+    ("schulze_winners", _c.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    ("schulze_ranking", _c.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    ("schulze_run", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
+    ("schulze_run_host", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _u32, _vp]),
+    # include/schulze_profile.h
+    ("schulze_profile_enable", _c.c_int, [_vp, _c.c_int]),
+    ("schulze_profile_read", _c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
+    ("schulze_launch_count", _i64, [_vp]),
+    ("schulze_probe_minmax", _c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_double),
+                                        _c.POINTER(_c.c_double)]),
+]
+
+
+class _KernelStats(ctypes.Structure):
+    _fields_ = [("name", _c.c_char * 32), ("launches", _i64), ("ms", _c.c_double), ("work", _c.c_double)]
+
+
+class SchulzeError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = load().schulze_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+def load():
+    """Load libschulze.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(lib, name)
+                f.restype, f.argtypes = res, args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise SchulzeError(rc, what)
+
+
+class Context:
+    """One library context (workspace + device status word) per device."""
+
+    def __init__(self, device: int):
+        lib = load()
+        h = _vp()
+        _check(lib.schulze_ctx_create(int(device), ctypes.byref(h)), "schulze_ctx_create")
+        self.handle, self.device, self._lib = h, int(device), lib
+
+    def reserve(self, m_max: int, n_max: int, k_max: int):
+        _check(self._lib.schulze_reserve(self.handle, m_max, n_max, k_max), "schulze_reserve")
+
+    def workspace_bytes(self) -> int:
+        return int(self._lib.schulze_workspace_bytes(self.handle))
+
+    def status(self, stream=None) -> int:
+        st = _i32(0)
+        _check(self._lib.schulze_get_status(self.handle, ctypes.byref(st), _stream(stream, self.device)),
+               "schulze_get_status")
+        return int(st.value)
+
+    def profile(self, enable: bool = True):
+        """Start (clearing) or stop per-kernel event timing of this context."""
+        _check(self._lib.schulze_profile_enable(self.handle, 1 if enable else 0), "schulze_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel class: {"launches", "ms", "work"}} accumulated since profile()."""
+        buf = (_KernelStats * 64)()
+        cnt = _c.c_int(0)
+        _check(self._lib.schulze_profile_read(self.handle, buf, 64, ctypes.byref(cnt)), "schulze_profile_read")
+        return {buf[i].name.decode(): {"launches": int(buf[i].launches), "ms": float(buf[i].ms),
+                                       "work": float(buf[i].work)} for i in range(min(cnt.value, 64))}
+
+    def launch_count(self) -> int:
+        return int(self._lib.schulze_launch_count(self.handle))
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self._lib.schulze_ctx_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def context(device=None) -> Context:
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    if dev not in _ctx:
+        _ctx[dev] = Context(dev)
+    return _ctx[dev]
+
+
+def _stream(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_i32(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.int32:
+        raise ValueError(f"{name} must be int32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def _out(t, shape, device, name):
+    if t is None:
+        return torch.empty(shape, dtype=torch.int32, device=device)
+    return _dev_i32(t, name, shape)
+
+
+def _ptr(t):
+    return _vp(t.data_ptr()) if t is not None else None
+
+
+def schulze_tally(ranks: torch.Tensor, m: int, d: torch.Tensor | None = None, flags: int = 0,
+                  ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """d[i][j] = #ballots preferring i to j; ranks int32 [n, k] on the GPU."""
+    ranks = _dev_i32(ranks, "ranks")
+    if ranks.dim() != 2:
+        raise ValueError("ranks must be [n, k]")
+    ctx = ctx or context(ranks.device)
+    n, k = ranks.shape
+    d = _out(d, (m, m), ranks.device, "d")
+    _check(load().schulze_tally(ctx.handle, _ptr(ranks), n, m, k, _ptr(d), flags, _stream(stream, ctx.device)),
+           "schulze_tally")
+    return d
+
+
+def schulze_strongest_paths(d: torch.Tensor, bound: int, p: torch.Tensor | None = None, flags: int = 0,
+                            ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """Widest-path widths with winning-votes edge weights; bound >= max(d)."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    _dev_i32(d, "d", (m, m))
+    ctx = ctx or context(d.device)
+    p = _out(p, (m, m), d.device, "p")
+    _check(load().schulze_strongest_paths(ctx.handle, _ptr(d), m, int(bound), _ptr(p), flags,
+                                          _stream(stream, ctx.device)), "schulze_strongest_paths")
+    return p
+
+
+def schulze_winners(p: torch.Tensor, winners: torch.Tensor | None = None, ctx: Context | None = None,
+                    stream=None) -> torch.Tensor:
+    p = _dev_i32(p, "p")
+    m = p.shape[0]
+    _dev_i32(p, "p", (m, m))
+    ctx = ctx or context(p.device)
+    winners = _out(winners, (m,), p.device, "winners")
+    _check(load().schulze_winners(ctx.handle, _ptr(p), m, _ptr(winners), _stream(stream, ctx.device)),
+           "schulze_winners")
+    return winners
+
+
+def schulze_ranking(p: torch.Tensor, order: torch.Tensor | None = None, beaten_by: torch.Tensor | None = None,
+                    ctx: Context | None = None, stream=None):
+    p = _dev_i32(p, "p")
+    m = p.shape[0]
+    _dev_i32(p, "p", (m, m))
+    ctx = ctx or context(p.device)
+    order = _out(order, (m,), p.device, "order")
+    beaten_by = _out(beaten_by, (m,), p.device, "beaten_by")
+    _check(load().schulze_ranking(ctx.handle, _ptr(p), m, _ptr(order), _ptr(beaten_by),
+                                  _stream(stream, ctx.device)), "schulze_ranking")
+    return order, beaten_by
+
+
+def schulze_run(ranks: torch.Tensor, m: int, flags: int = 0, out: dict | None = None, ctx: Context | None = None,
+                stream=None) -> dict:
+    """Tally, widest paths, winners and ranking for one election."""
+    ranks = _dev_i32(ranks, "ranks")
+    n, k = ranks.shape
+    ctx = ctx or context(ranks.device)
+    out = out or {}
+    dev = ranks.device
+    d = _out(out.get("d"), (m, m), dev, "d")
+    p = _out(out.get("p"), (m, m), dev, "p")
+    w = _out(out.get("winners"), (m,), dev, "winners")
+    o = _out(out.get("order"), (m,), dev, "order")
+    b = _out(out.get("beaten_by"), (m,), dev, "beaten_by")
+    _check(load().schulze_run(ctx.handle, _ptr(ranks), n, m, k, _ptr(d), _ptr(p), _ptr(w), _ptr(o), _ptr(b),
+                              flags, _stream(stream, ctx.device)), "schulze_run")
+    return {"d": d, "p": p, "winners": w, "order": o, "beaten_by": b}
+
+
+def probe_minmax(kind: int, blocks: int, iters: int, device: int = 0):
+    """(seconds, updates) of the integer min/max issue-rate probe; kind 0 int32,
+    1 packed int16x2, 2 packed int16x2 with a three-input max."""
+    sec, upd = _c.c_double(0), _c.c_double(0)
+    _check(load().schulze_probe_minmax(device, kind, blocks, iters, ctypes.byref(sec), ctypes.byref(upd)),
+           "schulze_probe_minmax")
+    return sec.value, upd.value
+
+
+def schulze_run_host(ranks: np.ndarray, m: int, flags: int = 0, winners: np.ndarray | None = None,
+                     order: np.ndarray | None = None, device=None, stream=None):
+    """Host buffers in and out (pinned or pageable numpy/torch CPU memory)."""
+    if isinstance(ranks, torch.Tensor):
+        if ranks.is_cuda or ranks.dtype != torch.int32 or not ranks.is_contiguous():
+            raise ValueError("ranks must be a contiguous int32 CPU tensor")
+        rptr, (n, k) = ranks.data_ptr(), ranks.shape
+    else:
+        if ranks.dtype != np.int32 or not ranks.flags.c_contiguous:
+            raise ValueError("ranks must be a contiguous int32 array")
+        rptr, (n, k) = ranks.ctypes.data, ranks.shape
+    ctx = context(device)
+    winners = np.empty(m, np.int32) if winners is None else winners
+    order = np.empty(m, np.int32) if order is None else order
+    wptr = winners.data_ptr() if isinstance(winners, torch.Tensor) else winners.ctypes.data
+    optr = order.data_ptr() if isinstance(order, torch.Tensor) else order.ctypes.data
+    _check(load().schulze_run_host(ctx.handle, _vp(rptr), n, m, k, _vp(wptr), _vp(optr), flags,
+                                   _stream(stream, ctx.device)), "schulze_run_host")
+    return winners, order

@@ -1,0 +1,230 @@
+// Context, workspace and the public entry points of include/schulze.h.
+#include <stdlib.h>
+
+#include <algorithm>
+#include <new>
+
+#include "internal.cuh"
+
+namespace schulze {
+
+int ensure_workspace(schulze_ctx* ctx, size_t bytes, cudaStream_t stream) {
+  if (bytes <= ctx->ws.bytes) return SCHULZE_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cs != cudaStreamCaptureStatusNone) return SCHULZE_ERANGE;
+  // Grow geometrically so that a sweep of sizes does not reallocate each call.
+  size_t want = std::max(bytes, ctx->ws.bytes + ctx->ws.bytes / 2);
+  want = align_up(want, size_t(1) << 20);
+  if (ctx->ws.base) {
+    // Work queued on any stream may still use the old buffer.
+    if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
+    cudaFree(ctx->ws.base);
+    ctx->ws.base = nullptr;
+    ctx->ws.bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return SCHULZE_ENOMEM;
+  }
+  ctx->ws.base = p;
+  ctx->ws.bytes = want;
+  return SCHULZE_OK;
+}
+
+bool use_s16(int64_t bound, uint32_t flags) {
+  if (flags & SCHULZE_F_FORCE_S32) return false;
+  if (flags & SCHULZE_F_FORCE_S16) return true;
+  return bound <= 32767;
+}
+
+static int set_device(schulze_ctx* ctx) {
+  return cudaSetDevice(ctx->device) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+}
+
+}  // namespace schulze
+
+using namespace schulze;
+
+extern "C" {
+
+const char* schulze_strerror(int code) {
+  switch (code) {
+    case SCHULZE_OK: return "ok";
+    case SCHULZE_EINVAL: return "invalid argument";
+    case SCHULZE_ENOMEM: return "out of device memory for the workspace";
+    case SCHULZE_ECUDA: return "CUDA runtime or launch failure";
+    case SCHULZE_EDATA: return "invalid data: ballot id out of range or repeated, or count out of range";
+    case SCHULZE_ETIMEOUT: return "a bounded device wait gave up";
+    case SCHULZE_ERANGE: return "workspace too small during stream capture (call schulze_reserve first)";
+    default: return "unknown status";
+  }
+}
+
+int schulze_ctx_create(int device, schulze_ctx** out) {
+  if (!out) return SCHULZE_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 ? SCHULZE_EINVAL : SCHULZE_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
+  schulze_ctx* c = new (std::nothrow) schulze_ctx();
+  if (!c) return SCHULZE_ENOMEM;
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = size_t(optin);
+  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->status) cudaFree(c->status);
+    delete c;
+    return SCHULZE_ENOMEM;
+  }
+  *out = c;
+  return SCHULZE_OK;
+}
+
+int schulze_ctx_destroy(schulze_ctx* ctx) {
+  if (!ctx) return SCHULZE_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws.base) cudaFree(ctx->ws.base);
+  if (ctx->status) cudaFree(ctx->status);
+  delete ctx;
+  return SCHULZE_OK;
+}
+
+size_t schulze_workspace_bytes(const schulze_ctx* ctx) { return ctx ? ctx->ws.bytes : 0; }
+
+int schulze_reserve(schulze_ctx* ctx, int32_t m_max, int64_t n_max, int32_t k_max) {
+  if (!ctx || m_max < 1 || m_max > kMaxM || n_max < 0 || k_max < 0 || k_max > m_max) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  size_t t = std::max(tally_workspace_bytes(n_max, m_max, k_max, 0),
+                      std::max(tally_workspace_bytes(n_max, m_max, k_max, SCHULZE_F_TALLY_DENSE),
+                               tally_workspace_bytes(n_max, m_max, k_max, SCHULZE_F_TALLY_SPARSE)));
+  size_t c = std::max(closure_workspace_bytes(m_max, n_max, 0), closure_workspace_bytes(m_max, 1, 0));
+  size_t x = extract_workspace_bytes(m_max);
+  size_t need = std::max(t, std::max(c, x));
+  // schulze_run_host keeps ranks, d and p in the workspace next to the stages
+  size_t host_path = align_up(size_t(n_max) * size_t(k_max) * 4, 256) +
+                     2 * align_up(size_t(m_max) * size_t(m_max) * 4, 256) + align_up(2 * size_t(m_max) * 4, 256) +
+                     need + 4096;
+  need = std::max(need, host_path);
+  int rc = ensure_workspace(ctx, need, nullptr);
+  if (rc) return rc;
+  return cudaDeviceSynchronize() == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+}
+
+int schulze_get_status(schulze_ctx* ctx, int32_t* status, schulze_stream_t stream) {
+  if (!ctx || !status) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  int32_t h = 0;
+  if (cudaMemcpyAsync(&h, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  if (cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return SCHULZE_ECUDA;
+  *status = h;
+  return SCHULZE_OK;
+}
+
+int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
+                  uint32_t flags, schulze_stream_t stream) {
+  if (!ctx || !d || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 || n >= (int64_t(1) << 31) ||
+      uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks))
+    return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_TALLY_DENSE) && (flags & SCHULZE_F_TALLY_SPARSE)) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, tally_workspace_bytes(n, m, k, flags), stream)) return rc;
+  return tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream);
+}
+
+int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                            uint32_t flags, schulze_stream_t stream) {
+  if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || bound < 0) return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || bound > 32767)) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, closure_workspace_bytes(m, bound, flags), stream)) return rc;
+  return closure_launch(ctx, d, m, bound, p, flags, ctx->ws.base, stream);
+}
+
+int schulze_winners(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, schulze_stream_t stream) {
+  if (!ctx || !p || !winners || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, extract_workspace_bytes(m), stream)) return rc;
+  return extract_launch(ctx, p, m, winners, nullptr, nullptr, ctx->ws.base, stream);
+}
+
+int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* order, int32_t* beaten_by,
+                    schulze_stream_t stream) {
+  if (!ctx || !p || !order || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, extract_workspace_bytes(m), stream)) return rc;
+  return extract_launch(ctx, p, m, nullptr, order, beaten_by, ctx->ws.base, stream);
+}
+
+int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d, int32_t* p,
+                int32_t* winners, int32_t* order, int32_t* beaten_by, uint32_t flags, schulze_stream_t stream) {
+  if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 ||
+      n >= (int64_t(1) << 31) || uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks))
+    return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_TALLY_DENSE) && (flags & SCHULZE_F_TALLY_SPARSE)) return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || n > 32767)) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  size_t need = std::max(tally_workspace_bytes(n, m, k, flags),
+                         std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
+  if (int rc = ensure_workspace(ctx, need, stream)) return rc;
+  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream)) return rc;
+  if (int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream)) return rc;
+  if (winners || order || beaten_by)
+    if (int rc = extract_launch(ctx, p, m, winners, order, beaten_by, ctx->ws.base, stream)) return rc;
+  return SCHULZE_OK;
+}
+
+int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
+                     int32_t* winners_host, int32_t* order_host, uint32_t flags, schulze_stream_t stream) {
+  if (!ctx || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 || n >= (int64_t(1) << 31) ||
+      uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks_host))
+    return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  size_t rbytes = size_t(n) * size_t(k) * sizeof(int32_t);
+  size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
+  size_t stage = std::max(tally_workspace_bytes(n, m, k, flags),
+                          std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
+  size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + align_up(2 * size_t(m) * 4, 256);
+  if (int rc = ensure_workspace(ctx, head + stage + 4096, stream)) return rc;
+  Carver cv(ctx->ws.base);
+  int32_t* ranks = cv.take<int32_t>(size_t(n) * size_t(k));
+  int32_t* d = cv.take<int32_t>(size_t(m) * size_t(m));
+  int32_t* p = cv.take<int32_t>(size_t(m) * size_t(m));
+  int32_t* win = cv.take<int32_t>(size_t(m));
+  int32_t* ord = cv.take<int32_t>(size_t(m));
+  void* rest = cv.take<char>(0);
+  if (rbytes && cudaMemcpyAsync(ranks, ranks_host, rbytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, stream)) return rc;
+  if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, stream)) return rc;
+  if (winners_host || order_host)
+    if (int rc = extract_launch(ctx, p, m, win, ord, nullptr, rest, stream)) return rc;
+  if (winners_host &&
+      cudaMemcpyAsync(winners_host, win, size_t(m) * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  if (order_host && cudaMemcpyAsync(order_host, ord, size_t(m) * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  int32_t st = 0;
+  if (cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (st != 0) {
+    cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), stream);
+    cudaStreamSynchronize(stream);
+    return st;
+  }
+  return SCHULZE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/schulze.h"
+#include "../../include/schulze_profile.h"
+
+namespace schulze {
+
+constexpr int kMaxM = 65535;
+
+// Device status word helpers: the first error recorded wins.
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace schulze
+
+namespace schulze {
+// One profiled launch: event pair plus the class it belongs to.
+struct ProfRecord {
+  int cls;
+  cudaEvent_t start, stop;
+  double work;
+};
+struct ProfClass {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0.0, work = 0.0;
+};
+}  // namespace schulze
+
+struct schulze_ctx {
+  int device = 0;
+  int32_t* status = nullptr;  // device word
+  schulze::Workspace ws;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<schulze::ProfRecord> prof_pending;
+  std::vector<schulze::ProfClass> prof_classes;
+  std::vector<cudaEvent_t> prof_free_events;
+};
+
+namespace schulze {
+
+// Make sure ctx->ws holds at least `bytes`; may cudaMalloc unless the stream
+// is capturing (then SCHULZE_ERANGE).
+int ensure_workspace(schulze_ctx* ctx, size_t bytes, cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of the workspace.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Workspace sizes (bytes) of each stage, for ensure_workspace and reserve.
+size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags);
+size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags);
+size_t extract_workspace_bytes(int32_t m);
+
+// Stage launchers operating on caller-provided workspace (no allocation).
+int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
+                 uint32_t flags, void* ws, cudaStream_t stream);
+int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
+                   void* ws, cudaStream_t stream);
+int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
+                   int32_t* beaten_by, void* ws, cudaStream_t stream);
+
+// Brackets one kernel launch: counts it and, when profiling is on, records
+// CUDA events around it on `stream`, filed under `name` with `work` units.
+class Launch {
+ public:
+  Launch(schulze_ctx* ctx, cudaStream_t stream, const char* name, double work);
+  ~Launch();
+
+ private:
+  schulze_ctx* ctx_;
+  cudaStream_t stream_;
+  int rec_ = -1;
+};
+
+inline int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+}
+
+bool use_s16(int64_t bound, uint32_t flags);
+
+}  // namespace schulze

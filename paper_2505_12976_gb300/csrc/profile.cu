@@ -1,0 +1,171 @@
+// Launch accounting, optional per-kernel event timing, and the integer
+// min/max issue-rate probe (include/schulze_profile.h).
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace schulze {
+
+static int class_index(schulze_ctx* ctx, const char* name) {
+  for (size_t i = 0; i < ctx->prof_classes.size(); ++i)
+    if (ctx->prof_classes[i].name == name) return int(i);
+  ProfClass c;
+  c.name = name;
+  ctx->prof_classes.push_back(c);
+  return int(ctx->prof_classes.size()) - 1;
+}
+
+static cudaEvent_t get_event(schulze_ctx* ctx) {
+  if (!ctx->prof_free_events.empty()) {
+    cudaEvent_t e = ctx->prof_free_events.back();
+    ctx->prof_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+Launch::Launch(schulze_ctx* ctx, cudaStream_t stream, const char* name, double work) : ctx_(ctx), stream_(stream) {
+  ctx->launches += 1;
+  if (!ctx->profiling) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  ProfRecord r;
+  r.cls = class_index(ctx, name);
+  r.start = get_event(ctx);
+  r.stop = get_event(ctx);
+  r.work = work;
+  if (!r.start || !r.stop) return;
+  cudaEventRecord(r.start, stream);
+  ctx->prof_pending.push_back(r);
+  rec_ = int(ctx->prof_pending.size()) - 1;
+}
+
+Launch::~Launch() {
+  if (rec_ >= 0) cudaEventRecord(ctx_->prof_pending[rec_].stop, stream_);
+}
+
+static void drain(schulze_ctx* ctx) {
+  for (ProfRecord& r : ctx->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      ProfClass& c = ctx->prof_classes[r.cls];
+      c.launches += 1;
+      c.ms += ms;
+      c.work += r.work;
+    } else {
+      cudaGetLastError();
+    }
+    ctx->prof_free_events.push_back(r.start);
+    ctx->prof_free_events.push_back(r.stop);
+  }
+  ctx->prof_pending.clear();
+}
+
+// ----------------------------------------------------------- probe
+
+template <int KIND>
+__global__ void __launch_bounds__(256) minmax_probe_kernel(int iters, uint32_t seed, uint32_t* sink) {
+  constexpr int C = 16;
+  uint32_t c[C], a[C];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    c[q] = (t * 2654435761u + q * 40503u + seed) & 0x3FFF3FFFu;
+    a[q] = (t * 97u + q * 7919u + seed * 3u) & 0x3FFF3FFFu;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      // a[] stays fixed; the other operand is another chain's running value,
+      // so nothing can be hoisted out of the loop
+      const uint32_t b = c[(q + 5) % C];
+      if (KIND == 0) {
+        c[q] = uint32_t(max(int32_t(c[q]), min(int32_t(a[q]), int32_t(b))));
+      } else if (KIND == 1) {
+        c[q] = __vmaxs2(c[q], __vmins2(a[q], b));
+      } else {
+        c[q] = __vimax3_s16x2(c[q], __vmins2(a[q], b), __vmins2(a[(q + 1) % C], c[(q + 9) % C]));
+      }
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < C; ++q) s ^= c[q];
+  if (s == 0x12345678u) sink[0] = s;
+}
+
+}  // namespace schulze
+
+using namespace schulze;
+
+extern "C" {
+
+int schulze_profile_enable(schulze_ctx* ctx, int enable) {
+  if (!ctx) return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
+  drain(ctx);
+  ctx->prof_classes.clear();
+  ctx->profiling = enable != 0;
+  return SCHULZE_OK;
+}
+
+int schulze_profile_read(schulze_ctx* ctx, schulze_kernel_stats* out, int max, int* count) {
+  if (!ctx || !count || (max > 0 && !out)) return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
+  drain(ctx);
+  int n = int(ctx->prof_classes.size());
+  for (int i = 0; i < n && i < max; ++i) {
+    const ProfClass& c = ctx->prof_classes[i];
+    memset(out[i].name, 0, sizeof(out[i].name));
+    strncpy(out[i].name, c.name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = c.launches;
+    out[i].ms = c.ms;
+    out[i].work = c.work;
+  }
+  *count = n;
+  return SCHULZE_OK;
+}
+
+int64_t schulze_launch_count(const schulze_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates) {
+  if (kind < 0 || kind > 2 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
+  uint32_t* sink = nullptr;
+  if (cudaMalloc(&sink, 4) != cudaSuccess) return SCHULZE_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto launch = [&](int it) {
+    if (kind == 0) minmax_probe_kernel<0><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 1) minmax_probe_kernel<1><<<blocks, 256>>>(it, 1u, sink);
+    else minmax_probe_kernel<2><<<blocks, 256>>>(it, 1u, sink);
+  };
+  launch(16);  // warm-up
+  cudaEventRecord(e0);
+  launch(iters);
+  cudaEventRecord(e1);
+  int rc = SCHULZE_OK;
+  if (cudaEventSynchronize(e1) != cudaSuccess) rc = SCHULZE_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *seconds = double(ms) * 1e-3;
+  const double lanes = kind == 0 ? 1.0 : (kind == 1 ? 2.0 : 4.0);
+  *updates = double(blocks) * 256.0 * double(iters) * 16.0 * lanes;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,433 @@
+// Pairwise tally: d[i][j] = number of ballots that prefer i to j (Sect. 2.1).
+//
+// Two exact kernels, chosen by cost:
+//  * dense  (position compare, O(n m^2)): ballots are turned into position
+//    rows pos[v][c] (unlisted = k) and every (i, j) tile counts
+//    pos[v][i] < pos[v][j] with packed 16-bit SIMD compares;
+//  * sparse (pair count, O(n k^2)): d[i][j] = cnt[i] - C[i][j], where cnt[i]
+//    is the number of ballots listing i and C[i][j] the number listing j
+//    above i. Ballot entries are grouped by candidate (counting sort), and
+//    each CTA owns a block of rows of d, counts C for them in shared memory
+//    and writes the rows of d once.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace schulze {
+namespace {
+
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------ dense
+
+constexpr int kDenseVoters = 32;  // ballots staged in shared memory per step
+constexpr int kMaxVoterChunk = 32768;  // 16-bit lane counters never overflow
+
+// pos[v][c] for v in [v0, v0 + nv): position of c in ballot v, k if unlisted.
+// One warp per ballot. Out-of-range ids and repeated ids set EDATA.
+__global__ void pos_build_kernel(const int32_t* __restrict__ ranks, int64_t v0, int64_t nv, int32_t m, int32_t k,
+                                 int32_t ldp, uint16_t* __restrict__ pos, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w = warp; w < nv; w += nwarps) {
+    const int32_t* row = ranks + (v0 + w) * k;
+    uint16_t* prow = pos + w * ldp;
+    for (int32_t c = lane; c < ldp; c += kWarp) prow[c] = uint16_t(k);
+    __syncwarp();
+    for (int32_t q = lane; q < k; q += kWarp) {
+      int32_t c = row[q];
+      if (c >= 0 && c < m)
+        prow[c] = uint16_t(q);
+      else
+        set_status(status, SCHULZE_EDATA);
+    }
+    __syncwarp();
+    // a repeated id keeps only one of its positions: the other one sees it
+    for (int32_t q = lane; q < k; q += kWarp) {
+      int32_t c = row[q];
+      if (c >= 0 && c < m && prow[c] != uint16_t(q)) set_status(status, SCHULZE_EDATA);
+    }
+    __syncwarp();
+  }
+}
+
+// One CTA counts a TILE x TILE block of d over a chunk of ballots.
+// Thread micro-tile RM x RN (RN even); lanes of a 32-bit word hold two
+// adjacent j columns; the row operand is duplicated into both halves.
+template <int TILE, int RM, int RN>
+__global__ void __launch_bounds__((TILE / RM) * (TILE / RN))
+    dense_tally_kernel(const uint16_t* __restrict__ pos, int32_t ldp, int64_t nv, int32_t m, int32_t nbt,
+                       int32_t vchunk, int upper_only, int add, int32_t* __restrict__ d) {
+  constexpr int TX = TILE / RN, TY = TILE / RM, NT = TX * TY, WN = RN / 2;
+  __shared__ __align__(16) uint32_t sI[kDenseVoters][TILE];      // row positions, duplicated
+  __shared__ __align__(16) uint16_t sJ[kDenseVoters][TILE];      // column positions
+  int32_t tile = blockIdx.x, bi, bj;
+  if (upper_only) {  // enumerate bi <= bj
+    bi = 0;
+    int32_t rem = tile;
+    while (rem >= nbt - bi) {
+      rem -= nbt - bi;
+      ++bi;
+    }
+    bj = bi + rem;
+  } else {
+    bi = tile / nbt;
+    bj = tile % nbt;
+  }
+  const int32_t I0 = bi * TILE, J0 = bj * TILE;
+  const int64_t vb = int64_t(blockIdx.y) * vchunk;
+  const int64_t ve = min(nv, vb + vchunk);
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  uint32_t acc[RM][WN];
+#pragma unroll
+  for (int r = 0; r < RM; ++r)
+#pragma unroll
+    for (int w = 0; w < WN; ++w) acc[r][w] = 0u;
+
+  for (int64_t v0 = vb; v0 < ve; v0 += kDenseVoters) {
+    const int nvs = int(ve - v0 < kDenseVoters ? ve - v0 : int64_t(kDenseVoters));
+    __syncthreads();
+    for (int t = threadIdx.x; t < kDenseVoters * TILE; t += NT) {
+      int vv = t / TILE, c = t % TILE;
+      uint32_t pi = 0xFFFFu, pj = 0u;  // padding never counts: pi is max, pj is min
+      if (vv < nvs) {
+        const uint16_t* prow = pos + (v0 + vv) * ldp;
+        pi = prow[I0 + c];
+        pj = prow[J0 + c];
+      }
+      sI[vv][c] = pi | (pi << 16);
+      sJ[vv][c] = uint16_t(pj);
+    }
+    __syncthreads();
+    for (int vv = 0; vv < nvs; ++vv) {
+      uint32_t a[RM], b[WN];
+#pragma unroll
+      for (int r = 0; r < RM; r += 4) {
+        uint4 t4 = *reinterpret_cast<const uint4*>(&sI[vv][ty * RM + r]);
+        a[r] = t4.x, a[r + 1] = t4.y, a[r + 2] = t4.z, a[r + 3] = t4.w;
+      }
+#pragma unroll
+      for (int w = 0; w < WN; w += 2) {
+        uint2 t2 = *reinterpret_cast<const uint2*>(&sJ[vv][tx * RN + 2 * w]);
+        b[w] = t2.x, b[w + 1] = t2.y;
+      }
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int w = 0; w < WN; ++w) acc[r][w] = __vsub2(acc[r][w], __vcmpltu2(a[r], b[w]));
+    }
+  }
+  // lanes -> int32 counts (added atomically when several CTAs share a tile)
+#pragma unroll
+  for (int r = 0; r < RM; ++r) {
+    int32_t i = I0 + ty * RM + r;
+    if (i >= m) continue;
+#pragma unroll
+    for (int w = 0; w < WN; ++w) {
+      int32_t j = J0 + tx * RN + 2 * w;
+      int32_t lo = int32_t(acc[r][w] & 0xFFFFu), hi = int32_t(acc[r][w] >> 16);
+      int32_t* dst = d + int64_t(i) * m + j;
+      if (j < m) {
+        if (add) atomicAdd(dst, lo); else dst[0] = lo;
+      }
+      if (j + 1 < m) {
+        if (add) atomicAdd(dst + 1, hi); else dst[1] = hi;
+      }
+    }
+  }
+}
+
+// Full rankings: d[j][i] = n - d[i][j]. Fills the strictly lower tiles from
+// the upper ones (tiles of size TILE; the diagonal tiles are complete).
+__global__ void mirror_kernel(int32_t* __restrict__ d, int32_t m, int32_t tile, int64_t n) {
+  __shared__ int32_t s[32][33];
+  const int32_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;  // source block (rows bi.., cols bj..), bi < bj tile
+  if ((bi / tile) >= (bj / tile)) return;  // only blocks inside strictly upper tiles
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int32_t i = bi + r, j = bj + threadIdx.x;
+    s[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int32_t i = bj + r, j = bi + threadIdx.x;  // destination (row in bj block, col in bi block)
+    if (i < m && j < m) d[int64_t(i) * m + j] = int32_t(n) - s[threadIdx.x][r];
+  }
+}
+
+// ----------------------------------------------------------------- sparse
+
+// cnt[c] += 1 for every listed c; checks ids (range, repeats within a
+// ballot via a per-warp bitmap in shared memory). One warp per ballot.
+__global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
+                                    int32_t* __restrict__ cnt, int32_t* status) {
+  extern __shared__ uint32_t bitmap[];  // warps_per_block * words
+  const int words = (m + 31) / 32;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* bm = bitmap + wib * words;
+  for (int t = lane; t < words; t += kWarp) bm[t] = 0u;
+  __syncwarp();
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int32_t* row = ranks + v * k;
+    for (int32_t q0 = 0; q0 < k; q0 += kWarp) {
+      int32_t q = q0 + lane;
+      bool act = q < k;
+      int32_t c = act ? row[q] : -1;
+      bool ok = act && c >= 0 && c < m;
+      if (act && !ok) set_status(status, SCHULZE_EDATA);
+      if (ok) {
+        uint32_t bit = 1u << (c & 31);
+        uint32_t old = atomicOr(&bm[c >> 5], bit);
+        if (old & bit)
+          set_status(status, SCHULZE_EDATA);
+        else
+          atomicAdd(&cnt[c], 1);
+      }
+    }
+    __syncwarp();
+    for (int32_t q = lane; q < k; q += kWarp) {  // clear what this ballot set
+      int32_t c = row[q];
+      if (c >= 0 && c < m) bm[c >> 5] = 0u;
+    }
+    __syncwarp();
+  }
+}
+
+// Exclusive scan of cnt[0..m) into off[0..m] and cursor[0..m) (one CTA).
+__global__ void scan_kernel(const int32_t* __restrict__ cnt, int32_t m, uint32_t* __restrict__ off,
+                            uint32_t* __restrict__ cursor) {
+  __shared__ uint32_t part[1024];
+  const int T = blockDim.x;
+  const int per = (m + T - 1) / T;
+  const int b = threadIdx.x * per, e = min(m, b + per);
+  uint32_t s = 0;
+  for (int c = b; c < e; ++c) s += uint32_t(cnt[c]);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {  // Hillis-Steele inclusive scan
+    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int c = b; c < e; ++c) {
+    off[c] = run;
+    cursor[c] = run;
+    run += uint32_t(cnt[c]);
+  }
+  if (threadIdx.x == T - 1) off[m] = part[T - 1];
+}
+
+// entries grouped by candidate: entries[cursor[c]++] = v * k + q.
+__global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
+                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int32_t c = ranks[e];
+    if (c < 0 || c >= m) continue;  // already reported by the count pass
+    uint32_t slot = atomicAdd(&cursor[c], 1u);
+    entries[slot] = e;
+  }
+}
+
+// One CTA per (block of RB rows, column chunk [J0, J0 + JW)). C counters in
+// shared memory: 16-bit lanes packed two per word when n <= 65535, else
+// 32-bit. Then d[c][j] = cnt[c] - C[c][j] for the owned rows.
+template <bool kPacked>
+__global__ void __launch_bounds__(512)
+    sparse_rows_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
+                       const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries, int32_t rb, int32_t jw,
+                       int32_t njc, int32_t* __restrict__ d) {
+  extern __shared__ uint32_t C[];
+  const int32_t rblk = blockIdx.x / njc, jc = blockIdx.x % njc;
+  const int32_t R0 = rblk * rb, R1 = min(m, R0 + rb);
+  const int32_t J0 = jc * jw, J1 = min(m, J0 + jw);
+  const int32_t wlen = J1 - J0;
+  const int32_t words_per_row = kPacked ? (jw + 1) / 2 : jw;
+  const int32_t nwords = (R1 - R0) * words_per_row;
+  for (int32_t t = threadIdx.x; t < nwords; t += blockDim.x) C[t] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t e0 = off[R0], e1 = off[R1];
+  for (uint32_t t = e0 + wib; t < e1; t += nw) {
+    const uint32_t e = entries[t];
+    const uint32_t v = e / uint32_t(k), q = e % uint32_t(k);
+    const int32_t c = ranks[e];
+    // only a ballot with a repeated id (already flagged) can misplace an entry
+    if (c < R0 || c >= R1) continue;
+    uint32_t* crow = C + (c - R0) * words_per_row;
+    const int32_t* row = ranks + uint64_t(v) * uint32_t(k);
+    for (uint32_t p = lane; p < q; p += kWarp) {
+      int32_t j = row[p] - J0;
+      if (j >= 0 && j < wlen) {
+        if (kPacked)
+          atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
+        else
+          atomicAdd(&crow[j], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int32_t r = R0; r < R1; ++r) {
+    const int32_t base = cnt[r];
+    const uint32_t* crow = C + (r - R0) * words_per_row;
+    int32_t* drow = d + int64_t(r) * m + J0;
+    for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
+      uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
+      drow[j] = (J0 + j == r) ? 0 : base - int32_t(cv);
+    }
+  }
+}
+
+struct SparsePlan {
+  int32_t rb, jw, njc;
+  bool packed;
+  size_t smem;
+};
+
+SparsePlan sparse_plan(int64_t n, int32_t m, size_t smem_budget) {
+  SparsePlan s;
+  s.packed = n <= 65535;
+  const size_t bytes_per = s.packed ? 2 : 4;
+  // whole rows when at least one fits, else split the columns
+  size_t row_bytes = align_up(size_t(m) * bytes_per, 4);
+  if (row_bytes <= smem_budget) {
+    s.jw = m;
+    s.njc = 1;
+    s.rb = int32_t(std::max<size_t>(1, smem_budget / row_bytes));
+    s.rb = std::min(s.rb, m);
+  } else {
+    s.njc = int32_t((row_bytes + smem_budget - 1) / smem_budget);
+    s.jw = (m + s.njc - 1) / s.njc;
+    s.jw = (s.jw + 1) & ~1;
+    s.njc = (m + s.jw - 1) / s.jw;
+    s.rb = 1;
+  }
+  size_t wpr = s.packed ? size_t(s.jw + 1) / 2 : size_t(s.jw);
+  s.smem = size_t(s.rb) * wpr * 4;
+  return s;
+}
+
+bool choose_dense(int64_t n, int32_t m, int32_t k, uint32_t flags) {
+  if (flags & SCHULZE_F_TALLY_DENSE) return true;
+  if (flags & SCHULZE_F_TALLY_SPARSE) return false;
+  // dense costs ~ m^2 / 2 packed ops per ballot, sparse ~ 4 k^2 / 2
+  return double(k) * double(k) * 4.0 > double(m) * double(m);
+}
+
+constexpr int kDenseTile = 128;
+
+int32_t dense_tile(int32_t m) { return m <= 64 ? 64 : kDenseTile; }
+
+int64_t dense_voter_chunk(int64_t n, int32_t m) {
+  (void)m;
+  return std::min<int64_t>(std::max<int64_t>(n, 1), 1 << 16);
+}
+
+}  // namespace
+
+size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
+  if (choose_dense(n, m, k, flags)) {
+    int32_t tile = dense_tile(m);
+    size_t ldp = align_up(size_t(m), size_t(tile));
+    return align_up(size_t(dense_voter_chunk(n, m)) * ldp * 2, 256) + 4096;
+  }
+  size_t total = size_t(n) * size_t(k);
+  return align_up(size_t(m) * 4, 256) + 2 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) + 4096;
+}
+
+int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
+                 uint32_t flags, void* ws, cudaStream_t stream) {
+  const size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
+  if (n == 0 || k == 0) {
+    return cudaMemsetAsync(d, 0, mm, stream) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+  }
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+  Carver cv(ws);
+  if (choose_dense(n, m, k, flags)) {
+    const int32_t tile = dense_tile(m);
+    const int32_t ldp = int32_t(align_up(size_t(m), size_t(tile)));
+    const int32_t nbt = ldp / tile;
+    const bool full = k >= m - 1;  // strict full orders: d[j][i] = n - d[i][j]
+    const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
+    const int64_t chunk = dense_voter_chunk(n, m);
+    uint16_t* pos = cv.take<uint16_t>(size_t(chunk) * size_t(ldp));
+    // voter split inside a chunk so that the grid covers the GPU
+    int32_t vsplit = int32_t(std::max<int64_t>(1, (2LL * sms + ntiles - 1) / ntiles));
+    vsplit = int32_t(std::min<int64_t>(vsplit, std::max<int64_t>(1, std::min<int64_t>(n, chunk) / 64)));
+    const bool accumulate = vsplit > 1 || n > chunk;
+    if (accumulate && cudaMemsetAsync(d, 0, mm, stream) != cudaSuccess) return SCHULZE_ECUDA;
+    for (int64_t v0 = 0; v0 < n; v0 += chunk) {
+      const int64_t nv = std::min<int64_t>(chunk, n - v0);
+      int32_t vchunk = int32_t((nv + vsplit - 1) / vsplit);
+      vchunk = std::min<int32_t>(vchunk, kMaxVoterChunk);
+      const int32_t gy = int32_t((nv + vchunk - 1) / vchunk);
+      int pb = int(std::min<int64_t>((nv + 7) / 8, int64_t(sms) * 16));
+      {
+        Launch L(ctx, stream, "tally_positions", double(nv) * (double(k) * 4.0 + double(ldp) * 2.0));
+        pos_build_kernel<<<pb, 256, 0, stream>>>(ranks, v0, nv, m, k, ldp, pos, ctx->status);
+      }
+      dim3 grid(ntiles, gy);
+      // gy > 1 or several chunks: the kernel adds atomically into zeroed d
+      Launch L(ctx, stream, "tally_dense", double(nv) * double(m) * double(m - 1) / (full ? 2.0 : 1.0));
+      if (tile == 64)
+        dense_tally_kernel<64, 8, 8><<<grid, 64, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
+                                                               accumulate ? 1 : 0, d);
+      else
+        dense_tally_kernel<128, 8, 8><<<grid, 256, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
+                                                                 accumulate ? 1 : 0, d);
+      if (int rc = check_launch()) return rc;
+    }
+    if (full && nbt > 1) {
+      Launch L(ctx, stream, "tally_mirror", double(m) * double(m) * 4.0);
+      dim3 g((m + 31) / 32, (m + 31) / 32), b(32, 8);
+      mirror_kernel<<<g, b, 0, stream>>>(d, m, tile, n);
+    }
+    return check_launch();
+  }
+  // sparse
+  const uint32_t total = uint32_t(uint64_t(n) * uint64_t(k));
+  int32_t* cnt = cv.take<int32_t>(size_t(m));
+  uint32_t* off = cv.take<uint32_t>(size_t(m) + 1);
+  uint32_t* cursor = cv.take<uint32_t>(size_t(m) + 1);
+  uint32_t* entries = cv.take<uint32_t>(total);
+  if (cudaMemsetAsync(cnt, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  {
+    const int threads = 256;
+    const size_t smem = size_t(threads / 32) * size_t((m + 31) / 32) * 4;
+    int blocks = int(std::min<int64_t>((n + 7) / 8, int64_t(sms) * 8));
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(sparse_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    Launch L(ctx, stream, "tally_count", double(total) * 4.0);
+    sparse_count_kernel<<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
+  }
+  {
+    Launch L(ctx, stream, "tally_scan", double(m) * 12.0);
+    scan_kernel<<<1, 1024, 0, stream>>>(cnt, m, off, cursor);
+  }
+  {
+    int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
+    Launch L(ctx, stream, "tally_group", double(total) * 8.0);
+    sparse_scatter_kernel<<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries);
+  }
+  if (int rc = check_launch()) return rc;
+  const size_t budget = 96 * 1024;
+  SparsePlan sp = sparse_plan(n, m, budget);
+  const int32_t nrb = (m + sp.rb - 1) / sp.rb;
+  const int blocks = nrb * sp.njc;
+  Launch L(ctx, stream, "tally_rows", double(m) * double(m) * 4.0 + double(total) * 4.0);
+  if (sp.packed) {
+    cudaFuncSetAttribute(sparse_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
+    sparse_rows_kernel<true><<<blocks, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, sp.rb, sp.jw,
+                                                                sp.njc, d);
+  } else {
+    cudaFuncSetAttribute(sparse_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
+    sparse_rows_kernel<false><<<blocks, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, sp.rb, sp.jw,
+                                                                 sp.njc, d);
+  }
+  return check_launch();
+}
+
+}  // namespace schulze

@@ -1,0 +1,298 @@
+"""CUDA path against the CPU oracle, element by element (bit-exact: every
+quantity is an integer)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from helpers import fig1, mcgarvey_ballots, topk_tie_counterexample
+
+pytestmark = pytest.mark.gpu
+
+S = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    global S
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_12976_gb300 as mod
+    S = mod
+    yield mod
+    assert S.context().status() == S.OK
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def eq(a, b, what=""):
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    bad = np.argwhere(a != b)
+    assert bad.size == 0, f"{what}: {len(bad)} mismatches, first {bad[:5].tolist()} " \
+                          f"gpu={a[tuple(bad[0])]} oracle={b[tuple(bad[0])]}"
+
+
+# --------------------------------------------------------- paper pins
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_fig1_table_on_gpu(flags):
+    _, mu, p_paper, win = fig1()
+    p = S.schulze_strongest_paths(cu(mu), bound=12, flags=flags)
+    eq(host(p), p_paper, "fig1 widths")
+    assert np.flatnonzero(host(S.schulze_winners(p))).tolist() == win
+
+
+def test_fig1_mcgarvey_on_gpu():
+    _, mu, p_paper, _ = fig1()
+    ballots = mcgarvey_ballots(mu)
+    out = S.schulze_run(cu(ballots), 4)
+    d, p, win, order, bb = oracle.schulze(ballots, 4)
+    eq(host(out["d"]), d)
+    eq(host(out["p"]), p)
+    assert host(out["order"]).tolist() == [0, 3, 1, 2]
+    assert host(out["beaten_by"]).tolist() == [0, 2, 3, 1]
+
+
+def test_topk_tie_counterexample_on_gpu():
+    g = topk_tie_counterexample()
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+        out = S.schulze_run(cu(g["ballots"]), g["m"], flags=flags)
+        eq(host(out["d"]), g["d"])
+        eq(host(out["p"]), g["p"])
+        assert np.flatnonzero(host(out["winners"])).tolist() == g["winners"]
+        assert host(out["order"]).tolist() == g["ranking"]
+        assert host(out["beaten_by"]).tolist() == g["beaten_by"]
+
+
+# ------------------------------------------------------------- tally
+
+TALLY_CASES = []
+for m in (1, 2, 3, 7, 31, 32, 33, 63, 64, 65, 127, 129, 300):
+    for n in (0, 1, 2, 37, 513):
+        for k in sorted({0, 1, max(0, m - 1), m, m // 2}):
+            TALLY_CASES.append((m, n, k))
+
+
+@pytest.mark.parametrize("m,n,k", TALLY_CASES)
+def test_tally_dense_and_sparse(m, n, k):
+    seed = m * 1000 + n * 10 + k
+    r = W.mallows(seed, n, m, k, 0.85, W.permutation(seed, m)) if k else np.zeros((n, 0), np.int32)
+    want = oracle.tally(r, m)
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, 0):
+        eq(host(S.schulze_tally(cu(r), m, flags=flags)), want, f"tally flags={flags}")
+
+
+def test_tally_many_ballots_chunked():
+    """More than 65536 ballots: dense path accumulates chunks, sparse path
+    switches to 32-bit counters."""
+    m, n = 40, 70001
+    r = W.impartial(5, n, m, m)
+    want = oracle.tally(r, m)
+    eq(host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_DENSE)), want, "dense chunks")
+    r2 = W.mallows(6, n, 300, 9, 0.9, W.permutation(6, 300))
+    eq(host(S.schulze_tally(cu(r2), 300, flags=S.F_TALLY_SPARSE)), oracle.tally(r2, 300), "sparse int32")
+
+
+def test_tally_column_split():
+    """Rows of d wider than the shared-memory budget: column chunks."""
+    m, n, k = 26000, 70000, 4
+    r = W.impartial(8, n, m, k)
+    d = host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE))
+    rs = np.random.Generator(np.random.PCG64(1))
+    for _ in range(40):
+        i, j = (int(x) for x in rs.integers(0, m, 2))
+        assert d[i, j] == oracle.tally_entry(r, m, i, j)
+    # pairs that actually co-occur in ballots
+    for v in range(0, n, 7001):
+        for a in range(k):
+            for b in range(k):
+                i, j = int(r[v, a]), int(r[v, b])
+                assert d[i, j] == oracle.tally_entry(r, m, i, j)
+    _check_row_col_sums(r, m, d)
+
+
+def _check_row_col_sums(r, m, d):
+    n, k = r.shape
+    rows = np.zeros(m, np.int64)
+    cols = np.full(m, n * k, np.int64)  # unlisted j has k candidates above it
+    np.add.at(rows, r.reshape(-1), (m - 1 - np.tile(np.arange(k), n)))
+    np.add.at(cols, r.reshape(-1), np.tile(np.arange(k), n) - k)
+    eq(d.sum(axis=1, dtype=np.int64), rows, "row sums")
+    eq(d.sum(axis=0, dtype=np.int64), cols, "column sums")
+
+
+def test_tally_rejects_bad_ids():
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    bad = np.array([[0, 1, 2], [1, 1, 0]], np.int32)
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+        S.schulze_tally(cu(bad), 4, flags=flags)
+        assert ctx.status() == S.EDATA
+    out_of_range = np.array([[0, 7, 2]], np.int32)
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+        S.schulze_tally(cu(out_of_range), 4, flags=flags)
+        assert ctx.status() == S.EDATA
+    S.schulze_tally(cu(np.array([[3, 1, 2]], np.int32)), 4)
+    assert ctx.status() == S.OK
+
+
+# ----------------------------------------------------------- closure
+
+CLOSURE_M = [1, 2, 3, 5, 63, 64, 65, 127, 128, 129, 200, 257, 511]
+
+
+@pytest.mark.parametrize("m", CLOSURE_M)
+def test_closure_and_extraction(m):
+    n = 301
+    r = W.mallows(m, n, m, min(m, 17), 0.93, W.permutation(m + 1, m))
+    d = oracle.tally(r, m)
+    p_want = oracle.strongest_paths(d)
+    win_want = oracle.winners(p_want)
+    order_want, bb_want = oracle.ranking(p_want)
+    dd = cu(d)
+    for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
+        p = S.schulze_strongest_paths(dd, bound=n, flags=flags)
+        eq(host(p), p_want, f"closure m={m} flags={flags}")
+    eq(host(S.schulze_winners(p)), win_want, "winners")
+    order, bb = S.schulze_ranking(p)
+    eq(host(order), order_want, "ranking")
+    eq(host(bb), bb_want, "beaten_by")
+
+
+def test_closure_random_weight_matrices():
+    """Arbitrary nonnegative count matrices, including ties and zeros."""
+    rs = np.random.Generator(np.random.PCG64(3))
+    for m in (7, 70, 190):
+        for density in (0.05, 0.5, 1.0):
+            d = rs.integers(0, 30000, size=(m, m)).astype(np.int32)
+            d[rs.random((m, m)) > density] = 0
+            np.fill_diagonal(d, 0)
+            want = oracle.strongest_paths(d)
+            for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
+                eq(host(S.schulze_strongest_paths(cu(d), 30000, flags=flags)), want, f"random m={m}")
+
+
+def test_closure_large_counts_int32():
+    rs = np.random.Generator(np.random.PCG64(4))
+    m = 150
+    d = rs.integers(0, 2_000_000_000, size=(m, m)).astype(np.int32)
+    np.fill_diagonal(d, 0)
+    eq(host(S.schulze_strongest_paths(cu(d), 2_000_000_000)), oracle.strongest_paths(d), "int32 counts")
+
+
+def test_closure_bound_violation_flagged():
+    ctx = S.context()
+    d = np.array([[0, 40000], [0, 0]], np.int32)
+    S.schulze_strongest_paths(cu(d), 30000)
+    assert ctx.status() == S.EDATA
+    with pytest.raises(S.SchulzeError):
+        S.schulze_strongest_paths(cu(d), 40000, flags=S.F_FORCE_S16)
+    S.schulze_strongest_paths(cu(d), 40000)
+    assert ctx.status() == S.OK
+
+
+# ------------------------------------------------------- end to end
+
+def test_degenerate_elections():
+    for m in (1, 2, 9):
+        for r in (np.zeros((0, m), np.int32), np.zeros((5, 0), np.int32)):
+            out = S.schulze_run(cu(r) if r.size else torch.zeros(r.shape, dtype=torch.int32, device="cuda"), m)
+            assert not host(out["d"]).any() and not host(out["p"]).any()
+            assert host(out["winners"]).tolist() == [1] * m
+            assert host(out["order"]).tolist() == list(range(m))
+    r = np.tile(np.array([4, 1, 6], np.int32), (9, 1))
+    out = S.schulze_run(cu(r), 8)
+    assert np.flatnonzero(host(out["winners"])).tolist() == [4]
+    assert host(out["order"]).tolist() == [4, 1, 6, 0, 2, 3, 5, 7]
+
+
+def test_small_mallows_workload_end_to_end():
+    e = W.small_mallows()
+    out = S.schulze_run(cu(e.ranks), e.m)
+    d, p, win, order, bb = oracle.schulze(e.ranks, e.m)
+    eq(host(out["d"]), d)
+    eq(host(out["p"]), p)
+    eq(host(out["winners"]), win)
+    eq(host(out["order"]), order)
+    eq(host(out["beaten_by"]), bb)
+
+
+def test_host_buffers_path_matches_device_path():
+    e = W.large_topk(seed=9, n=2000, m=700, k=30)
+    win, order = S.schulze_run_host(e.ranks, e.m)
+    _, p, win_o, order_o, _ = oracle.schulze(e.ranks, e.m, nthreads=8)
+    eq(win, win_o)
+    eq(order, order_o)
+    with pytest.raises(S.SchulzeError):
+        S.schulze_run_host(np.array([[0, 0]], np.int32), 3)
+
+
+def _sampled_closure_checks(w, p_gpu, rows):
+    for s in rows:
+        eq(p_gpu[s], oracle.widest_from(w, s), f"row {s}")
+        eq(p_gpu[:, s], oracle.widest_to(w, s), f"col {s}")
+
+
+def test_large_topk_workload_full_size():
+    """m=4096, n=20000, top-50 Mallows(0.9): whole d against the oracle, the
+    closure on sampled rows and columns (max-min Dijkstra), every winner
+    certified and sampled beaten_by counts recomputed."""
+    e = W.large_topk()
+    out = S.schulze_run(cu(e.ranks), e.m)
+    d = host(out["d"])
+    eq(d, oracle.tally(e.ranks, e.m), "tally")
+    w = oracle.weights(d)
+    p = host(out["p"])
+    rs = np.random.Generator(np.random.PCG64(2))
+    _sampled_closure_checks(w, p, [0, e.m - 1] + rs.integers(0, e.m, 6).tolist())
+    win = host(out["winners"])
+    bb = host(out["beaten_by"])
+    for c in np.flatnonzero(win):
+        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
+        assert np.all(fwd >= bwd), "certified winner"
+    for c in rs.integers(0, e.m, 6).tolist() + np.argsort(bb)[:4].tolist():
+        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
+        assert bb[c] == int(np.sum(bwd > fwd)), f"beaten_by[{c}]"
+    order = host(out["order"])
+    assert sorted(order.tolist()) == list(range(e.m))
+    assert np.all(np.diff(bb[order]) >= 0)
+
+
+def test_huge_pl_workload_full_size():
+    """m=16384, n=200000, top-20 Plackett-Luce Zipf(1.1): int32 closure.
+    Tally by row/column sums and sampled entries; closure on the
+    2048-candidate popular subsample against the oracle closure, and on full-m
+    sampled rows by Dijkstra; winners certified."""
+    e = W.huge_pl()
+    m = e.m
+    out = S.schulze_run(cu(e.ranks), m)
+    d = host(out["d"])
+    _check_row_col_sums(e.ranks, m, d)
+    sub = W.popular_subsample(m, 2048)
+    for a in range(0, 2048, 97):
+        for b in range(3, 2048, 331):
+            i, j = int(sub[a]), int(sub[b])
+            assert d[i, j] == oracle.tally_entry(e.ranks, m, i, j)
+    dS = np.ascontiguousarray(d[np.ix_(sub, sub)])
+    pS = S.schulze_strongest_paths(cu(dS), bound=e.n)
+    pS_want = oracle.strongest_paths(dS, nthreads=16)
+    eq(host(pS), pS_want, "subsample closure")
+    eq(host(S.schulze_winners(pS)), oracle.winners(pS_want), "subsample winners")
+    eq(host(S.schulze_ranking(pS)[0]), oracle.ranking(pS_want)[0], "subsample ranking")
+    w = oracle.weights(d)
+    p = host(out["p"])
+    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1]), 5])
+    for c in np.flatnonzero(host(out["winners"])):
+        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
+        assert np.all(fwd >= bwd)
