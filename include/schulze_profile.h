@@ -39,11 +39,13 @@ int64_t schulze_launch_count(const schulze_ctx* ctx);
 
 /*
  * Integer min/max issue-rate probe: a grid of `blocks` x 256 threads runs
- * `iters` iterations of 8 independent (max, min) chains per thread in the
+ * `iters` iterations of 16 independent (max, min) chains per thread in the
  * given lane format (kind 0: int32, 2 instructions per update; kind 1: packed
  * int16x2, 2 instructions per 2 updates; kind 2: packed int16x2 with a
- * three-input max folding two updates). *seconds receives the kernel time
- * (CUDA events) and *updates the number of (max, min) lane updates done.
+ * three-input max folding two updates, 3 instructions per 4 updates; kind 3:
+ * int32 with a three-input max, 3 instructions per 2 updates). *seconds
+ * receives the kernel time (CUDA events) and *updates the number of
+ * (max, min) lane updates done.
  * Synchronous.
  */
 int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates);

@@ -27,11 +27,6 @@ constexpr int kRN = 4;        // columns per thread
 constexpr int kTX = kB / kRN; // 16 column groups
 // rows: 8 groups of 8 -> 8 * 16 = 128 threads
 
-__device__ __forceinline__ int32_t maxmin_s32(int32_t c, int32_t a, int32_t b) { return max(c, min(a, b)); }
-__device__ __forceinline__ uint32_t maxmin_s16x2(uint32_t c, uint32_t a, uint32_t b) {
-  return __vmaxs2(c, __vmins2(a, b));
-}
-
 // ---------------------------------------------------------------- pack
 
 // W[i][j] = d[i][j] if d[i][j] > d[j][i] else 0 (i != j, both < m), 0 elsewhere.
@@ -65,35 +60,44 @@ __global__ void widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m, int
   const int64_t total = int64_t(m) * m;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     int64_t i = t / m, j = t % m;
-    p[t] = int32_t(W[i * mp + j]);
+    p[t] = i == j ? 0 : int32_t(W[i * mp + j]);
   }
 }
 
 // ------------------------------------------------------ tile routines
 
 // Closes the diagonal tile (r, r) in place: plain Floyd-Warshall over its
-// 64 vertices. Row k and column k do not change during step k because the
-// diagonal is 0, so one barrier per step suffices.
+// 64 vertices, 1024 threads with 4 independent entries each. Row k and
+// column k do not change during step k (min(x, y) <= x), so one barrier per
+// step suffices. The diagonal of the tile is left at whatever cycle width it
+// reaches: it never changes an off-diagonal entry and is zeroed on output.
+constexpr int kDiagThreads = 1024;
 template <typename E>
 __device__ void diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t* __restrict__ s /*[64][65]*/) {
   const int64_t base = int64_t(r) * kB * ld + int64_t(r) * kB;
-  for (int t = threadIdx.x; t < kB * kB; t += kThreads) {
+  for (int t = threadIdx.x; t < kB * kB; t += kDiagThreads) {
     int i = t / kB, j = t % kB;
-    s[i * (kB + 1) + j] = (i == j) ? 0 : int32_t(__ldcg(&W[base + int64_t(i) * ld + j]));
+    s[i * (kB + 1) + j] = int32_t(__ldcg(&W[base + int64_t(i) * ld + j]));
   }
   __syncthreads();
+  const int i = threadIdx.x / 16, j0 = threadIdx.x % 16;  // columns j0 + 16 q
+  int32_t* row = s + i * (kB + 1);
   for (int k = 0; k < kB; ++k) {
-    for (int t = threadIdx.x; t < kB * kB; t += kThreads) {
-      int i = t / kB, j = t % kB;
-      int32_t v = s[i * (kB + 1) + j];
-      v = max(v, min(s[i * (kB + 1) + k], s[k * (kB + 1) + j]));
-      s[i * (kB + 1) + j] = v;
+    const int32_t a = row[k];
+    const int32_t* rk = s + k * (kB + 1);
+    int32_t v[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q] = row[j0 + 16 * q];
+      b[q] = rk[j0 + 16 * q];
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) row[j0 + 16 * q] = max(v[q], min(a, b[q]));
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < kB * kB; t += kThreads) {
-    int i = t / kB, j = t % kB;
-    __stcg(&W[base + int64_t(i) * ld + j], E(s[i * (kB + 1) + j]));
+  for (int t = threadIdx.x; t < kB * kB; t += kDiagThreads) {
+    int ii = t / kB, jj = t % kB;
+    __stcg(&W[base + int64_t(ii) * ld + jj], E(s[ii * (kB + 1) + jj]));
   }
 }
 
@@ -141,17 +145,24 @@ __device__ void tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti,
     acc[rr][0] = v.x, acc[rr][1] = v.y, acc[rr][2] = v.z, acc[rr][3] = v.w;
   }
   __syncthreads();
-#pragma unroll 4
-  for (int k = 0; k < kB; ++k) {
-    int4 a0 = *reinterpret_cast<const int4*>(&sm.A[k][ty * kRM]);
-    int4 a1 = *reinterpret_cast<const int4*>(&sm.A[k][ty * kRM + 4]);
-    int4 b = *reinterpret_cast<const int4*>(&sm.B[k][tx * kRN]);
-    const int32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const int32_t bb[4] = {b.x, b.y, b.z, b.w};
+  // two k-steps per three-input max: max(c, min(a, b), min(a', b'))
+#pragma unroll 2
+  for (int k = 0; k < kB; k += 2) {
+    int32_t a[2][8], bb[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int4 a0 = *reinterpret_cast<const int4*>(&sm.A[k + h][ty * kRM]);
+      int4 a1 = *reinterpret_cast<const int4*>(&sm.A[k + h][ty * kRM + 4]);
+      int4 b = *reinterpret_cast<const int4*>(&sm.B[k + h][tx * kRN]);
+      a[h][0] = a0.x, a[h][1] = a0.y, a[h][2] = a0.z, a[h][3] = a0.w;
+      a[h][4] = a1.x, a[h][5] = a1.y, a[h][6] = a1.z, a[h][7] = a1.w;
+      bb[h][0] = b.x, bb[h][1] = b.y, bb[h][2] = b.z, bb[h][3] = b.w;
+    }
 #pragma unroll
     for (int rr = 0; rr < kRM; ++rr)
 #pragma unroll
-      for (int cc = 0; cc < kRN; ++cc) acc[rr][cc] = maxmin_s32(acc[rr][cc], a[rr], bb[cc]);
+      for (int cc = 0; cc < kRN; ++cc)
+        acc[rr][cc] = __vimax3_s32(acc[rr][cc], min(a[0][rr], bb[0][cc]), min(a[1][rr], bb[1][cc]));
   }
 #pragma unroll
   for (int rr = 0; rr < kRM; ++rr) {
@@ -196,17 +207,24 @@ __device__ void tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti,
     acc[rr][0] = v.x, acc[rr][1] = v.y;
   }
   __syncthreads();
-#pragma unroll 4
-  for (int k = 0; k < kB; ++k) {
-    uint4 a0 = *reinterpret_cast<const uint4*>(&sm.A[k][ty * kRM]);
-    uint4 a1 = *reinterpret_cast<const uint4*>(&sm.A[k][ty * kRM + 4]);
-    uint2 b = *reinterpret_cast<const uint2*>(&sm.B[k][tx * kRN]);
-    const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  // two k-steps per three-input max: max(c, min(a, b), min(a', b'))
+#pragma unroll 2
+  for (int k = 0; k < kB; k += 2) {
+    uint32_t a[2][8], b[2][2];
 #pragma unroll
-    for (int rr = 0; rr < kRM; ++rr) {
-      acc[rr][0] = maxmin_s16x2(acc[rr][0], a[rr], b.x);
-      acc[rr][1] = maxmin_s16x2(acc[rr][1], a[rr], b.y);
+    for (int h = 0; h < 2; ++h) {
+      uint4 a0 = *reinterpret_cast<const uint4*>(&sm.A[k + h][ty * kRM]);
+      uint4 a1 = *reinterpret_cast<const uint4*>(&sm.A[k + h][ty * kRM + 4]);
+      uint2 bv = *reinterpret_cast<const uint2*>(&sm.B[k + h][tx * kRN]);
+      a[h][0] = a0.x, a[h][1] = a0.y, a[h][2] = a0.z, a[h][3] = a0.w;
+      a[h][4] = a1.x, a[h][5] = a1.y, a[h][6] = a1.z, a[h][7] = a1.w;
+      b[h][0] = bv.x, b[h][1] = bv.y;
     }
+#pragma unroll
+    for (int rr = 0; rr < kRM; ++rr)
+#pragma unroll
+      for (int w = 0; w < 2; ++w)
+        acc[rr][w] = __vimax3_s16x2(acc[rr][w], __vmins2(a[0][rr], b[0][w]), __vmins2(a[1][rr], b[1][w]));
   }
 #pragma unroll
   for (int rr = 0; rr < kRM; ++rr)
@@ -234,7 +252,7 @@ struct Ops<int16_t> {
 // ------------------------------------------------- per-phase kernels
 
 template <typename E>
-__global__ void __launch_bounds__(kThreads) phase1_kernel(E* W, int32_t ld, int32_t r) {
+__global__ void __launch_bounds__(kDiagThreads) phase1_kernel(E* W, int32_t ld, int32_t r) {
   __shared__ int32_t s[kB * (kB + 1)];
   diag_closure<E>(W, ld, r, s);
 }
@@ -280,7 +298,7 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   for (int32_t r = 0; r < nb; ++r) {
     {
       Launch L(ctx, stream, "closure_diag", tile3);
-      phase1_kernel<E><<<1, kThreads, 0, stream>>>(W, mp, r);
+      phase1_kernel<E><<<1, kDiagThreads, 0, stream>>>(W, mp, r);
     }
     if (nb > 1) {
       {

@@ -91,8 +91,11 @@ __global__ void __launch_bounds__(256) minmax_probe_kernel(int iters, uint32_t s
         c[q] = uint32_t(max(int32_t(c[q]), min(int32_t(a[q]), int32_t(b))));
       } else if (KIND == 1) {
         c[q] = __vmaxs2(c[q], __vmins2(a[q], b));
-      } else {
+      } else if (KIND == 2) {
         c[q] = __vimax3_s16x2(c[q], __vmins2(a[q], b), __vmins2(a[(q + 1) % C], c[(q + 9) % C]));
+      } else {
+        c[q] = uint32_t(__vimax3_s32(int32_t(c[q]), min(int32_t(a[q]), int32_t(b)),
+                                     min(int32_t(a[(q + 1) % C]), int32_t(c[(q + 9) % C]))));
       }
     }
   }
@@ -139,7 +142,7 @@ int schulze_profile_read(schulze_ctx* ctx, schulze_kernel_stats* out, int max, i
 int64_t schulze_launch_count(const schulze_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates) {
-  if (kind < 0 || kind > 2 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
+  if (kind < 0 || kind > 3 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
   uint32_t* sink = nullptr;
   if (cudaMalloc(&sink, 4) != cudaSuccess) return SCHULZE_ENOMEM;
@@ -149,7 +152,8 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
   auto launch = [&](int it) {
     if (kind == 0) minmax_probe_kernel<0><<<blocks, 256>>>(it, 1u, sink);
     else if (kind == 1) minmax_probe_kernel<1><<<blocks, 256>>>(it, 1u, sink);
-    else minmax_probe_kernel<2><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 2) minmax_probe_kernel<2><<<blocks, 256>>>(it, 1u, sink);
+    else minmax_probe_kernel<3><<<blocks, 256>>>(it, 1u, sink);
   };
   launch(16);  // warm-up
   cudaEventRecord(e0);
@@ -163,7 +167,7 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
   cudaEventDestroy(e1);
   cudaFree(sink);
   *seconds = double(ms) * 1e-3;
-  const double lanes = kind == 0 ? 1.0 : (kind == 1 ? 2.0 : 4.0);
+  const double lanes = kind == 0 ? 1.0 : (kind == 1 ? 2.0 : (kind == 2 ? 4.0 : 2.0));
   *updates = double(blocks) * 256.0 * double(iters) * 16.0 * lanes;
   return rc;
 }

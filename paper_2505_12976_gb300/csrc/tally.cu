@@ -195,30 +195,55 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
   }
 }
 
-// Exclusive scan of cnt[0..m) into off[0..m] and cursor[0..m) (one CTA).
-__global__ void scan_kernel(const int32_t* __restrict__ cnt, int32_t m, uint32_t* __restrict__ off,
-                            uint32_t* __restrict__ cursor) {
-  __shared__ uint32_t part[1024];
+// Block-wide exclusive scan of v[0..len) (uint32) in place; returns the total.
+// Every thread of the block must call it.
+__device__ uint32_t block_exclusive_scan(uint32_t* v, int32_t len, uint32_t* part) {
   const int T = blockDim.x;
-  const int per = (m + T - 1) / T;
-  const int b = threadIdx.x * per, e = min(m, b + per);
+  const int per = (len + T - 1) / T;
+  const int b = threadIdx.x * per, e = min(len, b + per);
   uint32_t s = 0;
-  for (int c = b; c < e; ++c) s += uint32_t(cnt[c]);
+  for (int c = b; c < e; ++c) s += v[c];
   part[threadIdx.x] = s;
   __syncthreads();
-  for (int o = 1; o < T; o <<= 1) {  // Hillis-Steele inclusive scan
-    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+  for (int o = 1; o < T; o <<= 1) {  // Hillis-Steele inclusive scan of the partials
+    uint32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
     __syncthreads();
-    part[threadIdx.x] += v;
+    part[threadIdx.x] += x;
     __syncthreads();
   }
   uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
   for (int c = b; c < e; ++c) {
-    off[c] = run;
-    cursor[c] = run;
-    run += uint32_t(cnt[c]);
+    uint32_t x = v[c];
+    v[c] = run;
+    run += x;
   }
-  if (threadIdx.x == T - 1) off[m] = part[T - 1];
+  uint32_t total = part[T - 1];
+  __syncthreads();
+  return total;
+}
+
+// Plans the sparse tally on the device (one CTA of 1024 threads):
+//  * off[c] / cursor[c]: start of candidate c's entries (exclusive scan of cnt);
+//  * the rows are cut into blocks of rb rows; block b holds E_b entries and
+//    gets nu_b = max(1, ceil(E_b / emax)) work units, each a slice of at most
+//    emax of its entries; uoff[b] is the exclusive scan of nu_b.
+__global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb,
+                                                           int32_t nblocks, uint32_t emax, uint32_t* __restrict__ off,
+                                                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff) {
+  __shared__ uint32_t part[1024];
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) off[c] = uint32_t(cnt[c]);
+  __syncthreads();
+  const uint32_t total = block_exclusive_scan(off, m, part);
+  if (threadIdx.x == 0) off[m] = total;
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) cursor[c] = off[c];
+  __syncthreads();
+  for (int32_t b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const uint32_t e0 = off[b * rb], e1 = off[min(m, (b + 1) * rb)];
+    uoff[b] = max(1u, (e1 - e0 + emax - 1) / emax);
+  }
+  __syncthreads();
+  const uint32_t units = block_exclusive_scan(uoff, nblocks, part);
+  if (threadIdx.x == 0) uoff[nblocks] = units;
 }
 
 // entries grouped by candidate: entries[cursor[c]++] = v * k + q.
@@ -232,62 +257,114 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
   }
 }
 
-// One CTA per (block of RB rows, column chunk [J0, J0 + JW)). C counters in
-// shared memory: 16-bit lanes packed two per word when n <= 65535, else
-// 32-bit. Then d[c][j] = cnt[c] - C[c][j] for the owned rows.
+// Rows of blocks split into several units start as d[c][j] = cnt[c] (0 on
+// the diagonal); their units then subtract their partial counts atomically.
+__global__ void sparse_init_split_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb, int32_t jw,
+                                         const uint32_t* __restrict__ uoff, int32_t* __restrict__ d) {
+  const int32_t b = blockIdx.x, jc = blockIdx.y;
+  if (uoff[b + 1] - uoff[b] <= 1) return;
+  const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
+  const int32_t J0 = jc * jw, J1 = min(m, J0 + jw);
+  for (int32_t r = R0; r < R1; ++r) {
+    const int32_t base = cnt[r];
+    int32_t* drow = d + int64_t(r) * m;
+    for (int32_t j = J0 + threadIdx.x; j < J1; j += blockDim.x) drow[j] = (j == r) ? 0 : base;
+  }
+}
+
+// One CTA per (work unit, column chunk [J0, J0 + jw)). C counters for the
+// unit's rows live in shared memory: 16-bit lanes packed two per word when
+// n <= 65535, else 32-bit. C[c][j] counts the unit's entries (v, q) of
+// candidate c whose ballot lists j above position q. A whole-block unit then
+// writes d[c][j] = cnt[c] - C[c][j]; a unit holding a slice of a split block
+// subtracts its nonzero counts from the pre-initialised rows.
 template <bool kPacked>
 __global__ void __launch_bounds__(512)
-    sparse_rows_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
-                       const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries, int32_t rb, int32_t jw,
-                       int32_t njc, int32_t* __restrict__ d) {
+    sparse_units_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
+                        const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries,
+                        const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
+                        int32_t* __restrict__ d) {
   extern __shared__ uint32_t C[];
-  const int32_t rblk = blockIdx.x / njc, jc = blockIdx.x % njc;
-  const int32_t R0 = rblk * rb, R1 = min(m, R0 + rb);
-  const int32_t J0 = jc * jw, J1 = min(m, J0 + jw);
+  const uint32_t unit = blockIdx.x;
+  if (unit >= uoff[nblocks]) return;
+  int32_t lo = 0, hi = nblocks - 1;  // block b with uoff[b] <= unit < uoff[b + 1]
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (uoff[mid] <= unit) lo = mid; else hi = mid - 1;
+  }
+  const int32_t b = lo;
+  const uint32_t u = unit - uoff[b], nu = uoff[b + 1] - uoff[b];
+  const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
+  const int32_t J0 = blockIdx.y * jw, J1 = min(m, J0 + jw);
   const int32_t wlen = J1 - J0;
-  const int32_t words_per_row = kPacked ? (jw + 1) / 2 : jw;
-  const int32_t nwords = (R1 - R0) * words_per_row;
+  const int32_t wpr = kPacked ? (jw + 1) / 2 : jw;  // words per row
+  const int32_t nwords = (R1 - R0) * wpr;
   for (int32_t t = threadIdx.x; t < nwords; t += blockDim.x) C[t] = 0u;
   __syncthreads();
+  const uint32_t eb = off[R0], ee = off[R1];
+  const uint32_t s0 = eb + u * emax, s1 = min(ee, s0 + emax);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t e0 = off[R0], e1 = off[R1];
-  for (uint32_t t = e0 + wib; t < e1; t += nw) {
-    const uint32_t e = entries[t];
-    const uint32_t v = e / uint32_t(k), q = e % uint32_t(k);
-    const int32_t c = ranks[e];
-    // only a ballot with a repeated id (already flagged) can misplace an entry
-    if (c < R0 || c >= R1) continue;
-    uint32_t* crow = C + (c - R0) * words_per_row;
-    const int32_t* row = ranks + uint64_t(v) * uint32_t(k);
-    for (uint32_t p = lane; p < q; p += kWarp) {
-      int32_t j = row[p] - J0;
-      if (j >= 0 && j < wlen) {
-        if (kPacked)
-          atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
-        else
-          atomicAdd(&crow[j], 1u);
+  // a warp takes 32 entries at a time (one per lane), then walks them one by
+  // one with the lanes spread over the ballot prefix above the entry
+  for (uint32_t base = s0 + 32u * wib; base < s1; base += 32u * nw) {
+    const uint32_t t = base + lane;
+    const bool valid = t < s1;
+    const uint32_t e = valid ? entries[t] : 0u;
+    const int32_t q = valid ? int32_t(e % uint32_t(k)) : 0;
+    const int32_t c = valid ? ranks[e] : -1;
+    const int cntv = int(min(32u, s1 - base));
+#pragma unroll 2
+    for (int sidx = 0; sidx < cntv; ++sidx) {
+      const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx);
+      const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx);
+      const int32_t cs = __shfl_sync(0xFFFFFFFFu, c, sidx);
+      // only a ballot with a repeated id (already flagged) can misplace an entry
+      if (cs < R0 || cs >= R1) continue;
+      uint32_t* crow = C + (cs - R0) * wpr;
+      const int32_t* prefix = ranks + (es - uint32_t(qs));
+      for (int32_t p = lane; p < qs; p += 32) {
+        const int32_t j = prefix[p] - J0;
+        if (j >= 0 && j < wlen) {
+          if (kPacked)
+            atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
+          else
+            atomicAdd(&crow[j], 1u);
+        }
       }
     }
   }
   __syncthreads();
-  for (int32_t r = R0; r < R1; ++r) {
-    const int32_t base = cnt[r];
-    const uint32_t* crow = C + (r - R0) * words_per_row;
-    int32_t* drow = d + int64_t(r) * m + J0;
-    for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
-      uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
-      drow[j] = (J0 + j == r) ? 0 : base - int32_t(cv);
+  if (nu == 1) {
+    for (int32_t r = R0; r < R1; ++r) {
+      const int32_t cb = cnt[r];
+      const uint32_t* crow = C + (r - R0) * wpr;
+      int32_t* drow = d + int64_t(r) * m + J0;
+      for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
+        uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
+        drow[j] = (J0 + j == r) ? 0 : cb - int32_t(cv);
+      }
+    }
+  } else {
+    for (int32_t r = R0; r < R1; ++r) {
+      const uint32_t* crow = C + (r - R0) * wpr;
+      int32_t* drow = d + int64_t(r) * m + J0;
+      for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
+        uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
+        if (cv && J0 + j != r) atomicSub(&drow[j], int32_t(cv));
+      }
     }
   }
 }
 
 struct SparsePlan {
-  int32_t rb, jw, njc;
+  int32_t rb, jw, njc, nblocks;
   bool packed;
   size_t smem;
+  uint32_t emax, max_units;
 };
 
-SparsePlan sparse_plan(int64_t n, int32_t m, size_t smem_budget) {
+SparsePlan sparse_plan(int64_t n, int32_t m, int32_t k, int sms) {
+  const size_t smem_budget = 96 * 1024;
   SparsePlan s;
   s.packed = n <= 65535;
   const size_t bytes_per = s.packed ? 2 : 4;
@@ -305,8 +382,14 @@ SparsePlan sparse_plan(int64_t n, int32_t m, size_t smem_budget) {
     s.njc = (m + s.jw - 1) / s.jw;
     s.rb = 1;
   }
+  s.nblocks = (m + s.rb - 1) / s.rb;
   size_t wpr = s.packed ? size_t(s.jw + 1) / 2 : size_t(s.jw);
   s.smem = size_t(s.rb) * wpr * 4;
+  // about eight units per SM over all entries, but no slice below 512 entries
+  const uint64_t total = uint64_t(n) * uint64_t(k);
+  uint64_t emax = (total + uint64_t(sms) * 8 - 1) / (uint64_t(sms) * 8);
+  s.emax = uint32_t(std::max<uint64_t>(512, emax));
+  s.max_units = uint32_t(s.nblocks + (total + s.emax - 1) / s.emax);
   return s;
 }
 
@@ -335,7 +418,7 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
     return align_up(size_t(dense_voter_chunk(n, m)) * ldp * 2, 256) + 4096;
   }
   size_t total = size_t(n) * size_t(k);
-  return align_up(size_t(m) * 4, 256) + 2 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) + 4096;
+  return align_up(size_t(m) * 4, 256) + 3 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) + 4096;
 }
 
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
@@ -389,9 +472,11 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   }
   // sparse
   const uint32_t total = uint32_t(uint64_t(n) * uint64_t(k));
+  const SparsePlan sp = sparse_plan(n, m, k, sms);
   int32_t* cnt = cv.take<int32_t>(size_t(m));
   uint32_t* off = cv.take<uint32_t>(size_t(m) + 1);
   uint32_t* cursor = cv.take<uint32_t>(size_t(m) + 1);
+  uint32_t* uoff = cv.take<uint32_t>(size_t(sp.nblocks) + 1);
   uint32_t* entries = cv.take<uint32_t>(total);
   if (cudaMemsetAsync(cnt, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   {
@@ -404,28 +489,29 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
     sparse_count_kernel<<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
   }
   {
-    Launch L(ctx, stream, "tally_scan", double(m) * 12.0);
-    scan_kernel<<<1, 1024, 0, stream>>>(cnt, m, off, cursor);
+    Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
+    sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff);
   }
   {
     int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
     Launch L(ctx, stream, "tally_group", double(total) * 8.0);
     sparse_scatter_kernel<<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries);
   }
+  {
+    Launch L(ctx, stream, "tally_split_init", 0.0);
+    sparse_init_split_kernel<<<dim3(sp.nblocks, sp.njc), 256, 0, stream>>>(cnt, m, sp.rb, sp.jw, uoff, d);
+  }
   if (int rc = check_launch()) return rc;
-  const size_t budget = 96 * 1024;
-  SparsePlan sp = sparse_plan(n, m, budget);
-  const int32_t nrb = (m + sp.rb - 1) / sp.rb;
-  const int blocks = nrb * sp.njc;
+  dim3 grid(sp.max_units, sp.njc);
   Launch L(ctx, stream, "tally_rows", double(m) * double(m) * 4.0 + double(total) * 4.0);
   if (sp.packed) {
-    cudaFuncSetAttribute(sparse_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    sparse_rows_kernel<true><<<blocks, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, sp.rb, sp.jw,
-                                                                sp.njc, d);
+    cudaFuncSetAttribute(sparse_units_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
+    sparse_units_kernel<true><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
+                                                               sp.emax, sp.rb, sp.jw, d);
   } else {
-    cudaFuncSetAttribute(sparse_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    sparse_rows_kernel<false><<<blocks, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, sp.rb, sp.jw,
-                                                                 sp.njc, d);
+    cudaFuncSetAttribute(sparse_units_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
+    sparse_units_kernel<false><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
+                                                                sp.emax, sp.rb, sp.jw, d);
   }
   return check_launch();
 }
