@@ -3,16 +3,31 @@
 // in the (max, min) semiring.
 //
 // Edge weights are winning votes, w[i][j] = d[i][j] if d[i][j] > d[j][i]
-// else 0, packed into a zero-padded square workspace W (int16 when every
-// count fits in 15 bits, else int32). The closure runs on W in rounds of
-// B = 64 candidates: round r
+// else 0. They are packed into a zero-padded square workspace W (int16 when
+// every count fits in 15 bits, else int32) whose rows and columns follow a
+// relabeling of the candidates: candidates with at least one outgoing edge
+// first, then those without (ids kept in order inside each group). The
+// closure commutes with relabeling, and rows without edges stay zero, so
+// their tiles are never touched.
+//
+// The closure runs on W in rounds of B = 64 candidates; round r
 //   1. closes the diagonal tile (r, r) by plain Floyd-Warshall,
-//   2. updates the row and column panels: X = max(X, A (x) B) with A or B
-//      the closed diagonal tile,
-//   3. updates every other tile (i, j): X = max(X, W(i, r) (x) W(r, j)),
+//   2. updates the row and column panels: X = max(X, D (x) X) / max(X, X (x) D)
+//      with D the closed diagonal tile,
+//   3. updates every other tile: X(i, j) = max(X, W(i, r) (x) W(r, j)),
 // where (x) is the (max, min) product. Widths only grow and every value
 // written is the width of a real path, so the order of the updates inside a
-// phase does not matter and the result is the exact closure.
+// phase does not matter and the result is the exact closure. An update whose
+// operand tile is all zero cannot change anything and is skipped.
+//
+// All rounds run in ONE persistent cooperative launch: the CTAs take work
+// items from a global queue in a fixed order in which the next round's
+// diagonal and panel items come right after the current round's tiles in
+// that row and column ("lookahead"), so they overlap the rest of the round.
+// Each tile carries a progress word (rounds applied, plus a nonzero bit); an
+// item waits (bounded, clock-limited spin) until the tiles it reads have
+// reached its round. Every wait is on an item earlier in the queue, which a
+// resident CTA already holds, so the schedule cannot deadlock.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -20,85 +35,203 @@
 namespace schulze {
 namespace {
 
-constexpr int kB = 64;        // block / tile size
-constexpr int kThreads = 128; // threads per tile CTA
-constexpr int kRM = 8;        // rows per thread
-constexpr int kRN = 4;        // columns per thread
-constexpr int kTX = kB / kRN; // 16 column groups
-// rows: 8 groups of 8 -> 8 * 16 = 128 threads
+constexpr int kB = 64;         // block / tile size
+constexpr int kThreads = 128;  // threads per CTA
+constexpr int kRM = 8;         // rows per thread in a tile update
+constexpr int kRN = 4;         // columns per thread in a tile update
+constexpr int kTX = kB / kRN;  // 16 column groups x 8 row groups = 128 threads
 
-// ---------------------------------------------------------------- pack
+constexpr uint32_t kNZ = 1u << 30;         // progress word: tile has a nonzero entry
+constexpr uint32_t kRoundMask = kNZ - 1u;  // progress word: rounds applied
+constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
-// W[i][j] = d[i][j] if d[i][j] > d[j][i] else 0 (i != j, both < m), 0 elsewhere.
-template <typename E>
-__global__ void pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp, int64_t bound, E* __restrict__ W,
-                            int32_t* status) {
-  __shared__ int32_t s[32][33];
-  const int32_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;
-  // s = d[bj.., bi..] (the transposed block)
+// ------------------------------------------------------------ relabel
+
+// rowflag[i] = 1 iff candidate i has an outgoing edge (some j with
+// d[i][j] > d[j][i]). One CTA per 32 x 32 block pair (A, B), A <= B, reading
+// each d entry once.
+__global__ void rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int32_t* __restrict__ rowflag) {
+  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
+  if (A > B) return;
+  __shared__ int32_t t1[32][33], t2[32][33];  // t1 = d[A.., B..], t2 = d[B.., A..]
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int32_t i = bj + r, j = bi + threadIdx.x;
-    s[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+    int32_t i = A + r, j = B + threadIdx.x;
+    t1[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+    i = B + r, j = A + threadIdx.x;
+    t2[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int32_t i = bi + r, j = bj + threadIdx.x;
-    int32_t out = 0;
-    if (i < m && j < m) {
-      int32_t a = d[int64_t(i) * m + j];
-      int32_t b = s[threadIdx.x][r];  // d[j][i]
-      if (a < 0 || int64_t(a) > bound) set_status(status, SCHULZE_EDATA);
-      if (i != j && a > b) out = a;
-    }
-    if (i < mp && j < mp) W[int64_t(i) * mp + j] = E(out);
+    // row A + r: edge to B + c when t1[r][c] > t2[c][r]
+    int32_t i = A + r, j = B + threadIdx.x;
+    bool e1 = i < m && j < m && i != j && t1[r][threadIdx.x] > t2[threadIdx.x][r];
+    if (__any_sync(0xFFFFFFFFu, e1) && threadIdx.x == 0 && i < m) atomicOr(&rowflag[i], 1);
+    // row B + r: edge to A + c when t2[r][c] > t1[c][r]
+    i = B + r, j = A + threadIdx.x;
+    bool e2 = i < m && j < m && i != j && t2[r][threadIdx.x] > t1[threadIdx.x][r];
+    if (__any_sync(0xFFFFFFFFu, e2) && threadIdx.x == 0 && i < m) atomicOr(&rowflag[i], 1);
   }
 }
 
-// p[i][j] = W[i][j] for i, j < m (unpadded int32 output).
-template <typename E>
-__global__ void widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m, int32_t* __restrict__ p) {
-  const int64_t total = int64_t(m) * m;
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-    int64_t i = t / m, j = t % m;
-    p[t] = i == j ? 0 : int32_t(W[i * mp + j]);
+// Stable partition: perm[new] = old, candidates with edges first; inv[old] = new.
+__global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict__ rowflag, int32_t m,
+                                                       int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
+  __shared__ int32_t part[1024];
+  const int T = blockDim.x;
+  const int per = (m + T - 1) / T;
+  const int b = threadIdx.x * per, e = min(m, b + per);
+  int32_t s = 0;
+  for (int c = b; c < e; ++c) s += rowflag[c] ? 1 : 0;
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    int32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += x;
+    __syncthreads();
   }
+  const int32_t warm = part[T - 1];
+  int32_t before = threadIdx.x ? part[threadIdx.x - 1] : 0;  // warm candidates before b
+  for (int c = b; c < e; ++c) {
+    int32_t nw;
+    if (rowflag[c]) {
+      nw = before++;
+    } else {
+      nw = warm + (c - before);  // cold ones keep their order after the warm ones
+    }
+    perm[nw] = c;
+    inv[c] = nw;
+  }
+}
+
+// ---------------------------------------------------------------- pack
+
+// W[a][b] = w[perm[a]][perm[b]] (0 outside m x m, on the diagonal and where
+// d does not beat its transpose). One CTA per 32 x 32 block pair (A, B),
+// A <= B, writing both W[A][B] and W[B][A]; a warp that writes a nonzero sets
+// the nonzero bit of its 64 x 64 tile's progress word.
+template <typename E>
+__global__ void pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp, int64_t bound,
+                            const int32_t* __restrict__ perm, E* __restrict__ W, uint32_t* __restrict__ prog,
+                            int32_t nb, int32_t* status) {
+  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
+  if (A > B) return;
+  __shared__ int32_t t1[32][33], t2[32][33];  // t1[r][c] = d[perm[A+r]][perm[B+c]], t2 = (B, A)
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int32_t a = A + r, b = B + threadIdx.x;
+    t1[r][threadIdx.x] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
+    a = B + r, b = A + threadIdx.x;
+    t2[r][threadIdx.x] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int32_t a = (side ? B : A) + r, b = (side ? A : B) + threadIdx.x;
+      const int32_t x = side ? t2[r][threadIdx.x] : t1[r][threadIdx.x];
+      const int32_t y = side ? t1[threadIdx.x][r] : t2[threadIdx.x][r];
+      int32_t out = 0;
+      if (a < m && b < m) {
+        if (x < 0 || int64_t(x) > bound) set_status(status, SCHULZE_EDATA);
+        if (a != b && x > y) out = x;
+      }
+      if (a < mp && b < mp) W[int64_t(a) * mp + b] = E(out);
+      if (__any_sync(0xFFFFFFFFu, out != 0) && threadIdx.x == 0)
+        atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
+      if (A == B) break;  // a diagonal block pair is one block
+    }
+  }
+}
+
+// p[x][y] = W[inv[x]][inv[y]] for x != y < m; p[x][x] = 0.
+template <typename E>
+__global__ void widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m, const int32_t* __restrict__ inv,
+                             int32_t* __restrict__ p) {
+  const int32_t x = blockIdx.y;
+  const int32_t ix = inv[x];
+  const E* wrow = W + int64_t(ix) * mp;
+  int32_t* prow = p + int64_t(x) * m;
+  for (int32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < m; y += gridDim.x * blockDim.x)
+    prow[y] = (y == x) ? 0 : int32_t(wrow[inv[y]]);
 }
 
 // ------------------------------------------------------ tile routines
 
-// Closes the diagonal tile (r, r) in place: plain Floyd-Warshall over its
-// 64 vertices, 1024 threads with 4 independent entries each. Row k and
-// column k do not change during step k (min(x, y) <= x), so one barrier per
-// step suffices. The diagonal of the tile is left at whatever cycle width it
-// reaches: it never changes an off-diagonal entry and is zeroed on output.
-constexpr int kDiagThreads = 1024;
+// Closes the diagonal tile (r, r) in place by plain Floyd-Warshall over its
+// 64 vertices. Thread t keeps row t / 2, columns 32 (t % 2) .. + 31 in
+// registers; at step k the two owners of row k publish it through shared
+// memory and p[i][k] comes from the thread itself or its neighbour lane.
+// Row k and column k do not change during step k (min(x, y) <= x). The
+// tile's diagonal may pick up cycle widths; it never changes an off-diagonal
+// entry and is zeroed on output. Returns whether the tile holds a nonzero.
 template <typename E>
-__device__ void diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t* __restrict__ s /*[64][65]*/) {
-  const int64_t base = int64_t(r) * kB * ld + int64_t(r) * kB;
-  for (int t = threadIdx.x; t < kB * kB; t += kDiagThreads) {
-    int i = t / kB, j = t % kB;
-    s[i * (kB + 1) + j] = int32_t(__ldcg(&W[base + int64_t(i) * ld + j]));
-  }
-  __syncthreads();
-  const int i = threadIdx.x / 16, j0 = threadIdx.x % 16;  // columns j0 + 16 q
-  int32_t* row = s + i * (kB + 1);
-  for (int k = 0; k < kB; ++k) {
-    const int32_t a = row[k];
-    const int32_t* rk = s + k * (kB + 1);
-    int32_t v[4], b[4];
+__device__ bool diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t (*rowbuf)[kB]) {
+  const int tid = threadIdx.x;
+  const int i = tid >> 1, half = tid & 1;
+  E* base = W + (int64_t(r) * kB + i) * ld + int64_t(r) * kB + half * 32;
+  int32_t v[32];
+  if (sizeof(E) == 2) {
+    const uint4* src = reinterpret_cast<const uint4*>(base);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      v[q] = row[j0 + 16 * q];
-      b[q] = rk[j0 + 16 * q];
-    }
+      uint4 x = __ldcg(src + q);
+      const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) row[j0 + 16 * q] = max(v[q], min(a, b[q]));
+      for (int h = 0; h < 4; ++h) {
+        v[8 * q + 2 * h] = int32_t(int16_t(w4[h] & 0xFFFFu));
+        v[8 * q + 2 * h + 1] = int32_t(int16_t(w4[h] >> 16));
+      }
+    }
+  } else {
+    const int4* src = reinterpret_cast<const int4*>(base);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int4 x = __ldcg(src + q);
+      v[4 * q] = x.x, v[4 * q + 1] = x.y, v[4 * q + 2] = x.z, v[4 * q + 3] = x.w;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    int32_t* rb = rowbuf[k & 1];
+    if (i == k) {
+#pragma unroll
+      for (int c = 0; c < 32; c += 4)
+        *reinterpret_cast<int4*>(&rb[half * 32 + c]) = make_int4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+    }
     __syncthreads();
+    const int32_t mine = v[k & 31];
+    const int32_t other = __shfl_xor_sync(0xFFFFFFFFu, mine, 1);
+    const int32_t a = ((k >> 5) == half) ? mine : other;  // p[i][k]
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) {
+      int4 b = *reinterpret_cast<const int4*>(&rb[half * 32 + c]);
+      v[c] = max(v[c], min(a, b.x));
+      v[c + 1] = max(v[c + 1], min(a, b.y));
+      v[c + 2] = max(v[c + 2], min(a, b.z));
+      v[c + 3] = max(v[c + 3], min(a, b.w));
+    }
   }
-  for (int t = threadIdx.x; t < kB * kB; t += kDiagThreads) {
-    int ii = t / kB, jj = t % kB;
-    __stcg(&W[base + int64_t(ii) * ld + jj], E(s[ii * (kB + 1) + jj]));
+  int32_t any = 0;
+  if (sizeof(E) == 2) {
+    uint4* dst = reinterpret_cast<uint4*>(base);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w4[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        w4[h] = (uint32_t(v[8 * q + 2 * h]) & 0xFFFFu) | (uint32_t(v[8 * q + 2 * h + 1]) << 16);
+      __stcg(dst + q, make_uint4(w4[0], w4[1], w4[2], w4[3]));
+      any |= int32_t(w4[0] | w4[1] | w4[2] | w4[3]);
+    }
+  } else {
+    int4* dst = reinterpret_cast<int4*>(base);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      __stcg(dst + q, make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      any |= v[4 * q] | v[4 * q + 1] | v[4 * q + 2] | v[4 * q + 3];
+    }
   }
+  return __syncthreads_or(any != 0) != 0;
 }
 
 // Shared-memory operand layouts of one tile update.
@@ -111,16 +244,16 @@ struct SmemS16 {
   uint16_t B[kB][kB];  // B[k][j]
 };
 
-// X(ti, tj) = max(X, W(ti, r) (x) W(r, tj)), int32 lanes.
-__device__ void tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
+// X(ti, tj) = max(X, W(ti, r) (x) W(r, tj)), int32 lanes. Returns whether
+// the updated tile holds a nonzero.
+__device__ bool tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
                                 SmemS32& sm) {
   const int tid = threadIdx.x;
   const int tx = tid % kTX, ty = tid / kTX;
   const int32_t* Ag = W + int64_t(ti) * kB * ld + int64_t(r) * kB;
   const int32_t* Bg = W + int64_t(r) * kB * ld + int64_t(tj) * kB;
   int32_t* Cg = W + int64_t(ti) * kB * ld + int64_t(tj) * kB;
-  // A: row i = tid % 64, 32 consecutive k from (tid / 64) * 32
-  {
+  {  // A: row i = tid % 64, 32 consecutive k from (tid / 64) * 32
     const int i = tid % kB, k0 = (tid / kB) * 32;
     const int4* src = reinterpret_cast<const int4*>(Ag + int64_t(i) * ld + k0);
 #pragma unroll
@@ -132,8 +265,7 @@ __device__ void tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti,
       sm.A[k0 + 4 * q + 3][i] = v.w;
     }
   }
-  // B: straight copy, 16 int4 per row
-  for (int t = tid; t < kB * kB / 4; t += kThreads) {
+  for (int t = tid; t < kB * kB / 4; t += kThreads) {  // B: straight copy
     int k = t / 16, c4 = t % 16;
     int4 v = __ldcg(reinterpret_cast<const int4*>(Bg + int64_t(k) * ld) + c4);
     *reinterpret_cast<int4*>(&sm.B[k][c4 * 4]) = v;
@@ -164,16 +296,18 @@ __device__ void tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti,
       for (int cc = 0; cc < kRN; ++cc)
         acc[rr][cc] = __vimax3_s32(acc[rr][cc], min(a[0][rr], bb[0][cc]), min(a[1][rr], bb[1][cc]));
   }
+  int32_t any = 0;
 #pragma unroll
   for (int rr = 0; rr < kRM; ++rr) {
     int4 v = make_int4(acc[rr][0], acc[rr][1], acc[rr][2], acc[rr][3]);
     __stcg(reinterpret_cast<int4*>(Cg + int64_t(ty * kRM + rr) * ld + tx * kRN), v);
+    any |= v.x | v.y | v.z | v.w;
   }
-  __syncthreads();  // shared operands are reused by the next call
+  return __syncthreads_or(any != 0) != 0;  // also frees the shared operands
 }
 
 // X(ti, tj) = max(X, W(ti, r) (x) W(r, tj)), two 16-bit lanes per word.
-__device__ void tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
+__device__ bool tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
                                 SmemS16& sm) {
   const int tid = threadIdx.x;
   const int tx = tid % kTX, ty = tid / kTX;
@@ -207,7 +341,6 @@ __device__ void tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti,
     acc[rr][0] = v.x, acc[rr][1] = v.y;
   }
   __syncthreads();
-  // two k-steps per three-input max: max(c, min(a, b), min(a', b'))
 #pragma unroll 2
   for (int k = 0; k < kB; k += 2) {
     uint32_t a[2][8], b[2][2];
@@ -226,10 +359,13 @@ __device__ void tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti,
       for (int w = 0; w < 2; ++w)
         acc[rr][w] = __vimax3_s16x2(acc[rr][w], __vmins2(a[0][rr], b[0][w]), __vmins2(a[1][rr], b[1][w]));
   }
+  uint32_t any = 0;
 #pragma unroll
-  for (int rr = 0; rr < kRM; ++rr)
+  for (int rr = 0; rr < kRM; ++rr) {
     __stcg(reinterpret_cast<uint2*>(Cg + int64_t(ty * kRM + rr) * ld + tx * kRN), make_uint2(acc[rr][0], acc[rr][1]));
-  __syncthreads();
+    any |= acc[rr][0] | acc[rr][1];
+  }
+  return __syncthreads_or(any != 0u) != 0;
 }
 
 template <typename E>
@@ -237,49 +373,198 @@ struct Ops;
 template <>
 struct Ops<int32_t> {
   using Smem = SmemS32;
-  static __device__ void update(int32_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm) {
-    tile_update_s32(W, ld, ti, tj, r, sm);
+  static __device__ bool update(int32_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm) {
+    return tile_update_s32(W, ld, ti, tj, r, sm);
   }
 };
 template <>
 struct Ops<int16_t> {
   using Smem = SmemS16;
-  static __device__ void update(int16_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm) {
-    tile_update_s16(W, ld, ti, tj, r, sm);
+  static __device__ bool update(int16_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm) {
+    return tile_update_s16(W, ld, ti, tj, r, sm);
   }
 };
 
-// ------------------------------------------------- per-phase kernels
+// ----------------------------------------------------- work queue
 
-template <typename E>
-__global__ void __launch_bounds__(kDiagThreads) phase1_kernel(E* W, int32_t ld, int32_t r) {
-  __shared__ int32_t s[kB * (kB + 1)];
-  diag_closure<E>(W, ld, r, s);
+enum ItemKind : int32_t { kDiag = 0, kPanel = 1, kTile = 2 };
+struct Item {
+  int32_t kind, r, i, j;
+};
+
+// Queue order, stage by stage (nb tile rows):
+//   stage 0:           D(0) P(0) L(0)
+//   stage s (1..nb-1): D(s) P(s) R(s-1) L(s)      (no L in the last one)
+//   stage nb:          R(nb-1)
+// D(r): diagonal tile; P(r): the 2 (nb-1) panel tiles; L(r): round-r tiles
+// in tile row / column r+1 (the next round's panels); R(r): the other
+// round-r tiles.
+__device__ __forceinline__ int64_t stage_size(int32_t s, int32_t nb) {
+  int64_t z = 0;
+  if (s < nb) z += 1 + 2 * int64_t(nb - 1);
+  if (s >= 1) z += (s - 1 < nb - 1) ? int64_t(nb - 2) * (nb - 2) : int64_t(nb - 1) * (nb - 1);
+  if (s < nb - 1) z += 2 * int64_t(nb) - 3;
+  return z;
 }
 
-// blockIdx.x < nb - 1: row panel tile (r, j); else column panel tile (i, r).
-template <typename E>
-__global__ void __launch_bounds__(kThreads) phase2_kernel(E* W, int32_t ld, int32_t r, int32_t nb) {
-  __shared__ __align__(16) typename Ops<E>::Smem sm;
-  int32_t t = blockIdx.x;
-  if (t < nb - 1) {
-    int32_t j = t + (t >= r);
-    Ops<E>::update(W, ld, r, j, r, sm);
+__device__ Item decode_item(int64_t t, int32_t nb) {
+  int32_t s;
+  const int64_t s0 = stage_size(0, nb);
+  if (t < s0) {
+    s = 0;
   } else {
-    t -= nb - 1;
-    int32_t i = t + (t >= r);
-    Ops<E>::update(W, ld, i, r, r, sm);
+    t -= s0;
+    const int64_t mid = int64_t(nb) * nb;  // stages 1 .. nb-2 all hold nb^2 items
+    const int64_t nmid = nb >= 2 ? nb - 2 : 0;
+    if (t < nmid * mid) {
+      s = 1 + int32_t(t / mid);
+      t -= int64_t(s - 1) * mid;
+    } else {
+      t -= nmid * mid;
+      s = 1 + int32_t(nmid);
+      const int64_t z = stage_size(s, nb);
+      if (t >= z) {
+        t -= z;
+        s += 1;
+      }
+    }
+  }
+  Item it{kDiag, 0, 0, 0};
+  if (s < nb) {
+    if (t == 0) {
+      it.kind = kDiag, it.r = s, it.i = s, it.j = s;
+      return it;
+    }
+    t -= 1;
+    const int64_t np = 2 * int64_t(nb - 1);
+    if (t < np) {
+      it.kind = kPanel, it.r = s;
+      if (t < nb - 1) {
+        it.i = s, it.j = int32_t(t) + (t >= s);
+      } else {
+        const int32_t q = int32_t(t - (nb - 1));
+        it.i = q + (q >= s), it.j = s;
+      }
+      return it;
+    }
+    t -= np;
+  }
+  if (s >= 1) {
+    const int32_t r = s - 1;
+    const bool last = r == nb - 1;
+    const int32_t w = last ? nb - 1 : nb - 2;
+    const int64_t nr = int64_t(w) * w;
+    if (t < nr) {
+      const int32_t a = int32_t(t / w), b = int32_t(t % w);
+      it.kind = kTile, it.r = r;
+      if (last) {
+        it.i = a, it.j = b;  // every tile but row / column nb - 1
+      } else {
+        it.i = a < r ? a : a + 2;
+        it.j = b < r ? b : b + 2;
+      }
+      return it;
+    }
+    t -= nr;
+  }
+  // L(s): tile row s + 1 (columns != s), then tile column s + 1 (rows != s, s + 1)
+  const int32_t r = s;
+  it.kind = kTile, it.r = r;
+  if (t < nb - 1) {
+    it.i = r + 1, it.j = int32_t(t) + (t >= r);
+  } else {
+    const int32_t q = int32_t(t - (nb - 1));
+    it.i = q < r ? q : q + 2, it.j = r + 1;
+  }
+  return it;
+}
+
+struct Sync {
+  uint32_t* prog;        // [nb * nb] progress words
+  uint32_t* head;        // queue head
+  uint32_t* abort_flag;  // set when a wait times out
+  int32_t* status;
+};
+
+// Thread 0 waits until prog[idx] has applied at least `need` rounds; returns
+// the word, or 0xFFFFFFFF after a timeout (which also raises the abort flag).
+__device__ uint32_t wait_round(const Sync& sy, int32_t idx, uint32_t need) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sy.prog + idx) : "memory");
+    if ((v & kRoundMask) >= need) return v;
+    if (*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) return 0xFFFFFFFFu;
+    if (clock64() - t0 > kSpinLimitCycles) {
+      set_status(sy.status, SCHULZE_ETIMEOUT);
+      atomicExch(sy.abort_flag, 1u);
+      return 0xFFFFFFFFu;
+    }
+    __nanosleep(64);
   }
 }
 
+__device__ __forceinline__ void publish(const Sync& sy, int32_t idx, uint32_t word) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sy.prog + idx), "r"(word) : "memory");
+}
+
 template <typename E>
-__global__ void __launch_bounds__(kThreads) phase3_kernel(E* W, int32_t ld, int32_t r, int32_t nb) {
+__global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
+                                                                       int64_t total_items, Sync sy) {
   __shared__ __align__(16) typename Ops<E>::Smem sm;
-  int32_t t = blockIdx.x;
-  int32_t i = t / (nb - 1), j = t % (nb - 1);
-  i += (i >= r);
-  j += (j >= r);
-  Ops<E>::update(W, ld, i, j, r, sm);
+  __shared__ __align__(16) int32_t rowbuf[2][kB];
+  __shared__ int32_t s_item[4];
+  __shared__ uint32_t s_flags;
+  constexpr uint32_t kFail = 0xFFFFFFFFu;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = int64_t(atomicAdd(sy.head, 1u));
+      Item it{-1, 0, 0, 0};
+      uint32_t flags = 0;  // bit 0: skip the update; bit 1: tile already nonzero
+      if (t < total_items && !*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) {
+        it = decode_item(t, nb);
+        const uint32_t r = uint32_t(it.r);
+        const uint32_t own = wait_round(sy, it.i * nb + it.j, r);  // rounds 0 .. r-1 applied
+        uint32_t ok = own;
+        if (own != kFail) {
+          if (it.kind == kDiag) {
+            if (!(own & kNZ)) flags |= 1u;
+          } else if (it.kind == kPanel) {
+            const uint32_t dg = wait_round(sy, it.r * nb + it.r, r + 1);
+            ok = dg;
+            if (dg != kFail && (!(dg & kNZ) || !(own & kNZ))) flags |= 1u;
+          } else {
+            const uint32_t pa = wait_round(sy, it.i * nb + it.r, r + 1);
+            const uint32_t pb = pa != kFail ? wait_round(sy, it.r * nb + it.j, r + 1) : kFail;
+            ok = pb;
+            if (pb != kFail && (!(pa & kNZ) || !(pb & kNZ))) flags |= 1u;
+          }
+        }
+        if (ok == kFail) {
+          it.kind = -1;
+        } else {
+          __threadfence();
+          if (own & kNZ) flags |= 2u;
+        }
+      }
+      s_item[0] = it.kind, s_item[1] = it.r, s_item[2] = it.i, s_item[3] = it.j;
+      s_flags = flags;
+    }
+    __syncthreads();
+    const int32_t kind = s_item[0], r = s_item[1], i = s_item[2], j = s_item[3];
+    const uint32_t flags = s_flags;
+    __syncthreads();
+    if (kind < 0) return;
+    bool nz = (flags & 2u) != 0;
+    if (!(flags & 1u)) {
+      if (kind == kDiag)
+        nz = diag_closure<E>(W, ld, r, rowbuf);
+      else
+        nz = Ops<E>::update(W, ld, i, j, r, sm);
+    }
+    if (threadIdx.x == 0) publish(sy, i * nb + j, uint32_t(r + 1) | (nz ? kNZ : 0u));
+  }
 }
 
 template <typename E>
@@ -287,36 +572,58 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
                 cudaStream_t stream) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
-  E* W = static_cast<E*>(ws);
+  Carver cv(ws);
+  E* W = cv.take<E>(size_t(mp) * size_t(mp));
+  uint32_t* prog = cv.take<uint32_t>(size_t(nb) * size_t(nb) + 2);
+  int32_t* rowflag = cv.take<int32_t>(size_t(m));
+  int32_t* perm = cv.take<int32_t>(size_t(m));
+  int32_t* inv = cv.take<int32_t>(size_t(m));
+  uint32_t* head = prog + size_t(nb) * size_t(nb);
+  uint32_t* abort_flag = head + 1;
+  if (cudaMemsetAsync(prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaMemsetAsync(rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   const double mm = double(m) * double(m);
-  const double tile3 = double(kB) * kB * kB;
+  const int32_t nb32 = (m + 31) / 32;
   {
-    Launch L(ctx, stream, "closure_pack", mm * (8.0 + sizeof(E)));
-    dim3 g(mp / 32, mp / 32), b(32, 8);
-    pack_kernel<E><<<g, b, 0, stream>>>(d, m, mp, bound, W, ctx->status);
+    Launch L(ctx, stream, "closure_rowflags", mm * 4.0);
+    rowflag_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, rowflag);
   }
-  for (int32_t r = 0; r < nb; ++r) {
-    {
-      Launch L(ctx, stream, "closure_diag", tile3);
-      phase1_kernel<E><<<1, kDiagThreads, 0, stream>>>(W, mp, r);
-    }
-    if (nb > 1) {
-      {
-        Launch L(ctx, stream, "closure_panels", 2.0 * (nb - 1) * tile3);
-        phase2_kernel<E><<<2 * (nb - 1), kThreads, 0, stream>>>(W, mp, r, nb);
-      }
-      {
-        Launch L(ctx, stream, "closure_tiles", double(nb - 1) * (nb - 1) * tile3);
-        phase3_kernel<E><<<(nb - 1) * (nb - 1), kThreads, 0, stream>>>(W, mp, r, nb);
-      }
+  {
+    Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
+    relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv);
+  }
+  {
+    Launch L(ctx, stream, "closure_pack", mm * (4.0 + sizeof(E)));
+    const int32_t mp32 = mp / 32;
+    pack_kernel<E><<<dim3(mp32, mp32), dim3(32, 8), 0, stream>>>(d, m, mp, bound, perm, W, prog, nb, ctx->status);
+  }
+  if (int rc = check_launch()) return rc;
+  {
+    // persistent grid: every CTA resident (cooperative launch)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure_persistent_kernel<E>, kThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return SCHULZE_ECUDA;
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
+    const int64_t total_items = int64_t(nb) * nb * nb;
+    const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, total_items));
+    Sync sy{prog, head, abort_flag, ctx->status};
+    E* Wp = W;
+    int32_t ldp = mp, nbp = nb;
+    int64_t ti = total_items;
+    void* args[] = {&Wp, &ldp, &nbp, &ti, &sy};
+    Launch L(ctx, stream, "closure_persistent", double(m) * mm);
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(closure_persistent_kernel<E>), dim3(grid),
+                                    dim3(kThreads), args, 0, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return SCHULZE_ECUDA;
     }
   }
   {
     Launch L(ctx, stream, "closure_widen", mm * (4.0 + sizeof(E)));
-    int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
-    int64_t total = int64_t(m) * m;
-    int blocks = int(std::min<int64_t>((total + 255) / 256, int64_t(sms) * 32));
-    widen_kernel<E><<<blocks, 256, 0, stream>>>(W, mp, m, p);
+    const int32_t gx = std::max(1, std::min<int32_t>((m + 255) / 256, 8));
+    widen_kernel<E><<<dim3(gx, m), 256, 0, stream>>>(W, mp, m, inv, p);
   }
   return check_launch();
 }
@@ -325,7 +632,9 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
 
 size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
   size_t mp = align_up(size_t(m), kB);
-  return mp * mp * (use_s16(bound, flags) ? 2 : 4) + 4096;
+  size_t nb = mp / kB;
+  return align_up(mp * mp * (use_s16(bound, flags) ? 2 : 4), 256) + align_up((nb * nb + 2) * 4, 256) +
+         3 * align_up(size_t(m) * 4, 256) + 4096;
 }
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,

@@ -183,6 +183,21 @@ def test_closure_random_weight_matrices():
                 eq(host(S.schulze_strongest_paths(cu(d), 30000, flags=flags)), want, f"random m={m}")
 
 
+@pytest.mark.parametrize("m,cold_frac", [(700, 0.0), (700, 0.6), (1500, 0.9), (1029, 0.3)])
+def test_closure_many_rounds_with_edgeless_candidates(m, cold_frac):
+    """Candidates without outgoing edges interleaved with the others: the
+    relabeling moves them last and their tiles are skipped."""
+    rs = np.random.Generator(np.random.PCG64(m))
+    d = rs.integers(0, 20000, size=(m, m)).astype(np.int32)
+    d[rs.random((m, m)) < 0.5] = 0
+    cold = rs.random(m) < cold_frac
+    d[cold, :] = 0
+    np.fill_diagonal(d, 0)
+    want = oracle.strongest_paths(d, nthreads=16)
+    for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
+        eq(host(S.schulze_strongest_paths(cu(d), 20000, flags=flags)), want, f"m={m} cold={cold_frac}")
+
+
 def test_closure_large_counts_int32():
     rs = np.random.Generator(np.random.PCG64(4))
     m = 150
