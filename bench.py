@@ -225,11 +225,14 @@ def main():
     # a second pass of the same steps with per-kernel events on the library's
     # stream gives the breakdown and the dominant kernel's launch durations
     ctx.profile(True)
+    cc0 = ctx.closure_counters()
     for i in range(args.steps):
         flush.zero_()
         step()
     prof = ctx.profile_read()
+    cc1 = ctx.closure_counters()
     ctx.profile(False)
+    executed = {key: (cc1[key] - cc0[key]) / args.steps for key in cc0}
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -246,13 +249,18 @@ def main():
     if top[0] is not None:
         name, st = top
         per_launch_ms = st["ms"] / max(1, st["launches"])
-        if name.startswith("closure_tiles"):
+        if name == "closure_persistent":
             fmt = "s16x2" if s16 else "s32"
-            achieved = st["work"] / (st["ms"] * 1e-3)  # (max, min) updates / s
+            # (max, min) updates the kernel executed per launch: 64^3 per computed
+            # tile update or diagonal closure (all-zero updates are skipped)
+            upd = (executed["tile_updates"] + executed["diag_closures"]) * 64.0 ** 3
+            achieved = upd / (per_launch_ms * 1e-3)
             peak = max(probe["s16x2"], probe["s16x2_max3"]) if s16 else max(probe["s32"], probe["s32_max3"])
             roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e9, "peak": peak / 1e9,
                     "unit": "Gupdates/s", "frac": achieved / peak, "traffic": None,
                     "lane_format": fmt, "per_launch_ms": per_launch_ms, "launches": st["launches"],
+                    "executed_updates_per_launch": upd, "dense_updates_per_launch": float(m) ** 3,
+                    "queue_items_per_launch": executed["items"],
                     "peak_source": "schulze_probe_minmax measured in this run (best same-format variant)"}
         else:
             achieved = st["work"] / (st["ms"] * 1e-3)

@@ -37,6 +37,12 @@ int schulze_profile_read(schulze_ctx* ctx, schulze_kernel_stats* out, int max, i
 /* Kernel launches issued by this context since it was created. */
 int64_t schulze_launch_count(const schulze_ctx* ctx);
 
+/* Work the widest-path closure kernel actually executed on this context
+ * since it was created (synchronizes the device): 64 x 64 x 64 tile updates
+ * computed (skipped all-zero updates not counted), 64 x 64 diagonal-tile
+ * closures computed, and work items taken from the queue. */
+int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* diag_closures, int64_t* items);
+
 /*
  * Integer min/max issue-rate probe: a grid of `blocks` x 256 threads runs
  * `iters` iterations of 16 independent (max, min) chains per thread in the

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("schulze_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("schulze_profile_read", _c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
     ("schulze_launch_count", _i64, [_vp]),
+    ("schulze_closure_counters", _c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
     ("schulze_probe_minmax", _c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_double),
                                         _c.POINTER(_c.c_double)]),
 ]
@@ -126,6 +127,13 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.schulze_launch_count(self.handle))
+
+    def closure_counters(self) -> dict:
+        """Cumulative closure work: tile updates, diagonal closures, queue items."""
+        t, dg, it = _i64(0), _i64(0), _i64(0)
+        _check(self._lib.schulze_closure_counters(self.handle, ctypes.byref(t), ctypes.byref(dg), ctypes.byref(it)),
+               "schulze_closure_counters")
+        return {"tile_updates": t.value, "diag_closures": dg.value, "items": it.value}
 
     def __del__(self):
         try:

@@ -75,7 +75,8 @@ __global__ void rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int32_t
 
 // Stable partition: perm[new] = old, candidates with edges first; inv[old] = new.
 __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict__ rowflag, int32_t m,
-                                                       int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
+                                                       int32_t* __restrict__ perm, int32_t* __restrict__ inv,
+                                                       int32_t* __restrict__ warm_out) {
   __shared__ int32_t part[1024];
   const int T = blockDim.x;
   const int per = (m + T - 1) / T;
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
     __syncthreads();
   }
   const int32_t warm = part[T - 1];
+  if (threadIdx.x == 0) *warm_out = warm;
   int32_t before = threadIdx.x ? part[threadIdx.x - 1] : 0;  // warm candidates before b
   for (int c = b; c < e; ++c) {
     int32_t nw;
@@ -392,37 +394,59 @@ struct Item {
   int32_t kind, r, i, j;
 };
 
-// Queue order, stage by stage (nb tile rows):
-//   stage 0:           D(0) P(0) L(0)
-//   stage s (1..nb-1): D(s) P(s) R(s-1) L(s)      (no L in the last one)
-//   stage nb:          R(nb-1)
-// D(r): diagonal tile; P(r): the 2 (nb-1) panel tiles; L(r): round-r tiles
-// in tile row / column r+1 (the next round's panels); R(r): the other
-// round-r tiles.
-__device__ __forceinline__ int64_t stage_size(int32_t s, int32_t nb) {
+// The candidates with outgoing edges occupy the first nbr tile rows after
+// relabeling; the other rows of W are zero and stay zero, and a round over a
+// block of them cannot change anything (min(x, 0) = 0). So rounds run over
+// r < nbr and only tile rows i < nbr are updated, against all nb tile
+// columns: nbr * nbr * nb items in total.
+//
+// Queue order, stage by stage:
+//   stage 0:             D(0) P(0) L(0)
+//   stage s (1..nbr-1):  D(s) P(s) R(s-1) L(s)     (no L in the last one)
+//   stage nbr:           R(nbr-1)
+// D(r): diagonal tile; P(r): row panel (r, j != r) then column panel
+// (i < nbr, i != r); L(r): round-r tiles that are the next round's panels
+// (tile row r+1, then tile column r+1); R(r): the other round-r tiles.
+struct Shape {
+  int32_t nbr, nb;
+  int64_t P, L, Rmid, Rlast;
+};
+
+__device__ __forceinline__ Shape make_shape(int32_t nbr, int32_t nb) {
+  Shape sh;
+  sh.nbr = nbr, sh.nb = nb;
+  sh.P = int64_t(nb - 1) + (nbr - 1);
+  sh.L = int64_t(nb - 1) + (nbr - 2);
+  sh.Rmid = int64_t(nbr - 2) * (nb - 2);
+  sh.Rlast = int64_t(nbr - 1) * (nb - 1);
+  return sh;
+}
+
+__device__ __forceinline__ int64_t stage_size(int32_t s, const Shape& sh) {
   int64_t z = 0;
-  if (s < nb) z += 1 + 2 * int64_t(nb - 1);
-  if (s >= 1) z += (s - 1 < nb - 1) ? int64_t(nb - 2) * (nb - 2) : int64_t(nb - 1) * (nb - 1);
-  if (s < nb - 1) z += 2 * int64_t(nb) - 3;
+  if (s < sh.nbr) z += 1 + sh.P;
+  if (s >= 1) z += (s - 1 < sh.nbr - 1) ? sh.Rmid : sh.Rlast;
+  if (s < sh.nbr - 1) z += sh.L;
   return z;
 }
 
-__device__ Item decode_item(int64_t t, int32_t nb) {
+__device__ Item decode_item(int64_t t, const Shape& sh) {
+  const int32_t nbr = sh.nbr, nb = sh.nb;
   int32_t s;
-  const int64_t s0 = stage_size(0, nb);
+  const int64_t s0 = stage_size(0, sh);
   if (t < s0) {
     s = 0;
   } else {
     t -= s0;
-    const int64_t mid = int64_t(nb) * nb;  // stages 1 .. nb-2 all hold nb^2 items
-    const int64_t nmid = nb >= 2 ? nb - 2 : 0;
+    const int64_t mid = int64_t(nbr) * nb;  // stages 1 .. nbr-2 all hold nbr * nb items
+    const int64_t nmid = nbr >= 2 ? nbr - 2 : 0;
     if (t < nmid * mid) {
       s = 1 + int32_t(t / mid);
       t -= int64_t(s - 1) * mid;
     } else {
       t -= nmid * mid;
       s = 1 + int32_t(nmid);
-      const int64_t z = stage_size(s, nb);
+      const int64_t z = stage_size(s, sh);
       if (t >= z) {
         t -= z;
         s += 1;
@@ -430,14 +454,13 @@ __device__ Item decode_item(int64_t t, int32_t nb) {
     }
   }
   Item it{kDiag, 0, 0, 0};
-  if (s < nb) {
+  if (s < nbr) {
     if (t == 0) {
       it.kind = kDiag, it.r = s, it.i = s, it.j = s;
       return it;
     }
     t -= 1;
-    const int64_t np = 2 * int64_t(nb - 1);
-    if (t < np) {
+    if (t < sh.P) {
       it.kind = kPanel, it.r = s;
       if (t < nb - 1) {
         it.i = s, it.j = int32_t(t) + (t >= s);
@@ -447,28 +470,31 @@ __device__ Item decode_item(int64_t t, int32_t nb) {
       }
       return it;
     }
-    t -= np;
+    t -= sh.P;
   }
   if (s >= 1) {
     const int32_t r = s - 1;
-    const bool last = r == nb - 1;
-    const int32_t w = last ? nb - 1 : nb - 2;
-    const int64_t nr = int64_t(w) * w;
-    if (t < nr) {
-      const int32_t a = int32_t(t / w), b = int32_t(t % w);
-      it.kind = kTile, it.r = r;
-      if (last) {
-        it.i = a, it.j = b;  // every tile but row / column nb - 1
-      } else {
+    it.kind = kTile, it.r = r;
+    if (r == nbr - 1) {
+      const int32_t wc = nb - 1;
+      if (t < sh.Rlast) {
+        const int32_t a = int32_t(t / wc), b = int32_t(t % wc);
+        it.i = a + (a >= r), it.j = b + (b >= r);
+        return it;
+      }
+      t -= sh.Rlast;
+    } else {
+      const int32_t wc = nb - 2;
+      if (t < sh.Rmid) {
+        const int32_t a = int32_t(t / wc), b = int32_t(t % wc);
         it.i = a < r ? a : a + 2;
         it.j = b < r ? b : b + 2;
+        return it;
       }
-      return it;
+      t -= sh.Rmid;
     }
-    t -= nr;
   }
-  // L(s): tile row s + 1 (columns != s), then tile column s + 1 (rows != s, s + 1)
-  const int32_t r = s;
+  const int32_t r = s;  // L(s)
   it.kind = kTile, it.r = r;
   if (t < nb - 1) {
     it.i = r + 1, it.j = int32_t(t) + (t >= r);
@@ -480,10 +506,12 @@ __device__ Item decode_item(int64_t t, int32_t nb) {
 }
 
 struct Sync {
-  uint32_t* prog;        // [nb * nb] progress words
-  uint32_t* head;        // queue head
-  uint32_t* abort_flag;  // set when a wait times out
+  uint32_t* prog;                // [nb * nb] progress words
+  uint32_t* head;                // queue head
+  uint32_t* abort_flag;          // set when a wait times out
   int32_t* status;
+  const int32_t* warm;           // candidates with outgoing edges
+  unsigned long long* counters;  // [0] tile updates done, [1] diagonal closures done, [2] items
 };
 
 // Thread 0 waits until prog[idx] has applied at least `need` rounds; returns
@@ -511,19 +539,22 @@ __device__ __forceinline__ void publish(const Sync& sy, int32_t idx, uint32_t wo
 
 template <typename E>
 __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
-                                                                       int64_t total_items, Sync sy) {
+                                                                       Sync sy) {
   __shared__ __align__(16) typename Ops<E>::Smem sm;
   __shared__ __align__(16) int32_t rowbuf[2][kB];
   __shared__ int32_t s_item[4];
   __shared__ uint32_t s_flags;
   constexpr uint32_t kFail = 0xFFFFFFFFu;
+  const int32_t nbr = (*sy.warm + kB - 1) / kB;
+  const Shape sh = make_shape(nbr, nb);
+  const int64_t total_items = int64_t(nbr) * nbr * nb;
   for (;;) {
     if (threadIdx.x == 0) {
       const int64_t t = int64_t(atomicAdd(sy.head, 1u));
       Item it{-1, 0, 0, 0};
       uint32_t flags = 0;  // bit 0: skip the update; bit 1: tile already nonzero
       if (t < total_items && !*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) {
-        it = decode_item(t, nb);
+        it = decode_item(t, sh);
         const uint32_t r = uint32_t(it.r);
         const uint32_t own = wait_round(sy, it.i * nb + it.j, r);  // rounds 0 .. r-1 applied
         uint32_t ok = own;
@@ -563,7 +594,11 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
       else
         nz = Ops<E>::update(W, ld, i, j, r, sm);
     }
-    if (threadIdx.x == 0) publish(sy, i * nb + j, uint32_t(r + 1) | (nz ? kNZ : 0u));
+    if (threadIdx.x == 0) {
+      publish(sy, i * nb + j, uint32_t(r + 1) | (nz ? kNZ : 0u));
+      if (!(flags & 1u)) atomicAdd(&sy.counters[kind == kDiag ? 1 : 0], 1ull);
+      atomicAdd(&sy.counters[2], 1ull);
+    }
   }
 }
 
@@ -578,6 +613,7 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   int32_t* rowflag = cv.take<int32_t>(size_t(m));
   int32_t* perm = cv.take<int32_t>(size_t(m));
   int32_t* inv = cv.take<int32_t>(size_t(m));
+  int32_t* warm = cv.take<int32_t>(1);
   uint32_t* head = prog + size_t(nb) * size_t(nb);
   uint32_t* abort_flag = head + 1;
   if (cudaMemsetAsync(prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
@@ -590,7 +626,7 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv);
+    relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv, warm);
   }
   {
     Launch L(ctx, stream, "closure_pack", mm * (4.0 + sizeof(E)));
@@ -606,13 +642,12 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
         per_sm < 1)
       return SCHULZE_ECUDA;
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
-    const int64_t total_items = int64_t(nb) * nb * nb;
-    const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, total_items));
-    Sync sy{prog, head, abort_flag, ctx->status};
+    const int64_t max_items = int64_t(nb) * nb * nb;
+    const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, max_items));
+    Sync sy{prog, head, abort_flag, ctx->status, warm, ctx->counters};
     E* Wp = W;
     int32_t ldp = mp, nbp = nb;
-    int64_t ti = total_items;
-    void* args[] = {&Wp, &ldp, &nbp, &ti, &sy};
+    void* args[] = {&Wp, &ldp, &nbp, &sy};
     Launch L(ctx, stream, "closure_persistent", double(m) * mm);
     if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(closure_persistent_kernel<E>), dim3(grid),
                                     dim3(kThreads), args, 0, stream) != cudaSuccess) {
@@ -634,7 +669,7 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
   size_t mp = align_up(size_t(m), kB);
   size_t nb = mp / kB;
   return align_up(mp * mp * (use_s16(bound, flags) ? 2 : 4), 256) + align_up((nb * nb + 2) * 4, 256) +
-         3 * align_up(size_t(m) * 4, 256) + 4096;
+         4 * align_up(size_t(m) * 4, 256) + 4096;
 }
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,

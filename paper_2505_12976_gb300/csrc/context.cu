@@ -78,13 +78,14 @@ int schulze_ctx_create(int device, schulze_ctx** out) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->smem_optin = size_t(optin);
-  if (cudaMalloc(&c->status, sizeof(int32_t)) != cudaSuccess ||
-      cudaMemset(c->status, 0, sizeof(int32_t)) != cudaSuccess) {
+  // one small device block: status word, then the closure work counters
+  if (cudaMalloc(&c->status, 64) != cudaSuccess || cudaMemset(c->status, 0, 64) != cudaSuccess) {
     cudaGetLastError();
     if (c->status) cudaFree(c->status);
     delete c;
     return SCHULZE_ENOMEM;
   }
+  c->counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->status) + 8);
   *out = c;
   return SCHULZE_OK;
 }

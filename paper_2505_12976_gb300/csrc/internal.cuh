@@ -42,7 +42,8 @@ struct ProfClass {
 
 struct schulze_ctx {
   int device = 0;
-  int32_t* status = nullptr;  // device word
+  int32_t* status = nullptr;                // device word
+  unsigned long long* counters = nullptr;   // device: closure tile updates, diagonal closures, items
   schulze::Workspace ws;
   int sm_count = 0;
   size_t smem_optin = 0;

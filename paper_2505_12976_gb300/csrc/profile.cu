@@ -141,6 +141,19 @@ int schulze_profile_read(schulze_ctx* ctx, schulze_kernel_stats* out, int max, i
 
 int64_t schulze_launch_count(const schulze_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* diag_closures, int64_t* items) {
+  if (!ctx || !tile_updates || !diag_closures || !items) return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  unsigned long long h[3] = {0, 0, 0};
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  *tile_updates = int64_t(h[0]);
+  *diag_closures = int64_t(h[1]);
+  *items = int64_t(h[2]);
+  return SCHULZE_OK;
+}
+
 int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates) {
   if (kind < 0 || kind > 3 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
