@@ -37,14 +37,18 @@ WORKLOADS = {
 }
 
 
-def make_election(name: str, rank: int):
+def make_election(name: str, rank: int, m=None, n=None):
+    """The workload's election; m / n override its size (profiling runs)."""
     import workloads as W
+    size = {k: v for k, v in (("m", m), ("n", n)) if v}
     if name == "large_topk":
-        return W.large_topk(seed=W.SEED_BASE + 1 + 1000 * rank)
+        return W.large_topk(seed=W.SEED_BASE + 1 + 1000 * rank, **size)
     if name == "small_mallows":
+        if size:
+            raise SystemExit("small_mallows has a fixed size")
         return W.small_mallows(seed=W.SEED_BASE + 1000 * rank)
     if name == "huge_pl":
-        return W.huge_pl(seed=W.SEED_BASE + 2 + 1000 * rank)
+        return W.huge_pl(seed=W.SEED_BASE + 2 + 1000 * rank, **size)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -162,6 +166,8 @@ def main():
     ap.add_argument("--workload", default="large_topk", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None, help="override the workload's candidate count")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's ballot count")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -180,7 +186,7 @@ def main():
     __graft_entry__.build()
     import paper_2505_12976_gb300 as S
 
-    e = make_election(args.workload, rank)
+    e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)
     ctx = S.context(local)
@@ -303,8 +309,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int16x2" if s16 else "int32", "data": "synthetic",
-                "config": {"workload": args.workload, "detail": WORKLOADS[args.workload]["desc"],
-                           "m": m, "n": n, "k": k, "elections_per_step": world,
+                "config": {"workload": args.workload + ("" if not (args.m or args.n) else f" (m={m}, n={n})"),
+                           "detail": WORKLOADS[args.workload]["desc"], "m": m, "n": n, "k": k, "elections_per_step": world,
                            "closure": "16-bit packed" if s16 else "int32",
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "elections_per_sec": world / (ms * 1e-3),
