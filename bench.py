@@ -202,7 +202,8 @@ def main():
     # integer min/max issue rate (same lane format as the closure)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     probe = {}
-    for kind, name in ((0, "s32"), (1, "s16x2"), (2, "s16x2_max3"), (3, "s32_max3")):
+    for kind, name in ((0, "s32"), (1, "s16x2"), (2, "s16x2_max3"), (3, "s32_max3"), (4, "f32"),
+                       (5, "f32_max3"), (6, "s32_f32_mixed_max3")):
         sec, upd = S.probe_minmax(kind, sms * 8, 4096, local)
         probe[name] = upd / sec
 

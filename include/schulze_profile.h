@@ -49,7 +49,9 @@ int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* d
  * given lane format (kind 0: int32, 2 instructions per update; kind 1: packed
  * int16x2, 2 instructions per 2 updates; kind 2: packed int16x2 with a
  * three-input max folding two updates, 3 instructions per 4 updates; kind 3:
- * int32 with a three-input max, 3 instructions per 2 updates). *seconds
+ * int32 with a three-input max, 3 instructions per 2 updates; kind 4: fp32
+ * lanes; kind 5: fp32 with a three-input max; kind 6: half the chains as
+ * kind 3, half as kind 5). *seconds
  * receives the kernel time (CUDA events) and *updates the number of
  * (max, min) lane updates done.
  * Synchronous.

@@ -9,45 +9,46 @@
 namespace schulze {
 namespace {
 
-constexpr int kT = 32;
+constexpr int kT = 64;         // block of the beaten_by pass
+constexpr int kRankChunk = 256;  // keys per shared-memory chunk of the rank pass
 
-// beaten_by over one 32 x 32 block pair (I, J) with I <= J: both p[I, J] and
-// p[J, I] are staged in shared memory; a warp per row sums its comparisons
-// and adds them with one atomic per row (and per column when I < J).
-__global__ void beaten_by_kernel(const int32_t* __restrict__ p, int32_t m, int32_t nbt, int32_t* __restrict__ bb) {
+// beaten_by over one 64 x 64 block pair (I, J), I <= J (2D grid, the lower
+// half exits): p[I, J] and p[J, I] are staged in shared memory, each row of
+// both blocks is counted by four threads and added with one atomic per row.
+__global__ void __launch_bounds__(256) beaten_by_kernel(const int32_t* __restrict__ p, int32_t m,
+                                                        int32_t* __restrict__ bb) {
+  const int32_t I = blockIdx.y * kT, J = blockIdx.x * kT;
+  if (I > J) return;
   __shared__ int32_t a[kT][kT + 1];  // a[r][c] = p[I + r][J + c]
   __shared__ int32_t b[kT][kT + 1];  // b[r][c] = p[J + r][I + c]
-  int32_t t = blockIdx.x, bi = 0;
-  while (t >= nbt - bi) {
-    t -= nbt - bi;
-    ++bi;
-  }
-  const int32_t bj = bi + t;
-  const int32_t I = bi * kT, J = bj * kT;
-  const int lane = threadIdx.x, wy = threadIdx.y;  // blockDim = (32, 8)
-  for (int r = wy; r < kT; r += blockDim.y) {
-    int32_t i = I + r, j = J + lane;
-    a[r][lane] = (i < m && j < m) ? p[int64_t(i) * m + j] : 0;
-    int32_t i2 = J + r, j2 = I + lane;
-    b[r][lane] = (i2 < m && j2 < m) ? p[int64_t(i2) * m + j2] : 0;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < kT * kT; t += 256) {
+    const int r = t / kT, c = t % kT;
+    int32_t i = I + r, j = J + c;
+    a[r][c] = (i < m && j < m) ? p[int64_t(i) * m + j] : 0;
+    i = J + r, j = I + c;
+    b[r][c] = (i < m && j < m) ? p[int64_t(i) * m + j] : 0;
   }
   __syncthreads();
-  const bool diag = bi == bj;
-  // rows of I: beaten by J + c when p[J + c][I + r] > p[I + r][J + c]
-  for (int r = wy; r < kT; r += blockDim.y) {
-    int32_t i = I + r, j = J + lane;
-    int hit = (i < m && j < m && i != j && b[lane][r] > a[r][lane]) ? 1 : 0;
-    unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
-    if (lane == 0 && bal && i < m) atomicAdd(&bb[i], __popc(bal));
+  const int r = tid >> 2, q = tid & 3;  // row r, columns q * 16 .. + 15
+  // rows of I: I + r is beaten by J + c when p[J + c][I + r] > p[I + r][J + c]
+  int cnt_i = 0, cnt_j = 0;
+#pragma unroll
+  for (int cc = 0; cc < 16; ++cc) {
+    const int c = q * 16 + cc;
+    const bool valid = (I + r < m) && (J + c < m) && (I + r != J + c);
+    cnt_i += (valid && b[c][r] > a[r][c]) ? 1 : 0;
+    // rows of J: J + r is beaten by I + c when p[I + c][J + r] > p[J + r][I + c]
+    const bool valid2 = (J + r < m) && (I + c < m) && (I != J);
+    cnt_j += (valid2 && a[c][r] > b[r][c]) ? 1 : 0;
   }
-  if (!diag) {
-    // rows of J: J + c beaten by I + r when p[I + r][J + c] > p[J + c][I + r]
-    for (int c = wy; c < kT; c += blockDim.y) {
-      int32_t j = J + c, i = I + lane;
-      int hit = (i < m && j < m && a[lane][c] > b[c][lane]) ? 1 : 0;
-      unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
-      if (lane == 0 && bal && j < m) atomicAdd(&bb[j], __popc(bal));
-    }
+  cnt_i += __shfl_xor_sync(0xFFFFFFFFu, cnt_i, 1);
+  cnt_i += __shfl_xor_sync(0xFFFFFFFFu, cnt_i, 2);
+  cnt_j += __shfl_xor_sync(0xFFFFFFFFu, cnt_j, 1);
+  cnt_j += __shfl_xor_sync(0xFFFFFFFFu, cnt_j, 2);
+  if (q == 0) {
+    if (cnt_i) atomicAdd(&bb[I + r], cnt_i);
+    if (cnt_j) atomicAdd(&bb[J + r], cnt_j);
   }
 }
 
@@ -55,37 +56,41 @@ __global__ void winners_kernel(const int32_t* __restrict__ bb, int32_t m, int32_
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) win[i] = bb[i] == 0;
 }
 
-// order[pos(i)] = i with pos(i) = #{j : (bb[j], j) < (bb[i], i)}.
-__global__ void rank_kernel(const int32_t* __restrict__ bb, int32_t m, int32_t* __restrict__ order) {
-  __shared__ int64_t keys[1024];
+// pos[i] += #{j in this CTA's chunk : (bb[j], j) < (bb[i], i)}; 2D grid over
+// (chunks of i, chunks of j), pos zeroed before.
+__global__ void __launch_bounds__(256) rank_count_kernel(const int32_t* __restrict__ bb, int32_t m,
+                                                         int32_t* __restrict__ pos) {
+  __shared__ int64_t keys[kRankChunk];
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t mine = i < m ? (int64_t(bb[i]) << 32) | uint32_t(i) : INT64_MAX;
-  int32_t pos = 0;
-  for (int32_t j0 = 0; j0 < m; j0 += blockDim.x) {
-    __syncthreads();
-    int32_t j = j0 + threadIdx.x;
-    keys[threadIdx.x] = j < m ? (int64_t(bb[j]) << 32) | uint32_t(j) : INT64_MAX;
-    __syncthreads();
-    const int lim = min(int(blockDim.x), m - j0);
-    for (int t = 0; t < lim; ++t) pos += keys[t] < mine;
-  }
-  if (i < m) order[pos] = i;
+  const int32_t j0 = blockIdx.y * kRankChunk;
+  const int32_t j = j0 + threadIdx.x;
+  keys[threadIdx.x] = j < m ? (int64_t(bb[j]) << 32) | uint32_t(j) : INT64_MAX;
+  __syncthreads();
+  const int lim = min(kRankChunk, m - j0);
+  int32_t c = 0;
+  for (int t = 0; t < lim; ++t) c += keys[t] < mine;
+  if (i < m && c) atomicAdd(&pos[i], c);
+}
+
+__global__ void rank_scatter_kernel(const int32_t* __restrict__ pos, int32_t m, int32_t* __restrict__ order) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) order[pos[i]] = i;
 }
 
 }  // namespace
 
-size_t extract_workspace_bytes(int32_t m) { return align_up(size_t(m) * 4, 256) + 4096; }
+size_t extract_workspace_bytes(int32_t m) { return 2 * align_up(size_t(m) * 4, 256) + 4096; }
 
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream) {
   Carver cv(ws);
   int32_t* bb = beaten_by ? beaten_by : cv.take<int32_t>(size_t(m));
+  int32_t* pos = cv.take<int32_t>(size_t(m));
   if (cudaMemsetAsync(bb, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   const int32_t nbt = (m + kT - 1) / kT;
-  const int32_t npairs = nbt * (nbt + 1) / 2;
   {
     Launch L(ctx, stream, "extract_beaten_by", double(m) * double(m) * 4.0);
-    beaten_by_kernel<<<npairs, dim3(32, 8), 0, stream>>>(p, m, nbt, bb);
+    beaten_by_kernel<<<dim3(nbt, nbt), 256, 0, stream>>>(p, m, bb);
   }
   const int g = (m + 255) / 256;
   if (winners) {
@@ -93,8 +98,15 @@ int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winne
     winners_kernel<<<g, 256, 0, stream>>>(bb, m, winners);
   }
   if (order) {
-    Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
-    rank_kernel<<<(m + 255) / 256, 256, 0, stream>>>(bb, m, order);
+    if (cudaMemsetAsync(pos, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+    {
+      Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
+      rank_count_kernel<<<dim3(g, (m + kRankChunk - 1) / kRankChunk), 256, 0, stream>>>(bb, m, pos);
+    }
+    {
+      Launch L(ctx, stream, "extract_order", double(m) * 8.0);
+      rank_scatter_kernel<<<g, 256, 0, stream>>>(pos, m, order);
+    }
   }
   return check_launch();
 }

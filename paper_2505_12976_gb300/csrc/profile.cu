@@ -105,6 +105,46 @@ __global__ void __launch_bounds__(256) minmax_probe_kernel(int iters, uint32_t s
   if (s == 0x12345678u) sink[0] = s;
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Float lanes: KIND 4 fp32 max(c, min(a, b)); KIND 5 fp32 three-input max
+// folding two updates; KIND 6 half the chains int32 three-input max, half
+// fp32 three-input max (do the two pipes add up?).
+template <int KIND>
+__global__ void __launch_bounds__(256) minmax_probe_f32_kernel(int iters, uint32_t seed, uint32_t* sink) {
+  constexpr int C = 16;
+  float c[C], a[C];
+  int32_t ci[C], ai[C];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    ci[q] = int32_t((t * 2654435761u + q * 40503u + seed) & 0xFFFFFu);
+    ai[q] = int32_t((t * 97u + q * 7919u + seed * 3u) & 0xFFFFFu);
+    c[q] = float(ci[q]);
+    a[q] = float(ai[q]);
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      if (KIND == 4) {
+        c[q] = fmaxf(c[q], fminf(a[q], c[(q + 5) % C]));
+      } else if (KIND == 5 || (KIND == 6 && (q & 1))) {
+        c[q] = max3f(c[q], fminf(a[q], c[(q + 5) % C]), fminf(a[(q + 1) % C], c[(q + 9) % C]));
+      } else {
+        ci[q] = __vimax3_s32(ci[q], min(ai[q], ci[(q + 5) % C]), min(ai[(q + 1) % C], ci[(q + 9) % C]));
+      }
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < C; ++q) s ^= __float_as_uint(c[q]) ^ uint32_t(ci[q]);
+  if (s == 0x12345678u) sink[0] = s;
+}
+
 }  // namespace schulze
 
 using namespace schulze;
@@ -155,7 +195,7 @@ int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* d
 }
 
 int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates) {
-  if (kind < 0 || kind > 3 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
+  if (kind < 0 || kind > 6 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
   uint32_t* sink = nullptr;
   if (cudaMalloc(&sink, 4) != cudaSuccess) return SCHULZE_ENOMEM;
@@ -166,7 +206,10 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
     if (kind == 0) minmax_probe_kernel<0><<<blocks, 256>>>(it, 1u, sink);
     else if (kind == 1) minmax_probe_kernel<1><<<blocks, 256>>>(it, 1u, sink);
     else if (kind == 2) minmax_probe_kernel<2><<<blocks, 256>>>(it, 1u, sink);
-    else minmax_probe_kernel<3><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 3) minmax_probe_kernel<3><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 4) minmax_probe_f32_kernel<4><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 5) minmax_probe_f32_kernel<5><<<blocks, 256>>>(it, 1u, sink);
+    else minmax_probe_f32_kernel<6><<<blocks, 256>>>(it, 1u, sink);
   };
   launch(16);  // warm-up
   cudaEventRecord(e0);
@@ -180,7 +223,10 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
   cudaEventDestroy(e1);
   cudaFree(sink);
   *seconds = double(ms) * 1e-3;
-  const double lanes = kind == 0 ? 1.0 : (kind == 1 ? 2.0 : (kind == 2 ? 4.0 : 2.0));
+  // (max, min) updates per chain step: one, or two when a three-input max
+  // folds two steps, times the lanes per word
+  static const double per_step[7] = {1.0, 2.0, 4.0, 2.0, 1.0, 2.0, 2.0};
+  const double lanes = per_step[kind];
   *updates = double(blocks) * 256.0 * double(iters) * 16.0 * lanes;
   return rc;
 }

@@ -17,6 +17,8 @@ namespace schulze {
 namespace {
 
 constexpr int kWarp = 32;
+constexpr int kMaxRowsPerBlock = 256;  // rows of d owned by one sparse work unit
+constexpr int32_t kLocalHistMax = 16384;  // candidates counted in shared memory per CTA
 
 // ------------------------------------------------------------------ dense
 
@@ -158,15 +160,23 @@ __global__ void mirror_kernel(int32_t* __restrict__ d, int32_t m, int32_t tile, 
 // ----------------------------------------------------------------- sparse
 
 // cnt[c] += 1 for every listed c; checks ids (range, repeats within a
-// ballot via a per-warp bitmap in shared memory). One warp per ballot.
+// ballot via a per-warp bitmap in shared memory). One warp per ballot. With
+// kLocal the CTA first counts in a shared-memory histogram and adds it to
+// cnt once per candidate at the end (popular candidates would otherwise
+// serialise on one global counter).
+template <bool kLocal>
 __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
                                     int32_t* __restrict__ cnt, int32_t* status) {
-  extern __shared__ uint32_t bitmap[];  // warps_per_block * words
+  extern __shared__ uint32_t smem_count[];  // [m] histogram if kLocal, then warps_per_block * words
   const int words = (m + 31) / 32;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t* bm = bitmap + wib * words;
+  uint32_t* hist = smem_count;
+  uint32_t* bm = smem_count + (kLocal ? m : 0) + wib * words;
+  if (kLocal) {
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hist[c] = 0u;
+  }
   for (int t = lane; t < words; t += kWarp) bm[t] = 0u;
-  __syncwarp();
+  __syncthreads();
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t v = warp; v < n; v += nwarps) {
@@ -182,6 +192,8 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
         uint32_t old = atomicOr(&bm[c >> 5], bit);
         if (old & bit)
           set_status(status, SCHULZE_EDATA);
+        else if (kLocal)
+          atomicAdd(&hist[c], 1u);
         else
           atomicAdd(&cnt[c], 1);
       }
@@ -192,6 +204,11 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
       if (c >= 0 && c < m) bm[c >> 5] = 0u;
     }
     __syncwarp();
+  }
+  if (kLocal) {
+    __syncthreads();
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x)
+      if (hist[c]) atomicAdd(&cnt[c], int32_t(hist[c]));
   }
 }
 
@@ -246,14 +263,43 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
   if (threadIdx.x == 0) uoff[nblocks] = units;
 }
 
-// entries grouped by candidate: entries[cursor[c]++] = v * k + q.
+// entries grouped by candidate: entries[cursor[c]++] = v * k + q. With kLocal
+// each CTA takes a contiguous chunk of entries, counts it per candidate in
+// shared memory, reserves each candidate's slots with one global atomic and
+// then places its entries with shared-memory cursors.
+template <bool kLocal>
 __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+  if (!kLocal) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+      int32_t c = ranks[e];
+      if (c < 0 || c >= m) continue;  // already reported by the count pass
+      uint32_t slot = atomicAdd(&cursor[c], 1u);
+      entries[slot] = e;
+    }
+    return;
+  }
+  extern __shared__ uint32_t smem_scatter[];  // hist[m], base[m]
+  uint32_t* hist = smem_scatter;
+  uint32_t* basev = smem_scatter + m;
+  const uint32_t chunk = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t e0 = min(total, blockIdx.x * chunk), e1 = min(total, e0 + chunk);
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hist[c] = 0u;
+  __syncthreads();
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     int32_t c = ranks[e];
-    if (c < 0 || c >= m) continue;  // already reported by the count pass
-    uint32_t slot = atomicAdd(&cursor[c], 1u);
-    entries[slot] = e;
+    if (c >= 0 && c < m) atomicAdd(&hist[c], 1u);
+  }
+  __syncthreads();
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+    const uint32_t h = hist[c];
+    if (h) basev[c] = atomicAdd(&cursor[c], h);
+    hist[c] = 0u;
+  }
+  __syncthreads();
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int32_t c = ranks[e];
+    if (c >= 0 && c < m) entries[basev[c] + atomicAdd(&hist[c], 1u)] = e;
   }
 }
 
@@ -285,6 +331,7 @@ __global__ void __launch_bounds__(512)
                         const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
                         int32_t* __restrict__ d) {
   extern __shared__ uint32_t C[];
+  __shared__ uint32_t so[kMaxRowsPerBlock + 1];  // off[R0 .. R1]
   const uint32_t unit = blockIdx.x;
   if (unit >= uoff[nblocks]) return;
   int32_t lo = 0, hi = nblocks - 1;  // block b with uoff[b] <= unit < uoff[b + 1]
@@ -300,36 +347,62 @@ __global__ void __launch_bounds__(512)
   const int32_t wpr = kPacked ? (jw + 1) / 2 : jw;  // words per row
   const int32_t nwords = (R1 - R0) * wpr;
   for (int32_t t = threadIdx.x; t < nwords; t += blockDim.x) C[t] = 0u;
+  for (int32_t t = threadIdx.x; t <= R1 - R0; t += blockDim.x) so[t] = off[R0 + t];
   __syncthreads();
-  const uint32_t eb = off[R0], ee = off[R1];
+  const uint32_t eb = so[0], ee = so[R1 - R0];
   const uint32_t s0 = eb + u * emax, s1 = min(ee, s0 + emax);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // a warp takes 32 entries at a time (one per lane), then walks them one by
-  // one with the lanes spread over the ballot prefix above the entry
+  auto count = [&](uint32_t* crow, int32_t j) {
+    if (j >= 0 && j < wlen) {
+      if (kPacked)
+        atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
+      else
+        atomicAdd(&crow[j], 1u);
+    }
+  };
+  // A warp takes 32 entries at a time (one per lane) and finds each entry's
+  // candidate from the CSR offsets; it then walks them four at a time with the
+  // lanes spread over the ballot prefix above each entry, so that eight
+  // prefix loads per lane are in flight before the shared-memory counts.
   for (uint32_t base = s0 + 32u * wib; base < s1; base += 32u * nw) {
     const uint32_t t = base + lane;
     const bool valid = t < s1;
     const uint32_t e = valid ? entries[t] : 0u;
     const int32_t q = valid ? int32_t(e % uint32_t(k)) : 0;
-    const int32_t c = valid ? ranks[e] : -1;
+    int32_t c = -1;
+    if (valid) {  // row r with so[r - R0] <= t < so[r - R0 + 1]
+      int32_t a = 0, z = R1 - R0 - 1;
+      while (a < z) {
+        int32_t mid = (a + z + 1) >> 1;
+        if (so[mid] <= t) a = mid; else z = mid - 1;
+      }
+      c = R0 + a;
+    }
     const int cntv = int(min(32u, s1 - base));
-#pragma unroll 2
-    for (int sidx = 0; sidx < cntv; ++sidx) {
-      const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx);
-      const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx);
-      const int32_t cs = __shfl_sync(0xFFFFFFFFu, c, sidx);
-      // only a ballot with a repeated id (already flagged) can misplace an entry
-      if (cs < R0 || cs >= R1) continue;
-      uint32_t* crow = C + (cs - R0) * wpr;
-      const int32_t* prefix = ranks + (es - uint32_t(qs));
-      for (int32_t p = lane; p < qs; p += 32) {
-        const int32_t j = prefix[p] - J0;
-        if (j >= 0 && j < wlen) {
-          if (kPacked)
-            atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
-          else
-            atomicAdd(&crow[j], 1u);
-        }
+    for (int g = 0; g < cntv; g += 4) {
+      int32_t jv[4][2];
+      uint32_t* crow[4];
+      int32_t qv[4];
+      uint32_t rowstart[4];
+#pragma unroll
+      for (int uu = 0; uu < 4; ++uu) {
+        const int sidx = g + uu;
+        const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx & 31);
+        const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx & 31);
+        const int32_t cs = __shfl_sync(0xFFFFFFFFu, c, sidx & 31);
+        const bool ok = sidx < cntv && cs >= R0 && cs < R1;
+        const int32_t* prefix = ranks + (es - uint32_t(qs));
+        qv[uu] = ok ? qs : 0;
+        rowstart[uu] = es - uint32_t(qs);
+        crow[uu] = C + (ok ? cs - R0 : 0) * wpr;
+        jv[uu][0] = (ok && lane < qs) ? prefix[lane] - J0 : -1;
+        jv[uu][1] = (ok && lane + 32 < qs) ? prefix[lane + 32] - J0 : -1;
+      }
+#pragma unroll
+      for (int uu = 0; uu < 4; ++uu) {
+        count(crow[uu], jv[uu][0]);
+        count(crow[uu], jv[uu][1]);
+        for (int32_t p = 64 + lane; p < qv[uu]; p += 32) count(crow[uu], ranks[rowstart[uu] + p] - J0);
       }
     }
   }
@@ -374,7 +447,7 @@ SparsePlan sparse_plan(int64_t n, int32_t m, int32_t k, int sms) {
     s.jw = m;
     s.njc = 1;
     s.rb = int32_t(std::max<size_t>(1, smem_budget / row_bytes));
-    s.rb = std::min(s.rb, m);
+    s.rb = std::min(std::min(s.rb, m), kMaxRowsPerBlock);
   } else {
     s.njc = int32_t((row_bytes + smem_budget - 1) / smem_budget);
     s.jw = (m + s.njc - 1) / s.njc;
@@ -479,23 +552,35 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   uint32_t* uoff = cv.take<uint32_t>(size_t(sp.nblocks) + 1);
   uint32_t* entries = cv.take<uint32_t>(total);
   if (cudaMemsetAsync(cnt, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  const bool local_hist = m <= kLocalHistMax;
   {
-    const int threads = 256;
-    const size_t smem = size_t(threads / 32) * size_t((m + 31) / 32) * 4;
-    int blocks = int(std::min<int64_t>((n + 7) / 8, int64_t(sms) * 8));
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sparse_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int threads = 512;
+    const size_t smem = (local_hist ? size_t(m) * 4 : 0) + size_t(threads / 32) * size_t((m + 31) / 32) * 4;
+    const int blocks = int(std::min<int64_t>((n + 15) / 16, int64_t(sms)));
     Launch L(ctx, stream, "tally_count", double(total) * 4.0);
-    sparse_count_kernel<<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
+    if (local_hist) {
+      cudaFuncSetAttribute(sparse_count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      sparse_count_kernel<true><<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
+    } else {
+      cudaFuncSetAttribute(sparse_count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      sparse_count_kernel<false><<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
+    }
   }
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
     sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff);
   }
   {
-    int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
     Launch L(ctx, stream, "tally_group", double(total) * 8.0);
-    sparse_scatter_kernel<<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries);
+    if (local_hist) {
+      const size_t smem = size_t(m) * 8;
+      const int blocks = int(std::min<uint64_t>((uint64_t(total) + 4095) / 4096, uint64_t(sms)));
+      cudaFuncSetAttribute(sparse_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      sparse_scatter_kernel<true><<<blocks, 1024, smem, stream>>>(ranks, total, m, cursor, entries);
+    } else {
+      const int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
+      sparse_scatter_kernel<false><<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries);
+    }
   }
   {
     Launch L(ctx, stream, "tally_split_init", 0.0);
