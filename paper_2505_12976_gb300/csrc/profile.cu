@@ -132,10 +132,12 @@ __global__ void __launch_bounds__(256) minmax_probe_f32_kernel(int iters, uint32
     for (int q = 0; q < C; ++q) {
       if (KIND == 4) {
         c[q] = fmaxf(c[q], fminf(a[q], c[(q + 5) % C]));
-      } else if (KIND == 5 || (KIND == 6 && (q & 1))) {
+      } else if (KIND == 5) {
         c[q] = max3f(c[q], fminf(a[q], c[(q + 5) % C]), fminf(a[(q + 1) % C], c[(q + 9) % C]));
-      } else {
-        ci[q] = __vimax3_s32(ci[q], min(ai[q], ci[(q + 5) % C]), min(ai[(q + 1) % C], ci[(q + 9) % C]));
+      } else if (q & 1) {  // KIND 6: odd chains read odd chains only (all updated every step)
+        c[q] = max3f(c[q], fminf(a[q], c[(q + 2) % C]), fminf(a[(q + 4) % C], c[(q + 6) % C]));
+      } else {  // even chains read even chains only
+        ci[q] = __vimax3_s32(ci[q], min(ai[q], ci[(q + 2) % C]), min(ai[(q + 4) % C], ci[(q + 6) % C]));
       }
     }
   }
