@@ -48,7 +48,8 @@ enum schulze_status {
   SCHULZE_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
   SCHULZE_EDATA = -4,    /* (device status) bad ballot id, repeated id, negative or too large count */
   SCHULZE_ETIMEOUT = -5, /* (device status) a bounded device wait gave up */
-  SCHULZE_ERANGE = -6    /* workspace too small while the stream is being captured */
+  SCHULZE_ERANGE = -6,   /* workspace too small while the stream is being captured */
+  SCHULZE_ETOOBIG = -7   /* size beyond the fixed scratch of schulze_strongest_paths_static */
 };
 
 /* Closure flags (schulze_strongest_paths, schulze_run). */
@@ -110,6 +111,31 @@ int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, 
  */
 int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
                             uint32_t flags, schulze_stream_t stream);
+
+/*
+ * Same result as schulze_strongest_paths, without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code whose device memory is owned entirely by
+ * another allocator (a framework's caching pool, an arena reserved at
+ * start-up), or that runs under a rule forbidding allocation once set up
+ * (latency-critical serving loops). It needs no context either.
+ *   d, bound, p, flags  as for schulze_strongest_paths; 1 <= m <= 1024,
+ *          larger m returns SCHULZE_ETOOBIG.
+ *   status a device int32 where data errors found by the kernels are
+ *          recorded (SCHULZE_EDATA, SCHULZE_ETIMEOUT; the first one wins; the
+ *          caller zeroes it), or NULL to not record them.
+ * Scratch: one file-scope device array of about 4.1 MB (W for m <= 1024 in
+ * int32, progress words, relabeling), present on every GPU that loads the
+ * library until the process exits. The call runs on the calling thread's
+ * current device; its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it, so make that first call
+ * before any stream capture. The call resets the parts of the array that
+ * must start at zero; all calls share the one array, so calls that overlap
+ * on the GPU (other streams, other host threads) race and corrupt each
+ * other's results: order them on one stream.
+ */
+int schulze_strongest_paths_static(const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
+                                   int32_t* status, schulze_stream_t stream);
 
 /*
  * Winners (Sect. 2.1): i is a winner iff no j beats it, i.e. p[i][j] >=

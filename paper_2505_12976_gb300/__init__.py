@@ -26,7 +26,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libschulze.so")
 
-OK, EINVAL, ENOMEM, ECUDA, EDATA, ETIMEOUT, ERANGE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, EDATA, ETIMEOUT, ERANGE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE = 0, 1, 2, 4, 8
 
 _lock = threading.Lock()
@@ -50,6 +50,7 @@ SIGNATURES = [
     ("schulze_ranking", _c.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
     ("schulze_run", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
     ("schulze_run_host", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _u32, _vp]),
+    ("schulze_strongest_paths_static", _c.c_int, [_vp, _i32, _i64, _vp, _u32, _vp, _vp]),
     # include/schulze_profile.h
     ("schulze_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("schulze_profile_read", _c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
@@ -246,6 +247,24 @@ def schulze_run(ranks: torch.Tensor, m: int, flags: int = 0, out: dict | None = 
     _check(load().schulze_run(ctx.handle, _ptr(ranks), n, m, k, _ptr(d), _ptr(p), _ptr(w), _ptr(o), _ptr(b),
                               flags, _stream(stream, ctx.device)), "schulze_run")
     return {"d": d, "p": p, "winners": w, "order": o, "beaten_by": b}
+
+
+def schulze_strongest_paths_static(d: torch.Tensor, bound: int, p: torch.Tensor | None = None, flags: int = 0,
+                                   status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Widest paths without any device allocation inside the library, for
+    callers that cannot allocate device memory (m <= 1024; scratch is a fixed
+    array in the library). `status`: optional device int32 [1] receiving data
+    errors. Calls must not overlap on the GPU."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    _dev_i32(d, "d", (m, m))
+    p = _out(p, (m, m), d.device, "p")
+    if status is not None:
+        _dev_i32(status, "status", (1,))
+    with torch.cuda.device(d.device):
+        _check(load().schulze_strongest_paths_static(_ptr(d), m, int(bound), _ptr(p), flags, _ptr(status),
+                                                     _stream(stream, d.device)), "schulze_strongest_paths_static")
+    return p
 
 
 def probe_minmax(kind: int, blocks: int, iters: int, device: int = 0):

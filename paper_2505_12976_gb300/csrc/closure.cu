@@ -29,6 +29,7 @@
 // reached its round. Every wait is on an item earlier in the queue, which a
 // resident CTA already holds, so the schedule cannot deadlock.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -678,4 +679,110 @@ int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound,
   return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream);
 }
 
+// ------------------------------------------------- allocation-free variant
+//
+// schulze_strongest_paths_static runs the same kernels as closure_launch on
+// scratch that lives in a file-scope device array instead of a context's
+// cudaMalloc'ed workspace, for callers that cannot allocate device memory.
+// The array is sized for m <= kStaticMaxM; every GPU that loads the library
+// holds it until the process exits.
+
+namespace {
+
+constexpr int32_t kStaticMaxM = 1024;
+constexpr size_t kStaticMp = 1024;  // kStaticMaxM rounded up to the tile size
+constexpr size_t kStaticNb = kStaticMp / kB;
+// byte offsets inside the array (each 256-aligned)
+constexpr size_t kStW = 0;                                            // W: up to kStaticMp^2 int32
+constexpr size_t kStProg = kStW + kStaticMp * kStaticMp * 4;          // progress words + head + abort
+constexpr size_t kStRowflag = kStProg + align_up((kStaticNb * kStaticNb + 2) * 4, 256);
+constexpr size_t kStPerm = kStRowflag + kStaticMaxM * 4;
+constexpr size_t kStInv = kStPerm + kStaticMaxM * 4;
+constexpr size_t kStWarm = kStInv + kStaticMaxM * 4;
+constexpr size_t kStCounters = kStWarm + 256;                         // 3 x u64, never read back
+constexpr size_t kStaticBytes = kStCounters + 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+unsigned char* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device. In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up
+// once per device, with that device current, and cached.
+int static_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= kMaxDevices) return SCHULZE_EINVAL;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return SCHULZE_ECUDA;
+    }
+    g_static_ptr[device] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_static_ptr[device];
+  return SCHULZE_OK;
+}
+
+template <typename E>
+int run_closure_static(unsigned char* base, int device, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                       int32_t* status, cudaStream_t stream) {
+  const int32_t mp = int32_t(align_up(size_t(m), kB));
+  const int32_t nb = mp / kB;
+  E* W = reinterpret_cast<E*>(base + kStW);
+  uint32_t* prog = reinterpret_cast<uint32_t*>(base + kStProg);
+  int32_t* rowflag = reinterpret_cast<int32_t*>(base + kStRowflag);
+  int32_t* perm = reinterpret_cast<int32_t*>(base + kStPerm);
+  int32_t* inv = reinterpret_cast<int32_t*>(base + kStInv);
+  int32_t* warm = reinterpret_cast<int32_t*>(base + kStWarm);
+  auto* counters = reinterpret_cast<unsigned long long*>(base + kStCounters);
+  uint32_t* head = prog + size_t(nb) * size_t(nb);
+  uint32_t* abort_flag = head + 1;
+  // the array keeps the previous call's contents: reset what must start at zero
+  if (cudaMemsetAsync(prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaMemsetAsync(rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  const int32_t nb32 = (m + 31) / 32;
+  rowflag_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, rowflag);
+  relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv, warm);
+  const int32_t mp32 = mp / 32;
+  pack_kernel<E><<<dim3(mp32, mp32), dim3(32, 8), 0, stream>>>(d, m, mp, bound, perm, W, prog, nb, status);
+  if (int rc = check_launch()) return rc;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure_persistent_kernel<E>, kThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    return SCHULZE_ECUDA;
+  const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, int64_t(nb) * nb * nb));
+  Sync sy{prog, head, abort_flag, status, warm, counters};
+  E* Wp = W;
+  int32_t ldp = mp, nbp = nb;
+  void* args[] = {&Wp, &ldp, &nbp, &sy};
+  if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(closure_persistent_kernel<E>), dim3(grid), dim3(kThreads),
+                                  args, 0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SCHULZE_ECUDA;
+  }
+  const int32_t gx = std::max(1, std::min<int32_t>((m + 255) / 256, 8));
+  widen_kernel<E><<<dim3(gx, m), 256, 0, stream>>>(W, mp, m, inv, p);
+  return check_launch();
+}
+
+}  // namespace
+
 }  // namespace schulze
+
+extern "C" int schulze_strongest_paths_static(const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                                              uint32_t flags, int32_t* status, schulze_stream_t stream) {
+  using namespace schulze;
+  if (!d || !p || d == p || m < 1 || bound < 0) return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || bound > 32767)) return SCHULZE_EINVAL;
+  if (m > kStaticMaxM) return SCHULZE_ETOOBIG;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return SCHULZE_ECUDA;
+  unsigned char* base = nullptr;
+  if (int rc = static_scratch(device, &base)) return rc;
+  if (use_s16(bound, flags)) return run_closure_static<int16_t>(base, device, d, m, bound, p, status, stream);
+  return run_closure_static<int32_t>(base, device, d, m, bound, p, status, stream);
+}

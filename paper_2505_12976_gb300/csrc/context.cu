@@ -58,6 +58,7 @@ const char* schulze_strerror(int code) {
     case SCHULZE_EDATA: return "invalid data: ballot id out of range or repeated, or count out of range";
     case SCHULZE_ETIMEOUT: return "a bounded device wait gave up";
     case SCHULZE_ERANGE: return "workspace too small during stream capture (call schulze_reserve first)";
+    case SCHULZE_ETOOBIG: return "m above 1024, the limit of the allocation-free schulze_strongest_paths_static";
     default: return "unknown status";
   }
 }

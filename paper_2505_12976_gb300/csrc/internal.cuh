@@ -60,7 +60,7 @@ namespace schulze {
 // is capturing (then SCHULZE_ERANGE).
 int ensure_workspace(schulze_ctx* ctx, size_t bytes, cudaStream_t stream);
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Carves aligned sub-buffers out of the workspace.
 struct Carver {
