@@ -34,6 +34,8 @@ WORKLOADS = {
     "large_topk": dict(desc="m=4096, n=20000, top-50 Mallows phi=0.9, random reference order"),
     "small_mallows": dict(desc="m=64, n=1000, full Mallows phi=0.8, identity reference order"),
     "huge_pl": dict(desc="m=16384, n=200000, top-20 Plackett-Luce Zipf(1.1), int32 closure"),
+    "batch_mixed": dict(desc="4096 elections, m~U[8,512], n~U[50,5000], full rankings, half Mallows "
+                             "(phi~U[0.5,1]) half impartial culture, one persistent launch"),
 }
 
 
@@ -63,7 +65,118 @@ def cpu_sample_election(name: str):
     if name == "huge_pl":
         return (W.huge_pl(seed=W.SEED_BASE + 78, n=20000, m=1536),
                 "one m=1536, n=20000 top-20 Plackett-Luce Zipf(1.1) election")
+    if name == "batch_mixed":
+        return W.batch_mixed(E=48, seed=W.SEED_BASE + 79), "48 elections drawn like the 4096-election batch"
     raise SystemExit(name)
+
+
+def time_oracle_batch(b, nthreads: int):
+    """Wall time of the oracle's whole path over every election of a batch."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for e in range(b.E):
+        oracle.schulze(b.election(e).ranks, int(b.m[e]), nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def run_batch(args, world, rank, local):
+    """Batched elections: one step = one persistent launch over the whole batch
+    (inputs of 10.8 GB, far larger than L2). Also times one launch sequence
+    per election (schulze_run) on a sample for comparison."""
+    import torch
+    import torch.distributed as dist
+    import paper_2505_12976_gb300 as S
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    E = args.batch_size
+    bw = W.batch_mixed(E=E, seed=W.SEED_BASE + 3 + 1000 * rank)
+    ctx = S.context(local)
+    plan = S.SchulzeBatch(bw.n, bw.m, bw.k, ctx=ctx)
+    ranks = torch.from_numpy(bw.ranks).to(dev)
+    vec = lambda: torch.empty(plan.vec_elems, dtype=torch.int32, device=dev)
+    winners, order, beaten = vec(), vec(), vec()
+    tile, ordp = plan.autotune(ranks, os.path.join(tempfile.gettempdir(), "schulze_batch_autotune.txt"))
+    step = lambda: plan.run(ranks, winners=winners, order=order, beaten_by=beaten)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = ctx.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clock_info = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cubes = float(np.sum(bw.m.astype(np.float64) ** 3))
+    value = world * cubes / (ms * 1e-3)
+    eps = world * E / (ms * 1e-3)
+    # one launch sequence per election on a sample of the same batch
+    sample = list(range(0, E, max(1, E // 256)))[:256]
+    singles = [(torch.from_numpy(bw.election(e).ranks).to(dev), int(bw.m[e])) for e in sample]
+    for r, m in singles[:8]:
+        S.schulze_run(r, m, ctx=ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, m in singles:
+        S.schulze_run(r, m, ctx=ctx)
+    torch.cuda.synchronize()
+    single_eps = len(singles) / (time.perf_counter() - t0)
+    # end to end: pinned host ballots in, winners and order out, every step
+    ranks_h = torch.from_numpy(bw.ranks).pin_memory()
+    win_h = torch.empty(plan.vec_elems, dtype=torch.int32).pin_memory()
+    ord_h = torch.empty(plan.vec_elems, dtype=torch.int32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ranks.copy_(ranks_h, non_blocking=True)
+        step()
+        win_h.copy_(winners, non_blocking=True)
+        ord_h.copy_(order, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_sec = (time.perf_counter() - t0) / e2e_steps
+    status = ctx.status()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, sample_desc = cpu_sample_election("batch_mixed")
+        threads = os.cpu_count() or 1
+        sec = time_oracle_batch(cb, threads)
+        cpu = {"value": float(np.sum(cb.m.astype(np.float64) ** 3)) / sec, "unit": UNIT, "cores": threads,
+               "kind": "oracle", "sample": sample_desc + f" ({cb.E / sec:.1f} elections/s on the host)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
+                "config": {"workload": "batch_mixed", "detail": WORKLOADS["batch_mixed"]["desc"], "elections": E,
+                           "ballot_bytes": int(bw.ranks.nbytes), "schedule": {"tile_policy": tile,
+                                                                             "order_policy": ordp},
+                           "l2": "inputs (ballots) larger than L2"},
+                "elections_per_sec": eps, "one_launch_per_election_elections_per_sec": single_eps,
+                "batch_speedup_vs_one_launch_per_election": eps / world / single_eps,
+                "roofline": None, "cpu_baseline": cpu,
+                "e2e": {"value": world * cubes / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(bw.ranks.nbytes),
+                        "d2h_bytes_per_step": 2 * int(plan.vec_elems) * 4},
+                "gpu_launches": int(launches), "device_status": status, "clocks": clock_info}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 def time_oracle(e, nthreads: int):
@@ -139,13 +252,14 @@ def run_reference(args, world, rank):
         return 0
     e, sample = cpu_sample_election(args.workload)
     threads = os.cpu_count() or 1
+    batch = hasattr(e, "election")
     times = []
     for i in range(args.warmup + args.steps):
-        t = time_oracle(e, threads)
+        t = time_oracle_batch(e, threads) if batch else time_oracle(e, threads)
         if i >= args.warmup:
             times.append(t)
     sec = sum(times) / len(times)
-    value = float(e.m) ** 3 / sec
+    value = (float(np.sum(e.m.astype(np.float64) ** 3)) if batch else float(e.m) ** 3) / sec
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -168,6 +282,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--m", type=int, default=None, help="override the workload's candidate count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's ballot count")
+    ap.add_argument("--batch-size", type=int, default=4096, help="elections of the batch_mixed workload")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -186,6 +301,8 @@ def main():
     __graft_entry__.build()
     import paper_2505_12976_gb300 as S
 
+    if args.workload == "batch_mixed":
+        return run_batch(args, world, rank, local)
     e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)

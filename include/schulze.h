@@ -175,6 +175,52 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
 int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
                      int32_t* winners_host, int32_t* order_host, uint32_t flags, schulze_stream_t stream);
 
+/*
+ * Batched elections: E independent elections (each 1 <= m <= 1024) run in
+ * one persistent launch, one election per CTA at a time, longest first.
+ * Every election goes through the same path as schulze_run (Sect. 2.1:
+ * tally, winning-votes weights, widest paths, winners, ranking).
+ *
+ * Layout: the elections are packed back to back in the caller's order.
+ * Ballots of election e start at element ranks_off[e] = sum_{f<e} n_f k_f of
+ * `ranks`; its d and p start at mat_off[e] = sum_{f<e} m_f^2 (row-major,
+ * leading dimension m_e); its winners, order and beaten_by at vec_off[e] =
+ * sum_{f<e} m_f. schulze_batch_layout reports these offsets and the totals.
+ */
+typedef struct schulze_batch schulze_batch;
+
+/* Plan a batch from HOST arrays n[E], m[E], k[E]: computes the layout and the
+ * job order, uploads the job table and reserves per-CTA scratch (allocates;
+ * call before any stream capture). */
+int schulze_batch_create(schulze_ctx* ctx, int32_t E, const int32_t* n, const int32_t* m, const int32_t* k,
+                         schulze_batch** out);
+
+/* Free the plan (waits for the device). */
+int schulze_batch_destroy(schulze_batch* b);
+
+/* Totals (elements) and per-election offsets (host arrays of E, or NULL). */
+int schulze_batch_layout(const schulze_batch* b, int64_t* ranks_elems, int64_t* mat_elems, int64_t* vec_elems,
+                         int64_t* ranks_off, int64_t* mat_off, int64_t* vec_off);
+
+/* Run every election of the plan. ranks: device ballots in the plan's
+ * layout. d, p, winners, order, beaten_by: device outputs in the plan's
+ * layout, each may be NULL (not written). Allocates nothing, so a run can be
+ * captured in a CUDA graph and replayed. Bad ballots are reported as
+ * SCHULZE_EDATA in the context's status word. */
+int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
+                      int32_t* order, int32_t* beaten_by, schulze_stream_t stream);
+
+/* Schedule knobs: tile_policy for the tally tile (0: smallest of 32/64/128
+ * that covers m, 1: at least 64, 2: always 128); order_policy (0: longest
+ * election first, 1: the caller's order). Synchronous. */
+int schulze_batch_set_schedule(schulze_batch* b, int32_t tile_policy, int32_t order_policy);
+
+/* Autotuner: times every schedule on this batch (two runs each on `stream`),
+ * keeps the fastest and reports it. With cache_path, a previous result for
+ * the same batch signature and GPU is reused, and a new one appended. */
+int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tile,
+                           int32_t* best_order, schulze_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,12 @@ SIGNATURES = [
     ("schulze_run", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
     ("schulze_run_host", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _u32, _vp]),
     ("schulze_strongest_paths_static", _c.c_int, [_vp, _i32, _i64, _vp, _u32, _vp, _vp]),
+    ("schulze_batch_create", _c.c_int, [_vp, _i32, _vp, _vp, _vp, _c.POINTER(_vp)]),
+    ("schulze_batch_destroy", _c.c_int, [_vp]),
+    ("schulze_batch_layout", _c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64), _vp, _vp, _vp]),
+    ("schulze_batch_run", _c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("schulze_batch_set_schedule", _c.c_int, [_vp, _i32, _i32]),
+    ("schulze_batch_autotune", _c.c_int, [_vp, _vp, _c.c_char_p, _c.POINTER(_i32), _c.POINTER(_i32), _vp]),
     # include/schulze_profile.h
     ("schulze_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("schulze_profile_read", _c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
@@ -265,6 +271,67 @@ def schulze_strongest_paths_static(d: torch.Tensor, bound: int, p: torch.Tensor 
         _check(load().schulze_strongest_paths_static(_ptr(d), m, int(bound), _ptr(p), flags, _ptr(status),
                                                      _stream(stream, d.device)), "schulze_strongest_paths_static")
     return p
+
+
+class SchulzeBatch:
+    """A planned batch of independent elections (schulze_batch_create).
+
+    n, m, k: host int arrays of length E. Ballots and outputs are packed back
+    to back in this order; `ranks_off`, `mat_off`, `vec_off` give each
+    election's element offsets and `ranks_elems`, `mat_elems`, `vec_elems`
+    the totals."""
+
+    def __init__(self, n, m, k, ctx: Context | None = None):
+        lib = load()
+        self.ctx = ctx or context()
+        n, m, k = (np.ascontiguousarray(x, dtype=np.int32) for x in (n, m, k))
+        self.E = int(n.shape[0])
+        h = _vp()
+        _check(lib.schulze_batch_create(self.ctx.handle, self.E, _vp(n.ctypes.data), _vp(m.ctypes.data),
+                                        _vp(k.ctypes.data), ctypes.byref(h)), "schulze_batch_create")
+        self.handle, self._lib = h, lib
+        self.n, self.m, self.k = n, m, k
+        tr, tm, tv = _i64(0), _i64(0), _i64(0)
+        self.ranks_off = np.zeros(self.E, np.int64)
+        self.mat_off = np.zeros(self.E, np.int64)
+        self.vec_off = np.zeros(self.E, np.int64)
+        _check(lib.schulze_batch_layout(h, ctypes.byref(tr), ctypes.byref(tm), ctypes.byref(tv),
+                                        _vp(self.ranks_off.ctypes.data), _vp(self.mat_off.ctypes.data),
+                                        _vp(self.vec_off.ctypes.data)), "schulze_batch_layout")
+        self.ranks_elems, self.mat_elems, self.vec_elems = tr.value, tm.value, tv.value
+
+    def run(self, ranks: torch.Tensor, d=None, p=None, winners=None, order=None, beaten_by=None, stream=None):
+        """Run every election; outputs are optional flat int32 device tensors."""
+        ranks = _dev_i32(ranks, "ranks")
+        if ranks.numel() < self.ranks_elems:
+            raise ValueError("ranks is smaller than the plan's ballots")
+        for t, size, name in ((d, self.mat_elems, "d"), (p, self.mat_elems, "p"), (winners, self.vec_elems, "winners"),
+                              (order, self.vec_elems, "order"), (beaten_by, self.vec_elems, "beaten_by")):
+            if t is not None and (_dev_i32(t, name).numel() < size):
+                raise ValueError(f"{name} is smaller than the plan's layout")
+        _check(self._lib.schulze_batch_run(self.handle, _ptr(ranks), _ptr(d), _ptr(p), _ptr(winners), _ptr(order),
+                                           _ptr(beaten_by), _stream(stream, self.ctx.device)), "schulze_batch_run")
+
+    def set_schedule(self, tile_policy: int, order_policy: int):
+        _check(self._lib.schulze_batch_set_schedule(self.handle, tile_policy, order_policy),
+               "schulze_batch_set_schedule")
+
+    def autotune(self, ranks: torch.Tensor, cache_path: str | None = None, stream=None):
+        """Pick the fastest schedule for this batch; returns (tile_policy, order_policy)."""
+        ranks = _dev_i32(ranks, "ranks")
+        bt, bo = _i32(-1), _i32(-1)
+        _check(self._lib.schulze_batch_autotune(self.handle, _ptr(ranks),
+                                                cache_path.encode() if cache_path else None, ctypes.byref(bt),
+                                                ctypes.byref(bo), _stream(stream, self.ctx.device)),
+               "schulze_batch_autotune")
+        return bt.value, bo.value
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self._lib.schulze_batch_destroy(self.handle)
+        except Exception:
+            pass
 
 
 def probe_minmax(kind: int, blocks: int, iters: int, device: int = 0):

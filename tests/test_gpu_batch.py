@@ -1,0 +1,152 @@
+"""Batched elections (one persistent launch) against the oracle, election by
+election, bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+S = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    global S
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_12976_gb300 as mod
+    S = mod
+    yield mod
+    assert S.context().status() == S.OK
+
+
+def _mixed_elections(seed=3):
+    """Uneven elections: tiny to m = 300, n from 0 to 4000, full and top-k,
+    Mallows and impartial culture, plus degenerate ones."""
+    rs = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    sizes = [1, 2, 3, 8, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 257, 300]
+    for t, m in enumerate(sizes):
+        n = int(rs.integers(1, 4000)) if t % 5 else int(rs.integers(1, 60))
+        k = [m, max(0, m - 1), max(1, m // 3), 1][t % 4]
+        if t % 2:
+            r = W.impartial(100 + t, n, m, k)
+        else:
+            r = W.mallows(100 + t, n, m, k, float(rs.uniform(0.5, 1.0)), W.permutation(t, m))
+        out.append((r, m))
+    out.append((np.zeros((0, 5), np.int32), 5))  # no ballots
+    out.append((np.zeros((7, 0), np.int32), 4))  # empty ballots
+    out.append((np.tile(np.array([4, 1, 6], np.int32), (9, 1)), 8))  # all voters identical
+    return out
+
+
+def _pack(elections):
+    n = np.array([r.shape[0] for r, _ in elections], np.int32)
+    k = np.array([r.shape[1] for r, _ in elections], np.int32)
+    m = np.array([mm for _, mm in elections], np.int32)
+    flat = np.concatenate([r.reshape(-1) for r, _ in elections]).astype(np.int32) if len(elections) else \
+        np.zeros(0, np.int32)
+    return n, m, k, flat
+
+
+def _check(b, elections, outs):
+    d, p, win, order, bb = (t.cpu().numpy() if t is not None else None for t in outs)
+    for e, (r, m) in enumerate(elections):
+        mo, vo = int(b.mat_off[e]), int(b.vec_off[e])
+        dw, pw, ww, ow, bw = oracle.schulze(r, m)
+        if d is not None:
+            np.testing.assert_array_equal(d[mo:mo + m * m].reshape(m, m), dw, err_msg=f"d of election {e}")
+        if p is not None:
+            np.testing.assert_array_equal(p[mo:mo + m * m].reshape(m, m), pw, err_msg=f"p of election {e}")
+        np.testing.assert_array_equal(win[vo:vo + m], ww, err_msg=f"winners of election {e}")
+        np.testing.assert_array_equal(order[vo:vo + m], ow, err_msg=f"order of election {e}")
+        np.testing.assert_array_equal(bb[vo:vo + m], bw, err_msg=f"beaten_by of election {e}")
+
+
+def _outputs(b, with_matrices=True):
+    z = lambda size: torch.full((max(1, size),), -3, dtype=torch.int32, device="cuda")
+    return (z(b.mat_elems) if with_matrices else None, z(b.mat_elems) if with_matrices else None,
+            z(b.vec_elems), z(b.vec_elems), z(b.vec_elems))
+
+
+@pytest.mark.parametrize("tile_policy,order_policy", [(0, 0), (1, 0), (2, 1)])
+def test_batch_matches_oracle(tile_policy, order_policy):
+    els = _mixed_elections()
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k)
+    b.set_schedule(tile_policy, order_policy)
+    ranks = torch.from_numpy(flat).cuda() if flat.size else torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = _outputs(b)
+    b.run(ranks, *outs)
+    torch.cuda.synchronize()
+    _check(b, els, outs)
+
+
+def test_batch_without_matrices_and_int32_counts():
+    """More than 32767 ballots in one election selects the int32 closure; d
+    and p are not requested."""
+    els = [(W.impartial(5, 40000, 20, 20), 20), (W.mallows(6, 300, 90, 30, 0.8, W.permutation(6, 90)), 90)]
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k)
+    outs = _outputs(b, with_matrices=False)
+    b.run(torch.from_numpy(flat).cuda(), *outs)
+    torch.cuda.synchronize()
+    _check(b, els, outs)
+
+
+def test_batch_workload_sample_and_graph_replay():
+    """A sample of the mixed workload (m ~ U[8,512], n ~ U[50,5000]); the run is
+    captured in a CUDA graph and replayed on new ballots of the same shape."""
+    bw = W.batch_mixed(E=24, seed=77)
+    els = [(bw.election(e).ranks, int(bw.m[e])) for e in range(bw.E)]
+    b = S.SchulzeBatch(bw.n, bw.m, bw.k)
+    ranks = torch.from_numpy(bw.ranks).cuda()
+    outs = _outputs(b)
+    b.run(ranks, *outs)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run(ranks, *outs)
+    for t in outs:
+        t.fill_(-5)
+    g.replay()
+    torch.cuda.synchronize()
+    _check(b, els, outs)
+    # new ballots of the same shapes, copied into the captured buffer: replay again
+    for e in range(bw.E):
+        r = bw.election(e).ranks
+        r[:] = W.impartial(900 + e, r.shape[0], int(bw.m[e]), r.shape[1])
+    ranks.copy_(torch.from_numpy(bw.ranks))
+    g.replay()
+    torch.cuda.synchronize()
+    _check(b, [(bw.election(e).ranks, int(bw.m[e])) for e in range(bw.E)], outs)
+
+
+def test_batch_autotune_keeps_results_exact(tmp_path):
+    bw = W.batch_mixed(E=12, seed=5, m_range=(8, 200), n_range=(50, 800))
+    b = S.SchulzeBatch(bw.n, bw.m, bw.k)
+    ranks = torch.from_numpy(bw.ranks).cuda()
+    cache = str(tmp_path / "autotune.txt")
+    t1, o1 = b.autotune(ranks, cache)
+    assert 0 <= t1 <= 2 and 0 <= o1 <= 1
+    t2, o2 = b.autotune(ranks, cache)  # second call reads the cache
+    assert (t1, o1) == (t2, o2)
+    outs = _outputs(b)
+    b.run(ranks, *outs)
+    torch.cuda.synchronize()
+    _check(b, [(bw.election(e).ranks, int(bw.m[e])) for e in range(bw.E)], outs)
+
+
+def test_batch_reports_bad_ballots():
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    els = [(np.array([[0, 1, 2], [2, 2, 0]], np.int32), 3)]
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k)
+    b.run(torch.from_numpy(flat).cuda(), *_outputs(b))
+    assert ctx.status() == S.EDATA

@@ -62,7 +62,9 @@ def _load():
                                         ctypes.c_double, i32p, i32p, ctypes.c_int]
             lib.gen_plackett_luce_zipf.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_double, i32p, i32p, ctypes.c_int]
-            for f in (lib.gen_impartial, lib.gen_mallows, lib.gen_plackett_luce_zipf):
+            lib.gen_batch.argtypes = [ctypes.c_uint64, ctypes.c_int32, i32p, i32p, i32p, i32p,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32p, ctypes.c_int]
+            for f in (lib.gen_impartial, lib.gen_mallows, lib.gen_plackett_luce_zipf, lib.gen_batch):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -182,22 +184,18 @@ def batch_mixed(E: int = 4096, seed: int = SEED_BASE + 3, m_range=(8, 512), n_ra
     n = rs.integers(n_range[0], n_range[1] + 1, size=E).astype(np.int32)
     phi = rs.uniform(0.5, 1.0, size=E)
     k = m.copy()
+    kind = (np.arange(E) % 2).astype(np.int32)  # 0 Mallows, 1 impartial culture
     sizes = n.astype(np.int64) * k.astype(np.int64)
     off = np.zeros(E, dtype=np.int64)
     off[1:] = np.cumsum(sizes)[:-1]
     ranks = np.empty(int(sizes.sum()), dtype=np.int32)
-    kind = []
-    for e in range(E):
-        view = ranks[off[e]:off[e] + sizes[e]].reshape(int(n[e]), int(k[e]))
-        es = seed * 1000003 + e
-        if e % 2 == 0:
-            sigma0 = permutation(es ^ 0x33, int(m[e]))
-            mallows(es, int(n[e]), int(m[e]), int(k[e]), float(phi[e]), sigma0, out=view, nthreads=nthreads)
-            kind.append(f"mallows phi={phi[e]:.3f}")
-        else:
-            impartial(es, int(n[e]), int(m[e]), int(k[e]), out=view, nthreads=nthreads)
-            kind.append("ic")
-    return Batch(ranks, n, m, k, off, kind)
+    rc = _load().gen_batch(seed, E, _ptr(kind), _ptr(n), _ptr(m), _ptr(k),
+                           phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(ranks), _threads(nthreads))
+    if rc:
+        raise ValueError("gen_batch: bad arguments")
+    labels = [f"mallows phi={phi[e]:.3f}" if kind[e] == 0 else "ic" for e in range(E)]
+    return Batch(ranks, n, m, k, off, labels)
 
 
 def learned_elections(E: int, seed: int, m_range, n_range, k_range, phi_range, nthreads=None) -> Batch:

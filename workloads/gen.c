@@ -363,3 +363,71 @@ int gen_plackett_luce_zipf(uint64_t seed, int64_t n, int32_t m, int32_t k, doubl
   free(w), free(prob), free(alias), free(small), free(large);
   return 0;
 }
+
+/* ------------------------------------------------------ many elections */
+
+typedef struct {
+  uint64_t seed;
+  int32_t E;
+  const int32_t *kind, *n, *m, *k;
+  const double* phi;
+  const int64_t* off;
+  int32_t* out;
+  volatile int32_t next;
+  pthread_mutex_t lock;
+} batch_ctx;
+
+static void* batch_worker(void* a) {
+  batch_ctx* b = (batch_ctx*)a;
+  int32_t* sigma = NULL;
+  int32_t cap = 0;
+  for (;;) {
+    pthread_mutex_lock(&b->lock);
+    int32_t e = b->next++;
+    pthread_mutex_unlock(&b->lock);
+    if (e >= b->E) break;
+    uint64_t es = b->seed * 1000003ULL + (uint64_t)e;
+    int32_t* dst = b->out + b->off[e];
+    if (b->kind[e] == 0) {
+      if (b->m[e] > cap) {
+        free(sigma);
+        cap = b->m[e];
+        sigma = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+      }
+      gen_permutation(es ^ 0x33, b->m[e], sigma);
+      gen_mallows(es, b->n[e], b->m[e], b->k[e], b->phi[e], sigma, dst, 1);
+    } else {
+      gen_impartial(es, b->n[e], b->m[e], b->k[e], dst, 1);
+    }
+  }
+  free(sigma);
+  return NULL;
+}
+
+/* E elections in one buffer: election e's ballots at out + off[e]; kind 0 is
+ * Mallows(phi[e]) around a seeded random reference, kind 1 impartial
+ * culture. Same ballots as generating each election on its own with seed
+ * seed * 1000003 + e; the elections are spread over threads. */
+int gen_batch(uint64_t seed, int32_t E, const int32_t* kind, const int32_t* n, const int32_t* m, const int32_t* k,
+              const double* phi, const int64_t* off, int32_t* out, int nthreads) {
+  if (E < 0) return -1;
+  for (int32_t e = 0; e < E; ++e)
+    if (n[e] < 0 || m[e] < 1 || k[e] < 0 || k[e] > m[e] || (kind[e] == 0 && (!(phi[e] > 0.0) || phi[e] > 1.0)))
+      return -1;
+  batch_ctx b;
+  b.seed = seed, b.E = E, b.kind = kind, b.n = n, b.m = m, b.k = k, b.phi = phi, b.off = off, b.out = out;
+  b.next = 0;
+  pthread_mutex_init(&b.lock, NULL);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  pthread_t th[256];
+  int started = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    if (pthread_create(&th[t], NULL, batch_worker, &b) != 0) break;
+    ++started;
+  }
+  if (started == 0) batch_worker(&b);
+  for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+  pthread_mutex_destroy(&b.lock);
+  return 0;
+}
