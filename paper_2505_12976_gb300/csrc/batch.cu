@@ -76,7 +76,7 @@ union BatchSmem {
 // 16-bit lanes and are added into d every kFlushVoters ballots.
 template <int TILE>
 __device__ void tally_tile(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, int32_t I0,
-                           int32_t J0, BatchSmem& sm) {
+                           int32_t J0, BatchSmem& sm, int32_t* status) {
   constexpr int TT = (TILE / 8) * (TILE / 4);
   constexpr int G = kBT / TT;
   constexpr int VC = kStage / G;
@@ -97,11 +97,34 @@ __device__ void tally_tile(const Job& jb, const int32_t* __restrict__ ranks, int
     }
     __syncthreads();
     const int nv = int(n - v0 < kStage ? n - v0 : int64_t(kStage));
-    for (int t = tid; t < nv * k; t += kBT) {
-      const int vv = t / k, q = t % k;
-      const int32_t c = ranks[(v0 + vv) * k + q];
-      if (c >= I0 && c < I0 + TILE) sm.stage.sI[vv][c - I0] = uint32_t(q) | (uint32_t(q) << 16);
-      if (c >= J0 && c < J0 + TILE) sm.stage.sJ[vv][c - J0] = uint16_t(q);
+    // the staged ballots are one contiguous run of nv * k ids; sixteen loads
+    // per thread are issued before any of them is used (ballots stream from
+    // DRAM, so one dependent load per step would leave the SM waiting)
+    const int total = nv * k;
+    const int32_t* chunk = ranks + v0 * k;
+    for (int t0 = tid; t0 < total; t0 += kBT * 16) {
+      int32_t cv[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int t = t0 + u * kBT;
+        cv[u] = t < total ? __ldcs(chunk + t) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int t = t0 + u * kBT;
+        const int32_t c = cv[u];
+        if (t >= total) break;
+        const int vv = t / k, q = t % k;
+        // ballot checks ride along: an id out of range, or an id whose row
+        // slot was already taken by the same ballot (every id falls in some
+        // row tile), marks the data invalid
+        if (c < 0 || c >= m) set_status(status, SCHULZE_EDATA);
+        if (c >= I0 && c < I0 + TILE) {
+          const uint32_t old = atomicExch(&sm.stage.sI[vv][c - I0], uint32_t(q) | (uint32_t(q) << 16));
+          if (old != (unl | (unl << 16))) set_status(status, SCHULZE_EDATA);
+        }
+        if (c >= J0 && c < J0 + TILE) sm.stage.sJ[vv][c - J0] = uint16_t(q);
+      }
     }
     __syncthreads();
     for (int u = 0; u < VC; ++u) {
@@ -160,10 +183,11 @@ __device__ void tally_tile(const Job& jb, const int32_t* __restrict__ ranks, int
 }
 
 template <int TILE>
-__device__ void tally_all(const Job& jb, const int32_t* ranks, int32_t* dm, bool full, BatchSmem& sm) {
+__device__ void tally_all(const Job& jb, const int32_t* ranks, int32_t* dm, bool full, BatchSmem& sm,
+                          int32_t* status) {
   const int32_t nbt = (jb.m + TILE - 1) / TILE;
   for (int32_t bi = 0; bi < nbt; ++bi)
-    for (int32_t bj = full ? bi : 0; bj < nbt; ++bj) tally_tile<TILE>(jb, ranks, dm, bi * TILE, bj * TILE, sm);
+    for (int32_t bj = full ? bi : 0; bj < nbt; ++bj) tally_tile<TILE>(jb, ranks, dm, bi * TILE, bj * TILE, sm, status);
   __syncthreads();
   if (full && nbt > 1) {  // strict full orders: d[j][i] = n - d[i][j] below the diagonal tiles
     const int32_t m = jb.m;
@@ -176,34 +200,6 @@ __device__ void tally_all(const Job& jb, const int32_t* ranks, int32_t* dm, bool
 }
 
 // ----------------------------------------------------------- stages
-
-// Ballot checks: ids in range and distinct (one warp per ballot, bitmap per warp).
-__device__ void validate(const Job& jb, const int32_t* __restrict__ ranks, uint32_t (*bitmap)[kBatchMaxM / 32],
-                         int32_t* status) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* bm = bitmap[w];
-  for (int t = lane; t < kBatchMaxM / 32; t += 32) bm[t] = 0u;
-  __syncwarp();
-  for (int64_t v = w; v < jb.n; v += kBT / 32) {
-    const int32_t* row = ranks + v * jb.k;
-    for (int32_t q = lane; q < jb.k; q += 32) {
-      const int32_t c = row[q];
-      if (c < 0 || c >= jb.m) {
-        set_status(status, SCHULZE_EDATA);
-        continue;
-      }
-      const uint32_t bit = 1u << (c & 31);
-      if (atomicOr(&bm[c >> 5], bit) & bit) set_status(status, SCHULZE_EDATA);
-    }
-    __syncwarp();
-    for (int32_t q = lane; q < jb.k; q += 32) {
-      const int32_t c = row[q];
-      if (c >= 0 && c < jb.m) bm[c >> 5] = 0u;
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-}
 
 template <typename E>
 __device__ void pack(const int32_t* __restrict__ dm, int32_t m, int32_t mp, E* __restrict__ W) {
@@ -255,10 +251,19 @@ __device__ void extract(const Job& jb, const E* __restrict__ W, int32_t mp, cons
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int32_t i = w; i < m; i += kBT / 32) {
     int32_t beaten_i = 0;
-    for (int32_t j = i + 1 + lane; j < m; j += 32) {
-      const int32_t wij = int32_t(W[int64_t(i) * mp + j]), wji = int32_t(W[int64_t(j) * mp + i]);
-      if (wji > wij) ++beaten_i;
-      else if (wij > wji) atomicAdd(&bb[j], 1);
+    for (int32_t j0 = i + 1 + lane; j0 < m; j0 += 32 * 4) {
+      int32_t wij[4], wji[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {  // loads first: the transposed ones are strided
+        const int32_t j = j0 + 32 * u;
+        wij[u] = j < m ? int32_t(W[int64_t(i) * mp + j]) : 0;
+        wji[u] = j < m ? int32_t(W[int64_t(j) * mp + i]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (wji[u] > wij[u]) ++beaten_i;
+        else if (wij[u] > wji[u]) atomicAdd(&bb[j0 + 32 * u], 1);
+      }
     }
     for (int o = 16; o; o >>= 1) beaten_i += __shfl_xor_sync(0xFFFFFFFFu, beaten_i, o);
     if (lane == 0 && beaten_i) atomicAdd(&bb[i], beaten_i);
@@ -291,7 +296,6 @@ template <typename E>
 __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BatchSmem& sm = *reinterpret_cast<BatchSmem*>(smem_raw);
-  __shared__ uint32_t bitmap[kBT / 32][kBatchMaxM / 32];
   __shared__ int32_t s_job;
   unsigned char* slot = a.scratch + size_t(blockIdx.x) * a.slot_bytes;
   E* W = reinterpret_cast<E*>(slot);
@@ -305,7 +309,6 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
     const Job jb = a.jobs[ji];
     const int32_t* ranks = a.ranks + jb.ranks_off;
     int32_t* dm = a.d ? a.d + jb.mat_off : dslot;
-    if (jb.n > 0 && jb.k > 0) validate(jb, ranks, bitmap, a.status);
     const int32_t m = jb.m;
     if (jb.n == 0 || jb.k == 0) {
       for (int64_t t = threadIdx.x; t < int64_t(m) * m; t += kBT) dm[t] = 0;
@@ -314,11 +317,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
       const bool full = jb.k >= m - 1;
       const int tile = a.tile_policy == 2 ? 128 : (m <= 32 && a.tile_policy == 0 ? 32 : (m <= 64 ? 64 : 128));
       if (tile == 32)
-        tally_all<32>(jb, ranks, dm, full, sm);
+        tally_all<32>(jb, ranks, dm, full, sm, a.status);
       else if (tile == 64)
-        tally_all<64>(jb, ranks, dm, full, sm);
+        tally_all<64>(jb, ranks, dm, full, sm, a.status);
       else
-        tally_all<128>(jb, ranks, dm, full, sm);
+        tally_all<128>(jb, ranks, dm, full, sm, a.status);
     }
     const int32_t mp = int32_t(align_up(size_t(m), tiles::kB));
     pack<E>(dm, m, mp, W);
@@ -517,8 +520,10 @@ int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* c
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, b->ctx->device);
   char key[256];
-  snprintf(key, sizeof(key), "%s|E=%d|R=%lld|M=%lld|mmax=%d|s16=%d", prop.name, b->E, (long long)b->ranks_elems,
-           (long long)b->mat_elems, b->m_max, b->s16 ? 1 : 0);
+  snprintf(key, sizeof(key), "%.100s|E=%d|R=%lld|M=%lld|mmax=%d|s16=%d", prop.name, b->E,
+           (long long)b->ranks_elems, (long long)b->mat_elems, b->m_max, b->s16 ? 1 : 0);
+  for (char* c = key; *c; ++c)
+    if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';  // the cache line format splits on blanks
   int32_t bt = -1, bo = -1;
   if (cache_path) {  // line format: <key> <tile_policy> <order_policy>
     if (FILE* f = fopen(cache_path, "r")) {
