@@ -164,7 +164,7 @@ def run_batch(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
                 "config": {"workload": "batch_mixed", "detail": WORKLOADS["batch_mixed"]["desc"], "elections": E,
-                           "ballot_bytes": int(bw.ranks.nbytes), "schedule": {"tile_policy": tile,
+                           "ballot_bytes": int(bw.ranks.nbytes), "schedule": {"tally_policy": tile,
                                                                              "order_policy": ordp},
                            "l2": "inputs (ballots) larger than L2"},
                 "elections_per_sec": eps, "one_launch_per_election_elections_per_sec": single_eps,

@@ -210,16 +210,71 @@ int schulze_batch_layout(const schulze_batch* b, int64_t* ranks_elems, int64_t* 
 int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
                       int32_t* order, int32_t* beaten_by, schulze_stream_t stream);
 
-/* Schedule knobs: tile_policy for the tally tile (0: smallest of 32/64/128
- * that covers m, 1: at least 64, 2: always 128); order_policy (0: longest
- * election first, 1: the caller's order). Synchronous. */
-int schulze_batch_set_schedule(schulze_batch* b, int32_t tile_policy, int32_t order_policy);
+/* Schedule knobs: tally_policy, the ballots staged per tally step (0:
+ * sixteen, 1: eight); order_policy (0: longest election first, 1: the
+ * caller's order). Synchronous. */
+int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t order_policy);
 
 /* Autotuner: times every schedule on this batch (two runs each on `stream`),
  * keeps the fastest and reports it. With cache_path, a previous result for
  * the same batch signature and GPU is reused, and a new one appended. */
-int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tile,
+int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tally,
                            int32_t* best_order, schulze_stream_t stream);
+
+/*
+ * Learned winner proposal with exact certification. The paper has no learned
+ * component: a small MLP (16 -> 64 -> 64 -> 1, ReLU, FP32) proposes likely
+ * winners, and each proposal is certified with the definitions of Sect. 2.1
+ * (c wins iff p(c, j) >= p(j, c) for every j) by single-source and
+ * single-sink widest paths; the full closure decides when no proposal
+ * certifies. The winner set never depends on the model.
+ *
+ * Parameters: 5313 floats, W1 [64][16] at 0, b1 [64] at 1024, W2 [64][64] at
+ * 1088, b2 [64] at 5184, W3 [64] at 5248, b3 at 5312 (device memory).
+ */
+
+/* 16 FP32 features per candidate from d and the ballot count n (feat is
+ * [m, 16] row-major, device): Copeland wins / losses / ties over m-1;
+ * row and column sums of d over n(m-1); largest outgoing and incoming
+ * winning-votes edge over n; the loser filter of Sect. 4 (1 if the largest
+ * incoming edge is heavier); their difference; outgoing and incoming edge
+ * sums; smallest and largest margin; largest d[c][j]; the ranks of the row
+ * sum and of wins - losses among the candidates (0 = best, over m-1). */
+int schulze_features(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, float* feat, schulze_stream_t stream);
+
+/* score[c] = MLP(feat[c]) for N candidates (device arrays). */
+int schulze_mlp_forward(schulze_ctx* ctx, const float* params, const float* feat, int32_t N, float* score,
+                        schulze_stream_t stream);
+
+/* One training step on N candidates from nseg elections: election e owns
+ * candidates seg_off[e] .. seg_off[e+1]-1 (device int32 [nseg+1]); label[c]
+ * is 1 for a winner, else 0. Loss: listwise softmax cross-entropy with equal
+ * target mass on an election's winners, averaged over elections. Then one
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8, 1-based `step`) updates params
+ * and the moments adam_m, adam_v in place. loss (device float [1]) and grad
+ * (device float [5313]) may be NULL. Gradients are summed in a fixed order
+ * (deterministic). */
+int schulze_mlp_train_step(schulze_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t step,
+                           const float* feat, const int32_t* label, const int32_t* seg_off, int32_t nseg, int32_t N,
+                           float lr, float* loss, float* grad, schulze_stream_t stream);
+
+/* Certify proposals cand[0..ncand-1] (device int32, ncand <= 8) for the
+ * election with tally d: winners (device int32 [m]) receives the exact
+ * winner set when result[0] == 1 (device int32 [4]: [0] 1 if certified, 0 if
+ * the closure must decide; [1] index of the certified proposal or -1; [2]
+ * tied candidates checked; [3] widest-path relaxation rounds). Handles up to
+ * 2048 candidates with outgoing edges; beyond that result[0] is 0. */
+int schulze_certify(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const int32_t* cand, int32_t ncand,
+                    int32_t* winners, int32_t* result, schulze_stream_t stream);
+
+/* Winners of the election with tally d: features, proposals (the MLP with
+ * `params`, or the Copeland score wins - losses when params is NULL), the
+ * `top` best (<= 8) certified in order, the closure as fallback. Synchronous
+ * on `stream`. winners: device int32 [m]. stats (HOST int32 [4], may be
+ * NULL): [0] index of the proposal that certified (-1 if none), [1] 1 if the
+ * closure decided, [2] ties checked, [3] relaxation rounds. */
+int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const float* params, int32_t top,
+                         int32_t* winners, int32_t* stats, schulze_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,12 @@ SIGNATURES = [
     ("schulze_batch_run", _c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("schulze_batch_set_schedule", _c.c_int, [_vp, _i32, _i32]),
     ("schulze_batch_autotune", _c.c_int, [_vp, _vp, _c.c_char_p, _c.POINTER(_i32), _c.POINTER(_i32), _vp]),
+    ("schulze_features", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _vp]),
+    ("schulze_mlp_forward", _c.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    ("schulze_mlp_train_step", _c.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _c.c_float, _vp, _vp,
+                                          _vp]),
+    ("schulze_certify", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp]),
+    ("schulze_winners_fast", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp]),
     # include/schulze_profile.h
     ("schulze_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("schulze_profile_read", _c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
@@ -273,6 +279,92 @@ def schulze_strongest_paths_static(d: torch.Tensor, bound: int, p: torch.Tensor 
     return p
 
 
+NPARAM = 5313  # MLP parameters: W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64], b3
+
+
+def _dev_f32(t: torch.Tensor, name: str, numel=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements")
+    return t
+
+
+def schulze_features(d: torch.Tensor, n: int, feat: torch.Tensor | None = None, ctx: Context | None = None,
+                     stream=None) -> torch.Tensor:
+    """16 float32 features per candidate from the tally d (see include/schulze.h)."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    ctx = ctx or context(d.device)
+    feat = torch.empty((m, 16), dtype=torch.float32, device=d.device) if feat is None else _dev_f32(feat, "feat")
+    _check(load().schulze_features(ctx.handle, _ptr(d), m, int(n), _ptr(feat), _stream(stream, ctx.device)),
+           "schulze_features")
+    return feat
+
+
+def schulze_mlp_forward(params: torch.Tensor, feat: torch.Tensor, score: torch.Tensor | None = None,
+                        ctx: Context | None = None, stream=None) -> torch.Tensor:
+    params = _dev_f32(params, "params", NPARAM)
+    feat = _dev_f32(feat, "feat")
+    N = feat.shape[0]
+    ctx = ctx or context(feat.device)
+    score = torch.empty(N, dtype=torch.float32, device=feat.device) if score is None else _dev_f32(score, "score")
+    _check(load().schulze_mlp_forward(ctx.handle, _ptr(params), _ptr(feat), N, _ptr(score),
+                                      _stream(stream, ctx.device)), "schulze_mlp_forward")
+    return score
+
+
+def schulze_mlp_train_step(params, adam_m, adam_v, step: int, feat, label, seg_off, lr: float, loss=None, grad=None,
+                           ctx: Context | None = None, stream=None):
+    """One forward/backward/Adam step in place; returns (loss, grad) device tensors."""
+    params = _dev_f32(params, "params", NPARAM)
+    adam_m = _dev_f32(adam_m, "adam_m", NPARAM)
+    adam_v = _dev_f32(adam_v, "adam_v", NPARAM)
+    feat = _dev_f32(feat, "feat")
+    label = _dev_i32(label, "label")
+    seg_off = _dev_i32(seg_off, "seg_off")
+    N, nseg = feat.shape[0], seg_off.numel() - 1
+    ctx = ctx or context(feat.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device) if loss is None else _dev_f32(loss, "loss", 1)
+    grad = torch.empty(NPARAM, dtype=torch.float32, device=feat.device) if grad is None else \
+        _dev_f32(grad, "grad", NPARAM)
+    _check(load().schulze_mlp_train_step(ctx.handle, _ptr(params), _ptr(adam_m), _ptr(adam_v), int(step), _ptr(feat),
+                                         _ptr(label), _ptr(seg_off), nseg, N, float(lr), _ptr(loss), _ptr(grad),
+                                         _stream(stream, ctx.device)), "schulze_mlp_train_step")
+    return loss, grad
+
+
+def schulze_certify(d: torch.Tensor, n: int, cand: torch.Tensor, winners: torch.Tensor | None = None,
+                    ctx: Context | None = None, stream=None):
+    """(winners, result) for proposals cand (device int32); result[0] == 1 means exact."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    cand = _dev_i32(cand, "cand")
+    ctx = ctx or context(d.device)
+    winners = _out(winners, (m,), d.device, "winners")
+    result = torch.empty(4, dtype=torch.int32, device=d.device)
+    _check(load().schulze_certify(ctx.handle, _ptr(d), m, int(n), _ptr(cand), cand.numel(), _ptr(winners),
+                                  _ptr(result), _stream(stream, ctx.device)), "schulze_certify")
+    return winners, result
+
+
+def schulze_winners_fast(d: torch.Tensor, n: int, params: torch.Tensor | None = None, top: int = 4,
+                         winners: torch.Tensor | None = None, ctx: Context | None = None, stream=None):
+    """Exact winners via certified proposals (MLP, or Copeland when params is
+    None); returns (winners, stats) with stats = [certified proposal index or
+    -1, closure fallback 0/1, ties checked, relaxation rounds]."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    if params is not None:
+        params = _dev_f32(params, "params", NPARAM)
+    ctx = ctx or context(d.device)
+    winners = _out(winners, (m,), d.device, "winners")
+    stats = (_i32 * 4)()
+    _check(load().schulze_winners_fast(ctx.handle, _ptr(d), m, int(n), _ptr(params), int(top), _ptr(winners), stats,
+                                       _stream(stream, ctx.device)), "schulze_winners_fast")
+    return winners, list(stats)
+
+
 class SchulzeBatch:
     """A planned batch of independent elections (schulze_batch_create).
 
@@ -312,12 +404,12 @@ class SchulzeBatch:
         _check(self._lib.schulze_batch_run(self.handle, _ptr(ranks), _ptr(d), _ptr(p), _ptr(winners), _ptr(order),
                                            _ptr(beaten_by), _stream(stream, self.ctx.device)), "schulze_batch_run")
 
-    def set_schedule(self, tile_policy: int, order_policy: int):
-        _check(self._lib.schulze_batch_set_schedule(self.handle, tile_policy, order_policy),
+    def set_schedule(self, tally_policy: int, order_policy: int):
+        _check(self._lib.schulze_batch_set_schedule(self.handle, tally_policy, order_policy),
                "schulze_batch_set_schedule")
 
     def autotune(self, ranks: torch.Tensor, cache_path: str | None = None, stream=None):
-        """Pick the fastest schedule for this batch; returns (tile_policy, order_policy)."""
+        """Pick the fastest schedule for this batch; returns (tally_policy, order_policy)."""
         ranks = _dev_i32(ranks, "ranks")
         bt, bo = _i32(-1), _i32(-1)
         _check(self._lib.schulze_batch_autotune(self.handle, _ptr(ranks),

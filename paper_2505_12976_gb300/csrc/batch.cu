@@ -26,7 +26,6 @@ namespace {
 constexpr int kBT = 512;                        // threads per batch CTA
 constexpr int kGroups = kBT / tiles::kThreads;  // tile groups of 128 threads
 constexpr int32_t kBatchMaxM = 1024;
-constexpr int kStage = 32;  // ballots staged per tally step
 constexpr int64_t kFlushVoters = 32768;  // 16-bit lane counters are flushed before they can overflow
 
 struct Job {
@@ -48,16 +47,16 @@ struct BatchArgs {
   size_t slot_bytes;  // per CTA: W slot, then a d slot when the caller passes no d
   size_t w_bytes;
   int32_t* status;
-  int32_t tile_policy;  // tally tile: 0 tight (32 / 64 / 128), 1 at least 64, 2 always 128
+  int32_t tally_policy;  // ballots staged per tally step: 0 sixteen, 1 eight
 };
 
 // Dynamic shared memory of one batch CTA, reused stage by stage.
+constexpr int kChunkMax = 16;  // ballots staged per tally step (policy 0; policy 1 stages 8)
 union BatchSmem {
   struct {
-    uint32_t sI[kStage][128];  // row positions, duplicated into both halves
-    uint16_t sJ[kStage][128];  // column positions
+    uint32_t dup[kChunkMax][kBatchMaxM];  // position of every candidate, in both 16-bit halves
+    uint16_t pos[kChunkMax][kBatchMaxM];  // the same positions, one per 16-bit slot
   } stage;
-  uint32_t red[kBT * 16];  // cross-group reduction of tally counters
   struct {
     tiles::SmemS32 t[kGroups];
     int32_t rowbuf[2][tiles::kB];
@@ -71,129 +70,136 @@ union BatchSmem {
 
 // ------------------------------------------------------------- tally
 
-// One TILE x TILE block (I0, J0) of the election's d over all its ballots:
-// G groups of TT threads split each staged chunk of ballots, counts go to
-// 16-bit lanes and are added into d every kFlushVoters ballots.
-template <int TILE>
-__device__ void tally_tile(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, int32_t I0,
-                           int32_t J0, BatchSmem& sm, int32_t* status) {
-  constexpr int TT = (TILE / 8) * (TILE / 4);
-  constexpr int G = kBT / TT;
-  constexpr int VC = kStage / G;
-  const int tid = threadIdx.x;
-  const int g = tid / TT, lt = tid % TT;
-  const int tx = lt % (TILE / 4), ty = lt / (TILE / 4);
+constexpr int kTT = 64;  // tally tile: 64 x 64 counters per group, 8 x 4 per thread
+
+// The election's d, tile by tile: each of the four 128-thread groups owns one
+// 64 x 64 tile of d per round and counts it over all ballots in 16-bit lanes
+// (two columns per word, the row operand duplicated into both halves).
+// Ballots are staged `chunk` at a time as full position rows (unlisted
+// candidates at position k), so one staging serves the four tiles of a
+// round. Counters are added into d every kFlushVoters ballots. Full
+// rankings count only the tiles on and above the diagonal and mirror the
+// rest: d[j][i] = n - d[i][j]. The first round also checks the ballots: an
+// id out of range, or one whose position slot is already taken within the
+// same ballot, is reported as SCHULZE_EDATA.
+__device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, int chunk,
+                      BatchSmem& sm, int32_t* status) {
   const int32_t n = jb.n, m = jb.m, k = jb.k;
-  const uint32_t unl = uint32_t(k) & 0xFFFFu;
-  uint32_t acc[8][2];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0u;
-  bool first_flush = true;
-  for (int64_t v0 = 0; v0 < n; v0 += kStage) {
-    __syncthreads();
-    for (int t = tid; t < kStage * TILE; t += kBT) {
-      sm.stage.sI[t / TILE][t % TILE] = unl | (unl << 16);
-      sm.stage.sJ[t / TILE][t % TILE] = uint16_t(unl);
-    }
-    __syncthreads();
-    const int nv = int(n - v0 < kStage ? n - v0 : int64_t(kStage));
-    // the staged ballots are one contiguous run of nv * k ids; sixteen loads
-    // per thread are issued before any of them is used (ballots stream from
-    // DRAM, so one dependent load per step would leave the SM waiting)
-    const int total = nv * k;
-    const int32_t* chunk = ranks + v0 * k;
-    for (int t0 = tid; t0 < total; t0 += kBT * 16) {
-      int32_t cv[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int t = t0 + u * kBT;
-        cv[u] = t < total ? __ldcs(chunk + t) : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int t = t0 + u * kBT;
-        const int32_t c = cv[u];
-        if (t >= total) break;
-        const int vv = t / k, q = t % k;
-        // ballot checks ride along: an id out of range, or an id whose row
-        // slot was already taken by the same ballot (every id falls in some
-        // row tile), marks the data invalid
-        if (c < 0 || c >= m) set_status(status, SCHULZE_EDATA);
-        if (c >= I0 && c < I0 + TILE) {
-          const uint32_t old = atomicExch(&sm.stage.sI[vv][c - I0], uint32_t(q) | (uint32_t(q) << 16));
-          if (old != (unl | (unl << 16))) set_status(status, SCHULZE_EDATA);
-        }
-        if (c >= J0 && c < J0 + TILE) sm.stage.sJ[vv][c - J0] = uint16_t(q);
+  const bool full = k >= m - 1;
+  const int32_t nbt = (m + kTT - 1) / kTT;
+  const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
+  const int tid = threadIdx.x, g = tid / tiles::kThreads, lt = tid % tiles::kThreads;
+  const int tx = lt % (kTT / 4), ty = lt / (kTT / 4);
+  const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16);
+  const int32_t mpad = int32_t(align_up(size_t(m), kTT));
+  for (int32_t t0 = 0; t0 < ntiles; t0 += kGroups) {
+    // this group's tile (bi, bj)
+    const int32_t tt = t0 + g;
+    int32_t bi = 0, bj = 0;
+    if (tt < ntiles) {
+      if (full) {
+        int32_t rem = tt;
+        while (rem >= nbt - bi) rem -= nbt - bi, ++bi;
+        bj = bi + rem;
+      } else {
+        bi = tt / nbt, bj = tt % nbt;
       }
     }
-    __syncthreads();
-    for (int u = 0; u < VC; ++u) {
-      const int vv = g * VC + u;
-      if (vv >= nv) break;
-      uint32_t a[8], b[2];
+    const int32_t I0 = bi * kTT, J0 = bj * kTT;
+    const bool check = t0 == 0;
+    uint32_t acc[8][2];
 #pragma unroll
-      for (int r = 0; r < 8; r += 4) {
-        uint4 t4 = *reinterpret_cast<const uint4*>(&sm.stage.sI[vv][ty * 8 + r]);
-        a[r] = t4.x, a[r + 1] = t4.y, a[r + 2] = t4.z, a[r + 3] = t4.w;
-      }
-      uint2 t2 = *reinterpret_cast<const uint2*>(&sm.stage.sJ[vv][tx * 4]);
-      b[0] = t2.x, b[1] = t2.y;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        acc[r][0] = __vsub2(acc[r][0], __vcmpltu2(a[r], b[0]));
-        acc[r][1] = __vsub2(acc[r][1], __vcmpltu2(a[r], b[1]));
-      }
-    }
-    const bool last = v0 + kStage >= n;
-    if (last || ((v0 + kStage) % kFlushVoters) == 0) {
-      __syncthreads();  // staging buffers are free; reuse them for the reduction
-      if (G > 1) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          sm.red[(g * TT + lt) * 16 + 2 * r] = acc[r][0];
-          sm.red[(g * TT + lt) * 16 + 2 * r + 1] = acc[r][1];
+    for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0u;
+    bool first_flush = true;
+    for (int64_t v0 = 0; v0 < n; v0 += chunk) {
+      const int nv = int(n - v0 < chunk ? n - v0 : int64_t(chunk));
+      __syncthreads();
+      if (k < m || check) {  // unlisted candidates sit at position k
+        for (int t = tid; t < chunk * mpad; t += kBT) {
+          const int vv = t / mpad, c = t % mpad;
+          sm.stage.dup[vv][c] = unl2;
+          sm.stage.pos[vv][c] = uint16_t(unl);
         }
         __syncthreads();
+      } else if (mpad > m) {  // full ballots fill 0..m-1; the padding stays unlisted
+        for (int t = tid; t < chunk * (mpad - m); t += kBT) {
+          const int vv = t / (mpad - m), c = m + t % (mpad - m);
+          sm.stage.dup[vv][c] = unl2;
+          sm.stage.pos[vv][c] = uint16_t(unl);
+        }
       }
-      if (g == 0) {
+      // 32 lanes per ballot row, sixteen loads in flight per thread
+      const int lanes = kBT / chunk;  // threads per staged ballot (32 or 64)
+      const int vv = tid / lanes, q0 = tid % lanes;
+      if (vv < nv) {
+        const int32_t* row = ranks + (v0 + vv) * k;
+        for (int32_t qb = q0; qb < k; qb += lanes * 16) {
+          int32_t cv[16];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+          for (int u = 0; u < 16; ++u) {
+            const int32_t q = qb + u * lanes;
+            cv[u] = q < k ? __ldcs(row + q) : -1;
+          }
 #pragma unroll
-          for (int w = 0; w < 2; ++w) {
-            uint32_t lo = 0, hi = 0;
-            for (int gg = 0; gg < G; ++gg) {
-              const uint32_t x = (G > 1) ? sm.red[(gg * TT + lt) * 16 + 2 * r + w] : acc[r][w];
-              lo += x & 0xFFFFu;
-              hi += x >> 16;
+          for (int u = 0; u < 16; ++u) {
+            const int32_t q = qb + u * lanes;
+            if (q >= k) break;
+            const int32_t c = cv[u];
+            if (c < 0 || c >= m) {
+              if (check) set_status(status, SCHULZE_EDATA);
+              continue;
             }
-            const int32_t i = I0 + ty * 8 + r, j = J0 + tx * 4 + 2 * w;
-            if (i < m) {
-              int32_t* dst = dm + int64_t(i) * m + j;
-              if (j < m) dst[0] = (first_flush ? 0 : dst[0]) + int32_t(lo);
-              if (j + 1 < m) dst[1] = (first_flush ? 0 : dst[1]) + int32_t(hi);
+            const uint32_t q2 = uint32_t(q) | (uint32_t(q) << 16);
+            if (check) {
+              if (atomicExch(&sm.stage.dup[vv][c], q2) != unl2) set_status(status, SCHULZE_EDATA);
+            } else {
+              sm.stage.dup[vv][c] = q2;
             }
+            sm.stage.pos[vv][c] = uint16_t(q);
           }
         }
       }
+      __syncthreads();
+      if (tt < ntiles) {
+        for (int u = 0; u < nv; ++u) {
+          uint32_t a[8], b[2];
+          const uint4 a0 = *reinterpret_cast<const uint4*>(&sm.stage.dup[u][I0 + ty * 8]);
+          const uint4 a1 = *reinterpret_cast<const uint4*>(&sm.stage.dup[u][I0 + ty * 8 + 4]);
+          a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
+          const uint2 bv = *reinterpret_cast<const uint2*>(&sm.stage.pos[u][J0 + tx * 4]);
+          b[0] = bv.x, b[1] = bv.y;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0u;
-      first_flush = false;
+          for (int r = 0; r < 8; ++r) {
+            acc[r][0] = __vsub2(acc[r][0], __vcmpltu2(a[r], b[0]));
+            acc[r][1] = __vsub2(acc[r][1], __vcmpltu2(a[r], b[1]));
+          }
+        }
+        const bool last = v0 + chunk >= n;
+        if (last || ((v0 + chunk) % kFlushVoters) == 0) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int32_t i = I0 + ty * 8 + r;
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+              const int32_t j = J0 + tx * 4 + 2 * w;
+              if (i < m) {
+                int32_t* dst = dm + int64_t(i) * m + j;
+                if (j < m) dst[0] = (first_flush ? 0 : dst[0]) + int32_t(acc[r][w] & 0xFFFFu);
+                if (j + 1 < m) dst[1] = (first_flush ? 0 : dst[1]) + int32_t(acc[r][w] >> 16);
+              }
+            }
+            acc[r][0] = acc[r][1] = 0u;
+          }
+          first_flush = false;
+        }
+      }
     }
   }
-}
-
-template <int TILE>
-__device__ void tally_all(const Job& jb, const int32_t* ranks, int32_t* dm, bool full, BatchSmem& sm,
-                          int32_t* status) {
-  const int32_t nbt = (jb.m + TILE - 1) / TILE;
-  for (int32_t bi = 0; bi < nbt; ++bi)
-    for (int32_t bj = full ? bi : 0; bj < nbt; ++bj) tally_tile<TILE>(jb, ranks, dm, bi * TILE, bj * TILE, sm, status);
   __syncthreads();
-  if (full && nbt > 1) {  // strict full orders: d[j][i] = n - d[i][j] below the diagonal tiles
-    const int32_t m = jb.m;
+  if (full && nbt > 1) {
     for (int64_t t = threadIdx.x; t < int64_t(m) * m; t += kBT) {
       const int32_t i = int32_t(t / m), j = int32_t(t % m);
-      if (i / TILE > j / TILE) dm[t] = jb.n - dm[int64_t(j) * m + i];
+      if (i / kTT > j / kTT) dm[t] = n - dm[int64_t(j) * m + i];
     }
   }
   __syncthreads();
@@ -314,14 +320,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
       for (int64_t t = threadIdx.x; t < int64_t(m) * m; t += kBT) dm[t] = 0;
       __syncthreads();
     } else {
-      const bool full = jb.k >= m - 1;
-      const int tile = a.tile_policy == 2 ? 128 : (m <= 32 && a.tile_policy == 0 ? 32 : (m <= 64 ? 64 : 128));
-      if (tile == 32)
-        tally_all<32>(jb, ranks, dm, full, sm, a.status);
-      else if (tile == 64)
-        tally_all<64>(jb, ranks, dm, full, sm, a.status);
-      else
-        tally_all<128>(jb, ranks, dm, full, sm, a.status);
+      tally(jb, ranks, dm, a.tally_policy == 1 ? 8 : kChunkMax, sm, a.status);
     }
     const int32_t mp = int32_t(align_up(size_t(m), tiles::kB));
     pack<E>(dm, m, mp, W);
@@ -346,7 +345,7 @@ struct schulze_batch {
   unsigned char* scratch = nullptr;
   size_t slot_bytes = 0, w_bytes = 0;
   int grid = 0;
-  int32_t tile_policy = 0;
+  int32_t tally_policy = 0;
   int32_t order_policy = 0;  // 0 longest first, 1 the caller's order
   size_t smem = 0;
 };
@@ -490,7 +489,7 @@ int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_
   a.slot_bytes = b->slot_bytes;
   a.w_bytes = b->w_bytes;
   a.status = b->ctx->status;
-  a.tile_policy = b->tile_policy;
+  a.tally_policy = b->tally_policy;
   Launch L(b->ctx, stream, "batch_elections", double(b->E));
   if (b->s16)
     batch_kernel<int16_t><<<b->grid, kBT, b->smem, stream>>>(a);
@@ -499,11 +498,11 @@ int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_
   return check_launch();
 }
 
-int schulze_batch_set_schedule(schulze_batch* b, int32_t tile_policy, int32_t order_policy) {
-  if (!b || tile_policy < 0 || tile_policy > 2 || order_policy < 0 || order_policy > 1) return SCHULZE_EINVAL;
+int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t order_policy) {
+  if (!b || tally_policy < 0 || tally_policy > 1 || order_policy < 0 || order_policy > 1) return SCHULZE_EINVAL;
   if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
-  b->tile_policy = tile_policy;
+  b->tally_policy = tally_policy;
   if (order_policy != b->order_policy) {
     b->order_policy = order_policy;
     order_jobs(b);
@@ -525,7 +524,7 @@ int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* c
   for (char* c = key; *c; ++c)
     if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';  // the cache line format splits on blanks
   int32_t bt = -1, bo = -1;
-  if (cache_path) {  // line format: <key> <tile_policy> <order_policy>
+  if (cache_path) {  // line format: <key> <tally_policy> <order_policy>
     if (FILE* f = fopen(cache_path, "r")) {
       char line[512];
       while (fgets(line, sizeof(line), f)) {
@@ -542,7 +541,7 @@ int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* c
     cudaEventCreate(&e1);
     float best = 1e30f;
     for (int32_t o = 0; o <= 1; ++o)
-      for (int32_t t = 0; t <= 2; ++t) {
+      for (int32_t t = 0; t <= 1; ++t) {
         if (int rc = schulze_batch_set_schedule(b, t, o)) return rc;
         float total = 0.f;
         for (int rep = 0; rep < 2; ++rep) {

@@ -1,0 +1,826 @@
+// Learned winner proposal with exact certification.
+//
+// The paper has no learned component; this is an engineering addition that
+// keeps the Schulze winners exact. A small MLP scores candidates from 16
+// features of the tally (some of them quantities the paper uses: Copeland
+// wins and losses of the dominance relation, Sect. 2.1, and the loser filter
+// of Sect. 4). The best-scored candidates are then CERTIFIED with the
+// definitions of Sect. 2.1: c is a winner iff p(c, j) >= p(j, c) for all j,
+// with p(c, .) and p(., c) computed by single-source / single-sink widest
+// paths (the deterministic form of the wide-path questions of Sect. 3). If
+// no proposal certifies, the full closure decides.
+//
+// Structure used by certification: a candidate without outgoing edges
+// ("cold") ends every path it is on, so widest paths between the others
+// ("warm") only go through warm candidates, p(cold, .) = 0, and a cold
+// candidate is a winner iff it has no incoming edge either.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace schulze {
+namespace {
+
+constexpr int kNF = 16;  // features per candidate
+constexpr int kH = 64;   // hidden width
+constexpr int kNP = 5313;
+constexpr int kOffW1 = 0, kOffB1 = 1024, kOffW2 = 1088, kOffB2 = 5184, kOffW3 = 5248, kOffB3 = 5312;
+constexpr int32_t kCertifyMaxWarm = 2048;  // larger warm sets go straight to the closure
+constexpr int kMaxProposals = 8;
+constexpr int kMaxTies = 16;
+
+// ------------------------------------------------------------ features
+
+struct Acc {  // per-candidate accumulators of the features pass
+  int32_t* wins;
+  int32_t* losses;
+  int32_t* ties;
+  unsigned long long* rowsum;
+  unsigned long long* colsum;
+  int32_t* maxw_out;
+  int32_t* maxw_in;
+  unsigned long long* sumw_out;
+  unsigned long long* sumw_in;
+  int32_t* min_margin;
+  int32_t* max_margin;
+  int32_t* max_drow;
+};
+
+__global__ void acc_init_kernel(Acc a, int32_t m) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    a.wins[c] = a.losses[c] = a.ties[c] = 0;
+    a.rowsum[c] = a.colsum[c] = a.sumw_out[c] = a.sumw_in[c] = 0ull;
+    a.maxw_out[c] = a.maxw_in[c] = a.max_drow[c] = 0;
+    a.min_margin[c] = INT32_MAX;
+    a.max_margin[c] = INT32_MIN;
+  }
+}
+
+__device__ __forceinline__ int32_t warp_sum(int32_t v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum64(long long v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+__device__ __forceinline__ int32_t warp_max(int32_t v) {
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+__device__ __forceinline__ int32_t warp_min(int32_t v) {
+  for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+// Row statistics of rows `rows0 + r` against columns `cols0 + lane` of one
+// 32 x 32 block: x = d[row][col] (from `x`), y = d[col][row] (from `y`, the
+// transposed block). One warp per row; one atomic per row and statistic.
+__device__ void row_stats(const int32_t (*x)[33], const int32_t (*y)[33], int32_t rows0, int32_t cols0, int32_t m,
+                          const Acc& a) {
+  const int lane = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int32_t i = rows0 + r, j = cols0 + lane;
+    const bool v = i < m && j < m && i != j;
+    const int32_t dij = v ? x[r][lane] : 0, dji = v ? y[lane][r] : 0;
+    const int32_t win = v && dij > dji, loss = v && dji > dij, tie = v && dij == dji;
+    const int32_t wout = win ? dij : 0, win_w = loss ? dji : 0;
+    int32_t s_win = warp_sum(win), s_loss = warp_sum(loss), s_tie = warp_sum(tie);
+    long long s_row = warp_sum64(dij), s_col = warp_sum64(dji), s_wo = warp_sum64(wout), s_wi = warp_sum64(win_w);
+    int32_t mx_wo = warp_max(wout), mx_wi = warp_max(win_w), mx_d = warp_max(dij);
+    int32_t mn_mg = warp_min(v ? dij - dji : INT32_MAX), mx_mg = warp_max(v ? dij - dji : INT32_MIN);
+    if (lane == 0 && i < m) {
+      if (s_win) atomicAdd(&a.wins[i], s_win);
+      if (s_loss) atomicAdd(&a.losses[i], s_loss);
+      if (s_tie) atomicAdd(&a.ties[i], s_tie);
+      if (s_row) atomicAdd(&a.rowsum[i], (unsigned long long)s_row);
+      if (s_col) atomicAdd(&a.colsum[i], (unsigned long long)s_col);
+      if (s_wo) atomicAdd(&a.sumw_out[i], (unsigned long long)s_wo);
+      if (s_wi) atomicAdd(&a.sumw_in[i], (unsigned long long)s_wi);
+      atomicMax(&a.maxw_out[i], mx_wo);
+      atomicMax(&a.maxw_in[i], mx_wi);
+      atomicMax(&a.max_drow[i], mx_d);
+      atomicMin(&a.min_margin[i], mn_mg);
+      atomicMax(&a.max_margin[i], mx_mg);
+    }
+  }
+}
+
+// One CTA per 32 x 32 block pair (A, B), A <= B: each d entry is read once.
+__global__ void features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
+  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
+  if (A > B) return;
+  __shared__ int32_t t1[32][33], t2[32][33];  // t1 = d[A.., B..], t2 = d[B.., A..]
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int32_t i = A + r, j = B + threadIdx.x;
+    t1[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+    i = B + r, j = A + threadIdx.x;
+    t2[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+  }
+  __syncthreads();
+  row_stats(t1, t2, A, B, m, a);
+  if (A != B) row_stats(t2, t1, B, A, m, a);
+}
+
+// f[c][0..13] from the accumulators; ranks (14, 15) are counted afterwards.
+__global__ void features_finalize_kernel(Acc a, int32_t m, int64_t n, float* __restrict__ feat) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    float* f = feat + int64_t(c) * kNF;
+    for (int q = 0; q < kNF; ++q) f[q] = 0.f;
+    if (m < 2) continue;
+    const double nn = double(n > 0 ? n : 1), mm = double(m - 1);
+    f[0] = float(double(a.wins[c]) / mm);
+    f[1] = float(double(a.losses[c]) / mm);
+    f[2] = float(double(a.ties[c]) / mm);
+    f[3] = float(double(a.rowsum[c]) / (nn * mm));
+    f[4] = float(double(a.colsum[c]) / (nn * mm));
+    f[5] = float(double(a.maxw_out[c]) / nn);
+    f[6] = float(double(a.maxw_in[c]) / nn);
+    f[7] = a.maxw_in[c] > a.maxw_out[c] ? 1.f : 0.f;
+    f[8] = float(double(a.maxw_out[c] - a.maxw_in[c]) / nn);
+    f[9] = float(double(a.sumw_out[c]) / (nn * mm));
+    f[10] = float(double(a.sumw_in[c]) / (nn * mm));
+    f[11] = float(double(a.min_margin[c]) / nn);
+    f[12] = float(double(a.max_margin[c]) / nn);
+    f[13] = float(double(a.max_drow[c]) / nn);
+  }
+}
+
+// f[c][14] = #{j: rowsum[j] > rowsum[c]} / (m-1); f[c][15] likewise for
+// wins - losses. 2D grid: (chunks of c, chunks of j); counts added atomically.
+__global__ void __launch_bounds__(256) features_rank_kernel(Acc a, int32_t m, int32_t* __restrict__ cnt14,
+                                                            int32_t* __restrict__ cnt15) {
+  __shared__ unsigned long long rs[256];
+  __shared__ int32_t cp[256];
+  const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t j = blockIdx.y * 256 + threadIdx.x;
+  rs[threadIdx.x] = j < m ? a.rowsum[j] : 0ull;
+  cp[threadIdx.x] = j < m ? a.wins[j] - a.losses[j] : INT32_MIN;
+  __syncthreads();
+  if (c >= m) return;
+  const unsigned long long mine = a.rowsum[c];
+  const int32_t mycp = a.wins[c] - a.losses[c];
+  const int lim = min(256, m - int32_t(blockIdx.y) * 256);
+  int32_t k14 = 0, k15 = 0;
+  for (int t = 0; t < lim; ++t) {
+    k14 += rs[t] > mine;
+    k15 += cp[t] > mycp;
+  }
+  if (k14) atomicAdd(&cnt14[c], k14);
+  if (k15) atomicAdd(&cnt15[c], k15);
+}
+
+__global__ void features_rank_finalize_kernel(const int32_t* __restrict__ cnt14, const int32_t* __restrict__ cnt15,
+                                              int32_t m, float* __restrict__ feat) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    if (m < 2) continue;
+    feat[int64_t(c) * kNF + 14] = float(double(cnt14[c]) / double(m - 1));
+    feat[int64_t(c) * kNF + 15] = float(double(cnt15[c]) / double(m - 1));
+  }
+}
+
+// ----------------------------------------------------------------- MLP
+
+// Forward pass, one thread per candidate; parameters staged in shared
+// memory. h1, h2 (ReLU outputs) are stored when given (training).
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restrict__ theta,
+                                                          const float* __restrict__ feat, int32_t N,
+                                                          float* __restrict__ score, float* __restrict__ h1out,
+                                                          float* __restrict__ h2out) {
+  __shared__ float p[kNP];
+  for (int t = threadIdx.x; t < kNP; t += blockDim.x) p[t] = theta[t];
+  __syncthreads();
+  const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float x[kNF];
+#pragma unroll
+  for (int q = 0; q < kNF; ++q) x[q] = feat[int64_t(c) * kNF + q];
+  float h1[kH];
+#pragma unroll
+  for (int o = 0; o < kH; ++o) {
+    float s = p[kOffB1 + o];
+#pragma unroll
+    for (int q = 0; q < kNF; ++q) s = fmaf(p[kOffW1 + o * kNF + q], x[q], s);
+    h1[o] = fmaxf(s, 0.f);
+  }
+  float out = p[kOffB3];
+  for (int o = 0; o < kH; ++o) {
+    float s = p[kOffB2 + o];
+#pragma unroll
+    for (int q = 0; q < kH; ++q) s = fmaf(p[kOffW2 + o * kH + q], h1[q], s);
+    const float h = fmaxf(s, 0.f);
+    if (h2out) h2out[int64_t(c) * kH + o] = h;
+    out = fmaf(p[kOffW3 + o], h, out);
+  }
+  if (h1out) {
+#pragma unroll
+    for (int q = 0; q < kH; ++q) h1out[int64_t(c) * kH + q] = h1[q];
+  }
+  score[c] = out;
+}
+
+// Listwise softmax cross-entropy of one election (segment) per CTA: target
+// mass 1/|winners| on each winner. ds[c] = (softmax_c - t_c) / nseg; the
+// segment's loss goes to seg_loss[e].
+__global__ void __launch_bounds__(256) mlp_loss_kernel(const float* __restrict__ score,
+                                                       const int32_t* __restrict__ label,
+                                                       const int32_t* __restrict__ seg_off, int32_t nseg,
+                                                       float* __restrict__ ds, float* __restrict__ seg_loss) {
+  __shared__ float red[256];
+  __shared__ int32_t redi[256];
+  const int32_t e = blockIdx.x;
+  const int32_t a = seg_off[e], b = seg_off[e + 1];
+  float mx = -INFINITY;
+  int32_t nw = 0;
+  for (int32_t c = a + threadIdx.x; c < b; c += blockDim.x) {
+    mx = fmaxf(mx, score[c]);
+    nw += label[c] != 0;
+  }
+  red[threadIdx.x] = mx;
+  redi[threadIdx.x] = nw;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+      redi[threadIdx.x] += redi[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  mx = red[0];
+  nw = max(redi[0], 1);
+  __syncthreads();
+  float se = 0.f;
+  for (int32_t c = a + threadIdx.x; c < b; c += blockDim.x) se += expf(score[c] - mx);
+  red[threadIdx.x] = se;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const float lse = mx + logf(red[0]);
+  __syncthreads();
+  float l = 0.f;
+  const float inv_e = 1.f / float(nseg), inv_w = 1.f / float(nw);
+  for (int32_t c = a + threadIdx.x; c < b; c += blockDim.x) {
+    const float logp = score[c] - lse;
+    const float t = label[c] ? inv_w : 0.f;
+    l -= t * logp;
+    ds[c] = (expf(logp) - t) * inv_e;
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) seg_loss[e] = red[0];
+}
+
+constexpr int kChunk = 64;  // candidates per backward CTA
+
+// Backward over a chunk of kChunk candidates: dh2, dh1 per candidate, then
+// this chunk's sum of every parameter gradient into partial[chunk][kNP].
+struct BackwardSmem {
+  float W2[kH * kH], W3[kH];
+  float sx[kChunk][kNF], sh1[kChunk][kH + 1], sh2[kChunk][kH + 1], sd2[kChunk][kH + 1], sd1[kChunk][kH + 1];
+  float sds[kChunk];
+};
+
+__global__ void __launch_bounds__(256) mlp_backward_kernel(const float* __restrict__ theta,
+                                                           const float* __restrict__ feat,
+                                                           const float* __restrict__ h1g, const float* __restrict__ h2g,
+                                                           const float* __restrict__ ds, int32_t N,
+                                                           float* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char bw_raw[];
+  BackwardSmem& S = *reinterpret_cast<BackwardSmem*>(bw_raw);
+  float* W2 = S.W2;
+  float* W3 = S.W3;
+  auto& sx = S.sx;
+  auto& sh1 = S.sh1;
+  auto& sh2 = S.sh2;
+  auto& sd2 = S.sd2;
+  auto& sd1 = S.sd1;
+  float* sds = S.sds;
+  const int32_t c0 = blockIdx.x * kChunk;
+  const int nc = min(kChunk, N - c0);
+  for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) W2[t] = theta[kOffW2 + t];
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) W3[t] = theta[kOffW3 + t];
+  for (int t = threadIdx.x; t < kChunk * kH; t += blockDim.x) {
+    const int r = t / kH, q = t % kH;
+    sh1[r][q] = r < nc ? h1g[int64_t(c0 + r) * kH + q] : 0.f;
+    sh2[r][q] = r < nc ? h2g[int64_t(c0 + r) * kH + q] : 0.f;
+  }
+  for (int t = threadIdx.x; t < kChunk * kNF; t += blockDim.x) {
+    const int r = t / kNF, q = t % kNF;
+    sx[r][q] = r < nc ? feat[int64_t(c0 + r) * kNF + q] : 0.f;
+  }
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) sds[t] = t < nc ? ds[c0 + t] : 0.f;
+  __syncthreads();
+  // dh2[r][o] = ds_r * W3[o] * [h2 > 0]
+  for (int t = threadIdx.x; t < kChunk * kH; t += blockDim.x) {
+    const int r = t / kH, o = t % kH;
+    sd2[r][o] = sh2[r][o] > 0.f ? sds[r] * W3[o] : 0.f;
+  }
+  __syncthreads();
+  // dh1[r][q] = sum_o W2[o][q] dh2[r][o] * [h1 > 0]
+  for (int t = threadIdx.x; t < kChunk * kH; t += blockDim.x) {
+    const int r = t / kH, q = t % kH;
+    float s = 0.f;
+    for (int o = 0; o < kH; ++o) s = fmaf(W2[o * kH + q], sd2[r][o], s);
+    sd1[r][q] = sh1[r][q] > 0.f ? s : 0.f;
+  }
+  __syncthreads();
+  float* out = partial + int64_t(blockIdx.x) * kNP;
+  for (int t = threadIdx.x; t < kNP; t += blockDim.x) {
+    float g = 0.f;
+    if (t < kOffB1) {  // W1[o][q]: sum_r dh1[r][o] x[r][q]
+      const int o = t / kNF, q = t % kNF;
+      for (int r = 0; r < kChunk; ++r) g = fmaf(sd1[r][o], sx[r][q], g);
+    } else if (t < kOffW2) {
+      const int o = t - kOffB1;
+      for (int r = 0; r < kChunk; ++r) g += sd1[r][o];
+    } else if (t < kOffB2) {  // W2[o][q]: sum_r dh2[r][o] h1[r][q]
+      const int o = (t - kOffW2) / kH, q = (t - kOffW2) % kH;
+      for (int r = 0; r < kChunk; ++r) g = fmaf(sd2[r][o], sh1[r][q], g);
+    } else if (t < kOffW3) {
+      const int o = t - kOffB2;
+      for (int r = 0; r < kChunk; ++r) g += sd2[r][o];
+    } else if (t < kOffB3) {  // W3[o]: sum_r ds_r h2[r][o]
+      const int o = t - kOffW3;
+      for (int r = 0; r < kChunk; ++r) g = fmaf(sds[r], sh2[r][o], g);
+    } else {
+      for (int r = 0; r < kChunk; ++r) g += sds[r];
+    }
+    out[t] = g;
+  }
+}
+
+// grad[t] = sum over chunks of partial[chunk][t], in chunk order; loss =
+// sum of the segment losses / nseg. Deterministic.
+__global__ void mlp_reduce_kernel(const float* __restrict__ partial, int32_t nchunks, const float* __restrict__ seg_loss,
+                                  int32_t nseg, float* __restrict__ grad, float* __restrict__ loss) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kNP) {
+    float g = 0.f;
+    for (int32_t c = 0; c < nchunks; ++c) g += partial[int64_t(c) * kNP + t];
+    grad[t] = g;
+  }
+  if (t == 0 && loss) {
+    float l = 0.f;
+    for (int32_t e = 0; e < nseg; ++e) l += seg_loss[e];
+    *loss = l / float(nseg);
+  }
+}
+
+// Adam (Kingma and Ba, 2015), 1-based step.
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m1, float* __restrict__ m2,
+                            const float* __restrict__ grad, int64_t step, float lr, float b1, float b2, float eps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kNP) return;
+  const float g = grad[t];
+  const float a = b1 * m1[t] + (1.f - b1) * g;
+  const float v = b2 * m2[t] + (1.f - b2) * g * g;
+  m1[t] = a;
+  m2[t] = v;
+  const float mh = a / (1.f - powf(b1, float(step)));
+  const float vh = v / (1.f - powf(b2, float(step)));
+  theta[t] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// --------------------------------------------------------- proposals
+
+// The `top` best scores (ties: smaller id first), one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ score, int32_t m, int32_t top,
+                                                    int32_t* __restrict__ out) {
+  __shared__ float bs[1024];
+  __shared__ int32_t bi[1024];
+  __shared__ int32_t chosen[kMaxProposals];
+  for (int r = 0; r < top; ++r) {
+    float best = -INFINITY;
+    int32_t arg = INT32_MAX;
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+      bool taken = false;
+      for (int q = 0; q < r; ++q) taken |= chosen[q] == c;
+      if (taken) continue;
+      const float s = score[c];
+      if (s > best || (s == best && c < arg)) best = s, arg = c;
+    }
+    bs[threadIdx.x] = best;
+    bi[threadIdx.x] = arg;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+      if (threadIdx.x < o) {
+        const float s2 = bs[threadIdx.x + o];
+        const int32_t i2 = bi[threadIdx.x + o];
+        if (s2 > bs[threadIdx.x] || (s2 == bs[threadIdx.x] && i2 < bi[threadIdx.x]))
+          bs[threadIdx.x] = s2, bi[threadIdx.x] = i2;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      chosen[r] = bi[0] == INT32_MAX ? -1 : bi[0];
+      out[r] = chosen[r];
+    }
+    __syncthreads();
+  }
+}
+
+// Copeland score wins - losses as a non-learned proposer.
+__global__ void copeland_score_kernel(Acc a, int32_t m, float* __restrict__ score) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
+    score[c] = float(a.wins[c] - a.losses[c]);
+}
+
+// ------------------------------------------------------- certification
+
+// warm[a] = a-th candidate with an outgoing edge (wins > 0), in id order;
+// slot[c] = its index or -1. One CTA.
+__global__ void __launch_bounds__(1024) warm_list_kernel(const int32_t* __restrict__ wins, int32_t m,
+                                                         int32_t* __restrict__ warm, int32_t* __restrict__ slot,
+                                                         int32_t* __restrict__ nwarm) {
+  __shared__ int32_t part[1024];
+  const int T = blockDim.x;
+  const int per = (m + T - 1) / T;
+  const int b = threadIdx.x * per, e = min(m, b + per);
+  int32_t s = 0;
+  for (int c = b; c < e; ++c) s += wins[c] > 0;
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    int32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += x;
+    __syncthreads();
+  }
+  int32_t pos = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int c = b; c < e; ++c) {
+    if (wins[c] > 0) {
+      warm[pos] = c;
+      slot[c] = pos++;
+    } else {
+      slot[c] = -1;
+    }
+  }
+  if (threadIdx.x == T - 1) *nwarm = part[T - 1];
+}
+
+// Ww[a][b] = w(warm[a], warm[b]) and Wt[b][a] = the same (winning votes).
+__global__ void warm_pack_kernel(const int32_t* __restrict__ d, int32_t m, const int32_t* __restrict__ warm,
+                                 const int32_t* __restrict__ nwarm, int32_t* __restrict__ Ww, int32_t* __restrict__ Wt) {
+  const int32_t nw = *nwarm;
+  if (nw > kCertifyMaxWarm) return;
+  const int64_t total = int64_t(nw) * nw;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t a = int32_t(t / nw), b = int32_t(t % nw);
+    const int32_t i = warm[a], j = warm[b];
+    int32_t w = 0;
+    if (i != j) {
+      const int32_t x = d[int64_t(i) * m + j], y = d[int64_t(j) * m + i];
+      w = x > y ? x : 0;
+    }
+    Ww[t] = w;
+    Wt[int64_t(b) * nw + a] = w;
+  }
+}
+
+// Widest paths from (dir 0) or to (dir 1) warm candidate `s` inside the warm
+// subgraph, by (max, min) Bellman-Ford rounds until nothing changes (at most
+// nw rounds). x lives in shared memory; warp per target, lanes over sources.
+// dir 0: x[b] = max(x[b], max_a min(x[a], w[a][b])) reads Wt row b;
+// dir 1: x[b] = max(x[b], max_a min(w[b][a], x[a])) reads Ww row b.
+// x[s] is the empty path (+inf). Returns the number of rounds.
+__device__ int32_t widest_warm(const int32_t* __restrict__ Ww, const int32_t* __restrict__ Wt, int32_t nw, int32_t s,
+                               int dir, int32_t* __restrict__ x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int32_t* M = dir == 0 ? Wt : Ww;
+  for (int32_t b = threadIdx.x; b < nw; b += blockDim.x)
+    x[b] = b == s ? INT32_MAX : (dir == 0 ? Ww[int64_t(s) * nw + b] : Ww[int64_t(b) * nw + s]);
+  __syncthreads();
+  int32_t rounds = 0;
+  for (;;) {
+    ++rounds;
+    int changed = 0;
+    for (int32_t b = wid; b < nw; b += nwarps) {
+      const int32_t* row = M + int64_t(b) * nw;
+      int32_t best = 0;
+      for (int32_t a = lane; a < nw; a += 32) best = max(best, min(x[a], row[a]));
+      best = warp_max(best);
+      if (lane == 0 && b != s && best > x[b]) {
+        x[b] = best;  // monotone: reading old or new values elsewhere is still a valid lower bound
+        changed = 1;
+      }
+    }
+    if (!__syncthreads_or(changed) || rounds > nw + 1) break;
+  }
+  return rounds;
+}
+
+// Certification, one CTA of 1024 threads. Proposals are tried in order;
+// the first c with p(c, j) >= p(j, c) for every warm j is a winner (for cold
+// j, p(j, c) = 0). The other winners are the warm candidates tied with c
+// (each certified in turn) and the cold candidates without incoming edges.
+// res: [0] 1 if the winner set is exact, 0 if the closure must decide;
+// [1] index of the certified proposal (-1 none); [2] ties checked;
+// [3] Bellman-Ford rounds.
+__global__ void __launch_bounds__(1024) certify_kernel(const int32_t* __restrict__ Ww, const int32_t* __restrict__ Wt,
+                                                       const int32_t* __restrict__ nwarm_p,
+                                                       const int32_t* __restrict__ warm,
+                                                       const int32_t* __restrict__ slot,
+                                                       const int32_t* __restrict__ losses, int32_t m,
+                                                       const int32_t* __restrict__ cand, int32_t ncand,
+                                                       int32_t* __restrict__ fwd, int32_t* __restrict__ bwd,
+                                                       int32_t* __restrict__ winners, int32_t* __restrict__ res) {
+  __shared__ int32_t s_ok, s_ties[kMaxTies], s_nties, s_overflow;
+  const int32_t nw = *nwarm_p;
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) winners[c] = 0;
+  if (threadIdx.x == 0) res[0] = 0, res[1] = -1, res[2] = 0, res[3] = 0;
+  __syncthreads();
+  if (nw > kCertifyMaxWarm) return;  // closure decides
+  if (nw == 0) {  // no edges at all: every candidate is a winner
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) winners[c] = 1;
+    if (threadIdx.x == 0) res[0] = 1;
+    return;
+  }
+  int32_t rounds = 0;
+  int32_t found = -1;
+  for (int32_t p = 0; p < ncand && found < 0; ++p) {
+    const int32_t c = cand[p];
+    if (c < 0 || c >= m || slot[c] < 0) continue;  // cold proposals cannot be certified this way
+    const int32_t s = slot[c];
+    rounds += widest_warm(Ww, Wt, nw, s, 0, fwd);
+    rounds += widest_warm(Ww, Wt, nw, s, 1, bwd);
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    for (int32_t b = threadIdx.x; b < nw; b += blockDim.x)
+      if (b != s && fwd[b] < bwd[b]) s_ok = 0;
+    __syncthreads();
+    if (s_ok) found = p;
+    __syncthreads();
+  }
+  if (found < 0) {
+    if (threadIdx.x == 0) res[3] = rounds;
+    return;
+  }
+  const int32_t c = cand[found], s = slot[c];
+  // ties with c among the warm candidates
+  if (threadIdx.x == 0) s_nties = 0, s_overflow = 0;
+  __syncthreads();
+  for (int32_t b = threadIdx.x; b < nw; b += blockDim.x) {
+    if (b != s && fwd[b] == bwd[b]) {
+      const int32_t q = atomicAdd(&s_nties, 1);
+      if (q < kMaxTies) s_ties[q] = b;
+      else s_overflow = 1;
+    }
+  }
+  __syncthreads();
+  if (s_overflow) {
+    if (threadIdx.x == 0) res[1] = found, res[3] = rounds;
+    return;  // too many ties: the closure decides
+  }
+  const int32_t nt = s_nties;
+  // cold candidates without incoming edges are winners too
+  for (int32_t j = threadIdx.x; j < m; j += blockDim.x)
+    if (slot[j] < 0 && losses[j] == 0) winners[j] = 1;
+  if (threadIdx.x == 0) winners[c] = 1;
+  for (int32_t t = 0; t < nt; ++t) {
+    const int32_t sb = s_ties[t];
+    rounds += widest_warm(Ww, Wt, nw, sb, 0, fwd);
+    rounds += widest_warm(Ww, Wt, nw, sb, 1, bwd);
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    for (int32_t b = threadIdx.x; b < nw; b += blockDim.x)
+      if (b != sb && fwd[b] < bwd[b]) s_ok = 0;
+    __syncthreads();
+    if (s_ok && threadIdx.x == 0) winners[warm[sb]] = 1;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[0] = 1, res[1] = found, res[2] = nt, res[3] = rounds;
+}
+
+struct LearnedWs {
+  Acc acc;
+  int32_t *cnt14, *cnt15;
+  float* score;
+  int32_t *cand, *warm, *slot, *nwarm, *Ww, *Wt, *res;
+};
+
+size_t learned_ws_bytes(int32_t m) {
+  size_t b = 0;
+  b += 12 * align_up(size_t(m) * 8, 256);
+  b += 4 * align_up(size_t(m) * 4, 256);
+  b += 2 * align_up(size_t(std::min<int32_t>(m, kCertifyMaxWarm)) * size_t(std::min<int32_t>(m, kCertifyMaxWarm)) * 4,
+                    256);
+  return b + 8192;
+}
+
+LearnedWs carve_learned(void* ws, int32_t m) {
+  Carver cv(ws);
+  LearnedWs w;
+  w.acc.wins = cv.take<int32_t>(m);
+  w.acc.losses = cv.take<int32_t>(m);
+  w.acc.ties = cv.take<int32_t>(m);
+  w.acc.rowsum = cv.take<unsigned long long>(m);
+  w.acc.colsum = cv.take<unsigned long long>(m);
+  w.acc.maxw_out = cv.take<int32_t>(m);
+  w.acc.maxw_in = cv.take<int32_t>(m);
+  w.acc.sumw_out = cv.take<unsigned long long>(m);
+  w.acc.sumw_in = cv.take<unsigned long long>(m);
+  w.acc.min_margin = cv.take<int32_t>(m);
+  w.acc.max_margin = cv.take<int32_t>(m);
+  w.acc.max_drow = cv.take<int32_t>(m);
+  w.cnt14 = cv.take<int32_t>(m);
+  w.cnt15 = cv.take<int32_t>(m);
+  w.score = cv.take<float>(m);
+  w.slot = cv.take<int32_t>(m);
+  w.warm = cv.take<int32_t>(m);
+  w.cand = cv.take<int32_t>(kMaxProposals);
+  w.nwarm = cv.take<int32_t>(1);
+  w.res = cv.take<int32_t>(4);
+  const size_t cw = size_t(std::min<int32_t>(m, kCertifyMaxWarm));
+  w.Ww = cv.take<int32_t>(cw * cw);
+  w.Wt = cv.take<int32_t>(cw * cw);
+  return w;
+}
+
+int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, float* feat, const LearnedWs& w,
+                  cudaStream_t stream) {
+  const int g = std::max(1, std::min((m + 255) / 256, 1024));
+  {
+    Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
+    acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m);
+    const int32_t nb32 = (m + 31) / 32;
+    features_pass_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, w.acc);
+    features_finalize_kernel<<<g, 256, 0, stream>>>(w.acc, m, n, feat);
+  }
+  if (cudaMemsetAsync(w.cnt14, 0, size_t(m) * 4, stream) != cudaSuccess ||
+      cudaMemsetAsync(w.cnt15, 0, size_t(m) * 4, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  {
+    Launch L(ctx, stream, "learn_feature_ranks", double(m) * 16.0);
+    features_rank_kernel<<<dim3((m + 255) / 256, (m + 255) / 256), 256, 0, stream>>>(w.acc, m, w.cnt14, w.cnt15);
+    features_rank_finalize_kernel<<<g, 256, 0, stream>>>(w.cnt14, w.cnt15, m, feat);
+  }
+  return check_launch();
+}
+
+int certify_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, const int32_t* cand, int32_t ncand,
+                   int32_t* winners, int32_t* res, const LearnedWs& w, int32_t* fwd, int32_t* bwd,
+                   cudaStream_t stream) {
+  {
+    Launch L(ctx, stream, "certify_warm_list", double(m) * 8.0);
+    warm_list_kernel<<<1, 1024, 0, stream>>>(w.acc.wins, m, w.warm, w.slot, w.nwarm);
+  }
+  {
+    const int64_t cw = std::min<int32_t>(m, kCertifyMaxWarm);
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((cw * cw + 255) / 256, 4096)));
+    Launch L(ctx, stream, "certify_warm_pack", double(cw) * double(cw) * 16.0);
+    warm_pack_kernel<<<blocks, 256, 0, stream>>>(d, m, w.warm, w.nwarm, w.Ww, w.Wt);
+  }
+  {
+    Launch L(ctx, stream, "certify_paths", 0.0);
+    certify_kernel<<<1, 1024, 0, stream>>>(w.Ww, w.Wt, w.nwarm, w.warm, w.slot, w.acc.losses, m, cand, ncand, fwd,
+                                           bwd, winners, res);
+  }
+  return check_launch();
+}
+
+}  // namespace
+}  // namespace schulze
+
+using namespace schulze;
+
+extern "C" {
+
+int schulze_features(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, float* feat, schulze_stream_t stream) {
+  if (!ctx || !d || !feat || m < 1 || m > kMaxM || n < 0) return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (int rc = ensure_workspace(ctx, learned_ws_bytes(m), stream)) return rc;
+  const LearnedWs w = carve_learned(ctx->ws.base, m);
+  return features_into(ctx, d, m, n, feat, w, stream);
+}
+
+int schulze_mlp_forward(schulze_ctx* ctx, const float* params, const float* feat, int32_t N, float* score,
+                        schulze_stream_t stream) {
+  if (!ctx || !params || !feat || !score || N < 0) return SCHULZE_EINVAL;
+  if (N == 0) return SCHULZE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  Launch L(ctx, stream, "mlp_forward", double(N) * 5248.0 * 2.0);
+  mlp_forward_kernel<<<(N + 255) / 256, 256, 0, stream>>>(params, feat, N, score, nullptr, nullptr);
+  return check_launch();
+}
+
+int schulze_mlp_train_step(schulze_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t step,
+                           const float* feat, const int32_t* label, const int32_t* seg_off, int32_t nseg, int32_t N,
+                           float lr, float* loss, float* grad, schulze_stream_t stream) {
+  if (!ctx || !params || !adam_m || !adam_v || step < 1 || !feat || !label || !seg_off || nseg < 1 || N < 1 ||
+      !(lr >= 0.f))
+    return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  const int32_t nchunks = (N + kChunk - 1) / kChunk;
+  const size_t need = align_up(size_t(N) * 4, 256) * 2 + 2 * align_up(size_t(N) * kH * 4, 256) +
+                      align_up(size_t(nchunks) * kNP * 4, 256) + align_up(size_t(nseg) * 4, 256) +
+                      align_up(size_t(kNP) * 4, 256) + 4096;
+  if (int rc = ensure_workspace(ctx, need, stream)) return rc;
+  Carver cv(ctx->ws.base);
+  float* score = cv.take<float>(N);
+  float* ds = cv.take<float>(N);
+  float* h1 = cv.take<float>(size_t(N) * kH);
+  float* h2 = cv.take<float>(size_t(N) * kH);
+  float* partial = cv.take<float>(size_t(nchunks) * kNP);
+  float* seg_loss = cv.take<float>(nseg);
+  float* g = grad ? grad : cv.take<float>(kNP);
+  {
+    Launch L(ctx, stream, "mlp_train_forward", double(N) * 5248.0 * 2.0);
+    mlp_forward_kernel<<<(N + 255) / 256, 256, 0, stream>>>(params, feat, N, score, h1, h2);
+  }
+  {
+    Launch L(ctx, stream, "mlp_train_loss", double(N) * 8.0);
+    mlp_loss_kernel<<<nseg, 256, 0, stream>>>(score, label, seg_off, nseg, ds, seg_loss);
+  }
+  {
+    Launch L(ctx, stream, "mlp_train_backward", double(N) * 5248.0 * 4.0);
+    cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(BackwardSmem)));
+    mlp_backward_kernel<<<nchunks, 256, sizeof(BackwardSmem), stream>>>(params, feat, h1, h2, ds, N, partial);
+    mlp_reduce_kernel<<<(kNP + 255) / 256, 256, 0, stream>>>(partial, nchunks, seg_loss, nseg, g, loss);
+  }
+  {
+    Launch L(ctx, stream, "mlp_train_adam", double(kNP) * 16.0);
+    adam_kernel<<<(kNP + 255) / 256, 256, 0, stream>>>(params, adam_m, adam_v, g, step, lr, 0.9f, 0.999f, 1e-8f);
+  }
+  return check_launch();
+}
+
+int schulze_certify(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const int32_t* cand, int32_t ncand,
+                    int32_t* winners, int32_t* result, schulze_stream_t stream) {
+  if (!ctx || !d || !cand || !winners || !result || m < 1 || m > kMaxM || n < 0 || ncand < 0 ||
+      ncand > kMaxProposals)
+    return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  const size_t need = learned_ws_bytes(m) + align_up(size_t(m) * kNF * 4, 256) + 2 * align_up(size_t(m) * 4, 256);
+  if (int rc = ensure_workspace(ctx, need, stream)) return rc;
+  const LearnedWs w = carve_learned(ctx->ws.base, m);
+  Carver cv(static_cast<char*>(ctx->ws.base) + learned_ws_bytes(m));
+  float* feat = cv.take<float>(size_t(m) * kNF);
+  int32_t* fwd = cv.take<int32_t>(m);
+  int32_t* bwd = cv.take<int32_t>(m);
+  if (int rc = features_into(ctx, d, m, n, feat, w, stream)) return rc;  // wins / losses for the warm set
+  return certify_launch(ctx, d, m, cand, ncand, winners, result, w, fwd, bwd, stream);
+}
+
+int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const float* params, int32_t top,
+                         int32_t* winners, int32_t* stats, schulze_stream_t stream) {
+  if (!ctx || !d || !winners || m < 1 || m > kMaxM || n < 0 || top < 1 || top > kMaxProposals) return SCHULZE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  const size_t lw = learned_ws_bytes(m);
+  const size_t need = lw + align_up(size_t(m) * kNF * 4, 256) + 2 * align_up(size_t(m) * 4, 256) + 4096;
+  if (int rc = ensure_workspace(ctx, need, stream)) return rc;
+  const LearnedWs w = carve_learned(ctx->ws.base, m);
+  Carver cv(static_cast<char*>(ctx->ws.base) + lw);
+  float* feat = cv.take<float>(size_t(m) * kNF);
+  int32_t* fwd = cv.take<int32_t>(m);
+  int32_t* bwd = cv.take<int32_t>(m);
+  if (int rc = features_into(ctx, d, m, n, feat, w, stream)) return rc;
+  {
+    Launch L(ctx, stream, "proposal_scores", double(m) * 5248.0 * 2.0);
+    if (params)
+      mlp_forward_kernel<<<(m + 255) / 256, 256, 0, stream>>>(params, feat, m, w.score, nullptr, nullptr);
+    else
+      copeland_score_kernel<<<std::max(1, std::min((m + 255) / 256, 1024)), 256, 0, stream>>>(w.acc, m, w.score);
+  }
+  {
+    Launch L(ctx, stream, "proposal_topk", double(m) * 4.0);
+    topk_kernel<<<1, 1024, 0, stream>>>(w.score, m, std::min(top, m), w.cand);
+  }
+  if (int rc = certify_launch(ctx, d, m, w.cand, std::min(top, m), winners, w.res, w, fwd, bwd, stream)) return rc;
+  int32_t res[4] = {0, -1, 0, 0};
+  if (cudaMemcpyAsync(res, w.res, sizeof(res), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  int32_t fallback = 0;
+  if (!res[0]) {
+    // no proposal certified (or the warm set / tie set is too large): the
+    // full closure decides, on workspace memory after the certification data
+    fallback = 1;
+    const size_t mm4 = align_up(size_t(m) * size_t(m) * 4, 256);
+    const size_t stage = std::max(closure_workspace_bytes(m, n, 0), extract_workspace_bytes(m));
+    if (int rc = ensure_workspace(ctx, mm4 + stage + 4096, stream)) return rc;
+    Carver c2(ctx->ws.base);
+    int32_t* p = c2.take<int32_t>(size_t(m) * size_t(m));
+    void* rest = c2.take<char>(0);
+    if (int rc = closure_launch(ctx, d, m, n, p, 0, rest, stream)) return rc;
+    if (int rc = extract_launch(ctx, p, m, winners, nullptr, nullptr, rest, stream)) return rc;
+  }
+  if (stats) {
+    stats[0] = res[0] ? res[1] : -1;  // proposal index that certified
+    stats[1] = fallback;
+    stats[2] = res[2];  // ties checked
+    stats[3] = res[3];  // Bellman-Ford rounds
+  }
+  return SCHULZE_OK;
+}
+
+}  // extern "C"

@@ -74,12 +74,12 @@ def _outputs(b, with_matrices=True):
             z(b.vec_elems), z(b.vec_elems), z(b.vec_elems))
 
 
-@pytest.mark.parametrize("tile_policy,order_policy", [(0, 0), (1, 0), (2, 1)])
-def test_batch_matches_oracle(tile_policy, order_policy):
+@pytest.mark.parametrize("tally_policy,order_policy", [(0, 0), (1, 0), (0, 1)])
+def test_batch_matches_oracle(tally_policy, order_policy):
     els = _mixed_elections()
     n, m, k, flat = _pack(els)
     b = S.SchulzeBatch(n, m, k)
-    b.set_schedule(tile_policy, order_policy)
+    b.set_schedule(tally_policy, order_policy)
     ranks = torch.from_numpy(flat).cuda() if flat.size else torch.zeros(1, dtype=torch.int32, device="cuda")
     outs = _outputs(b)
     b.run(ranks, *outs)
@@ -133,7 +133,7 @@ def test_batch_autotune_keeps_results_exact(tmp_path):
     ranks = torch.from_numpy(bw.ranks).cuda()
     cache = str(tmp_path / "autotune.txt")
     t1, o1 = b.autotune(ranks, cache)
-    assert 0 <= t1 <= 2 and 0 <= o1 <= 1
+    assert 0 <= t1 <= 1 and 0 <= o1 <= 1
     t2, o2 = b.autotune(ranks, cache)  # second call reads the cache
     assert (t1, o1) == (t2, o2)
     outs = _outputs(b)

@@ -228,3 +228,15 @@ def learned_eval(E: int = 256, seed: int = SEED_BASE + 5, m: int = 8192, n: int 
                  phi: float = 0.9, **kw) -> Batch:
     """Evaluation set: E elections of m=8192, n=20000, top-50 Mallows phi=0.9."""
     return learned_elections(E, seed, (m, m), (n, n), (k, k), (phi, phi), **kw)
+
+
+def mlp_init(seed: int = SEED_BASE + 6) -> np.ndarray:
+    """Initial weights of the 16-64-64-1 proposal network (5313 float32):
+    He-normal weights, zero biases; a seeded draw, fed to both the GPU
+    training and its float64 reference."""
+    rs = np.random.Generator(np.random.PCG64(seed))
+    theta = np.zeros(5313)
+    theta[0:1024] = rs.normal(0, np.sqrt(2.0 / 16), 1024)
+    theta[1088:5184] = rs.normal(0, np.sqrt(2.0 / 64), 4096)
+    theta[5248:5312] = rs.normal(0, np.sqrt(1.0 / 64), 64)
+    return theta.astype(np.float32)
