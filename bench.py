@@ -36,6 +36,8 @@ WORKLOADS = {
     "huge_pl": dict(desc="m=16384, n=200000, top-20 Plackett-Luce Zipf(1.1), int32 closure"),
     "batch_mixed": dict(desc="4096 elections, m~U[8,512], n~U[50,5000], full rankings, half Mallows "
                              "(phi~U[0.5,1]) half impartial culture, one persistent launch"),
+    "learned": dict(desc="proposal network trained on 2000 GPU-solved top-k Mallows elections; "
+                         "32 evaluation elections m=8192, n=20000, top-50, phi=0.9"),
 }
 
 
@@ -78,6 +80,74 @@ def time_oracle_batch(b, nthreads: int):
     for e in range(b.E):
         oracle.schulze(b.election(e).ranks, int(b.m[e]), nthreads=nthreads)
     return time.perf_counter() - t0
+
+
+def run_learned(args, world, rank, local):
+    """Learned winner proposals: train the proposal network on GPU-solved
+    elections (m~U[256,2048], n~U[1000,20000], top-k k~U[10,100], Mallows
+    phi~U[0.6,1]), then on evaluation elections (m=8192, n=20000, top-50,
+    phi=0.9) time exact winner determination from the tally by (a) the full
+    closure + winners, (b) certified MLP proposals, (c) certified Copeland
+    proposals. Winner sets of (b) and (c) must equal (a) on every election."""
+    import torch
+    import paper_2505_12976_gb300 as S
+    from paper_2505_12976_gb300 import learned as L
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    ctx = S.context(local)
+    t_start = time.perf_counter()
+    data = L.Dataset(dev)
+    chunk = 256
+    for c0 in range(0, args.train_elections, chunk):
+        tb = W.learned_train(E=min(chunk, args.train_elections - c0), seed=W.SEED_BASE + 4 + 7919 * c0)
+        for e in range(tb.E):
+            data.add(torch.from_numpy(tb.election(e).ranks).to(dev), int(tb.m[e]))
+    t_data = time.perf_counter() - t_start
+    trainer = L.Trainer(W.mlp_init(), seed=W.SEED_BASE + 6)
+    t0 = time.perf_counter()
+    hist = trainer.train(data, epochs=args.epochs, elections_per_step=64, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ev = W.learned_eval(E=args.eval_elections, m=args.m or 8192, n=args.n or 20000)
+    rows = []
+    for e in range(ev.E):
+        r = torch.from_numpy(ev.election(e).ranks).to(dev)
+        d = S.schulze_tally(r, int(ev.m[e]), ctx=ctx)
+        if e == 0:  # warm-up of both paths
+            L.compare_on(d, int(ev.n[e]), trainer.params, ctx=ctx)
+            L.compare_on(d, int(ev.n[e]), None, ctx=ctx)
+        a = L.compare_on(d, int(ev.n[e]), trainer.params, ctx=ctx)
+        b = L.compare_on(d, int(ev.n[e]), None, ctx=ctx)
+        rows.append({"agree_mlp": bool(torch.equal(a["closure_winners"], a["fast_winners"])),
+                     "agree_copeland": bool(torch.equal(b["closure_winners"], b["fast_winners"])),
+                     "closure_ms": a["closure_ms"], "mlp_ms": a["fast_ms"], "copeland_ms": b["fast_ms"],
+                     "mlp_hit": a["stats"][0], "mlp_fallback": a["stats"][1],
+                     "copeland_hit": b["stats"][0], "copeland_fallback": b["stats"][1]})
+    E = len(rows)
+    closure_ms = sum(x["closure_ms"] for x in rows) / E
+    mlp_ms = sum(x["mlp_ms"] for x in rows) / E
+    cop_ms = sum(x["copeland_ms"] for x in rows) / E
+    line = {"metric": METRIC + " (learned-proposal workload: elections/sec of exact winner determination)",
+            "value": 1e3 / mlp_ms, "unit": "elections/s", "n_gpus": 1, "steps": E, "warmup": 1,
+            "ms_per_step": mlp_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32+fp32", "data": "synthetic",
+            "config": {"workload": "learned", "train_elections": len(data), "epochs": args.epochs,
+                       "eval": f"{E} elections, m={int(ev.m[0])}, n={int(ev.n[0])}, top-{int(ev.k[0])} Mallows "
+                               "phi=0.9", "proposals": 4},
+            "agreement_mlp": sum(x["agree_mlp"] for x in rows) / E,
+            "agreement_copeland": sum(x["agree_copeland"] for x in rows) / E,
+            "closure_ms_per_election": closure_ms, "mlp_ms_per_election": mlp_ms,
+            "copeland_ms_per_election": cop_ms, "speedup_mlp_vs_closure": closure_ms / mlp_ms,
+            "mlp_top1_hit_rate": sum(x["mlp_hit"] == 0 for x in rows) / E,
+            "mlp_fallback_rate": sum(x["mlp_fallback"] for x in rows) / E,
+            "copeland_top1_hit_rate": sum(x["copeland_hit"] == 0 for x in rows) / E,
+            "copeland_fallback_rate": sum(x["copeland_fallback"] for x in rows) / E,
+            "train": {"seconds": t_train, "data_seconds": t_data, "loss_first_epoch": hist[0],
+                      "loss_last_epoch": hist[-1]},
+            "device_status": ctx.status()}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_batch(args, world, rank, local):
@@ -283,6 +353,9 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="override the workload's candidate count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's ballot count")
     ap.add_argument("--batch-size", type=int, default=4096, help="elections of the batch_mixed workload")
+    ap.add_argument("--train-elections", type=int, default=2000, help="training elections (learned workload)")
+    ap.add_argument("--eval-elections", type=int, default=32, help="evaluation elections (learned workload)")
+    ap.add_argument("--epochs", type=int, default=20, help="training epochs (learned workload)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -303,6 +376,8 @@ def main():
 
     if args.workload == "batch_mixed":
         return run_batch(args, world, rank, local)
+    if args.workload == "learned":
+        return run_learned(args, world, rank, local)
     e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)

@@ -539,9 +539,9 @@ __global__ void __launch_bounds__(1024) certify_kernel(const int32_t* __restrict
   if (threadIdx.x == 0) res[0] = 0, res[1] = -1, res[2] = 0, res[3] = 0;
   __syncthreads();
   if (nw > kCertifyMaxWarm) return;  // closure decides
-  if (nw == 0) {  // no edges at all: every candidate is a winner
+  if (nw == 0) {  // no edges at all: every candidate is a winner, so the first proposal certifies
     for (int32_t c = threadIdx.x; c < m; c += blockDim.x) winners[c] = 1;
-    if (threadIdx.x == 0) res[0] = 1;
+    if (threadIdx.x == 0) res[0] = 1, res[1] = ncand > 0 ? 0 : -1;
     return;
   }
   int32_t rounds = 0;
