@@ -59,6 +59,7 @@ enum schulze_status {
 /* Tally flags (schulze_tally, schulze_run). */
 #define SCHULZE_F_TALLY_DENSE 4u  /* position-compare tally, O(n m^2) */
 #define SCHULZE_F_TALLY_SPARSE 8u /* pair-count tally, O(n k^2) */
+#define SCHULZE_F_TALLY_GROUPED 16u /* pair-count tally without the listed-candidate compaction */
 
 /* Human-readable text for a status code (static storage). */
 const char* schulze_strerror(int code);
@@ -90,7 +91,9 @@ int schulze_get_status(schulze_ctx* ctx, int32_t* status, schulze_stream_t strea
  *          all listed ones.
  *   d      [m, m] int32 device output: d[i][j] = #voters preferring i to j,
  *          d[i][i] = 0. Overwritten completely.
- *   flags  0 (choose by cost), SCHULZE_F_TALLY_DENSE or SCHULZE_F_TALLY_SPARSE.
+ *   flags  0 (choose by cost), SCHULZE_F_TALLY_DENSE or SCHULZE_F_TALLY_SPARSE;
+ *          SCHULZE_F_TALLY_GROUPED keeps the pair-count tally on its grouped
+ *          form even when few candidates are listed (same result).
  * Sizes: 1 <= m <= 65535, 0 <= k <= m, 0 <= n < 2^31, n*k < 2^32.
  * Bad ids are reported as SCHULZE_EDATA through schulze_get_status().
  */

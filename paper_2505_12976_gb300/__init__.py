@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libschulze.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDATA, ETIMEOUT, ERANGE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
-F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE = 0, 1, 2, 4, 8
+F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE, F_TALLY_GROUPED = 0, 1, 2, 4, 8, 16
 
 _lock = threading.Lock()
 _lib = None

@@ -10,7 +10,18 @@
 // closure commutes with relabeling, and rows without edges stay zero, so
 // their tiles are never touched.
 //
-// The closure runs on W in rounds of B = 64 candidates; round r
+// Only the candidates with edges (the "warm" ones, nw of them) need work:
+// rows of cold candidates are zero in W and in p. W holds the warm rows only
+// (padded to whole tiles), over all relabeled columns; warm columns come
+// first. The closure has two parts:
+//   * the warm square (nw x nw): paths between warm candidates never pass a
+//     cold one (no outgoing edges), so it is the closure of W restricted to
+//     them: one CTA for up to kSmallTiles tile rows, else the persistent
+//     kernel below;
+//   * the cold columns: p[i][c] = max(w[i][c], max_x min(p[i][x], w[x][c]))
+//     over warm x, one (max, min) product with the closed warm square.
+//
+// The warm-square closure runs in rounds of B = 64 candidates; round r
 //   1. closes the diagonal tile (r, r) by plain Floyd-Warshall,
 //   2. updates the row and column panels: X = max(X, D (x) X) / max(X, X (x) D)
 //      with D the closed diagonal tile,
@@ -28,11 +39,14 @@
 // item waits (bounded, clock-limited spin) until the tiles it reads have
 // reached its round. Every wait is on an item earlier in the queue, which a
 // resident CTA already holds, so the schedule cannot deadlock.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
 #include "tiles.cuh"
+#include "scan.cuh"
 
 namespace schulze {
 namespace {
@@ -50,113 +64,173 @@ constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
 // ------------------------------------------------------------ relabel
 
 // rowflag[i] = 1 iff candidate i has an outgoing edge (some j with
-// d[i][j] > d[j][i]). One CTA per 32 x 32 block pair (A, B), A <= B, reading
-// each d entry once.
-__global__ void rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int32_t* __restrict__ rowflag) {
-  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
-  if (A > B) return;
-  __shared__ int32_t t1[32][33], t2[32][33];  // t1 = d[A.., B..], t2 = d[B.., A..]
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int32_t i = A + r, j = B + threadIdx.x;
-    t1[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
-    i = B + r, j = A + threadIdx.x;
-    t2[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+// d[i][j] > d[j][i]); also reports SCHULZE_EDATA for an entry outside
+// [0, bound]. Each CTA takes 64 x 64 block pairs (A, B), A <= B: thread
+// (r, c) holds d[A+r][B+c..c+3] and d[B+r][A+c..c+3] in registers (16-byte
+// loads when rows are 16-byte aligned), both tiles go to shared memory, and
+// each held entry is compared with its transposed partner from there.
+constexpr int kFlagT = 64;
+__global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int64_t bound,
+                                                      int32_t* __restrict__ rowflag, int32_t* status) {
+  __shared__ int32_t t1[kFlagT][kFlagT + 1], t2[kFlagT][kFlagT + 1];  // t1 = d[A.., B..], t2 = d[B.., A..]
+  const int32_t nbt = (m + kFlagT - 1) / kFlagT;
+  const int64_t npairs = int64_t(nbt) * (nbt + 1) / 2;
+  const int lane = threadIdx.x & 31;
+  const int rq = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;  // rows rq + 16 q, columns c4 .. c4 + 3
+  const bool vec = (m & 3) == 0;
+  int32_t a = 0;           // pairs (a, b), a <= b, numbered row by row
+  int64_t rowstart = 0;    // number of the pair (a, a)
+  bool bad = false;
+  for (int64_t t = blockIdx.x; t < npairs; t += gridDim.x) {
+    while (t >= rowstart + (nbt - a)) rowstart += nbt - a, ++a;
+    const int32_t A = a * kFlagT, B = (a + int32_t(t - rowstart)) * kFlagT;
+    int32_t x1[4][4], x2[4][4];
+    auto load = [&](int32_t R, int32_t Cc, int32_t (&x)[4][4]) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t i = R + rq + 16 * q, j = Cc + c4;
+        if (vec) {
+          int4 v = make_int4(0, 0, 0, 0);
+          if (i < m && j < m) v = __ldcs(reinterpret_cast<const int4*>(d + int64_t(i) * m + j));
+          x[q][0] = v.x, x[q][1] = v.y, x[q][2] = v.z, x[q][3] = v.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) x[q][e] = (i < m && j + e < m) ? d[int64_t(i) * m + j + e] : 0;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) bad |= x[q][e] < 0 || int64_t(x[q][e]) > bound;
+      }
+    };
+    load(A, B, x1);
+    if (A != B) load(B, A, x2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        t1[rq + 16 * q][c4 + e] = x1[q][e];
+        if (A != B) t2[rq + 16 * q][c4 + e] = x2[q][e];
+      }
+    __syncthreads();
+    // side 0: row A + r, columns B + c: edge when t1[r][c] > (t2 or t1)[c][r]
+    // side 1: row B + r, columns A + c: edge when t2[r][c] > t1[c][r]
+    const int32_t(*T)[kFlagT + 1] = A == B ? t1 : t2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = rq + 16 * q;
+      bool e0 = false, e1 = false;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = c4 + e;
+        e0 |= (A + r != B + c) && x1[q][e] > T[c][r];
+        if (A != B) e1 |= x2[q][e] > t1[c][r];
+      }
+      // padding entries are 0 on both sides, so they never count
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, e0), b1 = __ballot_sync(0xFFFFFFFFu, e1);
+      if ((lane & 15) == 0) {
+        const uint32_t sh = lane & 16;
+        if ((b0 >> sh) & 0xFFFFu) atomicOr(&rowflag[A + r], 1);
+        if ((b1 >> sh) & 0xFFFFu) atomicOr(&rowflag[B + r], 1);
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    // row A + r: edge to B + c when t1[r][c] > t2[c][r]
-    int32_t i = A + r, j = B + threadIdx.x;
-    bool e1 = i < m && j < m && i != j && t1[r][threadIdx.x] > t2[threadIdx.x][r];
-    if (__any_sync(0xFFFFFFFFu, e1) && threadIdx.x == 0 && i < m) atomicOr(&rowflag[i], 1);
-    // row B + r: edge to A + c when t2[r][c] > t1[c][r]
-    i = B + r, j = A + threadIdx.x;
-    bool e2 = i < m && j < m && i != j && t2[r][threadIdx.x] > t1[threadIdx.x][r];
-    if (__any_sync(0xFFFFFFFFu, e2) && threadIdx.x == 0 && i < m) atomicOr(&rowflag[i], 1);
-  }
+  if (bad) set_status(status, SCHULZE_EDATA);
 }
 
 // Stable partition: perm[new] = old, candidates with edges first; inv[old] = new.
 __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict__ rowflag, int32_t m,
                                                        int32_t* __restrict__ perm, int32_t* __restrict__ inv,
                                                        int32_t* __restrict__ warm_out) {
-  __shared__ int32_t part[1024];
-  const int T = blockDim.x;
-  const int per = (m + T - 1) / T;
-  const int b = threadIdx.x * per, e = min(m, b + per);
-  int32_t s = 0;
-  for (int c = b; c < e; ++c) s += rowflag[c] ? 1 : 0;
-  part[threadIdx.x] = s;
+  __shared__ uint32_t part[32];
+  // inv[c] = 1 for warm c, scanned in place into the warm rank
+  uint32_t* rank = reinterpret_cast<uint32_t*>(inv);
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) rank[c] = rowflag[c] ? 1u : 0u;
   __syncthreads();
-  for (int o = 1; o < T; o <<= 1) {
-    int32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += x;
-    __syncthreads();
-  }
-  const int32_t warm = part[T - 1];
+  const int32_t warm = int32_t(block_exclusive_scan(rank, m, part));
   if (threadIdx.x == 0) *warm_out = warm;
-  int32_t before = threadIdx.x ? part[threadIdx.x - 1] : 0;  // warm candidates before b
-  for (int c = b; c < e; ++c) {
-    int32_t nw;
-    if (rowflag[c]) {
-      nw = before++;
-    } else {
-      nw = warm + (c - before);  // cold ones keep their order after the warm ones
-    }
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+    const int32_t before = int32_t(rank[c]);                 // warm candidates before c
+    const int32_t nw = rowflag[c] ? before : warm + (c - before);  // cold ones keep their order
     perm[nw] = c;
     inv[c] = nw;
   }
 }
 
-// ---------------------------------------------------------------- pack
-
-// W[a][b] = w[perm[a]][perm[b]] (0 outside m x m, on the diagonal and where
-// d does not beat its transpose). One CTA per 32 x 32 block pair (A, B),
-// A <= B, writing both W[A][B] and W[B][A]; a warp that writes a nonzero sets
-// the nonzero bit of its 64 x 64 tile's progress word.
+// W[a][b] = w[perm[a]][perm[b]] for the warm rows a < 64 * nbr (0 outside
+// m x m, on the diagonal and where d does not beat its transpose). CTAs take
+// 32 x 32 block pairs (X, Y), X <= Y and X inside the warm rows, writing
+// W[X][Y] and, when Y is inside them too, W[Y][X]; a warp that writes a
+// nonzero sets the nonzero bit of its 64 x 64 tile's progress word.
 template <typename E>
-__global__ void pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp, int64_t bound,
-                            const int32_t* __restrict__ perm, E* __restrict__ W, uint32_t* __restrict__ prog,
-                            int32_t nb, int32_t* status) {
-  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
-  if (A > B) return;
-  __shared__ int32_t t1[32][33], t2[32][33];  // t1[r][c] = d[perm[A+r]][perm[B+c]], t2 = (B, A)
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int32_t a = A + r, b = B + threadIdx.x;
-    t1[r][threadIdx.x] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
-    a = B + r, b = A + threadIdx.x;
-    t2[r][threadIdx.x] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int32_t a = (side ? B : A) + r, b = (side ? A : B) + threadIdx.x;
-      const int32_t x = side ? t2[r][threadIdx.x] : t1[r][threadIdx.x];
-      const int32_t y = side ? t1[threadIdx.x][r] : t2[threadIdx.x][r];
-      int32_t out = 0;
-      if (a < m && b < m) {
-        if (x < 0 || int64_t(x) > bound) set_status(status, SCHULZE_EDATA);
-        if (a != b && x > y) out = x;
-      }
-      if (a < mp && b < mp) W[int64_t(a) * mp + b] = E(out);
-      if (__any_sync(0xFFFFFFFFu, out != 0) && threadIdx.x == 0)
-        atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
-      if (A == B) break;  // a diagonal block pair is one block
+__global__ void __launch_bounds__(256) pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp,
+                                                   const int32_t* __restrict__ perm, const int32_t* __restrict__ warm,
+                                                   E* __restrict__ W, uint32_t* __restrict__ prog, int32_t nb) {
+  __shared__ int32_t t1[32][33], t2[32][33];  // t1[r][c] = d[perm[X+r]][perm[Y+c]], t2 = (Y, X)
+  const int32_t rows = (*warm + kB - 1) / kB * kB;  // W rows to write
+  const int32_t nx = rows / 32, ny = mp / 32;
+  const int64_t items = int64_t(nx) * ny;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+    const int32_t X = int32_t(t / ny) * 32, Y = int32_t(t % ny) * 32;
+    if (X > Y) continue;
+    for (int r = ty; r < 32; r += 8) {
+      int32_t a = X + r, b = Y + tx;
+      t1[r][tx] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
+      a = Y + r, b = X + tx;
+      t2[r][tx] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
     }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int32_t a = (side ? Y : X) + r, b = (side ? X : Y) + tx;
+        if (side && Y >= rows) break;  // row block outside W
+        const int32_t x = side ? t2[r][tx] : t1[r][tx];
+        const int32_t y = side ? t1[tx][r] : t2[tx][r];
+        const int32_t out = (a < m && b < m && a != b && x > y) ? x : 0;
+        if (b < mp) W[int64_t(a) * mp + b] = E(out);
+        if (__any_sync(0xFFFFFFFFu, out != 0) && tx == 0) atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
+        if (X == Y) break;  // a diagonal block pair is one block
+      }
+    }
+    __syncthreads();
   }
 }
 
-// p[x][y] = W[inv[x]][inv[y]] for x != y < m; p[x][x] = 0.
+// p[x][y] = W[inv[x]][inv[y]] for warm x and y != x; every other entry 0
+// (cold rows are written as zeros without reading W). One row per CTA pass.
 template <typename E>
-__global__ void widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m, const int32_t* __restrict__ inv,
-                             int32_t* __restrict__ p) {
-  const int32_t x = blockIdx.y;
-  const int32_t ix = inv[x];
-  const E* wrow = W + int64_t(ix) * mp;
-  int32_t* prow = p + int64_t(x) * m;
-  for (int32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < m; y += gridDim.x * blockDim.x)
-    prow[y] = (y == x) ? 0 : int32_t(wrow[inv[y]]);
+__global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
+                                                    const int32_t* __restrict__ inv,
+                                                    const int32_t* __restrict__ warm, int32_t* __restrict__ p) {
+  const int32_t nw = *warm;
+  for (int32_t x = blockIdx.x; x < m; x += gridDim.x) {
+    const int32_t ix = inv[x];
+    int32_t* prow = p + int64_t(x) * m;
+    if (ix >= nw) {
+      if ((m & 3) == 0) {
+        for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x)
+          *reinterpret_cast<int4*>(prow + y) = make_int4(0, 0, 0, 0);
+      } else {
+        for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = 0;
+      }
+      continue;
+    }
+    const E* wrow = W + int64_t(ix) * mp;
+    if ((m & 3) == 0) {
+      for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x) {
+        const int4 iv = *reinterpret_cast<const int4*>(inv + y);
+        int4 v = make_int4(int32_t(wrow[iv.x]), int32_t(wrow[iv.y]), int32_t(wrow[iv.z]), int32_t(wrow[iv.w]));
+        if (x >= y && x < y + 4) {
+          const int32_t t = x - y;
+          v.x = t == 0 ? 0 : v.x, v.y = t == 1 ? 0 : v.y, v.z = t == 2 ? 0 : v.z, v.w = t == 3 ? 0 : v.w;
+        }
+        *reinterpret_cast<int4*>(prow + y) = v;
+      }
+    } else {
+      for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = (y == x) ? 0 : int32_t(wrow[inv[y]]);
+    }
+  }
 }
 
 // ----------------------------------------------------- work queue
@@ -169,8 +243,9 @@ struct Item {
 // The candidates with outgoing edges occupy the first nbr tile rows after
 // relabeling; the other rows of W are zero and stay zero, and a round over a
 // block of them cannot change anything (min(x, 0) = 0). So rounds run over
-// r < nbr and only tile rows i < nbr are updated, against all nb tile
-// columns: nbr * nbr * nb items in total.
+// r < nbr and only tile rows i < nbr are updated. The queue is written for
+// nc >= nbr tile columns (nbr * nbr * nc items); the closure runs it on the
+// warm square (nc = nbr) and leaves the cold columns to cold_product_kernel.
 //
 // Queue order, stage by stage:
 //   stage 0:             D(0) P(0) L(0)
@@ -309,6 +384,12 @@ __device__ __forceinline__ void publish(const Sync& sy, int32_t idx, uint32_t wo
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sy.prog + idx), "r"(word) : "memory");
 }
 
+// Warm squares up to this size are closed by closure_cluster_kernel (the
+// square must fit one CTA's shared memory), larger ones by the persistent
+// kernel.
+template <typename E>
+constexpr int32_t kClusterMaxWarm = sizeof(E) == 2 ? 256 : 192;
+
 template <typename E>
 __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
                                                                        Sync sy) {
@@ -318,8 +399,9 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
   __shared__ uint32_t s_flags;
   constexpr uint32_t kFail = 0xFFFFFFFFu;
   const int32_t nbr = (*sy.warm + kB - 1) / kB;
-  const Shape sh = make_shape(nbr, nb);
-  const int64_t total_items = int64_t(nbr) * nbr * nb;
+  if (*sy.warm <= kClusterMaxWarm<E>) return;  // closure_cluster_kernel's case
+  const Shape sh = make_shape(nbr, nbr);  // the warm square; nb is the progress-word row stride
+  const int64_t total_items = int64_t(nbr) * nbr * nbr;
   for (;;) {
     if (threadIdx.x == 0) {
       const int64_t t = int64_t(atomicAdd(sy.head, 1u));
@@ -374,49 +456,266 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
   }
 }
 
+// Warm squares of at most kClusterMaxWarm candidates: blocked Floyd-Warshall
+// with 32 x 32 tiles on a cluster of kClusterCtas CTAs (one per SM). Every
+// CTA holds the whole square S (n = nw rounded up to 64, so that it covers
+// whole 64-wide tiles of W) in shared memory. Round r:
+//   1. every CTA closes the diagonal tile (r, r) of its own copy (the same
+//      result everywhere, so nothing is exchanged);
+//   2. the panel tiles (r, j) and (i, r) are shared out among the CTAs; each
+//      owner updates its tiles and writes them into every copy (distributed
+//      shared memory); cluster barrier;
+//   3. the other tiles likewise; cluster barrier.
+// A tile is written by one owner per phase and read by no other CTA in that
+// phase, so the copies stay identical. Rows of cold candidates are zero, so
+// rounds and tile rows stop at the warm ones; columns run over all of S.
+// CTA rank q then writes rows q, q + kClusterCtas, ... of S back into W and
+// sets the nonzero bits of the 64 x 64 tiles of W for cold_product_kernel.
+constexpr int kCB = 32;               // tile size of the cluster closure
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;  // one 16-bit pair (or two int32 entries) of a tile per thread
+
+// Thread t of a 32 x 32 tile owns row t / 16, entries 2 (t % 16) and
+// 2 (t % 16) + 1: one 32-bit word of 16-bit lanes, or two int32 entries.
 template <typename E>
-int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
-                cudaStream_t stream) {
+struct CTile;
+template <>
+struct CTile<int16_t> {
+  using Word = uint32_t;
+  static __device__ __forceinline__ uint32_t dup(uint32_t h) { return (h & 0xFFFFu) | (h << 16); }
+  static __device__ __forceinline__ int64_t word_index(int32_t n, int32_t ti, int32_t tj, int t) {
+    return int64_t(ti * kCB + (t >> 4)) * (n >> 1) + tj * (kCB / 2) + (t & 15);
+  }
+  // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): the new word of thread t
+  static __device__ __forceinline__ Word product(const int16_t* S, int32_t n, int32_t ti, int32_t tj, int32_t tr,
+                                                 int t) {
+    const uint32_t* Sw = reinterpret_cast<const uint32_t*>(S);
+    const int32_t nw2 = n >> 1;
+    const uint32_t* arow = Sw + int64_t(ti * kCB + (t >> 4)) * nw2 + tr * (kCB / 2);
+    const uint32_t* bcol = Sw + int64_t(tr * kCB) * nw2 + tj * (kCB / 2) + (t & 15);
+    uint32_t acc = Sw[word_index(n, ti, tj, t)];
+#pragma unroll 4
+    for (int kk = 0; kk < kCB; kk += 2) {
+      const uint32_t a = arow[kk >> 1];
+      const uint32_t b0 = bcol[int64_t(kk) * nw2], b1 = bcol[int64_t(kk + 1) * nw2];
+      acc = __vimax3_s16x2(acc, __vmins2(dup(a), b0), __vmins2(dup(a >> 16), b1));
+    }
+    return acc;
+  }
+  // Floyd-Warshall step k inside diagonal tile (r, r): the new word of thread t
+  static __device__ __forceinline__ Word fw_step(const int16_t* S, int32_t n, int32_t r, int k, int t) {
+    const int32_t i = r * kCB + (t >> 4);
+    const uint32_t a = dup(uint32_t(uint16_t(S[int64_t(i) * n + r * kCB + k])));
+    const uint32_t b = reinterpret_cast<const uint32_t*>(S)[int64_t(r * kCB + k) * (n >> 1) + r * (kCB / 2) + (t & 15)];
+    const uint32_t own = reinterpret_cast<const uint32_t*>(S)[word_index(n, r, r, t)];
+    return __vmaxs2(own, __vmins2(a, b));
+  }
+  static __device__ __forceinline__ bool any(Word v) { return v != 0u; }
+};
+template <>
+struct CTile<int32_t> {
+  using Word = int2;
+  static __device__ __forceinline__ int64_t word_index(int32_t n, int32_t ti, int32_t tj, int t) {
+    return int64_t(ti * kCB + (t >> 4)) * (n >> 1) + tj * (kCB / 2) + (t & 15);
+  }
+  static __device__ __forceinline__ Word product(const int32_t* S, int32_t n, int32_t ti, int32_t tj, int32_t tr,
+                                                 int t) {
+    const int2* Sw = reinterpret_cast<const int2*>(S);
+    const int32_t nw2 = n >> 1;
+    const int2* arow = Sw + int64_t(ti * kCB + (t >> 4)) * nw2 + tr * (kCB / 2);
+    const int2* bcol = Sw + int64_t(tr * kCB) * nw2 + tj * (kCB / 2) + (t & 15);
+    int2 acc = Sw[word_index(n, ti, tj, t)];
+#pragma unroll 4
+    for (int kk = 0; kk < kCB; kk += 2) {
+      const int2 a = arow[kk >> 1];
+      const int2 b0 = bcol[int64_t(kk) * nw2], b1 = bcol[int64_t(kk + 1) * nw2];
+      acc.x = __vimax3_s32(acc.x, min(a.x, b0.x), min(a.y, b1.x));
+      acc.y = __vimax3_s32(acc.y, min(a.x, b0.y), min(a.y, b1.y));
+    }
+    return acc;
+  }
+  static __device__ __forceinline__ Word fw_step(const int32_t* S, int32_t n, int32_t r, int k, int t) {
+    const int32_t i = r * kCB + (t >> 4);
+    const int32_t a = S[int64_t(i) * n + r * kCB + k];
+    const int2 b = reinterpret_cast<const int2*>(S)[int64_t(r * kCB + k) * (n >> 1) + r * (kCB / 2) + (t & 15)];
+    const int2 own = reinterpret_cast<const int2*>(S)[word_index(n, r, r, t)];
+    return make_int2(max(own.x, min(a, b.x)), max(own.y, min(a, b.y)));
+  }
+  static __device__ __forceinline__ bool any(Word v) { return (v.x | v.y) != 0; }
+};
+
+template <typename E>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 1)
+    closure_cluster_kernel(E* __restrict__ W, int32_t ld, int32_t nb, const int32_t* __restrict__ warm,
+                           uint32_t* __restrict__ prog, unsigned long long* counters) {
+  using T = CTile<E>;
+  using Word = typename T::Word;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int32_t nw = *warm;
+  if (nw == 0 || nw > kClusterMaxWarm<E>) return;  // the same branch in every CTA
+  extern __shared__ __align__(16) unsigned char cluster_smem[];
+  E* S = reinterpret_cast<E*>(cluster_smem);
+  __shared__ uint32_t tnz[4][4];  // 64 x 64 tiles of W holding a nonzero
+  const int32_t n = (nw + kB - 1) / kB * kB;  // square side: whole 64-wide tiles
+  const int32_t nt = n / kCB, ntw = (nw + kCB - 1) / kCB;  // tiles, tiles with warm rows
+  const int t = threadIdx.x;
+  const unsigned q = cl.block_rank();
+  constexpr int kPer16 = 16 / sizeof(E);  // entries per 16-byte piece
+  for (int32_t e = t; e < n * (n / kPer16); e += blockDim.x) {
+    const int32_t i = e / (n / kPer16), c = e % (n / kPer16);
+    reinterpret_cast<uint4*>(S)[e] = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(i) * ld) + c);
+  }
+  if (t < 16) tnz[t >> 2][t & 3] = 0u;
+  cl.sync();  // every copy loaded before any remote write
+  Word* remote[kClusterCtas];
+#pragma unroll
+  for (int c = 0; c < kClusterCtas; ++c) remote[c] = reinterpret_cast<Word*>(cl.map_shared_rank(S, c));
+  auto store_all = [&](int32_t ti, int32_t tj, Word v) {
+    const int64_t off = T::word_index(n, ti, tj, t);
+#pragma unroll
+    for (int c = 0; c < kClusterCtas; ++c) remote[c][off] = v;
+  };
+  Word* Sw = reinterpret_cast<Word*>(S);
+  unsigned long long ops = 0;
+  for (int32_t r = 0; r < ntw; ++r) {
+    // 1. diagonal tile, in every CTA; row k and column k do not change in
+    //    step k, so one barrier per step
+    for (int k = 0; k < kCB; ++k) {
+      const Word v = T::fw_step(S, n, r, k, t);
+      Sw[T::word_index(n, r, r, t)] = v;
+      __syncthreads();
+    }
+    // 2. panels: (r, j) for j != r, j < nt, then (i, r) for i != r, i < ntw
+    const int32_t np = (nt - 1) + (ntw - 1);
+    for (int32_t p = q; p < np; p += kClusterCtas) {
+      int32_t ti = r, tj = r;
+      if (p < nt - 1)
+        tj = p + (p >= r);
+      else
+        ti = (p - (nt - 1)) + ((p - (nt - 1)) >= r);
+      const Word v = T::product(S, n, ti, tj, r, t);
+      __syncthreads();  // the tile is its own operand: read it all before writing
+      store_all(ti, tj, v);
+      __syncthreads();
+      ++ops;
+    }
+    cl.sync();
+    // 3. the other tiles: i != r (i < ntw), j != r (j < nt)
+    const int32_t nr = (ntw - 1) * (nt - 1);
+    for (int32_t p = q; p < nr; p += kClusterCtas) {
+      const int32_t a = p / (nt - 1), b = p % (nt - 1);
+      const int32_t ti = a + (a >= r), tj = b + (b >= r);
+      store_all(ti, tj, T::product(S, n, ti, tj, r, t));  // operands are other tiles
+      ++ops;
+    }
+    cl.sync();
+  }
+  // write back rows q, q + 8, ... with a zero diagonal; nonzero bits per
+  // 64 x 64 tile of W
+  for (int32_t i = q; i < n; i += kClusterCtas) {
+    for (int32_t j = t; j < n; j += blockDim.x) {
+      const E v = i == j ? E(0) : S[int64_t(i) * n + j];
+      W[int64_t(i) * ld + j] = v;
+      if (v) tnz[i / kB][j / kB] = 1u;
+    }
+  }
+  __syncthreads();
+  if (t < 16 && tnz[t >> 2][t & 3]) atomicOr(&prog[(t >> 2) * nb + (t & 3)], kNZ);
+  if (t == 0 && q == 0) atomicAdd(&counters[1], 1ull * ntw);
+  if (t == 0 && ops) atomicAdd(&counters[0], (ops + 7) / 8);  // in 64 x 64 x 64 tile units
+  cl.sync();  // no CTA leaves while others may still write into it
+}
+
+// Cold columns: X(i, j) = max(X, W(i, k) (x) W(k, j)) for every warm tile row
+// i, cold tile column j and warm k, with the warm square already closed. Each
+// (i, j) is one work item (a 128-thread CTA applies its k in order). An item
+// may read a W(k, j) that another item is raising at the same time; every
+// value either one sees is the width of a real path and the closed square
+// composes with itself without growing (p(i,x) and p(x,y) give a walk no
+// wider than p(i,y)), so the result is the exact closure either way.
+template <typename E>
+__global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
+                                                                 const int32_t* __restrict__ warm,
+                                                                 const uint32_t* __restrict__ prog,
+                                                                 unsigned long long* counters) {
+  __shared__ __align__(16) typename Ops<E>::Smem sm;
+  const int32_t nbr = (*warm + kB - 1) / kB;
+  const int32_t nc = nb - nbr;
+  const int64_t items = int64_t(nbr) * nc;
+  unsigned long long done = 0;
+  for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+    const int32_t i = int32_t(t / nc), j = nbr + int32_t(t % nc);
+    for (int32_t k = 0; k < nbr; ++k) {
+      const uint32_t a = prog[i * nb + k], b = prog[k * nb + j];
+      if ((a & kNZ) && (b & kNZ)) {
+        Ops<E>::update(W, ld, i, j, k, sm, threadIdx.x, BlockBarrier{});
+        ++done;
+      }
+    }
+  }
+  if (threadIdx.x == 0 && done) atomicAdd(&counters[0], done);
+}
+
+// Scratch of one closure: W (warm rows x all columns, padded square), the
+// progress words, queue head, abort flag, and the relabeling.
+struct ClosureBufs {
+  void* W;
+  uint32_t* prog;
+  int32_t *rowflag, *perm, *inv, *warm;
+  unsigned long long* counters;
+};
+
+// Rowflags, relabel, pack, closure of the warm square, cold product, widen.
+// ctx may be null (no counting, no profiling).
+template <typename E>
+int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
-  Carver cv(ws);
-  E* W = cv.take<E>(size_t(mp) * size_t(mp));
-  uint32_t* prog = cv.take<uint32_t>(size_t(nb) * size_t(nb) + 2);
-  int32_t* rowflag = cv.take<int32_t>(size_t(m));
-  int32_t* perm = cv.take<int32_t>(size_t(m));
-  int32_t* inv = cv.take<int32_t>(size_t(m));
-  int32_t* warm = cv.take<int32_t>(1);
-  uint32_t* head = prog + size_t(nb) * size_t(nb);
+  E* W = static_cast<E*>(bf.W);
+  uint32_t* head = bf.prog + size_t(nb) * size_t(nb);
   uint32_t* abort_flag = head + 1;
-  if (cudaMemsetAsync(prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  if (cudaMemsetAsync(rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaMemsetAsync(bf.prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaMemsetAsync(bf.rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   const double mm = double(m) * double(m);
-  const int32_t nb32 = (m + 31) / 32;
+  auto grid_for = [&](const void* fn, int threads, size_t smem, int64_t cap) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    return int(std::max<int64_t>(1, std::min<int64_t>(int64_t(per_sm) * sms, cap)));
+  };
   {
+    const int64_t nbt = (m + kFlagT - 1) / kFlagT;
+    const int g = grid_for(reinterpret_cast<const void*>(rowflag_kernel), 256, 0, nbt * (nbt + 1) / 2);
     Launch L(ctx, stream, "closure_rowflags", mm * 4.0);
-    rowflag_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, rowflag);
+    rowflag_kernel<<<g, 256, 0, stream>>>(d, m, bound, bf.rowflag, status);
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv, warm);
+    relabel_kernel<<<1, 1024, 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm);
   }
   {
-    Launch L(ctx, stream, "closure_pack", mm * (4.0 + sizeof(E)));
-    const int32_t mp32 = mp / 32;
-    pack_kernel<E><<<dim3(mp32, mp32), dim3(32, 8), 0, stream>>>(d, m, mp, bound, perm, W, prog, nb, ctx->status);
+    const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 256, 0, int64_t(mp / 32) * (mp / 32));
+    Launch L(ctx, stream, "closure_pack", 0.0);
+    pack_kernel<E><<<g, 256, 0, stream>>>(d, m, mp, bf.perm, bf.warm, W, bf.prog, nb);
+  }
+  if (int rc = check_launch()) return rc;
+  {
+    const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E);
+    cudaFuncSetAttribute(closure_cluster_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    Launch L(ctx, stream, "closure_cluster", 0.0);
+    closure_cluster_kernel<E><<<kClusterCtas, kClusterThreads, smem, stream>>>(W, mp, nb, bf.warm, bf.prog,
+                                                                               bf.counters);
   }
   if (int rc = check_launch()) return rc;
   {
     // persistent grid: every CTA resident (cooperative launch)
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure_persistent_kernel<E>, kThreads, 0) !=
-            cudaSuccess ||
-        per_sm < 1)
-      return SCHULZE_ECUDA;
-    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
-    const int64_t max_items = int64_t(nb) * nb * nb;
-    const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, max_items));
-    Sync sy{prog, head, abort_flag, ctx->status, warm, ctx->counters};
+    const int grid = grid_for(reinterpret_cast<const void*>(closure_persistent_kernel<E>), kThreads, 0,
+                              int64_t(nb) * nb * nb);
+    Sync sy{bf.prog, head, abort_flag, status, bf.warm, bf.counters};
     E* Wp = W;
     int32_t ldp = mp, nbp = nb;
     void* args[] = {&Wp, &ldp, &nbp, &sy};
@@ -428,11 +727,34 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
     }
   }
   {
-    Launch L(ctx, stream, "closure_widen", mm * (4.0 + sizeof(E)));
-    const int32_t gx = std::max(1, std::min<int32_t>((m + 255) / 256, 8));
-    widen_kernel<E><<<dim3(gx, m), 256, 0, stream>>>(W, mp, m, inv, p);
+    const int g = grid_for(reinterpret_cast<const void*>(cold_product_kernel<E>), kThreads, 0, int64_t(nb) * nb);
+    Launch L(ctx, stream, "closure_cold", 0.0);
+    cold_product_kernel<E><<<g, kThreads, 0, stream>>>(W, mp, nb, bf.warm, bf.prog, bf.counters);
+  }
+  {
+    const int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
+    Launch L(ctx, stream, "closure_widen", mm * 4.0);
+    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.warm, p);
   }
   return check_launch();
+}
+
+template <typename E>
+int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
+                cudaStream_t stream) {
+  const int32_t mp = int32_t(align_up(size_t(m), kB));
+  const int32_t nb = mp / kB;
+  Carver cv(ws);
+  ClosureBufs bf;
+  bf.W = cv.take<E>(size_t(mp) * size_t(mp));
+  bf.prog = cv.take<uint32_t>(size_t(nb) * size_t(nb) + 2);
+  bf.rowflag = cv.take<int32_t>(size_t(m));
+  bf.perm = cv.take<int32_t>(size_t(m));
+  bf.inv = cv.take<int32_t>(size_t(m));
+  bf.warm = cv.take<int32_t>(1);
+  bf.counters = ctx->counters;
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
+  return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream);
 }
 
 }  // namespace
@@ -500,44 +822,20 @@ int static_scratch(int device, unsigned char** out) {
 template <typename E>
 int run_closure_static(unsigned char* base, int device, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
                        int32_t* status, cudaStream_t stream) {
-  const int32_t mp = int32_t(align_up(size_t(m), kB));
-  const int32_t nb = mp / kB;
-  E* W = reinterpret_cast<E*>(base + kStW);
-  uint32_t* prog = reinterpret_cast<uint32_t*>(base + kStProg);
-  int32_t* rowflag = reinterpret_cast<int32_t*>(base + kStRowflag);
-  int32_t* perm = reinterpret_cast<int32_t*>(base + kStPerm);
-  int32_t* inv = reinterpret_cast<int32_t*>(base + kStInv);
-  int32_t* warm = reinterpret_cast<int32_t*>(base + kStWarm);
-  auto* counters = reinterpret_cast<unsigned long long*>(base + kStCounters);
-  uint32_t* head = prog + size_t(nb) * size_t(nb);
-  uint32_t* abort_flag = head + 1;
-  // the array keeps the previous call's contents: reset what must start at zero
-  if (cudaMemsetAsync(prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  if (cudaMemsetAsync(rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  const int32_t nb32 = (m + 31) / 32;
-  rowflag_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, rowflag);
-  relabel_kernel<<<1, 1024, 0, stream>>>(rowflag, m, perm, inv, warm);
-  const int32_t mp32 = mp / 32;
-  pack_kernel<E><<<dim3(mp32, mp32), dim3(32, 8), 0, stream>>>(d, m, mp, bound, perm, W, prog, nb, status);
-  if (int rc = check_launch()) return rc;
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure_persistent_kernel<E>, kThreads, 0) !=
-          cudaSuccess ||
-      per_sm < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+  ClosureBufs bf;
+  bf.W = base + kStW;
+  bf.prog = reinterpret_cast<uint32_t*>(base + kStProg);
+  bf.rowflag = reinterpret_cast<int32_t*>(base + kStRowflag);
+  bf.perm = reinterpret_cast<int32_t*>(base + kStPerm);
+  bf.inv = reinterpret_cast<int32_t*>(base + kStInv);
+  bf.warm = reinterpret_cast<int32_t*>(base + kStWarm);
+  bf.counters = reinterpret_cast<unsigned long long*>(base + kStCounters);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
     return SCHULZE_ECUDA;
-  const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, int64_t(nb) * nb * nb));
-  Sync sy{prog, head, abort_flag, status, warm, counters};
-  E* Wp = W;
-  int32_t ldp = mp, nbp = nb;
-  void* args[] = {&Wp, &ldp, &nbp, &sy};
-  if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(closure_persistent_kernel<E>), dim3(grid), dim3(kThreads),
-                                  args, 0, stream) != cudaSuccess) {
-    cudaGetLastError();
-    return SCHULZE_ECUDA;
-  }
-  const int32_t gx = std::max(1, std::min<int32_t>((m + 255) / 256, 8));
-  widen_kernel<E><<<dim3(gx, m), 256, 0, stream>>>(W, mp, m, inv, p);
-  return check_launch();
+  // the array keeps the previous call's contents: the pipeline resets what
+  // must start at zero (progress words, queue head, abort flag, row flags)
+  return closure_pipeline<E>(nullptr, sms, d, m, bound, p, bf, status, stream);
 }
 
 }  // namespace

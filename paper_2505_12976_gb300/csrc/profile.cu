@@ -30,6 +30,7 @@ static cudaEvent_t get_event(schulze_ctx* ctx) {
 }
 
 Launch::Launch(schulze_ctx* ctx, cudaStream_t stream, const char* name, double work) : ctx_(ctx), stream_(stream) {
+  if (!ctx) return;  // callers without a context (no counting, no profiling)
   ctx->launches += 1;
   if (!ctx->profiling) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

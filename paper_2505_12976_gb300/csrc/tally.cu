@@ -6,12 +6,19 @@
 //    pos[v][i] < pos[v][j] with packed 16-bit SIMD compares;
 //  * sparse (pair count, O(n k^2)): d[i][j] = cnt[i] - C[i][j], where cnt[i]
 //    is the number of ballots listing i and C[i][j] the number listing j
-//    above i. Ballot entries are grouped by candidate (counting sort), and
-//    each CTA owns a block of rows of d, counts C for them in shared memory
-//    and writes the rows of d once.
+//    above i. C vanishes outside A x A, A the set of listed candidates.
+//    - compact form (|A| small): each CTA counts C over A x A for its slice
+//      of the ballots in a private shared-memory matrix, while d is filled
+//      as if C were zero in one streaming pass; a second kernel sums the
+//      slices and fixes the A x A entries of d;
+//    - grouped form: ballot entries are grouped by candidate (counting
+//      sort), and each CTA owns a block of rows of d, counts C for them in
+//      shared memory and writes the rows of d once.
+//    Which form runs is decided on the device once |A| is known.
 #include <algorithm>
 
 #include "internal.cuh"
+#include "scan.cuh"
 
 namespace schulze {
 namespace {
@@ -19,6 +26,12 @@ namespace {
 constexpr int kWarp = 32;
 constexpr int kMaxRowsPerBlock = 256;  // rows of d owned by one sparse work unit
 constexpr int32_t kLocalHistMax = 16384;  // candidates counted in shared memory per CTA
+// compact pair count: |A| limits (16-bit packed / 32-bit counters), CTAs, threads
+constexpr int32_t kCompactMaxPacked = 256;
+constexpr int32_t kCompactMaxWide = 224;
+constexpr int kCompactMaxCtas = 160;
+constexpr int kCompactThreads = 1024;
+constexpr uint16_t kNoSlot = 0xFFFFu;
 
 // ------------------------------------------------------------------ dense
 
@@ -212,42 +225,33 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
   }
 }
 
-// Block-wide exclusive scan of v[0..len) (uint32) in place; returns the total.
-// Every thread of the block must call it.
-__device__ uint32_t block_exclusive_scan(uint32_t* v, int32_t len, uint32_t* part) {
-  const int T = blockDim.x;
-  const int per = (len + T - 1) / T;
-  const int b = threadIdx.x * per, e = min(len, b + per);
-  uint32_t s = 0;
-  for (int c = b; c < e; ++c) s += v[c];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < T; o <<= 1) {  // Hillis-Steele inclusive scan of the partials
-    uint32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += x;
-    __syncthreads();
-  }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (int c = b; c < e; ++c) {
-    uint32_t x = v[c];
-    v[c] = run;
-    run += x;
-  }
-  uint32_t total = part[T - 1];
-  __syncthreads();
-  return total;
-}
-
 // Plans the sparse tally on the device (one CTA of 1024 threads):
 //  * off[c] / cursor[c]: start of candidate c's entries (exclusive scan of cnt);
 //  * the rows are cut into blocks of rb rows; block b holds E_b entries and
 //    gets nu_b = max(1, ceil(E_b / emax)) work units, each a slice of at most
 //    emax of its entries; uoff[b] is the exclusive scan of nu_b.
+//  * slot[c]: index of c among the listed candidates (-1 if unlisted), act
+//    the inverse, meta[0] = |A| and meta[1] = 1 when the compact form runs
+//    (|A| <= compact_max).
 __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb,
                                                            int32_t nblocks, uint32_t emax, uint32_t* __restrict__ off,
-                                                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff) {
+                                                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff,
+                                                           int32_t compact_max, int32_t* __restrict__ slot,
+                                                           int32_t* __restrict__ act, int32_t* __restrict__ meta) {
   __shared__ uint32_t part[1024];
+  {
+    uint32_t* flag = reinterpret_cast<uint32_t*>(slot);
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) flag[c] = cnt[c] > 0 ? 1u : 0u;
+    __syncthreads();
+    const uint32_t na = block_exclusive_scan(flag, m, part);
+    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+      const int32_t s = cnt[c] > 0 ? int32_t(flag[c]) : -1;
+      slot[c] = s;
+      if (s >= 0) act[s] = c;
+    }
+    if (threadIdx.x == 0) meta[0] = int32_t(na), meta[1] = int32_t(na) <= compact_max ? 1 : 0;
+    __syncthreads();
+  }
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) off[c] = uint32_t(cnt[c]);
   __syncthreads();
   const uint32_t total = block_exclusive_scan(off, m, part);
@@ -269,7 +273,9 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
 // then places its entries with shared-memory cursors.
 template <bool kLocal>
 __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
-                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
+                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
+                                      const int32_t* __restrict__ meta) {
+  if (meta[1]) return;  // compact form
   if (!kLocal) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
       int32_t c = ranks[e];
@@ -306,9 +312,10 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
 // Rows of blocks split into several units start as d[c][j] = cnt[c] (0 on
 // the diagonal); their units then subtract their partial counts atomically.
 __global__ void sparse_init_split_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb, int32_t jw,
-                                         const uint32_t* __restrict__ uoff, int32_t* __restrict__ d) {
+                                         const uint32_t* __restrict__ uoff, int32_t* __restrict__ d,
+                                         const int32_t* __restrict__ meta) {
   const int32_t b = blockIdx.x, jc = blockIdx.y;
-  if (uoff[b + 1] - uoff[b] <= 1) return;
+  if (meta[1] || uoff[b + 1] - uoff[b] <= 1) return;
   const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
   const int32_t J0 = jc * jw, J1 = min(m, J0 + jw);
   for (int32_t r = R0; r < R1; ++r) {
@@ -329,11 +336,11 @@ __global__ void __launch_bounds__(512)
     sparse_units_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
                         const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries,
                         const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
-                        int32_t* __restrict__ d) {
+                        int32_t* __restrict__ d, const int32_t* __restrict__ meta) {
   extern __shared__ uint32_t C[];
   __shared__ uint32_t so[kMaxRowsPerBlock + 1];  // off[R0 .. R1]
   const uint32_t unit = blockIdx.x;
-  if (unit >= uoff[nblocks]) return;
+  if (meta[1] || unit >= uoff[nblocks]) return;
   int32_t lo = 0, hi = nblocks - 1;  // block b with uoff[b] <= unit < uoff[b + 1]
   while (lo < hi) {
     int32_t mid = (lo + hi + 1) >> 1;
@@ -429,6 +436,142 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// Compact form, first kernel (one CTA per slice of the ballots).
+// (a) Fills the CTA's share of d, taken as a flat range of m*m entries, as if
+//     C were zero: d[i][j] = cnt[i] for listed i and j != i, else 0.
+// (b) Counts C over A x A for the slice in shared memory (cell [slot i]
+//     [slot j], 16-bit lanes packed two per word when a slice has at most
+//     65535 ballots, else 32-bit) and stores it as this CTA's partial.
+// A warp takes one ballot at a time: its listed slots are staged in shared
+// memory (the first 64 also in registers), and for every position q the
+// lanes add 1 to C[slot at q][slot at p] for p < q. Ids outside [0, m) are
+// skipped (the count pass reports them).
+template <bool kPacked>
+__global__ void __launch_bounds__(kCompactThreads, 1)
+    compact_pairs_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
+                         const int32_t* __restrict__ cnt, const int32_t* __restrict__ slot,
+                         const int32_t* __restrict__ meta, uint32_t* __restrict__ partial, int32_t stage_len,
+                         int32_t* __restrict__ d) {
+  if (!meta[1]) return;
+  extern __shared__ __align__(16) uint32_t smem_pairs[];
+  const int32_t na = meta[0];
+  const int32_t wpr = kPacked ? (na + 1) >> 1 : na;
+  const int32_t words = na * wpr;
+  uint32_t* C = smem_pairs;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint16_t* st = reinterpret_cast<uint16_t*>(smem_pairs + ((words + 3) & ~3)) + wib * stage_len;
+  for (int32_t t = threadIdx.x; t < words; t += blockDim.x) C[t] = 0u;
+
+  // (a) this CTA's rows of d, 16 bytes per store where rows allow it
+  {
+    const int32_t rper = (m + gridDim.x - 1) / gridDim.x;
+    const int32_t i0 = min(m, int32_t(blockIdx.x) * rper), i1 = min(m, i0 + rper);
+    for (int32_t i = i0; i < i1; ++i) {
+      const int32_t b = slot[i] < 0 ? 0 : cnt[i];
+      int32_t* drow = d + int64_t(i) * m;
+      if ((m & 3) == 0) {
+        for (int32_t j = 4 * threadIdx.x; j < m; j += 4 * blockDim.x) {
+          const int32_t t = i - j;  // diagonal lane inside the 4 entries, if any
+          *reinterpret_cast<int4*>(drow + j) =
+              make_int4(t == 0 ? 0 : b, t == 1 ? 0 : b, t == 2 ? 0 : b, t == 3 ? 0 : b);
+        }
+      } else {
+        for (int32_t j = threadIdx.x; j < m; j += blockDim.x) drow[j] = j == i ? 0 : b;
+      }
+    }
+  }
+  __syncthreads();
+
+  // (b) pair counts of this CTA's ballots
+  const int64_t vper = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t v0 = min(n, int64_t(blockIdx.x) * vper), v1 = min(n, v0 + vper);
+  for (int64_t v = v0 + wib; v < v1; v += nwarp) {
+    const int32_t* row = ranks + v * k;
+    for (int32_t q = lane; q < k; q += 32) {
+      const int32_t c = row[q];
+      const int32_t sc = (c >= 0 && c < m) ? slot[c] : -1;
+      st[q] = sc < 0 ? kNoSlot : uint16_t(sc);
+    }
+    __syncwarp();
+    // this lane's two low positions: counter word and increment, hoisted
+    const uint32_t r0 = lane < k ? st[lane] : kNoSlot;
+    const uint32_t r1 = lane + 32 < k ? st[lane + 32] : kNoSlot;
+    const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
+    const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+    const int32_t qlo = min(k, 32), qhi = min(k, 64);
+    for (int32_t q = 1; q < qlo; ++q) {  // row positions 1..31: lanes p < q
+      const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
+      if (sq == kNoSlot) continue;  // uniform over the warp
+      if (lane < q && r0 != kNoSlot) atomicAdd(C + int32_t(sq) * wpr + w0, i0);
+    }
+    for (int32_t q = 32; q < qhi; ++q) {  // 32..63: all low lanes, high lanes p < q
+      const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r1, q - 32);
+      if (sq == kNoSlot) continue;
+      uint32_t* crow = C + int32_t(sq) * wpr;
+      if (r0 != kNoSlot) atomicAdd(crow + w0, i0);
+      if (lane + 32 < q && r1 != kNoSlot) atomicAdd(crow + w1, i1);
+    }
+    for (int32_t q = 64; q < k; ++q) {  // long ballots
+      const uint32_t sq = st[q];
+      if (sq == kNoSlot) continue;
+      uint32_t* crow = C + int32_t(sq) * wpr;
+      if (r0 != kNoSlot) atomicAdd(crow + w0, i0);
+      if (r1 != kNoSlot) atomicAdd(crow + w1, i1);
+      for (int32_t p = 64 + lane; p < q; p += 32) {
+        const uint32_t sp = st[p];
+        if (sp != kNoSlot) atomicAdd(crow + (kPacked ? sp >> 1 : sp), kPacked ? 1u << ((sp & 1u) * 16u) : 1u);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  uint32_t* out = partial + int64_t(blockIdx.x) * words;
+  for (int32_t t = threadIdx.x; t < words; t += blockDim.x) out[t] = C[t];
+}
+
+// Compact form, second kernel (one CTA per listed candidate a): sums row a of
+// the partial counts over the G slices and sets d[act a][act b] = cnt - C for
+// every listed b != a.
+template <bool kPacked>
+__global__ void __launch_bounds__(512)
+    compact_fix_kernel(const uint32_t* __restrict__ partial, int32_t G, int32_t m, const int32_t* __restrict__ cnt,
+                       const int32_t* __restrict__ act, const int32_t* __restrict__ meta, int32_t* __restrict__ d) {
+  if (!meta[1]) return;
+  __shared__ uint32_t red[512][2];
+  const int32_t na = meta[0];
+  const int32_t wpr = kPacked ? (na + 1) >> 1 : na;
+  const int64_t words = int64_t(na) * wpr;
+  const int32_t groups = max(1, int32_t(blockDim.x) / max(wpr, 1));
+  for (int32_t a = blockIdx.x; a < na; a += gridDim.x) {
+    const int32_t gg = threadIdx.x / wpr, w = threadIdx.x - gg * wpr;
+    uint32_t lo = 0, hi = 0;
+    if (gg < groups) {
+      const uint32_t* src = partial + int64_t(a) * wpr + w;
+      for (int32_t g = gg; g < G; g += groups) {
+        const uint32_t x = src[int64_t(g) * words];
+        if (kPacked) {
+          lo += x & 0xFFFFu;
+          hi += x >> 16;
+        } else {
+          lo += x;
+        }
+      }
+    }
+    red[threadIdx.x][0] = lo, red[threadIdx.x][1] = hi;
+    __syncthreads();
+    if (threadIdx.x < wpr) {
+      for (int32_t g = 1; g < groups; ++g) lo += red[g * wpr + threadIdx.x][0], hi += red[g * wpr + threadIdx.x][1];
+      const int32_t i = act[a];
+      const int32_t base = cnt[i];
+      int32_t* drow = d + int64_t(i) * m;
+      const int32_t b0 = kPacked ? 2 * int32_t(threadIdx.x) : int32_t(threadIdx.x);
+      if (b0 != a) drow[act[b0]] = base - int32_t(lo);
+      if (kPacked && b0 + 1 < na && b0 + 1 != a) drow[act[b0 + 1]] = base - int32_t(hi);
+    }
+    __syncthreads();
+  }
+}
+
 struct SparsePlan {
   int32_t rb, jw, njc, nblocks;
   bool packed;
@@ -466,6 +609,30 @@ SparsePlan sparse_plan(int64_t n, int32_t m, int32_t k, int sms) {
   return s;
 }
 
+// Compact form limits for a launch over G CTAs: cmax = the largest |A| it
+// takes (0: never), stage = per-warp staging entries (>= k), smem bytes.
+struct CompactPlan {
+  int G;
+  bool packed;
+  int32_t cmax, stage;
+  size_t smem, partial_words;
+};
+
+CompactPlan compact_plan(int64_t n, int32_t m, int32_t k, int sms, uint32_t flags) {
+  CompactPlan c;
+  c.G = std::max(1, std::min(sms, kCompactMaxCtas));
+  const int64_t per = (n + c.G - 1) / c.G;
+  c.packed = per <= 65535;
+  c.cmax = std::min<int32_t>(m, c.packed ? kCompactMaxPacked : kCompactMaxWide);
+  if ((flags & SCHULZE_F_TALLY_GROUPED) || k > c.cmax) c.cmax = 0;
+  c.stage = (std::max(c.cmax, 64) + 7) & ~7;
+  const size_t wpr = c.packed ? size_t(c.cmax + 1) / 2 : size_t(c.cmax);
+  const size_t words = size_t(c.cmax) * wpr;
+  c.smem = align_up(words, 4) * 4 + size_t(kCompactThreads / 32) * size_t(c.stage) * 2;
+  c.partial_words = size_t(c.G) * std::max<size_t>(words, 1);
+  return c;
+}
+
 bool choose_dense(int64_t n, int32_t m, int32_t k, uint32_t flags) {
   if (flags & SCHULZE_F_TALLY_DENSE) return true;
   if (flags & SCHULZE_F_TALLY_SPARSE) return false;
@@ -491,7 +658,11 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
     return align_up(size_t(dense_voter_chunk(n, m)) * ldp * 2, 256) + 4096;
   }
   size_t total = size_t(n) * size_t(k);
-  return align_up(size_t(m) * 4, 256) + 3 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) + 4096;
+  // partial counts for up to kCompactMaxCtas slices, either counter width
+  const size_t cp = size_t(std::min(m, kCompactMaxPacked)), cw = size_t(std::min(m, kCompactMaxWide));
+  const size_t partial_words = size_t(kCompactMaxCtas) * std::max(cp * ((cp + 1) / 2), cw * cw);
+  return align_up(size_t(m) * 4, 256) + 3 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) +
+         2 * align_up(size_t(m) * 4, 256) + 256 + align_up(partial_words * 4, 256) + 4096;
 }
 
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
@@ -551,24 +722,41 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   uint32_t* cursor = cv.take<uint32_t>(size_t(m) + 1);
   uint32_t* uoff = cv.take<uint32_t>(size_t(sp.nblocks) + 1);
   uint32_t* entries = cv.take<uint32_t>(total);
+  int32_t* slot = cv.take<int32_t>(size_t(m));
+  int32_t* act = cv.take<int32_t>(size_t(m));
+  int32_t* meta = cv.take<int32_t>(2);
+  const CompactPlan cp = compact_plan(n, m, k, sms, flags);
+  uint32_t* partial = cv.take<uint32_t>(cp.partial_words);
   if (cudaMemsetAsync(cnt, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   const bool local_hist = m <= kLocalHistMax;
   {
     const int threads = 512;
     const size_t smem = (local_hist ? size_t(m) * 4 : 0) + size_t(threads / 32) * size_t((m + 31) / 32) * 4;
-    const int blocks = int(std::min<int64_t>((n + 15) / 16, int64_t(sms)));
+    auto kern = local_hist ? sparse_count_kernel<true> : sparse_count_kernel<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    // about one ballot per warp: the pass is bound by load latency
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 15) / 16, int64_t(sms) * per_sm)));
     Launch L(ctx, stream, "tally_count", double(total) * 4.0);
-    if (local_hist) {
-      cudaFuncSetAttribute(sparse_count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      sparse_count_kernel<true><<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
-    } else {
-      cudaFuncSetAttribute(sparse_count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      sparse_count_kernel<false><<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
-    }
+    kern<<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
   }
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
-    sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff);
+    sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot,
+                                               act, meta);
+  }
+  if (cp.cmax > 0) {
+    Launch L(ctx, stream, "tally_compact_pairs", double(m) * double(m) * 4.0 + double(total) * 4.0);
+    auto kern = cp.packed ? compact_pairs_kernel<true> : compact_pairs_kernel<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.smem));
+    kern<<<cp.G, kCompactThreads, cp.smem, stream>>>(ranks, n, m, k, cnt, slot, meta, partial, cp.stage, d);
+  }
+  if (cp.cmax > 0) {
+    Launch L(ctx, stream, "tally_compact_fix", 0.0);
+    auto kern = cp.packed ? compact_fix_kernel<true> : compact_fix_kernel<false>;
+    kern<<<std::min(cp.cmax, 2 * sms), 512, 0, stream>>>(partial, cp.G, m, cnt, act, meta, d);
   }
   {
     Launch L(ctx, stream, "tally_group", double(total) * 8.0);
@@ -576,15 +764,15 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
       const size_t smem = size_t(m) * 8;
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 4095) / 4096, uint64_t(sms)));
       cudaFuncSetAttribute(sparse_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      sparse_scatter_kernel<true><<<blocks, 1024, smem, stream>>>(ranks, total, m, cursor, entries);
+      sparse_scatter_kernel<true><<<blocks, 1024, smem, stream>>>(ranks, total, m, cursor, entries, meta);
     } else {
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
-      sparse_scatter_kernel<false><<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries);
+      sparse_scatter_kernel<false><<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries, meta);
     }
   }
   {
     Launch L(ctx, stream, "tally_split_init", 0.0);
-    sparse_init_split_kernel<<<dim3(sp.nblocks, sp.njc), 256, 0, stream>>>(cnt, m, sp.rb, sp.jw, uoff, d);
+    sparse_init_split_kernel<<<dim3(sp.nblocks, sp.njc), 256, 0, stream>>>(cnt, m, sp.rb, sp.jw, uoff, d, meta);
   }
   if (int rc = check_launch()) return rc;
   dim3 grid(sp.max_units, sp.njc);
@@ -592,11 +780,11 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   if (sp.packed) {
     cudaFuncSetAttribute(sparse_units_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
     sparse_units_kernel<true><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
-                                                               sp.emax, sp.rb, sp.jw, d);
+                                                               sp.emax, sp.rb, sp.jw, d, meta);
   } else {
     cudaFuncSetAttribute(sparse_units_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
     sparse_units_kernel<false><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
-                                                                sp.emax, sp.rb, sp.jw, d);
+                                                                sp.emax, sp.rb, sp.jw, d, meta);
   }
   return check_launch();
 }

@@ -66,7 +66,7 @@ def test_fig1_mcgarvey_on_gpu():
 
 def test_topk_tie_counterexample_on_gpu():
     g = topk_tie_counterexample()
-    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
         out = S.schulze_run(cu(g["ballots"]), g["m"], flags=flags)
         eq(host(out["d"]), g["d"])
         eq(host(out["p"]), g["p"])
@@ -89,8 +89,36 @@ def test_tally_dense_and_sparse(m, n, k):
     seed = m * 1000 + n * 10 + k
     r = W.mallows(seed, n, m, k, 0.85, W.permutation(seed, m)) if k else np.zeros((n, 0), np.int32)
     want = oracle.tally(r, m)
-    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, 0):
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED, 0):
         eq(host(S.schulze_tally(cu(r), m, flags=flags)), want, f"tally flags={flags}")
+
+
+@pytest.mark.parametrize("m,n,k,phi", [(4096, 3000, 50, 0.9), (1000, 777, 20, 0.97), (600, 2000, 256, 0.995),
+                                       (256, 4000, 5, 1.0), (257, 4000, 5, 1.0), (5003, 1500, 3, 0.5)])
+def test_tally_compact_and_grouped_agree(m, n, k, phi):
+    """Top-k ballots over few listed candidates (the compact pair count) and
+    over many (the grouped one), both forms forced, against the oracle;
+    256 listed candidates is the largest compact case, 257 the smallest
+    grouped one."""
+    r = W.mallows(m + n + k, n, m, k, phi, W.permutation(m + k, m))
+    want = oracle.tally(r, m)
+    for flags in (S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
+        eq(host(S.schulze_tally(cu(r), m, flags=flags)), want, f"tally flags={flags}")
+
+
+def test_tally_compact_wide_counters():
+    """More ballots per slice than 16-bit counters hold: the compact pair
+    count switches to 32-bit counters. Sampled entries against the
+    definition, all row and column sums against their closed forms."""
+    m, n, k = 180, 10_500_000, 3
+    r = W.mallows(77, n, m, k, 0.7, W.permutation(78, m))
+    d = host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE))
+    listed = np.unique(r)
+    rs = np.random.Generator(np.random.PCG64(3))
+    for _ in range(12):
+        i, j = (int(x) for x in rs.choice(listed, 2, replace=False))
+        assert d[i, j] == oracle.tally_entry(r, m, i, j)
+    _check_row_col_sums(r, m, d)
 
 
 def test_tally_many_ballots_chunked():
@@ -136,11 +164,11 @@ def test_tally_rejects_bad_ids():
     ctx = S.context()
     assert ctx.status() == S.OK
     bad = np.array([[0, 1, 2], [1, 1, 0]], np.int32)
-    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
         S.schulze_tally(cu(bad), 4, flags=flags)
         assert ctx.status() == S.EDATA
     out_of_range = np.array([[0, 7, 2]], np.int32)
-    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE):
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
         S.schulze_tally(cu(out_of_range), 4, flags=flags)
         assert ctx.status() == S.EDATA
     S.schulze_tally(cu(np.array([[3, 1, 2]], np.int32)), 4)
@@ -196,6 +224,25 @@ def test_closure_many_rounds_with_edgeless_candidates(m, cold_frac):
     want = oracle.strongest_paths(d, nthreads=16)
     for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
         eq(host(S.schulze_strongest_paths(cu(d), 20000, flags=flags)), want, f"m={m} cold={cold_frac}")
+
+
+@pytest.mark.parametrize("nw", [1, 31, 32, 33, 64, 65, 151, 192, 193, 255, 256, 257, 300])
+def test_closure_warm_set_sizes(nw):
+    """nw candidates with outgoing edges spread over m = 600 ids, the rest
+    edgeless: the cluster closure takes warm sets up to 256 (16-bit) or 192
+    (int32) candidates, the persistent kernel the larger ones; cold columns
+    come from the product with the closed warm square."""
+    m = 600
+    rs = np.random.Generator(np.random.PCG64(1000 + nw))
+    warm = rs.choice(m, nw, replace=False)
+    d = np.zeros((m, m), np.int32)
+    d[np.ix_(warm, np.arange(m))] = rs.integers(1, 30000, size=(nw, m)) * (rs.random((nw, m)) < 0.3)
+    cold = np.setdiff1d(np.arange(m), warm)
+    d[warm, cold[rs.integers(0, cold.size, nw)]] = rs.integers(1, 30000, nw)  # every warm one has an edge
+    np.fill_diagonal(d, 0)
+    want = oracle.strongest_paths(d, nthreads=16)
+    for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
+        eq(host(S.schulze_strongest_paths(cu(d), 30000, flags=flags)), want, f"nw={nw} flags={flags}")
 
 
 def test_closure_large_counts_int32():
