@@ -402,10 +402,25 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    step()
+    launches_per_step = ctx.launch_count() - l0
+    # the step as a CUDA graph: the same library call, captured once (the
+    # reserved workspace means nothing is allocated inside it)
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        step()
+    torch.cuda.current_stream().wait_stream(cap)
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    launches0 = ctx.launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -413,20 +428,27 @@ def main():
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record()
-        step()
+        graph.replay()
         evs[i][1].record()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clock_info = clocks.stop()
-    launches = ctx.launch_count() - launches0
+    launches = launches_per_step * args.steps
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    # a second pass of the same steps with per-kernel events on the library's
-    # stream gives the breakdown and the dominant kernel's launch durations
+    graph_out = {key: t.clone() for key, t in out.items()}
+    step()  # eager, for the check that the graph computed the same
+    torch.cuda.synchronize()
+    graph_matches = all(torch.equal(graph_out[key], out[key]) for key in out)
+    # a second pass of the same steps, eager, with per-kernel events on the
+    # library's stream: the breakdown and the dominant kernel's durations. A
+    # GPU sleep ahead of each step lets the host queue every launch first, so
+    # the events time the kernels and not the launch gaps.
     ctx.profile(True)
     cc0 = ctx.closure_counters()
     for i in range(args.steps):
         flush.zero_()
+        torch.cuda._sleep(2_000_000)
         step()
     prof = ctx.profile_read()
     cc1 = ctx.closure_counters()
@@ -442,30 +464,50 @@ def main():
     # happens in the tests; here the device status must be clean
     status = ctx.status()
 
-    # roofline of the dominant kernel class
-    top = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
-    roof = None
-    if top[0] is not None:
-        name, st = top
+    # roofline of the dominant kernel class, and of every class for context:
+    # algorithmic bytes (HBM-bound passes) or (max, min) updates (ALU-bound
+    # closures) per launch over the mean launch duration
+    dd = out["d"]
+    nw = int(((dd > dd.t()).any(dim=1)).sum().item())  # candidates with an outgoing edge
+    esz = 2 if s16 else 4
+    nwp = -(-nw // 64) * 64
+    alu_peak = max(probe["s16x2"], probe["s16x2_max3"]) if s16 else max(probe["s32"], probe["s32_max3"])
+    hbm_peak = 6797.2  # GB/s, MEASURED_PEAKS.json (STREAM-style copy on the GB300s)
+    mm4 = float(m) * m * 4
+    work = {  # kernel class -> (bound, algorithmic units per launch, what)
+        "tally_compact_pairs": ("hbm", mm4 + float(n) * k * 4, "d written once, ballots read once"),
+        "tally_rows": ("hbm", mm4 + float(n) * k * 4, "d written once, ballots read once"),
+        "tally_dense": ("alu", float(n) * m * (m - 1) / 2, "pair compares"),
+        "tally_count": ("hbm", float(n) * k * 4, "ballots read once"),
+        "closure_rowflags": ("hbm", mm4, "d read once"),
+        "closure_widen": ("hbm", mm4, "p written once"),
+        "closure_pack": ("hbm", float(nwp) * m * (8 + esz), "warm rows of d and d^T read, W written"),
+        "closure_cluster": ("alu", float(nw) ** 3, "(max, min) updates of the warm square"),
+        "closure_cold": ("alu", float(nw) ** 2 * (m - nw), "(max, min) updates of the cold columns"),
+        "closure_persistent": ("alu", (executed["tile_updates"] + executed["diag_closures"]) * 64.0 ** 3,
+                               "(max, min) updates executed (64^3 per tile update)"),
+        "extract_beaten_by": ("hbm", 2 * mm4, "p and p^T read"),
+    }
+
+    def roofline(name, st):
         per_launch_ms = st["ms"] / max(1, st["launches"])
-        if name == "closure_persistent":
-            fmt = "s16x2" if s16 else "s32"
-            # (max, min) updates the kernel executed per launch: 64^3 per computed
-            # tile update or diagonal closure (all-zero updates are skipped)
-            upd = (executed["tile_updates"] + executed["diag_closures"]) * 64.0 ** 3
-            achieved = upd / (per_launch_ms * 1e-3)
-            peak = max(probe["s16x2"], probe["s16x2_max3"]) if s16 else max(probe["s32"], probe["s32_max3"])
-            roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                    "unit": "Gupdates/s", "frac": achieved / peak, "traffic": None,
-                    "lane_format": fmt, "per_launch_ms": per_launch_ms, "launches": st["launches"],
-                    "executed_updates_per_launch": upd, "dense_updates_per_launch": float(m) ** 3,
-                    "queue_items_per_launch": executed["items"],
+        bound, units, what = work.get(name, ("hbm", st["work"], "library estimate"))
+        achieved = units / (per_launch_ms * 1e-3)
+        if bound == "alu":
+            return {"bound": "alu", "kernel": name, "achieved": achieved / 1e9, "peak": alu_peak / 1e9,
+                    "unit": "Gupdates/s", "frac": achieved / alu_peak, "traffic": None,
+                    "lane_format": "s16x2" if s16 else "s32", "work_per_launch": units, "work": what,
+                    "per_launch_ms": per_launch_ms, "launches": st["launches"],
                     "peak_source": "schulze_probe_minmax measured in this run (best same-format variant)"}
-        else:
-            achieved = st["work"] / (st["ms"] * 1e-3)
-            roof = {"bound": "hbm", "kernel": name, "achieved": achieved / 1e9, "peak": 6797.2,
-                    "unit": "GB/s", "frac": achieved / 1e9 / 6797.2, "traffic": None,
-                    "per_launch_ms": per_launch_ms, "launches": st["launches"]}
+        return {"bound": "hbm", "kernel": name, "achieved": achieved / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / 1e9 / hbm_peak, "traffic": None, "bytes_per_launch": units, "work": what,
+                "per_launch_ms": per_launch_ms, "launches": st["launches"],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
+    roof = roofline(*ranked[0]) if ranked else None
+    roof_all = {name: {key: r[key] for key in ("bound", "frac", "achieved", "unit", "per_launch_ms")}
+                for name, r in ((name, roofline(name, st)) for name, st in ranked[:8])}
     breakdown = {kname: {"ms_per_step": st["ms"] / args.steps, "launches_per_step": st["launches"] / args.steps}
                  for kname, st in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     tally_ms = sum(st["ms"] for kname, st in prof.items() if kname.startswith("tally")) / args.steps
@@ -509,11 +551,13 @@ def main():
                 "elections_per_sec": world / (ms * 1e-3),
                 "tally": {"ms_per_step": tally_ms, "algorithmic_GBps": tally_bytes / (tally_ms * 1e-3) / 1e9
                           if tally_ms else None},
-                "roofline": roof, "probe_updates_per_s": probe, "kernels": breakdown,
+                "roofline": roof, "roofline_top_kernels": roof_all, "warm_candidates": nw,
+                "probe_updates_per_s": probe, "kernels": breakdown,
                 "cpu_baseline": cpu,
                 "e2e": {"value": world * float(m) ** 3 / e2e_sec, "unit": UNIT,
                         "h2d_bytes_per_step": int(n) * int(k) * 4, "d2h_bytes_per_step": 2 * int(m) * 4 + 4},
-                "gpu_launches": int(launches), "device_status": status, "clocks": clock_info}
+                "gpu_launches": int(launches), "timed_as": "CUDA graph of one schulze_run call, replayed",
+                "graph_matches_eager": graph_matches, "device_status": status, "clocks": clock_info}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -71,7 +71,9 @@ constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
 // each held entry is compared with its transposed partner from there.
 constexpr int kFlagT = 64;
 __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int64_t bound,
-                                                      int32_t* __restrict__ rowflag, int32_t* status) {
+                                                      int32_t* __restrict__ rowflag, int32_t* status,
+                                                      const int32_t* __restrict__ hint_valid) {
+  if (hint_valid && *hint_valid) return;  // the caller's tally already knows the flags
   __shared__ int32_t t1[kFlagT][kFlagT + 1], t2[kFlagT][kFlagT + 1];  // t1 = d[A.., B..], t2 = d[B.., A..]
   const int32_t nbt = (m + kFlagT - 1) / kFlagT;
   const int64_t npairs = int64_t(nbt) * (nbt + 1) / 2;
@@ -138,10 +140,15 @@ __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict_
 }
 
 // Stable partition: perm[new] = old, candidates with edges first; inv[old] = new.
+// The flags come from rowflag_kernel, or from the tally (hint) when it set
+// *hint_valid.
 __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict__ rowflag, int32_t m,
                                                        int32_t* __restrict__ perm, int32_t* __restrict__ inv,
-                                                       int32_t* __restrict__ warm_out) {
+                                                       int32_t* __restrict__ warm_out,
+                                                       const int32_t* __restrict__ hint,
+                                                       const int32_t* __restrict__ hint_valid) {
   __shared__ uint32_t part[32];
+  if (hint_valid && *hint_valid) rowflag = hint;
   // inv[c] = 1 for warm c, scanned in place into the warm rank
   uint32_t* rank = reinterpret_cast<uint32_t*>(inv);
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) rank[c] = rowflag[c] ? 1u : 0u;
@@ -458,90 +465,103 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
 
 // Warm squares of at most kClusterMaxWarm candidates: blocked Floyd-Warshall
 // with 32 x 32 tiles on a cluster of kClusterCtas CTAs (one per SM). Every
-// CTA holds the whole square S (n = nw rounded up to 64, so that it covers
-// whole 64-wide tiles of W) in shared memory. Round r:
-//   1. every CTA closes the diagonal tile (r, r) of its own copy (the same
-//      result everywhere, so nothing is exchanged);
-//   2. the panel tiles (r, j) and (i, r) are shared out among the CTAs; each
-//      owner updates its tiles and writes them into every copy (distributed
-//      shared memory); cluster barrier;
+// CTA holds a copy of the whole square S (n = nw rounded up to 64, so that it
+// covers whole 64-wide tiles of W) in shared memory, stored tile by tile
+// (each 32 x 32 tile contiguous). Round r:
+//   1. every CTA closes the diagonal tile (r, r) of its own copy (one warp,
+//      the tile in registers; the same result everywhere);
+//   2. the panel tiles (r, j) and (i, r) are dealt out among the CTAs; each
+//      updates its tiles and copies them into every other copy (distributed
+//      shared memory, 16 bytes per store); cluster barrier;
 //   3. the other tiles likewise; cluster barrier.
-// A tile is written by one owner per phase and read by no other CTA in that
+// A tile is written by one CTA per phase and read by no other CTA in that
 // phase, so the copies stay identical. Rows of cold candidates are zero, so
 // rounds and tile rows stop at the warm ones; columns run over all of S.
-// CTA rank q then writes rows q, q + kClusterCtas, ... of S back into W and
-// sets the nonzero bits of the 64 x 64 tiles of W for cold_product_kernel.
+// CTA q then writes tiles q, q + kClusterCtas, ... back into W and sets the
+// nonzero bits of the 64 x 64 tiles of W for cold_product_kernel.
 constexpr int kCB = 32;               // tile size of the cluster closure
 constexpr int kClusterCtas = 8;
 constexpr int kClusterThreads = 512;  // one 16-bit pair (or two int32 entries) of a tile per thread
 
 // Thread t of a 32 x 32 tile owns row t / 16, entries 2 (t % 16) and
-// 2 (t % 16) + 1: one 32-bit word of 16-bit lanes, or two int32 entries.
+// 2 (t % 16) + 1: one 32-bit word of 16-bit lanes, or two int32 entries
+// (a Word). Tiles are contiguous: tile (ti, tj) of the nt x nt grid starts
+// at Word (ti * nt + tj) * 512.
 template <typename E>
 struct CTile;
 template <>
 struct CTile<int16_t> {
   using Word = uint32_t;
   static __device__ __forceinline__ uint32_t dup(uint32_t h) { return (h & 0xFFFFu) | (h << 16); }
-  static __device__ __forceinline__ int64_t word_index(int32_t n, int32_t ti, int32_t tj, int t) {
-    return int64_t(ti * kCB + (t >> 4)) * (n >> 1) + tj * (kCB / 2) + (t & 15);
-  }
   // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): the new word of thread t
-  static __device__ __forceinline__ Word product(const int16_t* S, int32_t n, int32_t ti, int32_t tj, int32_t tr,
+  static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
                                                  int t) {
-    const uint32_t* Sw = reinterpret_cast<const uint32_t*>(S);
-    const int32_t nw2 = n >> 1;
-    const uint32_t* arow = Sw + int64_t(ti * kCB + (t >> 4)) * nw2 + tr * (kCB / 2);
-    const uint32_t* bcol = Sw + int64_t(tr * kCB) * nw2 + tj * (kCB / 2) + (t & 15);
-    uint32_t acc = Sw[word_index(n, ti, tj, t)];
+    const Word* arow = S + (ti * nt + tr) * 512 + (t >> 4) * 16;
+    const Word* bcol = S + (tr * nt + tj) * 512 + (t & 15);
+    uint32_t acc = S[(ti * nt + tj) * 512 + t];
 #pragma unroll 4
     for (int kk = 0; kk < kCB; kk += 2) {
       const uint32_t a = arow[kk >> 1];
-      const uint32_t b0 = bcol[int64_t(kk) * nw2], b1 = bcol[int64_t(kk + 1) * nw2];
+      const uint32_t b0 = bcol[kk * 16], b1 = bcol[(kk + 1) * 16];
       acc = __vimax3_s16x2(acc, __vmins2(dup(a), b0), __vmins2(dup(a >> 16), b1));
     }
     return acc;
   }
-  // Floyd-Warshall step k inside diagonal tile (r, r): the new word of thread t
-  static __device__ __forceinline__ Word fw_step(const int16_t* S, int32_t n, int32_t r, int k, int t) {
-    const int32_t i = r * kCB + (t >> 4);
-    const uint32_t a = dup(uint32_t(uint16_t(S[int64_t(i) * n + r * kCB + k])));
-    const uint32_t b = reinterpret_cast<const uint32_t*>(S)[int64_t(r * kCB + k) * (n >> 1) + r * (kCB / 2) + (t & 15)];
-    const uint32_t own = reinterpret_cast<const uint32_t*>(S)[word_index(n, r, r, t)];
-    return __vmaxs2(own, __vmins2(a, b));
+  // Floyd-Warshall of diagonal tile (r, r) by one warp: lane i keeps row i
+  // (16 words) in registers, row k comes by shuffles from lane k. Row k and
+  // column k do not change in step k.
+  static __device__ __forceinline__ void diag_warp(Word* S, int32_t nt, int32_t r, int lane) {
+    uint4* row = reinterpret_cast<uint4*>(S + (r * nt + r) * 512 + lane * 16);
+    uint32_t v[16];
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const uint4 x = row[q4];
+      v[4 * q4] = x.x, v[4 * q4 + 1] = x.y, v[4 * q4 + 2] = x.z, v[4 * q4 + 3] = x.w;
+    }
+#pragma unroll
+    for (int k = 0; k < kCB; ++k) {
+      const uint32_t a = dup((k & 1) ? v[k >> 1] >> 16 : v[k >> 1]);
+#pragma unroll
+      for (int w = 0; w < 16; ++w) v[w] = __vmaxs2(v[w], __vmins2(a, __shfl_sync(0xFFFFFFFFu, v[w], k)));
+    }
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) row[q4] = make_uint4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
   }
-  static __device__ __forceinline__ bool any(Word v) { return v != 0u; }
 };
 template <>
 struct CTile<int32_t> {
   using Word = int2;
-  static __device__ __forceinline__ int64_t word_index(int32_t n, int32_t ti, int32_t tj, int t) {
-    return int64_t(ti * kCB + (t >> 4)) * (n >> 1) + tj * (kCB / 2) + (t & 15);
-  }
-  static __device__ __forceinline__ Word product(const int32_t* S, int32_t n, int32_t ti, int32_t tj, int32_t tr,
+  static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
                                                  int t) {
-    const int2* Sw = reinterpret_cast<const int2*>(S);
-    const int32_t nw2 = n >> 1;
-    const int2* arow = Sw + int64_t(ti * kCB + (t >> 4)) * nw2 + tr * (kCB / 2);
-    const int2* bcol = Sw + int64_t(tr * kCB) * nw2 + tj * (kCB / 2) + (t & 15);
-    int2 acc = Sw[word_index(n, ti, tj, t)];
+    const Word* arow = S + (ti * nt + tr) * 512 + (t >> 4) * 16;
+    const Word* bcol = S + (tr * nt + tj) * 512 + (t & 15);
+    int2 acc = S[(ti * nt + tj) * 512 + t];
 #pragma unroll 4
     for (int kk = 0; kk < kCB; kk += 2) {
       const int2 a = arow[kk >> 1];
-      const int2 b0 = bcol[int64_t(kk) * nw2], b1 = bcol[int64_t(kk + 1) * nw2];
+      const int2 b0 = bcol[kk * 16], b1 = bcol[(kk + 1) * 16];
       acc.x = __vimax3_s32(acc.x, min(a.x, b0.x), min(a.y, b1.x));
       acc.y = __vimax3_s32(acc.y, min(a.x, b0.y), min(a.y, b1.y));
     }
     return acc;
   }
-  static __device__ __forceinline__ Word fw_step(const int32_t* S, int32_t n, int32_t r, int k, int t) {
-    const int32_t i = r * kCB + (t >> 4);
-    const int32_t a = S[int64_t(i) * n + r * kCB + k];
-    const int2 b = reinterpret_cast<const int2*>(S)[int64_t(r * kCB + k) * (n >> 1) + r * (kCB / 2) + (t & 15)];
-    const int2 own = reinterpret_cast<const int2*>(S)[word_index(n, r, r, t)];
-    return make_int2(max(own.x, min(a, b.x)), max(own.y, min(a, b.y)));
+  static __device__ __forceinline__ void diag_warp(Word* S, int32_t nt, int32_t r, int lane) {
+    int4* row = reinterpret_cast<int4*>(S + (r * nt + r) * 512 + lane * 16);
+    int32_t v[32];
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) {
+      const int4 x = row[q4];
+      v[4 * q4] = x.x, v[4 * q4 + 1] = x.y, v[4 * q4 + 2] = x.z, v[4 * q4 + 3] = x.w;
+    }
+#pragma unroll
+    for (int k = 0; k < kCB; ++k) {
+      const int32_t a = v[k];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] = max(v[c], min(a, __shfl_sync(0xFFFFFFFFu, v[c], k)));
+    }
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) row[q4] = make_int4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
   }
-  static __device__ __forceinline__ bool any(Word v) { return (v.x | v.y) != 0; }
 };
 
 template <typename E>
@@ -555,37 +575,40 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   const int32_t nw = *warm;
   if (nw == 0 || nw > kClusterMaxWarm<E>) return;  // the same branch in every CTA
   extern __shared__ __align__(16) unsigned char cluster_smem[];
-  E* S = reinterpret_cast<E*>(cluster_smem);
+  Word* S = reinterpret_cast<Word*>(cluster_smem);
+  E* Se = reinterpret_cast<E*>(cluster_smem);
   __shared__ uint32_t tnz[4][4];  // 64 x 64 tiles of W holding a nonzero
   const int32_t n = (nw + kB - 1) / kB * kB;  // square side: whole 64-wide tiles
   const int32_t nt = n / kCB, ntw = (nw + kCB - 1) / kCB;  // tiles, tiles with warm rows
   const int t = threadIdx.x;
   const unsigned q = cl.block_rank();
-  constexpr int kPer16 = 16 / sizeof(E);  // entries per 16-byte piece
+  constexpr int kPer16 = 16 / sizeof(E);       // entries per 16-byte piece
+  constexpr int kChunks = kCB * kCB / kPer16;  // 16-byte pieces per tile
+  // element (i, j) of S lives at tile (i / 32, j / 32), row i % 32, column j % 32
+  auto at = [&](int32_t i, int32_t j) { return ((i / kCB) * nt + j / kCB) * (kCB * kCB) + (i % kCB) * kCB + j % kCB; };
   for (int32_t e = t; e < n * (n / kPer16); e += blockDim.x) {
-    const int32_t i = e / (n / kPer16), c = e % (n / kPer16);
-    reinterpret_cast<uint4*>(S)[e] = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(i) * ld) + c);
+    const int32_t i = e / (n / kPer16), j = (e % (n / kPer16)) * kPer16;
+    *reinterpret_cast<uint4*>(Se + at(i, j)) = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(i) * ld + j));
   }
   if (t < 16) tnz[t >> 2][t & 3] = 0u;
   cl.sync();  // every copy loaded before any remote write
-  Word* remote[kClusterCtas];
+  uint4* remote[kClusterCtas];
 #pragma unroll
-  for (int c = 0; c < kClusterCtas; ++c) remote[c] = reinterpret_cast<Word*>(cl.map_shared_rank(S, c));
-  auto store_all = [&](int32_t ti, int32_t tj, Word v) {
-    const int64_t off = T::word_index(n, ti, tj, t);
+  for (int c = 0; c < kClusterCtas; ++c) remote[c] = reinterpret_cast<uint4*>(cl.map_shared_rank(S, c));
+  // tile (ti, tj) is final in this CTA's copy: copy it into the others
+  auto broadcast = [&](int32_t tile) {
+    if (t < kChunks) {
+      const int32_t off = tile * kChunks + t;
+      const uint4 v = reinterpret_cast<const uint4*>(S)[off];
 #pragma unroll
-    for (int c = 0; c < kClusterCtas; ++c) remote[c][off] = v;
+      for (int c = 0; c < kClusterCtas; ++c)
+        if (c != int(q)) remote[c][off] = v;
+    }
   };
-  Word* Sw = reinterpret_cast<Word*>(S);
   unsigned long long ops = 0;
   for (int32_t r = 0; r < ntw; ++r) {
-    // 1. diagonal tile, in every CTA; row k and column k do not change in
-    //    step k, so one barrier per step
-    for (int k = 0; k < kCB; ++k) {
-      const Word v = T::fw_step(S, n, r, k, t);
-      Sw[T::word_index(n, r, r, t)] = v;
-      __syncthreads();
-    }
+    if (t < 32) T::diag_warp(S, nt, r, t);  // 1. diagonal tile, in every CTA
+    __syncthreads();
     // 2. panels: (r, j) for j != r, j < nt, then (i, r) for i != r, i < ntw
     const int32_t np = (nt - 1) + (ntw - 1);
     for (int32_t p = q; p < np; p += kClusterCtas) {
@@ -594,10 +617,11 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
         tj = p + (p >= r);
       else
         ti = (p - (nt - 1)) + ((p - (nt - 1)) >= r);
-      const Word v = T::product(S, n, ti, tj, r, t);
+      const Word v = T::product(S, nt, ti, tj, r, t);
       __syncthreads();  // the tile is its own operand: read it all before writing
-      store_all(ti, tj, v);
+      S[(ti * nt + tj) * 512 + t] = v;
       __syncthreads();
+      broadcast(ti * nt + tj);
       ++ops;
     }
     cl.sync();
@@ -606,16 +630,20 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     for (int32_t p = q; p < nr; p += kClusterCtas) {
       const int32_t a = p / (nt - 1), b = p % (nt - 1);
       const int32_t ti = a + (a >= r), tj = b + (b >= r);
-      store_all(ti, tj, T::product(S, n, ti, tj, r, t));  // operands are other tiles
+      S[(ti * nt + tj) * 512 + t] = T::product(S, nt, ti, tj, r, t);  // operands are other tiles
+      __syncthreads();
+      broadcast(ti * nt + tj);
       ++ops;
     }
     cl.sync();
   }
-  // write back rows q, q + 8, ... with a zero diagonal; nonzero bits per
+  // write back tiles q, q + 8, ... with a zero diagonal; nonzero bits per
   // 64 x 64 tile of W
-  for (int32_t i = q; i < n; i += kClusterCtas) {
-    for (int32_t j = t; j < n; j += blockDim.x) {
-      const E v = i == j ? E(0) : S[int64_t(i) * n + j];
+  for (int32_t tile = q; tile < nt * nt; tile += kClusterCtas) {
+    const int32_t ti = tile / nt, tj = tile % nt;
+    for (int32_t e = t; e < kCB * kCB; e += blockDim.x) {
+      const int32_t i = ti * kCB + e / kCB, j = tj * kCB + e % kCB;
+      const E v = i == j ? E(0) : Se[tile * (kCB * kCB) + e];
       W[int64_t(i) * ld + j] = v;
       if (v) tnz[i / kB][j / kB] = 1u;
     }
@@ -657,6 +685,41 @@ __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ 
   if (threadIdx.x == 0 && done) atomicAdd(&counters[0], done);
 }
 
+// beaten_by straight from the closed warm rows of W, for callers that need
+// the ranking but not a second pass over p: a cold candidate x (no outgoing
+// edge, p[x][*] = 0) is beaten by every warm j with p[j][x] > 0; a warm x by
+// every warm j with p[j][x] > p[x][j]; cold candidates beat nobody. CTA =
+// 32 relabeled columns x 8 row groups.
+template <typename E>
+__global__ void __launch_bounds__(256) wextract_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
+                                                       const int32_t* __restrict__ perm,
+                                                       const int32_t* __restrict__ warm, int32_t* __restrict__ bb) {
+  __shared__ int32_t part[8][33];
+  const int32_t nw = *warm;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  for (int32_t b0 = blockIdx.x * 32; b0 < m; b0 += gridDim.x * 32) {
+    const int32_t b = b0 + lane;
+    int32_t c = 0;
+    if (b < m) {
+      if (b < nw) {
+        for (int32_t j = g; j < nw; j += 8) c += (j != b && int32_t(W[int64_t(j) * mp + b]) > int32_t(W[int64_t(b) * mp + j]));
+      } else {
+#pragma unroll 4
+        for (int32_t j = g; j < nw; j += 8) c += W[int64_t(j) * mp + b] != E(0);
+      }
+    }
+    part[g][lane] = c;
+    __syncthreads();
+    if (g == 0 && b < m) {
+      int32_t tot = 0;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) tot += part[h][lane];
+      bb[perm[b]] = tot;
+    }
+    __syncthreads();
+  }
+}
+
 // Scratch of one closure: W (warm rows x all columns, padded square), the
 // progress words, queue head, abort flag, and the relabeling.
 struct ClosureBufs {
@@ -664,13 +727,16 @@ struct ClosureBufs {
   uint32_t* prog;
   int32_t *rowflag, *perm, *inv, *warm;
   unsigned long long* counters;
+  // optional: warm flags known from the tally, used when *hint_valid != 0
+  const int32_t* hint = nullptr;
+  const int32_t* hint_valid = nullptr;
 };
 
 // Rowflags, relabel, pack, closure of the warm square, cold product, widen.
 // ctx may be null (no counting, no profiling).
 template <typename E>
 int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
-                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream) {
+                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out = nullptr) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   E* W = static_cast<E*>(bf.W);
@@ -691,11 +757,11 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     const int64_t nbt = (m + kFlagT - 1) / kFlagT;
     const int g = grid_for(reinterpret_cast<const void*>(rowflag_kernel), 256, 0, nbt * (nbt + 1) / 2);
     Launch L(ctx, stream, "closure_rowflags", mm * 4.0);
-    rowflag_kernel<<<g, 256, 0, stream>>>(d, m, bound, bf.rowflag, status);
+    rowflag_kernel<<<g, 256, 0, stream>>>(d, m, bound, bf.rowflag, status, bf.hint_valid);
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    relabel_kernel<<<1, 1024, 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm);
+    relabel_kernel<<<1, 1024, 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm, bf.hint, bf.hint_valid);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 256, 0, int64_t(mp / 32) * (mp / 32));
@@ -736,12 +802,16 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     Launch L(ctx, stream, "closure_widen", mm * 4.0);
     widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.warm, p);
   }
+  if (bb_out) {
+    Launch L(ctx, stream, "closure_beaten_by", 0.0);
+    wextract_kernel<E><<<(m + 31) / 32, 256, 0, stream>>>(W, mp, m, bf.perm, bf.warm, bb_out);
+  }
   return check_launch();
 }
 
 template <typename E>
 int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
-                cudaStream_t stream) {
+                cudaStream_t stream, int32_t* bb_out, const int32_t* hint, const int32_t* hint_valid) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   Carver cv(ws);
@@ -753,8 +823,10 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   bf.inv = cv.take<int32_t>(size_t(m));
   bf.warm = cv.take<int32_t>(1);
   bf.counters = ctx->counters;
+  bf.hint = hint;
+  bf.hint_valid = hint_valid;
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
-  return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream);
+  return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream, bb_out);
 }
 
 }  // namespace
@@ -767,9 +839,11 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
 }
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
-                   void* ws, cudaStream_t stream) {
-  if (use_s16(bound, flags)) return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream);
-  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream);
+                   void* ws, cudaStream_t stream, int32_t* beaten_by, const int32_t* hint,
+                   const int32_t* hint_valid) {
+  if (use_s16(bound, flags))
+    return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid);
+  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid);
 }
 
 // ------------------------------------------------- allocation-free variant

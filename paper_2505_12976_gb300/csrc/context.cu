@@ -111,11 +111,12 @@ int schulze_reserve(schulze_ctx* ctx, int32_t m_max, int64_t n_max, int32_t k_ma
                                tally_workspace_bytes(n_max, m_max, k_max, SCHULZE_F_TALLY_SPARSE)));
   size_t c = std::max(closure_workspace_bytes(m_max, n_max, 0), closure_workspace_bytes(m_max, 1, 0));
   size_t x = extract_workspace_bytes(m_max);
-  size_t need = std::max(t, std::max(c, x));
-  // schulze_run_host keeps ranks, d and p in the workspace next to the stages
+  // schulze_run keeps the tally's warm flags and beaten_by after the stages
+  const size_t mv = align_up(size_t(m_max) * 4, 256);
+  size_t need = std::max(align_up(std::max(t, c), 256) + 2 * mv + 256, x);
+  // schulze_run_host keeps ranks, d, p and four vectors next to the stages
   size_t host_path = align_up(size_t(n_max) * size_t(k_max) * 4, 256) +
-                     2 * align_up(size_t(m_max) * size_t(m_max) * 4, 256) + align_up(2 * size_t(m_max) * 4, 256) +
-                     need + 4096;
+                     2 * align_up(size_t(m_max) * size_t(m_max) * 4, 256) + 4 * mv + 256 + need + 4096;
   need = std::max(need, host_path);
   int rc = ensure_workspace(ctx, need, nullptr);
   if (rc) return rc;
@@ -177,13 +178,25 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
   if ((flags & SCHULZE_F_TALLY_DENSE) && (flags & SCHULZE_F_TALLY_SPARSE)) return SCHULZE_EINVAL;
   if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || n > 32767)) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
-  size_t need = std::max(tally_workspace_bytes(n, m, k, flags),
-                         std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
+  // beaten_by comes out of the closure (from its warm rows), kept after the
+  // closure's scratch when the caller does not want it
+  // warm flags from the tally and the closure's beaten_by live after both
+  // stages' scratch
+  const size_t mv = align_up(size_t(m) * 4, 256);
+  const size_t keep = std::max(align_up(tally_workspace_bytes(n, m, k, flags), 256),
+                               align_up(closure_workspace_bytes(m, n, flags), 256));
+  size_t need = std::max(keep + 2 * mv + 256, extract_workspace_bytes(m));
   if (int rc = ensure_workspace(ctx, need, stream)) return rc;
-  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream)) return rc;
-  if (int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream)) return rc;
-  if (winners || order || beaten_by)
-    if (int rc = extract_launch(ctx, p, m, winners, order, beaten_by, ctx->ws.base, stream)) return rc;
+  char* tail = static_cast<char*>(ctx->ws.base) + keep;
+  int32_t* hint = reinterpret_cast<int32_t*>(tail);
+  int32_t* hint_valid = reinterpret_cast<int32_t*>(tail + mv);
+  int32_t* bb = beaten_by ? beaten_by : reinterpret_cast<int32_t*>(tail + mv + 256);
+  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream, hint, hint_valid)) return rc;
+  const bool ext = winners || order || beaten_by;
+  if (int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream, ext ? bb : nullptr, hint, hint_valid))
+    return rc;
+  if (ext && (winners || order))
+    if (int rc = extract_from_beaten_by(ctx, bb, m, winners, order, ctx->ws.base, stream)) return rc;
   return SCHULZE_OK;
 }
 
@@ -197,7 +210,7 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
   size_t stage = std::max(tally_workspace_bytes(n, m, k, flags),
                           std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
-  size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + align_up(2 * size_t(m) * 4, 256);
+  size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + 4 * align_up(size_t(m) * 4, 256) + 256;
   if (int rc = ensure_workspace(ctx, head + stage + 4096, stream)) return rc;
   Carver cv(ctx->ws.base);
   int32_t* ranks = cv.take<int32_t>(size_t(n) * size_t(k));
@@ -205,13 +218,18 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   int32_t* p = cv.take<int32_t>(size_t(m) * size_t(m));
   int32_t* win = cv.take<int32_t>(size_t(m));
   int32_t* ord = cv.take<int32_t>(size_t(m));
+  int32_t* bb = cv.take<int32_t>(size_t(m));
+  int32_t* hint = cv.take<int32_t>(size_t(m));
+  int32_t* hint_valid = cv.take<int32_t>(1);
   void* rest = cv.take<char>(0);
   if (rbytes && cudaMemcpyAsync(ranks, ranks_host, rbytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return SCHULZE_ECUDA;
-  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, stream)) return rc;
-  if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, stream)) return rc;
-  if (winners_host || order_host)
-    if (int rc = extract_launch(ctx, p, m, win, ord, nullptr, rest, stream)) return rc;
+  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, stream, hint, hint_valid)) return rc;
+  const bool ext = winners_host || order_host;
+  if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, stream, ext ? bb : nullptr, hint, hint_valid))
+    return rc;
+  if (ext)
+    if (int rc = extract_from_beaten_by(ctx, bb, m, win, ord, rest, stream)) return rc;
   if (winners_host &&
       cudaMemcpyAsync(winners_host, win, size_t(m) * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return SCHULZE_ECUDA;

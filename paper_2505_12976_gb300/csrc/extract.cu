@@ -73,8 +73,32 @@ __global__ void __launch_bounds__(256) rank_count_kernel(const int32_t* __restri
   if (i < m && c) atomicAdd(&pos[i], c);
 }
 
-__global__ void rank_scatter_kernel(const int32_t* __restrict__ pos, int32_t m, int32_t* __restrict__ order) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) order[pos[i]] = i;
+// order[pos[i]] = i; with winners, also winners[i] = (bb[i] == 0).
+__global__ void rank_scatter_kernel(const int32_t* __restrict__ pos, const int32_t* __restrict__ bb, int32_t m,
+                                    int32_t* __restrict__ order, int32_t* __restrict__ winners) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    order[pos[i]] = i;
+    if (winners) winners[i] = bb[i] == 0;
+  }
+}
+
+// winners and ranking from beaten_by; pos is scratch [m]
+int finish(schulze_ctx* ctx, const int32_t* bb, int32_t* pos, int32_t m, int32_t* winners, int32_t* order,
+           cudaStream_t stream) {
+  const int g = (m + 255) / 256;
+  if (order) {
+    if (cudaMemsetAsync(pos, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+    {
+      Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
+      rank_count_kernel<<<dim3(g, (m + kRankChunk - 1) / kRankChunk), 256, 0, stream>>>(bb, m, pos);
+    }
+    Launch L(ctx, stream, "extract_order", double(m) * 8.0);
+    rank_scatter_kernel<<<g, 256, 0, stream>>>(pos, bb, m, order, winners);
+  } else if (winners) {
+    Launch L(ctx, stream, "extract_winners", double(m) * 8.0);
+    winners_kernel<<<g, 256, 0, stream>>>(bb, m, winners);
+  }
+  return check_launch();
 }
 
 }  // namespace
@@ -92,23 +116,15 @@ int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winne
     Launch L(ctx, stream, "extract_beaten_by", double(m) * double(m) * 4.0);
     beaten_by_kernel<<<dim3(nbt, nbt), 256, 0, stream>>>(p, m, bb);
   }
-  const int g = (m + 255) / 256;
-  if (winners) {
-    Launch L(ctx, stream, "extract_winners", double(m) * 8.0);
-    winners_kernel<<<g, 256, 0, stream>>>(bb, m, winners);
-  }
-  if (order) {
-    if (cudaMemsetAsync(pos, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-    {
-      Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
-      rank_count_kernel<<<dim3(g, (m + kRankChunk - 1) / kRankChunk), 256, 0, stream>>>(bb, m, pos);
-    }
-    {
-      Launch L(ctx, stream, "extract_order", double(m) * 8.0);
-      rank_scatter_kernel<<<g, 256, 0, stream>>>(pos, m, order);
-    }
-  }
-  return check_launch();
+  if (int rc = check_launch()) return rc;
+  return finish(ctx, bb, pos, m, winners, order, stream);
+}
+
+int extract_from_beaten_by(schulze_ctx* ctx, const int32_t* beaten_by, int32_t m, int32_t* winners, int32_t* order,
+                           void* ws, cudaStream_t stream) {
+  Carver cv(ws);
+  int32_t* pos = cv.take<int32_t>(size_t(m));
+  return finish(ctx, beaten_by, pos, m, winners, order, stream);
 }
 
 }  // namespace schulze

@@ -82,12 +82,27 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags);
 size_t extract_workspace_bytes(int32_t m);
 
 // Stage launchers operating on caller-provided workspace (no allocation).
+// With hint / hint_valid (int32 [m] and one word, outside ws), a top-k
+// tally also reports which candidates have an outgoing edge: when some
+// candidate is listed on no ballot, exactly the listed ones do (each beats
+// every unlisted one, and an unlisted one prefers nobody). *hint_valid is
+// set to 1 when hint holds them, else 0.
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
-                 uint32_t flags, void* ws, cudaStream_t stream);
+                 uint32_t flags, void* ws, cudaStream_t stream, int32_t* hint = nullptr,
+                 int32_t* hint_valid = nullptr);
+// With beaten_by non-null the closure also fills it (int32 [m]) from its
+// warm rows, so extract_from_beaten_by can finish without reading p. With
+// hint / hint_valid (from tally_launch, outside ws) the closure takes the
+// warm flags from the tally when *hint_valid is set, skipping its own pass
+// over d (and that pass's bound check, which the tally's d meets).
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
-                   void* ws, cudaStream_t stream);
+                   void* ws, cudaStream_t stream, int32_t* beaten_by = nullptr, const int32_t* hint = nullptr,
+                   const int32_t* hint_valid = nullptr);
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream);
+// Winners (beaten_by == 0) and the ranking from a filled beaten_by.
+int extract_from_beaten_by(schulze_ctx* ctx, const int32_t* beaten_by, int32_t m, int32_t* winners, int32_t* order,
+                           void* ws, cudaStream_t stream);
 
 // Brackets one kernel launch: counts it and, when profiling is on, records
 // CUDA events around it on `stream`, filed under `name` with `work` units.

@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
                                                            int32_t nblocks, uint32_t emax, uint32_t* __restrict__ off,
                                                            uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff,
                                                            int32_t compact_max, int32_t* __restrict__ slot,
-                                                           int32_t* __restrict__ act, int32_t* __restrict__ meta) {
+                                                           int32_t* __restrict__ act, int32_t* __restrict__ meta,
+                                                           int32_t* __restrict__ hint,
+                                                           int32_t* __restrict__ hint_valid) {
   __shared__ uint32_t part[1024];
   {
     uint32_t* flag = reinterpret_cast<uint32_t*>(slot);
@@ -250,6 +252,10 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
       if (s >= 0) act[s] = c;
     }
     if (threadIdx.x == 0) meta[0] = int32_t(na), meta[1] = int32_t(na) <= compact_max ? 1 : 0;
+    if (hint) {  // warm flags for the closure: the listed candidates, when one is never listed
+      for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hint[c] = cnt[c] > 0 ? 1 : 0;
+      if (threadIdx.x == 0) *hint_valid = int32_t(na) < m ? 1 : 0;
+    }
     __syncthreads();
   }
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) off[c] = uint32_t(cnt[c]);
@@ -666,8 +672,9 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
 }
 
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
-                 uint32_t flags, void* ws, cudaStream_t stream) {
+                 uint32_t flags, void* ws, cudaStream_t stream, int32_t* hint, int32_t* hint_valid) {
   const size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
+  if (hint && cudaMemsetAsync(hint_valid, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
   if (n == 0 || k == 0) {
     return cudaMemsetAsync(d, 0, mm, stream) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
   }
@@ -745,7 +752,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
     sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot,
-                                               act, meta);
+                                               act, meta, hint, hint_valid);
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_pairs", double(m) * double(m) * 4.0 + double(total) * 4.0);
