@@ -442,16 +442,29 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-// Compact form, first kernel (one CTA per slice of the ballots).
-// (a) Fills the CTA's share of d, taken as a flat range of m*m entries, as if
-//     C were zero: d[i][j] = cnt[i] for listed i and j != i, else 0.
-// (b) Counts C over A x A for the slice in shared memory (cell [slot i]
-//     [slot j], 16-bit lanes packed two per word when a slice has at most
-//     65535 ballots, else 32-bit) and stores it as this CTA's partial.
-// A warp takes one ballot at a time: its listed slots are staged in shared
-// memory (the first 64 also in registers), and for every position q the
-// lanes add 1 to C[slot at q][slot at p] for p < q. Ids outside [0, m) are
-// skipped (the count pass reports them).
+// Compact form, first kernel (one CTA per slice of the ballots), its warps
+// split between two jobs that run side by side:
+// (a) kFillWarps warps fill the CTA's rows of d as if C were zero: d[i][j] =
+//     cnt[i] for listed i and j != i, else 0 (stores, bound by HBM);
+// (b) the others count C over A x A for the slice in shared memory (cell
+//     [slot i][slot j], 16-bit lanes packed two per word when a slice has at
+//     most 65535 ballots, else 32-bit; bound by shared-memory atomics) and
+//     store it as this CTA's partial.
+// Counting: a warp per ballot, its slots staged in shared memory; for every
+// position q the lanes add 1 to C[slot at q][slot at p] for p < q, so the
+// lanes of one atomic always hit distinct counters (ballots drawn around a
+// common order would make lanes on different ballots collide). Ids outside
+// [0, m) are skipped (the count pass reports them).
+constexpr int kFillWarps = 4;
+
+template <bool kPacked>
+__device__ __forceinline__ void count_pair(uint32_t* crow, uint32_t sp) {
+  if (kPacked)
+    atomicAdd(crow + (sp >> 1), 1u << ((sp & 1u) * 16u));
+  else
+    atomicAdd(crow + sp, 1u);
+}
+
 template <bool kPacked>
 __global__ void __launch_bounds__(kCompactThreads, 1)
     compact_pairs_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
@@ -465,70 +478,74 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
   const int32_t words = na * wpr;
   uint32_t* C = smem_pairs;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  uint16_t* st = reinterpret_cast<uint16_t*>(smem_pairs + ((words + 3) & ~3)) + wib * stage_len;
+  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_pairs + ((words + 3) & ~3));
   for (int32_t t = threadIdx.x; t < words; t += blockDim.x) C[t] = 0u;
+  __syncthreads();
 
-  // (a) this CTA's rows of d, 16 bytes per store where rows allow it
-  {
+  if (wib < kFillWarps) {
+    // (a) this CTA's rows of d, 16 bytes per store where rows allow it
+    const int ft = threadIdx.x, nft = kFillWarps * 32;
     const int32_t rper = (m + gridDim.x - 1) / gridDim.x;
     const int32_t i0 = min(m, int32_t(blockIdx.x) * rper), i1 = min(m, i0 + rper);
     for (int32_t i = i0; i < i1; ++i) {
       const int32_t b = slot[i] < 0 ? 0 : cnt[i];
       int32_t* drow = d + int64_t(i) * m;
       if ((m & 3) == 0) {
-        for (int32_t j = 4 * threadIdx.x; j < m; j += 4 * blockDim.x) {
+        for (int32_t j = 4 * ft; j < m; j += 4 * nft) {
           const int32_t t = i - j;  // diagonal lane inside the 4 entries, if any
           *reinterpret_cast<int4*>(drow + j) =
               make_int4(t == 0 ? 0 : b, t == 1 ? 0 : b, t == 2 ? 0 : b, t == 3 ? 0 : b);
         }
       } else {
-        for (int32_t j = threadIdx.x; j < m; j += blockDim.x) drow[j] = j == i ? 0 : b;
+        for (int32_t j = ft; j < m; j += nft) drow[j] = j == i ? 0 : b;
       }
     }
-  }
-  __syncthreads();
-
-  // (b) pair counts of this CTA's ballots
-  const int64_t vper = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t v0 = min(n, int64_t(blockIdx.x) * vper), v1 = min(n, v0 + vper);
-  for (int64_t v = v0 + wib; v < v1; v += nwarp) {
-    const int32_t* row = ranks + v * k;
-    for (int32_t q = lane; q < k; q += 32) {
-      const int32_t c = row[q];
-      const int32_t sc = (c >= 0 && c < m) ? slot[c] : -1;
-      st[q] = sc < 0 ? kNoSlot : uint16_t(sc);
-    }
-    __syncwarp();
-    // this lane's two low positions: counter word and increment, hoisted
-    const uint32_t r0 = lane < k ? st[lane] : kNoSlot;
-    const uint32_t r1 = lane + 32 < k ? st[lane + 32] : kNoSlot;
-    const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
-    const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
-    const int32_t qlo = min(k, 32), qhi = min(k, 64);
-    for (int32_t q = 1; q < qlo; ++q) {  // row positions 1..31: lanes p < q
-      const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
-      if (sq == kNoSlot) continue;  // uniform over the warp
-      if (lane < q && r0 != kNoSlot) atomicAdd(C + int32_t(sq) * wpr + w0, i0);
-    }
-    for (int32_t q = 32; q < qhi; ++q) {  // 32..63: all low lanes, high lanes p < q
-      const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r1, q - 32);
-      if (sq == kNoSlot) continue;
-      uint32_t* crow = C + int32_t(sq) * wpr;
-      if (r0 != kNoSlot) atomicAdd(crow + w0, i0);
-      if (lane + 32 < q && r1 != kNoSlot) atomicAdd(crow + w1, i1);
-    }
-    for (int32_t q = 64; q < k; ++q) {  // long ballots
-      const uint32_t sq = st[q];
-      if (sq == kNoSlot) continue;
-      uint32_t* crow = C + int32_t(sq) * wpr;
-      if (r0 != kNoSlot) atomicAdd(crow + w0, i0);
-      if (r1 != kNoSlot) atomicAdd(crow + w1, i1);
-      for (int32_t p = 64 + lane; p < q; p += 32) {
-        const uint32_t sp = st[p];
-        if (sp != kNoSlot) atomicAdd(crow + (kPacked ? sp >> 1 : sp), kPacked ? 1u << ((sp & 1u) * 16u) : 1u);
+  } else {
+    // (b) pair counts of this CTA's ballots
+    const int64_t vper = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t v0 = min(n, int64_t(blockIdx.x) * vper), v1 = min(n, v0 + vper);
+    const int cw = wib - kFillWarps;  // counting warp
+    {
+      uint16_t* st = stage + cw * stage_len;
+      const int ncw = nwarp - kFillWarps;
+      for (int64_t v = v0 + cw; v < v1; v += ncw) {
+        const int32_t* row = ranks + v * k;
+        for (int32_t q = lane; q < k; q += 32) {
+          const int32_t c = row[q];
+          const int32_t sc = (c >= 0 && c < m) ? slot[c] : -1;
+          st[q] = sc < 0 ? kNoSlot : uint16_t(sc);
+        }
+        __syncwarp();
+        // this lane's two low positions (p = lane, lane + 32) in registers
+        const uint32_t r0 = lane < k ? st[lane] : kNoSlot;
+        const uint32_t r1 = lane + 32 < k ? st[lane + 32] : kNoSlot;
+        const int32_t qlo = min(k, 32), qhi = min(k, 64);
+        for (int32_t q = 1; q < qlo; ++q) {  // rows 1..31: lanes p < q
+          const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
+          if (sq == kNoSlot) continue;  // uniform over the warp
+          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0);
+        }
+        for (int32_t q = 32; q < qhi; ++q) {  // rows 32..63: all low lanes, high lanes p < q
+          const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r1, q - 32);
+          if (sq == kNoSlot) continue;
+          uint32_t* crow = C + int32_t(sq) * wpr;
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
+          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+        }
+        for (int32_t q = 64; q < k; ++q) {  // long ballots
+          const uint32_t sq = st[q];
+          if (sq == kNoSlot) continue;
+          uint32_t* crow = C + int32_t(sq) * wpr;
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
+          if (r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+          for (int32_t p = 64 + lane; p < q; p += 32) {
+            const uint32_t sp = st[p];
+            if (sp != kNoSlot) count_pair<kPacked>(crow, sp);
+          }
+        }
+        __syncwarp();
       }
     }
-    __syncwarp();
   }
   __syncthreads();
   uint32_t* out = partial + int64_t(blockIdx.x) * words;

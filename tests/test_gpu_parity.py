@@ -93,13 +93,15 @@ def test_tally_dense_and_sparse(m, n, k):
         eq(host(S.schulze_tally(cu(r), m, flags=flags)), want, f"tally flags={flags}")
 
 
-@pytest.mark.parametrize("m,n,k,phi", [(4096, 3000, 50, 0.9), (1000, 777, 20, 0.97), (600, 2000, 256, 0.995),
+@pytest.mark.parametrize("m,n,k,phi", [(4096, 3000, 50, 0.9), (1000, 777, 20, 0.97), (1000, 3000, 100, 0.9),
+                                       (600, 2000, 256, 0.995),
                                        (256, 4000, 5, 1.0), (257, 4000, 5, 1.0), (5003, 1500, 3, 0.5)])
 def test_tally_compact_and_grouped_agree(m, n, k, phi):
-    """Top-k ballots over few listed candidates (the compact pair count) and
-    over many (the grouped one), both forms forced, against the oracle;
-    256 listed candidates is the largest compact case, 257 the smallest
-    grouped one."""
+    """Top-k ballots over few listed candidates (the compact pair count:
+    a lane per ballot up to 64 entries, a warp per ballot beyond) and over
+    many (the grouped one), both forms forced, against the oracle; 256
+    listed candidates is the largest compact case, 257 the smallest grouped
+    one."""
     r = W.mallows(m + n + k, n, m, k, phi, W.permutation(m + k, m))
     want = oracle.tally(r, m)
     for flags in (S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
