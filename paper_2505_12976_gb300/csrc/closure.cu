@@ -21,6 +21,13 @@
 //   * the cold columns: p[i][c] = max(w[i][c], max_x min(p[i][x], w[x][c]))
 //     over warm x, one (max, min) product with the closed warm square.
 //
+// When the caller's tally says the warm candidates are exactly the listed
+// ones of a top-k profile (hint), every cold column is the same vector: for
+// an unlisted c and a listed x, d[x][c] = cnt[x] (every ballot listing x puts
+// it above c) and d[c][x] = 0, so w[x][c] = cnt[x] for all such c. The cold
+// product then reduces to one column u[i] = max(w[i][c], max_x min(p[i][x],
+// w[x][c])), which p, W's cold columns and beaten_by take from there.
+//
 // The warm-square closure runs in rounds of B = 64 candidates; round r
 //   1. closes the diagonal tile (r, r) by plain Floyd-Warshall,
 //   2. updates the row and column panels: X = max(X, D (x) X) / max(X, X (x) D)
@@ -43,6 +50,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "tiles.cuh"
@@ -164,43 +172,52 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
 }
 
 // W[a][b] = w[perm[a]][perm[b]] for the warm rows a < 64 * nbr (0 outside
-// m x m, on the diagonal and where d does not beat its transpose). CTAs take
-// 32 x 32 block pairs (X, Y), X <= Y and X inside the warm rows, writing
-// W[X][Y] and, when Y is inside them too, W[Y][X]; a warp that writes a
+// m x m, on the diagonal and where d does not beat its transpose). One CTA
+// pass per row a: with x = perm[a], the threads walk b, reading d[x][perm b]
+// (along row x) and d[perm b][x] (down column x); a warp that writes a
 // nonzero sets the nonzero bit of its 64 x 64 tile's progress word.
+//
+// With the tally's flags (hint valid), a candidate y without edges is one no
+// ballot lists, so d[y][x] = 0 and that read is skipped.
+// With uniform cold columns only the square (b < 64 nbr) is written, and
+// ucol[a] receives the cold columns' common value for row a.
 template <typename E>
-__global__ void __launch_bounds__(256) pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp,
+__global__ void __launch_bounds__(512) pack_kernel(const int32_t* __restrict__ d, int32_t m, int32_t mp,
                                                    const int32_t* __restrict__ perm, const int32_t* __restrict__ warm,
-                                                   E* __restrict__ W, uint32_t* __restrict__ prog, int32_t nb) {
-  __shared__ int32_t t1[32][33], t2[32][33];  // t1[r][c] = d[perm[X+r]][perm[Y+c]], t2 = (Y, X)
+                                                   E* __restrict__ W, uint32_t* __restrict__ prog, int32_t nb,
+                                                   const int32_t* __restrict__ hint,
+                                                   const int32_t* __restrict__ hint_valid, int32_t* __restrict__ ucol) {
+  const bool hv = hint_valid && *hint_valid;
   const int32_t rows = (*warm + kB - 1) / kB * kB;  // W rows to write
-  const int32_t nx = rows / 32, ny = mp / 32;
-  const int64_t items = int64_t(nx) * ny;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
-    const int32_t X = int32_t(t / ny) * 32, Y = int32_t(t % ny) * 32;
-    if (X > Y) continue;
-    for (int r = ty; r < 32; r += 8) {
-      int32_t a = X + r, b = Y + tx;
-      t1[r][tx] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
-      a = Y + r, b = X + tx;
-      t2[r][tx] = (a < m && b < m) ? d[int64_t(perm[a]) * m + perm[b]] : 0;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
+  const bool uc = hv && rows < m;                    // uniform cold columns beyond the square
+  const int32_t bend = uc ? rows : mp;
+  const int lane = threadIdx.x & 31;
+  constexpr int kU = 8;  // columns per thread and pass, their loads issued together
+  for (int32_t a = blockIdx.x; a < rows; a += gridDim.x) {
+    E* wrow = W + int64_t(a) * mp;
+    const int32_t x = a < m ? perm[a] : -1;
+    const int32_t* drow = x >= 0 ? d + int64_t(x) * m : nullptr;
+    if (uc && threadIdx.x == 0) ucol[a] = (x >= 0 && a < *warm) ? max(drow[perm[rows]], 0) : 0;
+    for (int32_t b0 = 0; b0 < bend; b0 += kU * blockDim.x) {
+      int32_t y[kU], v[kU], u[kU];
 #pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int32_t a = (side ? Y : X) + r, b = (side ? X : Y) + tx;
-        if (side && Y >= rows) break;  // row block outside W
-        const int32_t x = side ? t2[r][tx] : t1[r][tx];
-        const int32_t y = side ? t1[tx][r] : t2[tx][r];
-        const int32_t out = (a < m && b < m && a != b && x > y) ? x : 0;
-        if (b < mp) W[int64_t(a) * mp + b] = E(out);
-        if (__any_sync(0xFFFFFFFFu, out != 0) && tx == 0) atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
-        if (X == Y) break;  // a diagonal block pair is one block
+      for (int q = 0; q < kU; ++q) {
+        const int32_t b = b0 + q * blockDim.x + threadIdx.x;
+        y[q] = (x >= 0 && b < m && b < bend && b != a) ? perm[b] : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        v[q] = y[q] >= 0 ? drow[y[q]] : 0;
+        u[q] = (y[q] >= 0 && !(hv && !hint[y[q]])) ? d[int64_t(y[q]) * m + x] : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int32_t b = b0 + q * blockDim.x + threadIdx.x;
+        const int32_t out = v[q] > u[q] ? v[q] : 0;
+        if (b < bend) wrow[b] = E(out);
+        if (__any_sync(0xFFFFFFFFu, out != 0) && lane == 0) atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -209,8 +226,12 @@ __global__ void __launch_bounds__(256) pack_kernel(const int32_t* __restrict__ d
 template <typename E>
 __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
                                                     const int32_t* __restrict__ inv,
-                                                    const int32_t* __restrict__ warm, int32_t* __restrict__ p) {
+                                                    const int32_t* __restrict__ warm, int32_t* __restrict__ p,
+                                                    const int32_t* __restrict__ hint_valid,
+                                                    const int32_t* __restrict__ ucold) {
   const int32_t nw = *warm;
+  const int32_t rows = (nw + kB - 1) / kB * kB;
+  const bool uc = hint_valid && *hint_valid && rows < m;  // cold columns beyond the square: ucold[ix]
   for (int32_t x = blockIdx.x; x < m; x += gridDim.x) {
     const int32_t ix = inv[x];
     int32_t* prow = p + int64_t(x) * m;
@@ -225,17 +246,36 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
     }
     const E* wrow = W + int64_t(ix) * mp;
     if ((m & 3) == 0) {
-      for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x) {
-        const int4 iv = *reinterpret_cast<const int4*>(inv + y);
-        int4 v = make_int4(int32_t(wrow[iv.x]), int32_t(wrow[iv.y]), int32_t(wrow[iv.z]), int32_t(wrow[iv.w]));
-        if (x >= y && x < y + 4) {
-          const int32_t t = x - y;
-          v.x = t == 0 ? 0 : v.x, v.y = t == 1 ? 0 : v.y, v.z = t == 2 ? 0 : v.z, v.w = t == 3 ? 0 : v.w;
+      constexpr int kU = 4;  // int4 groups per thread and pass, loads issued together
+      for (int32_t y0 = 0; y0 < m; y0 += 4 * kU * blockDim.x) {
+        int4 iv[kU];
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+          const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
+          iv[q] = y < m ? *reinterpret_cast<const int4*>(inv + y) : make_int4(0, 0, 0, 0);
         }
-        *reinterpret_cast<int4*>(prow + y) = v;
+        int4 v[kU];
+        const int32_t uv = uc ? ucold[ix] : 0;
+        auto at = [&](int32_t iy) { return (uc && iy >= rows) ? uv : int32_t(wrow[iy]); };
+#pragma unroll
+        for (int q = 0; q < kU; ++q) v[q] = make_int4(at(iv[q].x), at(iv[q].y), at(iv[q].z), at(iv[q].w));
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+          const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
+          if (y >= m) continue;
+          if (x >= y && x < y + 4) {
+            const int32_t t = x - y;
+            v[q].x = t == 0 ? 0 : v[q].x, v[q].y = t == 1 ? 0 : v[q].y;
+            v[q].z = t == 2 ? 0 : v[q].z, v[q].w = t == 3 ? 0 : v[q].w;
+          }
+          *reinterpret_cast<int4*>(prow + y) = v[q];
+        }
       }
     } else {
-      for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = (y == x) ? 0 : int32_t(wrow[inv[y]]);
+      for (int32_t y = threadIdx.x; y < m; y += blockDim.x) {
+        const int32_t iy = inv[y];
+        prow[y] = (y == x) ? 0 : (uc && iy >= rows) ? ucold[ix] : int32_t(wrow[iy]);
+      }
     }
   }
 }
@@ -655,6 +695,122 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   cl.sync();  // no CTA leaves while others may still write into it
 }
 
+// Uniform cold columns: u[i] = max(ucol[i], max_x min(W[i][x], ucol[x]))
+// over the warm x (a warp per warm row i, lanes over x), and ucount = the
+// number of warm rows with u > 0.
+template <typename E>
+__global__ void __launch_bounds__(256) uniform_cold_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
+                                                           const int32_t* __restrict__ warm,
+                                                           const int32_t* __restrict__ hint_valid,
+                                                           const int32_t* __restrict__ ucol, int32_t* __restrict__ u,
+                                                           int32_t* __restrict__ ucount) {
+  const int32_t nw = *warm;
+  const int32_t rows = (nw + kB - 1) / kB * kB;
+  if (!(hint_valid && *hint_valid && rows < m)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = wid; i < nw; i += nwarps) {
+    const E* wrow = W + i * mp;
+    int32_t best = 0;
+    for (int32_t x = lane; x < nw; x += 32) best = max(best, min(int32_t(wrow[x]), ucol[x]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+    if (lane == 0) {
+      const int32_t ui = max(best, ucol[i]);
+      u[i] = ui;
+      if (ui > 0) atomicAdd(ucount, 1);
+    }
+  }
+}
+
+// Cold columns for warm squares that fit shared memory (the cluster
+// closure's sizes): every CTA keeps the closed square P (nwp x nwp, rows
+// padded by one word against bank conflicts) and walks strips of
+// kStripWords words (16-bit pairs, or int32 entries) of cold columns:
+// X[i][j] = max(X[i][j], max_k min(P[i][k], X[k][j])) for the warm rows i,
+// with X[k][j] staged before any row of the strip is written. Thread t keeps
+// words w and w + 8 (w = t % 8) of rows t / 8 + 64 r, r < 4, so that each
+// load of P or of the strip feeds several updates.
+constexpr int kStripWords = 16;
+
+template <typename E>
+__global__ void __launch_bounds__(512, 1) cold_strip_kernel(E* __restrict__ W, int32_t ld, int32_t m,
+                                                            const int32_t* __restrict__ warm,
+                                                            unsigned long long* counters,
+                                                            const int32_t* __restrict__ hint_valid) {
+  using Wd = typename std::conditional<sizeof(E) == 2, uint32_t, int32_t>::type;  // one word
+  constexpr int kPer = sizeof(Wd) / sizeof(E);                                  // entries per word
+  const int32_t nw = *warm;
+  if (nw == 0 || nw > kClusterMaxWarm<E>) return;  // the tile kernel's case
+  const int32_t nwp = (nw + kB - 1) / kB * kB;
+  if (hint_valid && *hint_valid && nwp < m) return;  // uniform cold columns
+  const int32_t rowwords = ld / kPer;
+  const int32_t nstrips = (rowwords - nwp / kPer + kStripWords - 1) / kStripWords;
+  if (int32_t(blockIdx.x) >= nstrips) return;
+  extern __shared__ __align__(16) unsigned char strip_smem[];
+  const int32_t pw = nwp / kPer, pst = pw + 1;  // words per row of P, padded (odd)
+  Wd* P = reinterpret_cast<Wd*>(strip_smem);
+  Wd* B = P + nwp * pst;  // [nwp][kStripWords]
+  const int t = threadIdx.x;
+  for (int32_t e = t; e < nwp * (pw / 4); e += blockDim.x) {  // 16-byte reads of W
+    const int32_t i = e / (pw / 4), c4 = e % (pw / 4);
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(i) * ld) + c4);
+    Wd* dst = P + i * pst + 4 * c4;
+    dst[0] = Wd(v.x), dst[1] = Wd(v.y), dst[2] = Wd(v.z), dst[3] = Wd(v.w);
+  }
+  const int w = t & 7, rg = t >> 3;  // words w, w + 8; rows rg + 64 r
+  const int32_t K = (nw + 1) & ~1;   // rows >= nw are zero
+  unsigned long long done = 0;
+  for (int32_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
+    const int32_t c0 = pw + s * kStripWords;  // first word of the strip
+    __syncthreads();  // P loaded / the previous strip's B consumed
+    for (int32_t e = t; e < nwp * kStripWords; e += blockDim.x) {
+      const int32_t k = e / kStripWords, c = c0 + e % kStripWords;
+      B[e] = c < rowwords ? reinterpret_cast<const Wd*>(W + int64_t(k) * ld)[c] : Wd(0);
+    }
+    __syncthreads();
+    Wd acc[4][2];
+    bool row_ok[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int32_t i = rg + 64 * r;
+      row_ok[r] = i < nw;
+      acc[r][0] = row_ok[r] ? B[i * kStripWords + w] : Wd(0);
+      acc[r][1] = row_ok[r] ? B[i * kStripWords + w + 8] : Wd(0);
+    }
+#pragma unroll 2
+    for (int32_t k = 0; k < K; k += 2) {
+      const Wd b00 = B[k * kStripWords + w], b01 = B[k * kStripWords + w + 8];
+      const Wd b10 = B[(k + 1) * kStripWords + w], b11 = B[(k + 1) * kStripWords + w + 8];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (!row_ok[r]) continue;
+        const Wd* prow = P + (rg + 64 * r) * pst;
+        if constexpr (sizeof(E) == 2) {
+          const uint32_t a = prow[k >> 1];
+          const uint32_t alo = (a & 0xFFFFu) | (a << 16), ahi = (a >> 16) | (a & 0xFFFF0000u);
+          acc[r][0] = __vimax3_s16x2(acc[r][0], __vmins2(alo, b00), __vmins2(ahi, b10));
+          acc[r][1] = __vimax3_s16x2(acc[r][1], __vmins2(alo, b01), __vmins2(ahi, b11));
+        } else {
+          const int32_t a0 = prow[k], a1 = prow[k + 1];
+          acc[r][0] = __vimax3_s32(acc[r][0], min(a0, b00), min(a1, b10));
+          acc[r][1] = __vimax3_s32(acc[r][1], min(a0, b01), min(a1, b11));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (!row_ok[r]) continue;
+      Wd* dst = reinterpret_cast<Wd*>(W + int64_t(rg + 64 * r) * ld) + c0;
+      if (c0 + w < rowwords) dst[w] = acc[r][0];
+      if (c0 + w + 8 < rowwords) dst[w + 8] = acc[r][1];
+    }
+    ++done;
+  }
+  if (t == 0 && done) atomicAdd(&counters[0], done);
+}
+
 // Cold columns: X(i, j) = max(X, W(i, k) (x) W(k, j)) for every warm tile row
 // i, cold tile column j and warm k, with the warm square already closed. Each
 // (i, j) is one work item (a 128-thread CTA applies its k in order). An item
@@ -664,10 +820,13 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
 // wider than p(i,y)), so the result is the exact closure either way.
 template <typename E>
 __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
-                                                                 const int32_t* __restrict__ warm,
+                                                                 int32_t m, const int32_t* __restrict__ warm,
                                                                  const uint32_t* __restrict__ prog,
-                                                                 unsigned long long* counters) {
+                                                                 unsigned long long* counters,
+                                                                 const int32_t* __restrict__ hint_valid) {
   __shared__ __align__(16) typename Ops<E>::Smem sm;
+  if (*warm <= kClusterMaxWarm<E>) return;  // cold_strip_kernel's case
+  if (hint_valid && *hint_valid && (*warm + kB - 1) / kB * kB < m) return;  // uniform cold columns
   const int32_t nbr = (*warm + kB - 1) / kB;
   const int32_t nc = nb - nbr;
   const int64_t items = int64_t(nbr) * nc;
@@ -691,21 +850,32 @@ __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ 
 // every warm j with p[j][x] > p[x][j]; cold candidates beat nobody. CTA =
 // 32 relabeled columns x 8 row groups.
 template <typename E>
-__global__ void __launch_bounds__(256) wextract_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
+__global__ void __launch_bounds__(512) wextract_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
                                                        const int32_t* __restrict__ perm,
-                                                       const int32_t* __restrict__ warm, int32_t* __restrict__ bb) {
-  __shared__ int32_t part[8][33];
+                                                       const int32_t* __restrict__ warm, int32_t* __restrict__ bb,
+                                                       const int32_t* __restrict__ hint_valid,
+                                                       const int32_t* __restrict__ ucount) {
+  constexpr int kG = 16;  // row groups
+  __shared__ int32_t part[kG][33];
   const int32_t nw = *warm;
+  const int32_t rows = (nw + kB - 1) / kB * kB;
+  const bool uc = hint_valid && *hint_valid && rows < m;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   for (int32_t b0 = blockIdx.x * 32; b0 < m; b0 += gridDim.x * 32) {
+    if (uc && b0 >= rows) {  // uniform cold columns: beaten by the warm rows with u > 0
+      if (g == 0 && b0 + lane < m) bb[perm[b0 + lane]] = *ucount;
+      continue;
+    }
     const int32_t b = b0 + lane;
     int32_t c = 0;
     if (b < m) {
       if (b < nw) {
-        for (int32_t j = g; j < nw; j += 8) c += (j != b && int32_t(W[int64_t(j) * mp + b]) > int32_t(W[int64_t(b) * mp + j]));
-      } else {
 #pragma unroll 4
-        for (int32_t j = g; j < nw; j += 8) c += W[int64_t(j) * mp + b] != E(0);
+        for (int32_t j = g; j < nw; j += kG)
+          c += (j != b && int32_t(W[int64_t(j) * mp + b]) > int32_t(W[int64_t(b) * mp + j]));
+      } else {
+#pragma unroll 8
+        for (int32_t j = g; j < nw; j += kG) c += W[int64_t(j) * mp + b] != E(0);
       }
     }
     part[g][lane] = c;
@@ -713,7 +883,7 @@ __global__ void __launch_bounds__(256) wextract_kernel(const E* __restrict__ W, 
     if (g == 0 && b < m) {
       int32_t tot = 0;
 #pragma unroll
-      for (int h = 0; h < 8; ++h) tot += part[h][lane];
+      for (int h = 0; h < kG; ++h) tot += part[h][lane];
       bb[perm[b]] = tot;
     }
     __syncthreads();
@@ -730,6 +900,8 @@ struct ClosureBufs {
   // optional: warm flags known from the tally, used when *hint_valid != 0
   const int32_t* hint = nullptr;
   const int32_t* hint_valid = nullptr;
+  // uniform cold columns (used only with a valid hint): ucol, u [m], ucount
+  int32_t *ucol = nullptr, *ucold = nullptr, *ucount = nullptr;
 };
 
 // Rowflags, relabel, pack, closure of the warm square, cold product, widen.
@@ -764,9 +936,10 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     relabel_kernel<<<1, 1024, 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm, bf.hint, bf.hint_valid);
   }
   {
-    const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 256, 0, int64_t(mp / 32) * (mp / 32));
+    const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 512, 0, mp);
     Launch L(ctx, stream, "closure_pack", 0.0);
-    pack_kernel<E><<<g, 256, 0, stream>>>(d, m, mp, bf.perm, bf.warm, W, bf.prog, nb);
+    pack_kernel<E><<<g, 512, 0, stream>>>(d, m, mp, bf.perm, bf.warm, W, bf.prog, nb, bf.hint, bf.hint_valid,
+                                          bf.ucol);
   }
   if (int rc = check_launch()) return rc;
   {
@@ -793,18 +966,32 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     }
   }
   {
+    const size_t cw = size_t(kClusterMaxWarm<E>);
+    const size_t smem = (cw * (cw * sizeof(E) / 4 + 1) + cw * kStripWords) * 4;
+    cudaFuncSetAttribute(cold_strip_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    Launch L(ctx, stream, "closure_cold_strips", 0.0);
+    cold_strip_kernel<E><<<sms, 512, smem, stream>>>(W, mp, m, bf.warm, bf.counters, bf.hint_valid);
+  }
+  {
     const int g = grid_for(reinterpret_cast<const void*>(cold_product_kernel<E>), kThreads, 0, int64_t(nb) * nb);
     Launch L(ctx, stream, "closure_cold", 0.0);
-    cold_product_kernel<E><<<g, kThreads, 0, stream>>>(W, mp, nb, bf.warm, bf.prog, bf.counters);
+    cold_product_kernel<E><<<g, kThreads, 0, stream>>>(W, mp, nb, m, bf.warm, bf.prog, bf.counters, bf.hint_valid);
+  }
+  if (bf.hint_valid) {
+    if (cudaMemsetAsync(bf.ucount, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+    Launch L(ctx, stream, "closure_cold_uniform", 0.0);
+    uniform_cold_kernel<E><<<std::max(1, std::min(sms, (m + 7) / 8)), 256, 0, stream>>>(
+        W, mp, m, bf.warm, bf.hint_valid, bf.ucol, bf.ucold, bf.ucount);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
     Launch L(ctx, stream, "closure_widen", mm * 4.0);
-    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.warm, p);
+    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.warm, p, bf.hint_valid, bf.ucold);
   }
   if (bb_out) {
     Launch L(ctx, stream, "closure_beaten_by", 0.0);
-    wextract_kernel<E><<<(m + 31) / 32, 256, 0, stream>>>(W, mp, m, bf.perm, bf.warm, bb_out);
+    wextract_kernel<E><<<(m + 31) / 32, 512, 0, stream>>>(W, mp, m, bf.perm, bf.warm, bb_out, bf.hint_valid,
+                                                           bf.ucount);
   }
   return check_launch();
 }
@@ -822,6 +1009,9 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   bf.perm = cv.take<int32_t>(size_t(m));
   bf.inv = cv.take<int32_t>(size_t(m));
   bf.warm = cv.take<int32_t>(1);
+  bf.ucol = cv.take<int32_t>(size_t(m));
+  bf.ucold = cv.take<int32_t>(size_t(m));
+  bf.ucount = cv.take<int32_t>(1);
   bf.counters = ctx->counters;
   bf.hint = hint;
   bf.hint_valid = hint_valid;
@@ -835,7 +1025,7 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
   size_t mp = align_up(size_t(m), kB);
   size_t nb = mp / kB;
   return align_up(mp * mp * (use_s16(bound, flags) ? 2 : 4), 256) + align_up((nb * nb + 2) * 4, 256) +
-         4 * align_up(size_t(m) * 4, 256) + 4096;
+         6 * align_up(size_t(m) * 4, 256) + 4096;
 }
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,

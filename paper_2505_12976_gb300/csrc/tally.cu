@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
       for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hint[c] = cnt[c] > 0 ? 1 : 0;
       if (threadIdx.x == 0) *hint_valid = int32_t(na) < m ? 1 : 0;
     }
+    if (int32_t(na) <= compact_max) return;  // the compact form needs no grouping plan
     __syncthreads();
   }
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) off[c] = uint32_t(cnt[c]);
@@ -570,7 +571,22 @@ __global__ void __launch_bounds__(512)
     uint32_t lo = 0, hi = 0;
     if (gg < groups) {
       const uint32_t* src = partial + int64_t(a) * wpr + w;
-      for (int32_t g = gg; g < G; g += groups) {
+      int32_t g = gg;
+      for (; g + 7 * groups < G; g += 8 * groups) {  // eight loads in flight
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = src[int64_t(g + u * groups) * words];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (kPacked) {
+            lo += x[u] & 0xFFFFu;
+            hi += x[u] >> 16;
+          } else {
+            lo += x[u];
+          }
+        }
+      }
+      for (; g < G; g += groups) {
         const uint32_t x = src[int64_t(g) * words];
         if (kPacked) {
           lo += x & 0xFFFFu;

@@ -319,7 +319,12 @@ def test_large_topk_workload_full_size():
     w = oracle.weights(d)
     p = host(out["p"])
     rs = np.random.Generator(np.random.PCG64(2))
-    _sampled_closure_checks(w, p, [0, e.m - 1] + rs.integers(0, e.m, 6).tolist())
+    # the listed candidates: paths between them never leave them (the others
+    # have no outgoing edge), so p on A x A is the oracle closure of d[A, A]
+    A = np.unique(e.ranks)
+    dA = np.ascontiguousarray(d[np.ix_(A, A)])
+    eq(p[np.ix_(A, A)], oracle.strongest_paths(dA, nthreads=16), "closure on the listed candidates")
+    _sampled_closure_checks(w, p, [0, e.m - 1] + rs.integers(0, e.m, 4).tolist() + rs.choice(A, 4).tolist())
     win = host(out["winners"])
     bb = host(out["beaten_by"])
     for c in np.flatnonzero(win):
