@@ -521,6 +521,31 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         const uint32_t r0 = lane < k ? st[lane] : kNoSlot;
         const uint32_t r1 = lane + 32 < k ? st[lane + 32] : kNoSlot;
         const int32_t qlo = min(k, 32), qhi = min(k, 64);
+        bool clean = (lane >= k || r0 != kNoSlot) && (lane + 32 >= k || r1 != kNoSlot);
+        for (int32_t q = 64 + lane; q < k; q += 32) clean &= st[q] != kNoSlot;
+        if (__all_sync(0xFFFFFFFFu, clean)) {  // every id valid (the usual case): no per-entry checks
+          const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
+          const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+#pragma unroll 4
+          for (int32_t q = 1; q < qlo; ++q) {
+            const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
+            if (lane < q) atomicAdd(C + int32_t(sq) * wpr + w0, i0);
+          }
+#pragma unroll 4
+          for (int32_t q = 32; q < qhi; ++q) {
+            uint32_t* crow = C + int32_t(__shfl_sync(0xFFFFFFFFu, r1, q - 32)) * wpr;
+            atomicAdd(crow + w0, i0);
+            if (lane + 32 < q) atomicAdd(crow + w1, i1);
+          }
+          for (int32_t q = 64; q < k; ++q) {
+            uint32_t* crow = C + int32_t(st[q]) * wpr;
+            atomicAdd(crow + w0, i0);
+            atomicAdd(crow + w1, i1);
+            for (int32_t p = 64 + lane; p < q; p += 32) count_pair<kPacked>(crow, st[p]);
+          }
+          __syncwarp();
+          continue;
+        }
         for (int32_t q = 1; q < qlo; ++q) {  // rows 1..31: lanes p < q
           const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
           if (sq == kNoSlot) continue;  // uniform over the warp
