@@ -53,6 +53,8 @@ def _load():
             lib.oracle_validate.restype = ctypes.c_int
             lib.oracle_tally.argtypes = [i32p, i64, i32, i32, i32p]
             lib.oracle_tally.restype = ctypes.c_int
+            lib.oracle_tally_positions.argtypes = [i32p, i64, i32, i32p]
+            lib.oracle_tally_positions.restype = ctypes.c_int
             lib.oracle_tally_entry.argtypes = [i32p, i64, i32, i32, i32, i32]
             lib.oracle_tally_entry.restype = i64
             lib.oracle_weights.argtypes = [i32p, i32, i32p]
@@ -101,6 +103,20 @@ def tally(ranks, m: int) -> np.ndarray:
     n, k = r.shape
     d = np.zeros((m, m), dtype=np.int32)
     rc = _load().oracle_tally(_p(r), n, m, k, _p(d))
+    if rc:
+        raise OracleError(rc)
+    return d
+
+
+def tally_positions(pos) -> np.ndarray:
+    """Weak-order ballots in position form (Sect. 2.1): pos [n, m], smaller
+    is better, equal positions tied; d[i][j] = #{v : pos[v][i] < pos[v][j]}."""
+    p = _i32(pos)
+    if p.ndim != 2:
+        raise OracleError(EINVAL)
+    n, m = p.shape
+    d = np.zeros((m, m), dtype=np.int32)
+    rc = _load().oracle_tally_positions(_p(p), n, m, _p(d))
     if rc:
         raise OracleError(rc)
     return d

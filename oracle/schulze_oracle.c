@@ -93,6 +93,30 @@ int oracle_tally(const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t*
   return ORACLE_OK;
 }
 
+/*
+ * Pairwise tally of weak-order ballots in position form (Sect. 2.1: a voter
+ * may rank candidates equally): pos[v][c] is the position of c on ballot v,
+ * smaller is better, equal positions are tied. d[i][j] = #{v : pos[v][i] <
+ * pos[v][j]}; a tied pair counts for neither. Positions must lie in
+ * [0, 65534] (else ORACLE_EDATA). O(n * m^2); d is int32 [m, m], overwritten.
+ */
+int oracle_tally_positions(const int32_t* pos, int64_t n, int32_t m, int32_t* d) {
+  if (n < 0 || m < 1 || (n > 0 && !pos) || !d) return ORACLE_EINVAL;
+  for (int64_t t = 0; t < n * (int64_t)m; ++t)
+    if (pos[t] < 0 || pos[t] > 65534) return ORACLE_EDATA;
+  int64_t* acc = (int64_t*)calloc((size_t)m * (size_t)m, sizeof(int64_t));
+  if (!acc) return ORACLE_ENOMEM;
+  for (int64_t v = 0; v < n; ++v) {
+    const int32_t* row = pos + v * m;
+    for (int32_t i = 0; i < m; ++i)
+      for (int32_t j = 0; j < m; ++j)
+        if (row[i] < row[j]) acc[(int64_t)i * m + j] += 1;
+  }
+  for (int64_t t = 0; t < (int64_t)m * m; ++t) d[t] = (int32_t)acc[t];
+  free(acc);
+  return ORACLE_OK;
+}
+
 /* One tally entry d[i][j], counted voter by voter (for sampled checks of
  * large profiles). Returns -1 on bad arguments. */
 int64_t oracle_tally_entry(const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t i, int32_t j) {

@@ -17,10 +17,15 @@ SRC = os.path.join(ROOT, "oracle", "schulze_oracle.c")
 MUTANTS = {
     "tally_position_off_by_one": ("for (int32_t q = 0; q < k; ++q) pos[row[q]] = q;",
                                   "for (int32_t q = 0; q < k; ++q) pos[row[q]] = q + 1;"),
-    "tally_transposed": ("acc[(int64_t)i * m + j] += 1", "acc[(int64_t)j * m + i] += 1"),
+    "tally_transposed": ("if (j != i && pos[i] < pos[j]) acc[(int64_t)i * m + j] += 1",
+                         "if (j != i && pos[i] < pos[j]) acc[(int64_t)j * m + i] += 1"),
     "tally_unlisted_on_top": ("for (int32_t c = 0; c < m; ++c) pos[c] = k;",
                               "for (int32_t c = 0; c < m; ++c) pos[c] = -1;"),
     "weights_ties_are_edges": ("(i != j && a > b) ? a : 0", "(i != j && a >= b) ? a : 0"),
+    "positions_ties_counted": ("if (row[i] < row[j]) acc[(int64_t)i * m + j] += 1;",
+                               "if (i != j && row[i] <= row[j]) acc[(int64_t)i * m + j] += 1;"),
+    "positions_transposed": ("if (row[i] < row[j]) acc[(int64_t)i * m + j] += 1;",
+                             "if (row[i] < row[j]) acc[(int64_t)j * m + i] += 1;"),
     "closure_max_instead_of_min": ("pi[j] = imax(pi[j], imin(pik, pk[j]));",
                                    "pi[j] = imax(pi[j], imax(pik, pk[j]));"),
     "closure_no_accumulate": ("pi[j] = imax(pi[j], imin(pik, pk[j]));", "pi[j] = imin(pik, pk[j]);"),

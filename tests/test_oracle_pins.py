@@ -331,3 +331,55 @@ def test_degenerate_inputs():
     d, p, win, order, bb = oracle.schulze(r, 8)
     assert np.flatnonzero(win).tolist() == [4]
     assert order.tolist() == [4, 1, 6, 0, 2, 3, 5, 7]
+
+
+# ----------------------------------------------- weak orders, position form
+
+def test_tally_positions_hand_derived():
+    """Three weak orders over (a, b, c, d): a ~ b > c > d; all tied;
+    d > b ~ c > a. A tied pair counts for neither candidate (Sect. 2.1)."""
+    pos = np.array([[0, 0, 1, 2], [0, 0, 0, 0], [5, 1, 1, 0]], np.int32)
+    want = np.zeros((4, 4), np.int32)
+    for i, j in [(0, 2), (0, 3), (1, 2), (1, 3), (2, 3),   # first ballot
+                 (3, 1), (3, 2), (3, 0), (1, 0), (2, 0)]:  # third ballot
+        want[i, j] += 1
+    np.testing.assert_array_equal(oracle.tally_positions(pos), want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tally_positions_equals_order_form(seed):
+    """Order-form ballots (unlisted candidates at position k) give the same
+    counts through the position form as through the order-form tally."""
+    m, n, k = 11, 40, 6
+    r = W.mallows(seed, n, m, k, 0.8, W.permutation(seed, m))
+    pos = np.full((n, m), k, np.int32)
+    for v in range(n):
+        pos[v, r[v]] = np.arange(k)
+    np.testing.assert_array_equal(oracle.tally_positions(pos), oracle.tally(r, m))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tally_positions_tie_splitting(seed):
+    """Breaking one tie (i ~ j on ballot v) both ways: d(i ahead) + d(j
+    ahead) = 2 d(tied) + e_ij + e_ji, every other count unchanged."""
+    rs = np.random.Generator(np.random.PCG64(seed))
+    m, n = 8, 25
+    pos = rs.integers(0, 4, size=(n, m)).astype(np.int32)  # many ties
+    v = int(rs.integers(0, n))
+    pos[v] = rs.permutation(m)  # ballot v: strict except candidates 1 ~ 5
+    pos[v, 5] = pos[v, 1]
+    base = oracle.tally_positions(pos)
+    p1, p2 = 2 * pos, 2 * pos
+    p1[v, 5] += 1  # 1 ahead of 5, every other relation of ballot v kept
+    p2[v, 1] += 1  # 5 ahead of 1
+    e = np.zeros((m, m), np.int64)
+    e[1, 5] = e[5, 1] = 1
+    np.testing.assert_array_equal(oracle.tally_positions(p1).astype(np.int64) + oracle.tally_positions(p2),
+                                  2 * base.astype(np.int64) + e)
+
+
+def test_tally_positions_rejects_out_of_range():
+    with pytest.raises(oracle.OracleError):
+        oracle.tally_positions(np.array([[0, 65535]], np.int32))
+    with pytest.raises(oracle.OracleError):
+        oracle.tally_positions(np.array([[-1, 0]], np.int32))
