@@ -56,6 +56,8 @@ enum schulze_status {
 #define SCHULZE_F_AUTO 0u         /* 16-bit packed closure when bound <= 32767, else int32 */
 #define SCHULZE_F_FORCE_S32 1u    /* always the int32 closure */
 #define SCHULZE_F_FORCE_S16 2u    /* always the 16-bit closure; EINVAL if bound > 32767 */
+#define SCHULZE_F_MARGIN 32u      /* edge weights are the margins d[i][j] - d[j][i] > 0 (Sect. 2.1)
+                                     instead of winning votes */
 /* Tally flags (schulze_tally, schulze_run). */
 #define SCHULZE_F_TALLY_DENSE 4u  /* position-compare tally, O(n m^2) */
 #define SCHULZE_F_TALLY_SPARSE 8u /* pair-count tally, O(n k^2) */
@@ -101,6 +103,21 @@ int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, 
                   uint32_t flags, schulze_stream_t stream);
 
 /*
+ * Pairwise tally of weak-order ballots (Sect. 2.1: a voter may rank
+ * candidates equally), given in position form.
+ *   pos    [n, m] int32 device, pos[v][c] = position of candidate c on ballot
+ *          v: smaller is better, equal positions are tied (a tied pair counts
+ *          for neither); every position in [0, 65534]. An unranked candidate
+ *          is simply given a position behind the ranked ones.
+ *   d      [m, m] int32 device output: d[i][j] = #{v : pos[v][i] < pos[v][j]},
+ *          d[i][i] = 0. Overwritten completely. O(n m^2) position compares.
+ * Sizes: 1 <= m <= 65535, 0 <= n < 2^31, n*m < 2^40. A position out of range
+ * is reported as SCHULZE_EDATA through schulze_get_status() (d unspecified).
+ */
+int schulze_tally_positions(schulze_ctx* ctx, const int32_t* pos, int64_t n, int32_t m, int32_t* d,
+                            schulze_stream_t stream);
+
+/*
  * Widest paths (Sect. 2.1: p(a,b) = the largest width min over the edges of
  * a path from a to b; Sect. 4: all pairs by Floyd-Warshall). Edge weights
  * are winning votes: w[i][j] = d[i][j] if d[i][j] > d[j][i], else 0.
@@ -110,7 +127,9 @@ int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, 
  *          above it, or below 0, is reported as SCHULZE_EDATA.
  *   p      [m, m] int32 device output: p[i][j] = widest-path width from i to
  *          j, 0 if j is unreachable, p[i][i] = 0. May not alias d.
- *   flags  SCHULZE_F_AUTO, SCHULZE_F_FORCE_S32 or SCHULZE_F_FORCE_S16.
+ *   flags  SCHULZE_F_AUTO, SCHULZE_F_FORCE_S32 or SCHULZE_F_FORCE_S16, plus
+ *          SCHULZE_F_MARGIN for the paper's margin weights
+ *          w[i][j] = d[i][j] - d[j][i] when positive (same edges).
  */
 int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
                             uint32_t flags, schulze_stream_t stream);

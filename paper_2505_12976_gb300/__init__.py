@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libschulze.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDATA, ETIMEOUT, ERANGE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
-F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE, F_TALLY_GROUPED = 0, 1, 2, 4, 8, 16
+F_AUTO, F_FORCE_S32, F_FORCE_S16, F_TALLY_DENSE, F_TALLY_SPARSE, F_TALLY_GROUPED, F_MARGIN = 0, 1, 2, 4, 8, 16, 32
 
 _lock = threading.Lock()
 _lib = None
@@ -45,6 +45,7 @@ SIGNATURES = [
     ("schulze_workspace_bytes", _c.c_size_t, [_vp]),
     ("schulze_get_status", _c.c_int, [_vp, _c.POINTER(_i32), _vp]),
     ("schulze_tally", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _u32, _vp]),
+    ("schulze_tally_positions", _c.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("schulze_strongest_paths", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _u32, _vp]),
     ("schulze_winners", _c.c_int, [_vp, _vp, _i32, _vp, _vp]),
     ("schulze_ranking", _c.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
@@ -202,6 +203,21 @@ def schulze_tally(ranks: torch.Tensor, m: int, d: torch.Tensor | None = None, fl
     d = _out(d, (m, m), ranks.device, "d")
     _check(load().schulze_tally(ctx.handle, _ptr(ranks), n, m, k, _ptr(d), flags, _stream(stream, ctx.device)),
            "schulze_tally")
+    return d
+
+
+def schulze_tally_positions(pos: torch.Tensor, d: torch.Tensor | None = None, ctx: Context | None = None,
+                            stream=None) -> torch.Tensor:
+    """Weak-order ballots: pos int32 [n, m] on the GPU (smaller is better,
+    equal is tied); d[i][j] = #{v : pos[v][i] < pos[v][j]}."""
+    pos = _dev_i32(pos, "pos")
+    if pos.dim() != 2:
+        raise ValueError("pos must be [n, m]")
+    ctx = ctx or context(pos.device)
+    n, m = pos.shape
+    d = _out(d, (m, m), pos.device, "d")
+    _check(load().schulze_tally_positions(ctx.handle, _ptr(pos), n, m, _ptr(d), _stream(stream, ctx.device)),
+           "schulze_tally_positions")
     return d
 
 

@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
 }
 
 // W[a][b] = w[perm[a]][perm[b]] for the warm rows a < 64 * nbr (0 outside
-// m x m, on the diagonal and where d does not beat its transpose). One CTA
+// m x m, on the diagonal and where d does not beat its transpose; w is d, or
+// the margin d - d^T with `margin`). One CTA
 // pass per row a: with x = perm[a], the threads walk b, reading d[x][perm b]
 // (along row x) and d[perm b][x] (down column x); a warp that writes a
 // nonzero sets the nonzero bit of its 64 x 64 tile's progress word.
@@ -186,7 +187,8 @@ __global__ void __launch_bounds__(512) pack_kernel(const int32_t* __restrict__ d
                                                    const int32_t* __restrict__ perm, const int32_t* __restrict__ warm,
                                                    E* __restrict__ W, uint32_t* __restrict__ prog, int32_t nb,
                                                    const int32_t* __restrict__ hint,
-                                                   const int32_t* __restrict__ hint_valid, int32_t* __restrict__ ucol) {
+                                                   const int32_t* __restrict__ hint_valid, int32_t* __restrict__ ucol,
+                                                   int margin) {
   const bool hv = hint_valid && *hint_valid;
   const int32_t rows = (*warm + kB - 1) / kB * kB;  // W rows to write
   const bool uc = hv && rows < m;                    // uniform cold columns beyond the square
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const int32_t* __restrict__ d
 #pragma unroll
       for (int q = 0; q < kU; ++q) {
         const int32_t b = b0 + q * blockDim.x + threadIdx.x;
-        const int32_t out = v[q] > u[q] ? v[q] : 0;
+        const int32_t out = v[q] > u[q] ? (margin ? v[q] - u[q] : v[q]) : 0;
         if (b < bend) wrow[b] = E(out);
         if (__any_sync(0xFFFFFFFFu, out != 0) && lane == 0) atomicOr(&prog[(a / kB) * nb + (b / kB)], kNZ);
       }
@@ -902,6 +904,7 @@ struct ClosureBufs {
   const int32_t* hint_valid = nullptr;
   // uniform cold columns (used only with a valid hint): ucol, u [m], ucount
   int32_t *ucol = nullptr, *ucold = nullptr, *ucount = nullptr;
+  bool margin = false;  // margin weights instead of winning votes
 };
 
 // Rowflags, relabel, pack, closure of the warm square, cold product, widen.
@@ -939,7 +942,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 512, 0, mp);
     Launch L(ctx, stream, "closure_pack", 0.0);
     pack_kernel<E><<<g, 512, 0, stream>>>(d, m, mp, bf.perm, bf.warm, W, bf.prog, nb, bf.hint, bf.hint_valid,
-                                          bf.ucol);
+                                          bf.ucol, bf.margin ? 1 : 0);
   }
   if (int rc = check_launch()) return rc;
   {
@@ -998,7 +1001,8 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
 
 template <typename E>
 int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
-                cudaStream_t stream, int32_t* bb_out, const int32_t* hint, const int32_t* hint_valid) {
+                cudaStream_t stream, int32_t* bb_out, const int32_t* hint, const int32_t* hint_valid,
+                bool margin) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   Carver cv(ws);
@@ -1015,6 +1019,7 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   bf.counters = ctx->counters;
   bf.hint = hint;
   bf.hint_valid = hint_valid;
+  bf.margin = margin;
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
   return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream, bb_out);
 }
@@ -1031,9 +1036,10 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
                    void* ws, cudaStream_t stream, int32_t* beaten_by, const int32_t* hint,
                    const int32_t* hint_valid) {
+  const bool margin = (flags & SCHULZE_F_MARGIN) != 0;
   if (use_s16(bound, flags))
-    return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid);
-  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid);
+    return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin);
+  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin);
 }
 
 // ------------------------------------------------- allocation-free variant
@@ -1085,8 +1091,9 @@ int static_scratch(int device, unsigned char** out) {
 
 template <typename E>
 int run_closure_static(unsigned char* base, int device, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
-                       int32_t* status, cudaStream_t stream) {
+                       int32_t* status, cudaStream_t stream, bool margin) {
   ClosureBufs bf;
+  bf.margin = margin;
   bf.W = base + kStW;
   bf.prog = reinterpret_cast<uint32_t*>(base + kStProg);
   bf.rowflag = reinterpret_cast<int32_t*>(base + kStRowflag);
@@ -1116,6 +1123,8 @@ extern "C" int schulze_strongest_paths_static(const int32_t* d, int32_t m, int64
   if (cudaGetDevice(&device) != cudaSuccess) return SCHULZE_ECUDA;
   unsigned char* base = nullptr;
   if (int rc = static_scratch(device, &base)) return rc;
-  if (use_s16(bound, flags)) return run_closure_static<int16_t>(base, device, d, m, bound, p, status, stream);
-  return run_closure_static<int32_t>(base, device, d, m, bound, p, status, stream);
+  const bool margin = (flags & SCHULZE_F_MARGIN) != 0;
+  if (use_s16(bound, flags))
+    return run_closure_static<int16_t>(base, device, d, m, bound, p, status, stream, margin);
+  return run_closure_static<int32_t>(base, device, d, m, bound, p, status, stream, margin);
 }

@@ -146,6 +146,16 @@ int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, 
   return tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream);
 }
 
+int schulze_tally_positions(schulze_ctx* ctx, const int32_t* pos, int64_t n, int32_t m, int32_t* d,
+                            schulze_stream_t stream) {
+  if (!ctx || !d || m < 1 || m > kMaxM || n < 0 || n >= (int64_t(1) << 31) ||
+      uint64_t(n) * uint64_t(m) >= (uint64_t(1) << 40) || (n > 0 && !pos))
+    return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, tally_positions_workspace_bytes(n, m), stream)) return rc;
+  return tally_positions_launch(ctx, pos, n, m, d, ctx->ws.base, stream);
+}
+
 int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
                             uint32_t flags, schulze_stream_t stream) {
   if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || bound < 0) return SCHULZE_EINVAL;

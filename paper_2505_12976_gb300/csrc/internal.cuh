@@ -81,6 +81,8 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags);
 size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags);
 size_t extract_workspace_bytes(int32_t m);
 
+size_t tally_positions_workspace_bytes(int64_t n, int32_t m);
+
 // Stage launchers operating on caller-provided workspace (no allocation).
 // With hint / hint_valid (int32 [m] and one word, outside ws), a top-k
 // tally also reports which candidates have an outgoing edge: when some
@@ -90,6 +92,10 @@ size_t extract_workspace_bytes(int32_t m);
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
                  uint32_t flags, void* ws, cudaStream_t stream, int32_t* hint = nullptr,
                  int32_t* hint_valid = nullptr);
+// Tally of weak-order ballots given as int32 positions [n, m].
+int tally_positions_launch(schulze_ctx* ctx, const int32_t* pos, int64_t n, int32_t m, int32_t* d, void* ws,
+                           cudaStream_t stream);
+
 // With beaten_by non-null the closure also fills it (int32 [m]) from its
 // warm rows, so extract_from_beaten_by can finish without reading p. With
 // hint / hint_valid (from tally_launch, outside ws) the closure takes the

@@ -67,6 +67,28 @@ __global__ void pos_build_kernel(const int32_t* __restrict__ ranks, int64_t v0, 
   }
 }
 
+// Weak orders in position form: pos[v][c] for v in [v0, v0 + nv) copied from
+// the caller's int32 positions (smaller is better, equal is tied) into the
+// 16-bit rows; a position outside [0, 65534] sets EDATA. Padding columns
+// (c >= m) hold 0xFFFF; their counts are never written.
+__global__ void pos_copy_kernel(const int32_t* __restrict__ src, int64_t v0, int64_t nv, int32_t m, int32_t ldp,
+                                uint16_t* __restrict__ pos, int32_t* status) {
+  const int64_t total = nv * ldp;
+  bool bad = false;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t w = e / ldp;
+    const int32_t c = int32_t(e - w * ldp);
+    uint16_t v = 0xFFFFu;
+    if (c < m) {
+      const int32_t x = src[(v0 + w) * m + c];
+      bad |= x < 0 || x > 65534;
+      v = uint16_t(x < 0 ? 0 : (x > 65534 ? 65534 : x));
+    }
+    pos[e] = v;
+  }
+  if (bad) set_status(status, SCHULZE_EDATA);
+}
+
 // One CTA counts a TILE x TILE block of d over a chunk of ballots.
 // Thread micro-tile RM x RN (RN even); lanes of a 32-bit word hold two
 // adjacent j columns; the row operand is duplicated into both halves.
@@ -713,6 +735,51 @@ int64_t dense_voter_chunk(int64_t n, int32_t m) {
   return std::min<int64_t>(std::max<int64_t>(n, 1), 1 << 16);
 }
 
+// Position-compare tally over n ballots whose 16-bit position rows build()
+// writes chunk by chunk: build(v0, nv, ldp, pos) fills rows v0 .. v0+nv-1.
+// `full`: strict full orders, only the upper tiles are counted and mirrored.
+template <class Build>
+int dense_tally(schulze_ctx* ctx, int64_t n, int32_t m, bool full, int32_t* d, void* ws, cudaStream_t stream,
+                Build build) {
+  const size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+  Carver cv(ws);
+  const int32_t tile = dense_tile(m);
+  const int32_t ldp = int32_t(align_up(size_t(m), size_t(tile)));
+  const int32_t nbt = ldp / tile;
+  const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
+  const int64_t chunk = dense_voter_chunk(n, m);
+  uint16_t* pos = cv.take<uint16_t>(size_t(chunk) * size_t(ldp));
+  // voter split inside a chunk so that the grid covers the GPU
+  int32_t vsplit = int32_t(std::max<int64_t>(1, (2LL * sms + ntiles - 1) / ntiles));
+  vsplit = int32_t(std::min<int64_t>(vsplit, std::max<int64_t>(1, std::min<int64_t>(n, chunk) / 64)));
+  const bool accumulate = vsplit > 1 || n > chunk;
+  if (accumulate && cudaMemsetAsync(d, 0, mm, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  for (int64_t v0 = 0; v0 < n; v0 += chunk) {
+    const int64_t nv = std::min<int64_t>(chunk, n - v0);
+    int32_t vchunk = int32_t((nv + vsplit - 1) / vsplit);
+    vchunk = std::min<int32_t>(vchunk, kMaxVoterChunk);
+    const int32_t gy = int32_t((nv + vchunk - 1) / vchunk);
+    build(v0, nv, ldp, pos);
+    dim3 grid(ntiles, gy);
+    // gy > 1 or several chunks: the kernel adds atomically into zeroed d
+    Launch L(ctx, stream, "tally_dense", double(nv) * double(m) * double(m - 1) / (full ? 2.0 : 1.0));
+    if (tile == 64)
+      dense_tally_kernel<64, 8, 8><<<grid, 64, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
+                                                             accumulate ? 1 : 0, d);
+    else
+      dense_tally_kernel<128, 8, 8><<<grid, 256, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
+                                                               accumulate ? 1 : 0, d);
+    if (int rc = check_launch()) return rc;
+  }
+  if (full && nbt > 1) {
+    Launch L(ctx, stream, "tally_mirror", double(m) * double(m) * 4.0);
+    dim3 g((m + 31) / 32, (m + 31) / 32), b(32, 8);
+    mirror_kernel<<<g, b, 0, stream>>>(d, m, tile, n);
+  }
+  return check_launch();
+}
+
 }  // namespace
 
 size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
@@ -739,45 +806,13 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
   Carver cv(ws);
   if (choose_dense(n, m, k, flags)) {
-    const int32_t tile = dense_tile(m);
-    const int32_t ldp = int32_t(align_up(size_t(m), size_t(tile)));
-    const int32_t nbt = ldp / tile;
-    const bool full = k >= m - 1;  // strict full orders: d[j][i] = n - d[i][j]
-    const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
-    const int64_t chunk = dense_voter_chunk(n, m);
-    uint16_t* pos = cv.take<uint16_t>(size_t(chunk) * size_t(ldp));
-    // voter split inside a chunk so that the grid covers the GPU
-    int32_t vsplit = int32_t(std::max<int64_t>(1, (2LL * sms + ntiles - 1) / ntiles));
-    vsplit = int32_t(std::min<int64_t>(vsplit, std::max<int64_t>(1, std::min<int64_t>(n, chunk) / 64)));
-    const bool accumulate = vsplit > 1 || n > chunk;
-    if (accumulate && cudaMemsetAsync(d, 0, mm, stream) != cudaSuccess) return SCHULZE_ECUDA;
-    for (int64_t v0 = 0; v0 < n; v0 += chunk) {
-      const int64_t nv = std::min<int64_t>(chunk, n - v0);
-      int32_t vchunk = int32_t((nv + vsplit - 1) / vsplit);
-      vchunk = std::min<int32_t>(vchunk, kMaxVoterChunk);
-      const int32_t gy = int32_t((nv + vchunk - 1) / vchunk);
-      int pb = int(std::min<int64_t>((nv + 7) / 8, int64_t(sms) * 16));
-      {
-        Launch L(ctx, stream, "tally_positions", double(nv) * (double(k) * 4.0 + double(ldp) * 2.0));
-        pos_build_kernel<<<pb, 256, 0, stream>>>(ranks, v0, nv, m, k, ldp, pos, ctx->status);
-      }
-      dim3 grid(ntiles, gy);
-      // gy > 1 or several chunks: the kernel adds atomically into zeroed d
-      Launch L(ctx, stream, "tally_dense", double(nv) * double(m) * double(m - 1) / (full ? 2.0 : 1.0));
-      if (tile == 64)
-        dense_tally_kernel<64, 8, 8><<<grid, 64, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
-                                                               accumulate ? 1 : 0, d);
-      else
-        dense_tally_kernel<128, 8, 8><<<grid, 256, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
-                                                                 accumulate ? 1 : 0, d);
-      if (int rc = check_launch()) return rc;
-    }
-    if (full && nbt > 1) {
-      Launch L(ctx, stream, "tally_mirror", double(m) * double(m) * 4.0);
-      dim3 g((m + 31) / 32, (m + 31) / 32), b(32, 8);
-      mirror_kernel<<<g, b, 0, stream>>>(d, m, tile, n);
-    }
-    return check_launch();
+    // strict full orders: d[j][i] = n - d[i][j]
+    return dense_tally(ctx, n, m, k >= m - 1, d, ws, stream,
+                       [&](int64_t v0, int64_t nv, int32_t ldp, uint16_t* pos) {
+                         const int pb = int(std::min<int64_t>((nv + 7) / 8, int64_t(sms) * 16));
+                         Launch L(ctx, stream, "tally_positions", double(nv) * (double(k) * 4.0 + double(ldp) * 2.0));
+                         pos_build_kernel<<<pb, 256, 0, stream>>>(ranks, v0, nv, m, k, ldp, pos, ctx->status);
+                       });
   }
   // sparse
   const uint32_t total = uint32_t(uint64_t(n) * uint64_t(k));
@@ -852,6 +887,23 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
                                                                 sp.emax, sp.rb, sp.jw, d, meta);
   }
   return check_launch();
+}
+
+size_t tally_positions_workspace_bytes(int64_t n, int32_t m) {
+  const int32_t tile = dense_tile(m);
+  const size_t ldp = align_up(size_t(m), size_t(tile));
+  return align_up(size_t(dense_voter_chunk(n, m)) * ldp * 2, 256) + 4096;
+}
+
+int tally_positions_launch(schulze_ctx* ctx, const int32_t* pos_in, int64_t n, int32_t m, int32_t* d, void* ws,
+                           cudaStream_t stream) {
+  if (n == 0) return cudaMemsetAsync(d, 0, size_t(m) * size_t(m) * 4, stream) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+  return dense_tally(ctx, n, m, false, d, ws, stream, [&](int64_t v0, int64_t nv, int32_t ldp, uint16_t* pos) {
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>((nv * ldp + 255) / 256, int64_t(sms) * 8)));
+    Launch L(ctx, stream, "tally_positions_copy", double(nv) * double(m) * 4.0);
+    pos_copy_kernel<<<g, 256, 0, stream>>>(pos_in, v0, nv, m, ldp, pos, ctx->status);
+  });
 }
 
 }  // namespace schulze

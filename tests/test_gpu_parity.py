@@ -365,3 +365,77 @@ def test_huge_pl_workload_full_size():
     for c in np.flatnonzero(host(out["winners"])):
         fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
         assert np.all(fwd >= bwd)
+
+
+# ------------------------------------------ margins and weak-order ballots
+
+def test_fig1_margin_closure_on_gpu():
+    """Fig. 1 realised by 42 ballots (McGarvey): with margin weights the GPU
+    closure of the tally reproduces the printed width table itself."""
+    _, mu, p_paper, win = fig1()
+    ballots = mcgarvey_ballots(mu)
+    d = S.schulze_tally(cu(ballots), 4)
+    for flags in (S.F_MARGIN | S.F_FORCE_S16, S.F_MARGIN | S.F_FORCE_S32):
+        p = S.schulze_strongest_paths(d, bound=42, flags=flags)
+        eq(host(p), p_paper, "fig1 margin widths")
+        assert np.flatnonzero(host(S.schulze_winners(p))).tolist() == win
+
+
+@pytest.mark.parametrize("m", [7, 70, 190, 300])
+def test_margin_closure_random(m):
+    rs = np.random.Generator(np.random.PCG64(50 + m))
+    d = rs.integers(0, 30000, size=(m, m)).astype(np.int32)
+    d[rs.random((m, m)) > 0.6] = 0
+    np.fill_diagonal(d, 0)
+    want = oracle.closure(oracle.weights_margin(d), nthreads=8)
+    for flags in (S.F_MARGIN | S.F_FORCE_S16, S.F_MARGIN | S.F_FORCE_S32):
+        eq(host(S.schulze_strongest_paths(cu(d), 30000, flags=flags)), want, f"margin m={m}")
+
+
+@pytest.mark.parametrize("m,n,k", [(700, 2000, 30), (150, 500, 150)])
+def test_margin_run_end_to_end(m, n, k):
+    """schulze_run with margin weights: top-k ballots with unlisted candidates
+    (one uniform cold column) and full rankings, against the oracle."""
+    r = W.mallows(m + k, n, m, k, 0.9, W.permutation(m, m))
+    out = S.schulze_run(cu(r), m, flags=S.F_MARGIN)
+    d = oracle.tally(r, m)
+    p = oracle.closure(oracle.weights_margin(d), nthreads=8)
+    eq(host(out["p"]), p, "margin p")
+    eq(host(out["winners"]), oracle.winners(p), "margin winners")
+    order, bb = oracle.ranking(p)
+    eq(host(out["order"]), order, "margin order")
+    eq(host(out["beaten_by"]), bb, "margin beaten_by")
+
+
+@pytest.mark.parametrize("m,n,levels", [(1, 5, 1), (5, 40, 2), (65, 300, 4), (150, 700, 20), (300, 100, 300)])
+def test_tally_positions_weak_orders(m, n, levels):
+    """Weak orders (positions drawn from `levels` values, so ties abound)
+    against the oracle's position-form tally."""
+    rs = np.random.Generator(np.random.PCG64(m * 7 + n))
+    pos = rs.integers(0, levels, size=(n, m)).astype(np.int32)
+    eq(host(S.schulze_tally_positions(cu(pos))), oracle.tally_positions(pos), f"weak m={m}")
+
+
+def test_tally_positions_many_ballots_and_order_form():
+    """More ballots than one chunk of position rows; and order-form ballots
+    written as positions give the order-form tally."""
+    rs = np.random.Generator(np.random.PCG64(9))
+    pos = rs.integers(0, 6, size=(70001, 40)).astype(np.int32)
+    eq(host(S.schulze_tally_positions(cu(pos))), oracle.tally_positions(pos), "weak chunked")
+    m, n, k = 200, 900, 12
+    r = W.mallows(4, n, m, k, 0.9, W.permutation(4, m))
+    pos = np.full((n, m), k, np.int32)
+    for v in range(n):
+        pos[v, r[v]] = np.arange(k)
+    eq(host(S.schulze_tally_positions(cu(pos))), host(S.schulze_tally(cu(r), m)), "positions vs order form")
+
+
+def test_tally_positions_rejects_out_of_range():
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    S.schulze_tally_positions(cu(np.array([[0, 65535, 2]], np.int32)))
+    assert ctx.status() == S.EDATA
+    S.schulze_tally_positions(cu(np.array([[0, -3, 2]], np.int32)))
+    assert ctx.status() == S.EDATA
+    S.schulze_tally_positions(cu(np.array([[0, 65534, 2]], np.int32)))
+    assert ctx.status() == S.OK
