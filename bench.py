@@ -38,6 +38,8 @@ WORKLOADS = {
                              "(phi~U[0.5,1]) half impartial culture, one persistent launch"),
     "learned": dict(desc="proposal network trained on 2000 GPU-solved top-k Mallows elections; "
                          "32 evaluation elections m=8192, n=20000, top-50, phi=0.9"),
+    "weak_orders": dict(desc="m=1024, n=20000 weak orders in position form: Mallows(0.97) rankings cut into "
+                             "tiers of 16 tied places; position-compare tally, closure, winners, ranking"),
 }
 
 
@@ -148,6 +150,157 @@ def run_learned(args, world, rank, local):
             "device_status": ctx.status()}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_weak(args, world, rank, local):
+    """Weak-order ballots: one step = schulze_tally_positions, then
+    schulze_strongest_paths (winning votes, or margins with --margin),
+    schulze_winners and schulze_ranking, captured as one CUDA graph."""
+    import torch
+    import torch.distributed as dist
+    import paper_2505_12976_gb300 as S
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    m, n = args.m or 1024, args.n or 20000
+    pos_h = W.weak_orders(seed=W.SEED_BASE + 7 + 1000 * rank, n=n, m=m)
+    pos_d = torch.from_numpy(pos_h).to(dev)
+    ctx = S.context(local)
+    ctx.reserve(m, n, m)
+    flags = S.F_MARGIN if args.margin else 0
+    d = torch.empty((m, m), dtype=torch.int32, device=dev)
+    p = torch.empty((m, m), dtype=torch.int32, device=dev)
+    win = torch.empty(m, dtype=torch.int32, device=dev)
+    order = torch.empty(m, dtype=torch.int32, device=dev)
+    bb = torch.empty(m, dtype=torch.int32, device=dev)
+
+    def step(src):
+        S.schulze_tally_positions(src, d=d, ctx=ctx)
+        S.schulze_strongest_paths(d, n, p=p, flags=flags, ctx=ctx)
+        S.schulze_winners(p, winners=win, ctx=ctx)
+        S.schulze_ranking(p, order=order, beaten_by=bb, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step(pos_d)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    step(pos_d)
+    launches_per_step = ctx.launch_count() - l0
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        step(pos_d)
+    torch.cuda.current_stream().wait_stream(cap)
+    with torch.cuda.graph(graph):
+        step(pos_d)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record()
+        graph.replay()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clock_info = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ref = (win.clone(), order.clone())
+    step(pos_d)
+    torch.cuda.synchronize()
+    graph_matches = torch.equal(ref[0], win) and torch.equal(ref[1], order)
+    ctx.profile(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda._sleep(2_000_000)
+        step(pos_d)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # dense tally: n m (m - 1) position compares, ALU-bound; 16-bit packed
+    # compare + subtract = one instruction per compare and lane pair
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    tally = prof.get("tally_dense")
+    roof = None
+    if tally:
+        per = tally["ms"] / max(1, tally["launches"])
+        cmp_per_launch = float(n) * m * (m - 1) / max(1, tally["launches"] // args.steps)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 64 * 2 * 2.07e9  # 64 lanes/clk/SM, 2 compares per packed op, vsub + vcmp per pair: see DESIGN
+        roof = {"bound": "alu", "kernel": "tally_dense", "achieved": cmp_per_launch / (per * 1e-3) / 1e9,
+                "peak": peak / 2 / 1e9, "unit": "Gcompares/s", "frac": cmp_per_launch / (per * 1e-3) / (peak / 2),
+                "traffic": None, "per_launch_ms": per,
+                "peak_source": "152 SMs x 64 int lanes/clk x 2 lanes per 16-bit op x 2.07 GHz / 2 ops per compare"}
+    # end to end: host positions (pinned) in, winners and order out, through the same calls
+    pos_pin = torch.from_numpy(pos_h).pin_memory()
+    win_h = torch.empty(m, dtype=torch.int32).pin_memory()
+    ord_h = torch.empty(m, dtype=torch.int32).pin_memory()
+    stage = torch.empty_like(pos_d)
+    tot = 0.0
+    e2e_steps = args.e2e_steps or max(3, args.steps)
+    for _ in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stage.copy_(pos_pin, non_blocking=True)
+        step(stage)
+        win_h.copy_(win, non_blocking=True)
+        ord_h.copy_(order, non_blocking=True)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0 if _ else 0.0
+    e2e_sec = tot / e2e_steps
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sm_, sn_ = 256, 2000
+        sample = W.weak_orders(seed=W.SEED_BASE + 80, n=sn_, m=sm_)
+        sec = time_oracle_weak(sample, args.margin, os.cpu_count() or 1)
+        cpu = {"value": float(sm_) ** 3 / sec, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"one m={sm_}, n={sn_} weak-order election of the same model "
+                         f"(tally, closure, winners, ranking in {sec:.2f} s; cand^3/s = m^3 / time)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * float(m) ** 3 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int16x2" if n <= 32767 else "int32",
+                "data": "synthetic",
+                "config": {"workload": "weak_orders", "detail": WORKLOADS["weak_orders"]["desc"], "m": m, "n": n,
+                           "weights": "margin" if args.margin else "winning votes",
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "elections_per_sec": world / (ms * 1e-3), "roofline": roof,
+                "kernels": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in
+                            sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+                "dominant_kernel": top[0], "cpu_baseline": cpu,
+                "e2e": {"value": world * float(m) ** 3 / e2e_sec, "unit": UNIT,
+                        "h2d_bytes_per_step": int(n) * int(m) * 4, "d2h_bytes_per_step": 2 * int(m) * 4},
+                "gpu_launches": int(launches_per_step * args.steps),
+                "timed_as": "CUDA graph of the four calls, replayed", "graph_matches_eager": graph_matches,
+                "device_status": ctx.status(), "clocks": clock_info}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_oracle_weak(pos, margin: bool, nthreads: int):
+    """Wall time of the oracle's whole path on weak-order ballots."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    d = oracle.tally_positions(pos)
+    w = oracle.weights_margin(d) if margin else oracle.weights(d)
+    p = oracle.closure(w, nthreads=nthreads)
+    oracle.winners(p)
+    oracle.ranking(p)
+    return time.perf_counter() - t0
 
 
 def run_batch(args, world, rank, local):
@@ -356,6 +509,7 @@ def main():
     ap.add_argument("--train-elections", type=int, default=2000, help="training elections (learned workload)")
     ap.add_argument("--eval-elections", type=int, default=32, help="evaluation elections (learned workload)")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs (learned workload)")
+    ap.add_argument("--margin", action="store_true", help="margin edge weights instead of winning votes")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -378,6 +532,8 @@ def main():
         return run_batch(args, world, rank, local)
     if args.workload == "learned":
         return run_learned(args, world, rank, local)
+    if args.workload == "weak_orders":
+        return run_weak(args, world, rank, local)
     e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)
@@ -388,8 +544,10 @@ def main():
                               ("beaten_by", (m,)))}
     s16 = n <= 32767
 
+    run_flags = S.F_MARGIN if args.margin else 0
+
     def step():
-        S.schulze_run(ranks_d, m, out=out, ctx=ctx)
+        S.schulze_run(ranks_d, m, out=out, flags=run_flags, ctx=ctx)
 
     # integer min/max issue rate (same lane format as the closure)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -518,13 +676,13 @@ def main():
     win_h = torch.empty(m, dtype=torch.int32).pin_memory()
     ord_h = torch.empty(m, dtype=torch.int32).pin_memory()
     e2e_steps = args.e2e_steps or max(3, args.steps)
-    S.schulze_run_host(ranks_h, m, winners=win_h, order=ord_h, device=local)
+    S.schulze_run_host(ranks_h, m, flags=run_flags, winners=win_h, order=ord_h, device=local)
     tot = 0.0
     for _ in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S.schulze_run_host(ranks_h, m, winners=win_h, order=ord_h, device=local)
+        S.schulze_run_host(ranks_h, m, flags=run_flags, winners=win_h, order=ord_h, device=local)
         tot += time.perf_counter() - t0
     e2e_sec = tot / e2e_steps
     if world > 1:
@@ -547,6 +705,7 @@ def main():
                 "config": {"workload": args.workload + ("" if not (args.m or args.n) else f" (m={m}, n={n})"),
                            "detail": WORKLOADS[args.workload]["desc"], "m": m, "n": n, "k": k, "elections_per_step": world,
                            "closure": "16-bit packed" if s16 else "int32",
+                           "weights": "margin" if args.margin else "winning votes",
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "elections_per_sec": world / (ms * 1e-3),
                 "tally": {"ms_per_step": tally_ms, "algorithmic_GBps": tally_bytes / (tally_ms * 1e-3) / 1e9

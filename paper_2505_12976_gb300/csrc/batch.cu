@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "count.cuh"
 #include "internal.cuh"
 #include "tiles.cuh"
 
@@ -90,7 +91,9 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
   const int tid = threadIdx.x, g = tid / tiles::kThreads, lt = tid % tiles::kThreads;
   const int tx = lt % (kTT / 4), ty = lt / (kTT / 4);
-  const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16);
+  // positions are below 2^15 (m <= 1024): the row operand carries the guard
+  // bits of count_lt2
+  const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16) | kGuard2;
   const int32_t mpad = int32_t(align_up(size_t(m), kTT));
   for (int32_t t0 = 0; t0 < ntiles; t0 += kGroups) {
     // this group's tile (bi, bj)
@@ -149,7 +152,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
               if (check) set_status(status, SCHULZE_EDATA);
               continue;
             }
-            const uint32_t q2 = uint32_t(q) | (uint32_t(q) << 16);
+            const uint32_t q2 = uint32_t(q) | (uint32_t(q) << 16) | kGuard2;
             if (check) {
               if (atomicExch(&sm.stage.dup[vv][c], q2) != unl2) set_status(status, SCHULZE_EDATA);
             } else {
@@ -170,8 +173,8 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
           b[0] = bv.x, b[1] = bv.y;
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
-            acc[r][0] = __vsub2(acc[r][0], __vcmpltu2(a[r], b[0]));
-            acc[r][1] = __vsub2(acc[r][1], __vcmpltu2(a[r], b[1]));
+            acc[r][0] = count_lt2(acc[r][0], a[r], b[0]);
+            acc[r][1] = count_lt2(acc[r][1], a[r], b[1]);
           }
         }
         const bool last = v0 + chunk >= n;

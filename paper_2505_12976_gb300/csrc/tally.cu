@@ -17,6 +17,7 @@
 //    Which form runs is decided on the device once |A| is known.
 #include <algorithm>
 
+#include "count.cuh"
 #include "internal.cuh"
 #include "scan.cuh"
 
@@ -69,33 +70,41 @@ __global__ void pos_build_kernel(const int32_t* __restrict__ ranks, int64_t v0, 
 
 // Weak orders in position form: pos[v][c] for v in [v0, v0 + nv) copied from
 // the caller's int32 positions (smaller is better, equal is tied) into the
-// 16-bit rows; a position outside [0, 65534] sets EDATA. Padding columns
-// (c >= m) hold 0xFFFF; their counts are never written.
+// 16-bit rows; a position outside [0, 65534] sets EDATA, one above 32767
+// sets *wide. Padding columns (c >= m) hold 0x7FFF; their counts are never
+// written.
 __global__ void pos_copy_kernel(const int32_t* __restrict__ src, int64_t v0, int64_t nv, int32_t m, int32_t ldp,
-                                uint16_t* __restrict__ pos, int32_t* status) {
+                                uint16_t* __restrict__ pos, int32_t* status, int32_t* __restrict__ wide) {
   const int64_t total = nv * ldp;
-  bool bad = false;
+  bool bad = false, big = false;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t w = e / ldp;
     const int32_t c = int32_t(e - w * ldp);
-    uint16_t v = 0xFFFFu;
+    uint16_t v = 0x7FFFu;
     if (c < m) {
       const int32_t x = src[(v0 + w) * m + c];
       bad |= x < 0 || x > 65534;
+      big |= x > 32767;
       v = uint16_t(x < 0 ? 0 : (x > 65534 ? 65534 : x));
     }
     pos[e] = v;
   }
   if (bad) set_status(status, SCHULZE_EDATA);
+  if (big) *wide = 1;  // positions need the 16-bit compare
 }
 
 // One CTA counts a TILE x TILE block of d over a chunk of ballots.
 // Thread micro-tile RM x RN (RN even); lanes of a 32-bit word hold two
 // adjacent j columns; the row operand is duplicated into both halves.
+// Positions below 2^15 (guard_ok, and no wide position flagged in *wide)
+// are compared with count_lt2, others with a packed 16-bit compare.
 template <int TILE, int RM, int RN>
 __global__ void __launch_bounds__((TILE / RM) * (TILE / RN))
     dense_tally_kernel(const uint16_t* __restrict__ pos, int32_t ldp, int64_t nv, int32_t m, int32_t nbt,
-                       int32_t vchunk, int upper_only, int add, int32_t* __restrict__ d) {
+                       int32_t vchunk, int upper_only, int add, int guard_ok, const int32_t* __restrict__ wide,
+                       int32_t* __restrict__ d) {
+  const bool guard = guard_ok && !(wide && *wide);
+  const uint32_t gbits = guard ? kGuard2 : 0u;
   constexpr int TX = TILE / RN, TY = TILE / RM, NT = TX * TY, WN = RN / 2;
   __shared__ __align__(16) uint32_t sI[kDenseVoters][TILE];      // row positions, duplicated
   __shared__ __align__(16) uint16_t sJ[kDenseVoters][TILE];      // column positions
@@ -127,13 +136,13 @@ __global__ void __launch_bounds__((TILE / RM) * (TILE / RN))
     __syncthreads();
     for (int t = threadIdx.x; t < kDenseVoters * TILE; t += NT) {
       int vv = t / TILE, c = t % TILE;
-      uint32_t pi = 0xFFFFu, pj = 0u;  // padding never counts: pi is max, pj is min
+      uint32_t pi = 0x7FFFu, pj = 0u;  // padding never counts: pi is not below pj
       if (vv < nvs) {
         const uint16_t* prow = pos + (v0 + vv) * ldp;
         pi = prow[I0 + c];
         pj = prow[J0 + c];
       }
-      sI[vv][c] = pi | (pi << 16);
+      sI[vv][c] = pi | (pi << 16) | gbits;
       sJ[vv][c] = uint16_t(pj);
     }
     __syncthreads();
@@ -149,10 +158,17 @@ __global__ void __launch_bounds__((TILE / RM) * (TILE / RN))
         uint2 t2 = *reinterpret_cast<const uint2*>(&sJ[vv][tx * RN + 2 * w]);
         b[w] = t2.x, b[w + 1] = t2.y;
       }
+      if (guard) {
 #pragma unroll
-      for (int r = 0; r < RM; ++r)
+        for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int w = 0; w < WN; ++w) acc[r][w] = __vsub2(acc[r][w], __vcmpltu2(a[r], b[w]));
+          for (int w = 0; w < WN; ++w) acc[r][w] = count_lt2(acc[r][w], a[r], b[w]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+          for (int w = 0; w < WN; ++w) acc[r][w] = __vsub2(acc[r][w], __vcmpltu2(a[r], b[w]));
+      }
     }
   }
   // lanes -> int32 counts (added atomically when several CTAs share a tile)
@@ -739,8 +755,8 @@ int64_t dense_voter_chunk(int64_t n, int32_t m) {
 // writes chunk by chunk: build(v0, nv, ldp, pos) fills rows v0 .. v0+nv-1.
 // `full`: strict full orders, only the upper tiles are counted and mirrored.
 template <class Build>
-int dense_tally(schulze_ctx* ctx, int64_t n, int32_t m, bool full, int32_t* d, void* ws, cudaStream_t stream,
-                Build build) {
+int dense_tally(schulze_ctx* ctx, int64_t n, int32_t m, bool full, bool guard_ok, int32_t* wide, int32_t* d,
+                void* ws, cudaStream_t stream, Build build) {
   const size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
   Carver cv(ws);
@@ -766,10 +782,10 @@ int dense_tally(schulze_ctx* ctx, int64_t n, int32_t m, bool full, int32_t* d, v
     Launch L(ctx, stream, "tally_dense", double(nv) * double(m) * double(m - 1) / (full ? 2.0 : 1.0));
     if (tile == 64)
       dense_tally_kernel<64, 8, 8><<<grid, 64, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
-                                                             accumulate ? 1 : 0, d);
+                                                             accumulate ? 1 : 0, guard_ok ? 1 : 0, wide, d);
     else
       dense_tally_kernel<128, 8, 8><<<grid, 256, 0, stream>>>(pos, ldp, nv, m, nbt, vchunk, full ? 1 : 0,
-                                                               accumulate ? 1 : 0, d);
+                                                               accumulate ? 1 : 0, guard_ok ? 1 : 0, wide, d);
     if (int rc = check_launch()) return rc;
   }
   if (full && nbt > 1) {
@@ -807,7 +823,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   Carver cv(ws);
   if (choose_dense(n, m, k, flags)) {
     // strict full orders: d[j][i] = n - d[i][j]
-    return dense_tally(ctx, n, m, k >= m - 1, d, ws, stream,
+    return dense_tally(ctx, n, m, k >= m - 1, k <= 32767, nullptr, d, ws, stream,
                        [&](int64_t v0, int64_t nv, int32_t ldp, uint16_t* pos) {
                          const int pb = int(std::min<int64_t>((nv + 7) / 8, int64_t(sms) * 16));
                          Launch L(ctx, stream, "tally_positions", double(nv) * (double(k) * 4.0 + double(ldp) * 2.0));
@@ -899,11 +915,15 @@ int tally_positions_launch(schulze_ctx* ctx, const int32_t* pos_in, int64_t n, i
                            cudaStream_t stream) {
   if (n == 0) return cudaMemsetAsync(d, 0, size_t(m) * size_t(m) * 4, stream) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
-  return dense_tally(ctx, n, m, false, d, ws, stream, [&](int64_t v0, int64_t nv, int32_t ldp, uint16_t* pos) {
-    const int g = int(std::max<int64_t>(1, std::min<int64_t>((nv * ldp + 255) / 256, int64_t(sms) * 8)));
-    Launch L(ctx, stream, "tally_positions_copy", double(nv) * double(m) * 4.0);
-    pos_copy_kernel<<<g, 256, 0, stream>>>(pos_in, v0, nv, m, ldp, pos, ctx->status);
-  });
+  // the flag word sits after the position rows in the workspace
+  int32_t* wide = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + tally_positions_workspace_bytes(n, m) - 256);
+  if (cudaMemsetAsync(wide, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+  return dense_tally(ctx, n, m, false, true, wide, d, ws, stream,
+                     [&](int64_t v0, int64_t nv, int32_t ldp, uint16_t* pos) {
+                       const int g = int(std::max<int64_t>(1, std::min<int64_t>((nv * ldp + 255) / 256, int64_t(sms) * 8)));
+                       Launch L(ctx, stream, "tally_positions_copy", double(nv) * double(m) * 4.0);
+                       pos_copy_kernel<<<g, 256, 0, stream>>>(pos_in, v0, nv, m, ldp, pos, ctx->status, wide);
+                     });
 }
 
 }  // namespace schulze

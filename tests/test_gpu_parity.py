@@ -416,6 +416,18 @@ def test_tally_positions_weak_orders(m, n, levels):
     eq(host(S.schulze_tally_positions(cu(pos))), oracle.tally_positions(pos), f"weak m={m}")
 
 
+def test_tally_positions_wide_positions():
+    """Positions above 32767 take the 16-bit compare instead of the guard-bit
+    count; both against the oracle, with ties."""
+    rs = np.random.Generator(np.random.PCG64(11))
+    pos = rs.integers(0, 65535, size=(300, 130)).astype(np.int32)
+    pos[:, 7] = pos[:, 3]  # ties
+    pos[5, :] = 65534
+    eq(host(S.schulze_tally_positions(cu(pos))), oracle.tally_positions(pos), "wide positions")
+    small = (pos // 2).astype(np.int32)  # below 2^15
+    eq(host(S.schulze_tally_positions(cu(small))), oracle.tally_positions(small), "narrow positions")
+
+
 def test_tally_positions_many_ballots_and_order_form():
     """More ballots than one chunk of position rows; and order-form ballots
     written as positions give the order-form tally."""

@@ -230,6 +230,18 @@ def learned_eval(E: int = 256, seed: int = SEED_BASE + 5, m: int = 8192, n: int 
     return learned_elections(E, seed, (m, m), (n, n), (k, k), (phi, phi), **kw)
 
 
+def weak_orders(seed: int = SEED_BASE + 7, n: int = 20000, m: int = 1024, tier: int = 16,
+                phi: float = 0.97) -> np.ndarray:
+    """Weak-order ballots in position form, int32 [n, m]: a full Mallows(phi)
+    ranking around a seeded random reference order, cut into tiers of `tier`
+    consecutive places (tied inside a tier): pos[v][c] = place of c // tier."""
+    r = mallows(seed, n, m, m, phi, permutation(seed ^ 0x5A, m))
+    pos = np.empty((n, m), dtype=np.int32)
+    rows = np.arange(n)[:, None]
+    pos[rows, r] = (np.arange(m, dtype=np.int32) // tier)[None, :]
+    return pos
+
+
 def mlp_init(seed: int = SEED_BASE + 6) -> np.ndarray:
     """Initial weights of the 16-64-64-1 proposal network (5313 float32):
     He-normal weights, zero biases; a seeded draw, fed to both the GPU
