@@ -38,6 +38,8 @@ WORKLOADS = {
                              "(phi~U[0.5,1]) half impartial culture, one persistent launch"),
     "learned": dict(desc="proposal network trained on 2000 GPU-solved top-k Mallows elections; "
                          "32 evaluation elections m=8192, n=20000, top-50, phi=0.9"),
+    "spotify_like": dict(desc="m=18407, n=15553, top-200 Plackett-Luce Zipf(1.1): the shape of the paper's "
+                              "largest Spotify profile, synthetic"),
     "weak_orders": dict(desc="m=1024, n=20000 weak orders in position form: Mallows(0.97) rankings cut into "
                              "tiers of 16 tied places; position-compare tally, closure, winners, ranking"),
 }
@@ -55,6 +57,8 @@ def make_election(name: str, rank: int, m=None, n=None):
         return W.small_mallows(seed=W.SEED_BASE + 1000 * rank)
     if name == "huge_pl":
         return W.huge_pl(seed=W.SEED_BASE + 2 + 1000 * rank, **size)
+    if name == "spotify_like":
+        return W.spotify_like(seed=W.SEED_BASE + 8 + 1000 * rank, **size)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -69,6 +73,9 @@ def cpu_sample_election(name: str):
     if name == "huge_pl":
         return (W.huge_pl(seed=W.SEED_BASE + 78, n=20000, m=1536),
                 "one m=1536, n=20000 top-20 Plackett-Luce Zipf(1.1) election")
+    if name == "spotify_like":
+        return (W.spotify_like(seed=W.SEED_BASE + 81, m=1536),
+                "one m=1536, n=15553 top-200 Plackett-Luce Zipf(1.1) election")
     if name == "batch_mixed":
         return W.batch_mixed(E=48, seed=W.SEED_BASE + 79), "48 elections drawn like the 4096-election batch"
     raise SystemExit(name)

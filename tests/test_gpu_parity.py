@@ -451,3 +451,34 @@ def test_tally_positions_rejects_out_of_range():
     assert ctx.status() == S.EDATA
     S.schulze_tally_positions(cu(np.array([[0, 65534, 2]], np.int32)))
     assert ctx.status() == S.OK
+
+
+def test_spotify_like_workload_full_size():
+    """m=18407, n=15553, top-200 Plackett-Luce Zipf(1.1) (the shape of the
+    paper's largest Spotify profile). Tally by row/column sums and sampled
+    entries; the closure on the 2048 most popular candidates against the
+    oracle closure, and on full-m sampled rows and columns by Dijkstra;
+    winners certified."""
+    e = W.spotify_like()
+    m = e.m
+    out = S.schulze_run(cu(e.ranks), m)
+    d = host(out["d"])
+    _check_row_col_sums(e.ranks, m, d)
+    sub = W.spotify_popular(m, 2048)
+    for a in range(0, 2048, 211):
+        for b in range(5, 2048, 397):
+            i, j = int(sub[a]), int(sub[b])
+            assert d[i, j] == oracle.tally_entry(e.ranks, m, i, j)
+    dS = np.ascontiguousarray(d[np.ix_(sub, sub)])
+    pS = S.schulze_strongest_paths(cu(dS), bound=e.n)
+    eq(host(pS), oracle.strongest_paths(dS, nthreads=16), "subsample closure")
+    w = oracle.weights(d)
+    p = host(out["p"])
+    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1000]), m - 1])
+    for c in np.flatnonzero(host(out["winners"])):
+        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
+        assert np.all(fwd >= bwd)
+    bb = host(out["beaten_by"])
+    order = host(out["order"])
+    assert sorted(order.tolist()) == list(range(m))
+    assert np.all(np.diff(bb[order]) >= 0)

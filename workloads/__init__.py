@@ -155,6 +155,21 @@ def popular_subsample(m: int, size: int, seed: int = SEED_BASE + 2) -> np.ndarra
     return np.sort(perm[:size]).astype(np.int64)
 
 
+def spotify_like(seed: int = SEED_BASE + 8, n: int = 15553, m: int = 18407, k: int = 200) -> Election:
+    """Shaped like the paper's largest Spotify profile (Sect. 5.1: about 18.4k
+    candidates, 15.5k voters, top-200 lists): top-200 Plackett-Luce with
+    Zipf(1.1) weights on a seeded id permutation. Synthetic; no item of any
+    data set is reproduced."""
+    perm = permutation(seed ^ 0x5B5B, m)
+    return Election(plackett_luce_zipf(seed, n, m, k, 1.1, perm), m, f"pl-zipf1.1-top{k} m={m} n={n}")
+
+
+def spotify_popular(m: int, size: int, seed: int = SEED_BASE + 8) -> np.ndarray:
+    """The `size` highest-weight candidate ids of ``spotify_like``."""
+    perm = permutation(seed ^ 0x5B5B, m)
+    return np.sort(perm[:size]).astype(np.int64)
+
+
 @dataclass
 class Batch:
     """E independent elections packed back to back."""
