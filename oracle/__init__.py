@@ -53,6 +53,8 @@ def _load():
             lib.oracle_validate.restype = ctypes.c_int
             lib.oracle_tally.argtypes = [i32p, i64, i32, i32, i32p]
             lib.oracle_tally.restype = ctypes.c_int
+            lib.oracle_ranking_iterated.argtypes = [i32p, i32, i32, ctypes.c_int, i32p, i32p]
+            lib.oracle_ranking_iterated.restype = ctypes.c_int
             lib.oracle_tally_positions.argtypes = [i32p, i64, i32, i32p]
             lib.oracle_tally_positions.restype = ctypes.c_int
             lib.oracle_tally_entry.argtypes = [i32p, i64, i32, i32, i32, i32]
@@ -214,3 +216,17 @@ def schulze(ranks, m: int, nthreads: int = 1):
     win = winners(p)
     order, bb = ranking(p)
     return d, p, win, order, bb
+
+
+def ranking_iterated(d, k_top: int | None = None, margin: bool = False):
+    """Top-k ranking by iterated winner removal (Sect. 4, closing remark):
+    (level [m], number of levels); level 0 = not placed."""
+    d = _i32(d)
+    m = d.shape[0]
+    level = np.zeros(m, dtype=np.int32)
+    nl = np.zeros(1, dtype=np.int32)
+    rc = _load().oracle_ranking_iterated(_p(d), m, m if k_top is None else int(k_top), int(bool(margin)),
+                                         _p(level), _p(nl))
+    if rc:
+        raise OracleError(rc)
+    return level, int(nl[0])

@@ -250,3 +250,48 @@ void oracle_widest_one(const int32_t* w, int32_t m, int32_t s, int transpose, in
   free(done);
   free(best);
 }
+
+/*
+ * Top-k ranking by iterated winner removal (Sect. 4, closing remark: run the
+ * method again after removing the Schulze winners). Level t is the winner
+ * set of the profile restricted to the candidates not placed in levels
+ * 1 .. t-1; pairwise counts do not depend on the other candidates, so the
+ * restricted profile's d is d on the remaining rows and columns. Levels are
+ * assigned until at least k_top candidates are placed (or all are).
+ * level[c] = t >= 1 for a placed candidate, 0 otherwise; *levels = number of
+ * levels. margin != 0 uses margin weights instead of winning votes.
+ */
+int oracle_ranking_iterated(const int32_t* d, int32_t m, int32_t k_top, int margin, int32_t* level,
+                            int32_t* levels) {
+  if (m < 1 || !d || !level || !levels) return ORACLE_EINVAL;
+  int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  int32_t* sd = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * (size_t)m);
+  int32_t* sw = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * (size_t)m);
+  int32_t* sp = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * (size_t)m);
+  int32_t* win = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  if (!idx || !sd || !sw || !sp || !win) {
+    free(idx), free(sd), free(sw), free(sp), free(win);
+    return ORACLE_ENOMEM;
+  }
+  for (int32_t c = 0; c < m; ++c) level[c] = 0;
+  int32_t placed = 0, t = 0;
+  while (placed < m && placed < k_top) {
+    int32_t r = 0;  /* the remaining candidates, in id order */
+    for (int32_t c = 0; c < m; ++c)
+      if (level[c] == 0) idx[r++] = c;
+    for (int32_t a = 0; a < r; ++a)
+      for (int32_t b = 0; b < r; ++b) sd[(int64_t)a * r + b] = d[(int64_t)idx[a] * m + idx[b]];
+    if (margin)
+      oracle_weights_margin(sd, r, sw);
+    else
+      oracle_weights(sd, r, sw);
+    oracle_closure(sw, r, sp, 1);
+    oracle_winners(sp, r, win);
+    ++t;
+    for (int32_t a = 0; a < r; ++a)
+      if (win[a]) level[idx[a]] = t, ++placed;
+  }
+  *levels = t;
+  free(idx), free(sd), free(sw), free(sp), free(win);
+  return ORACLE_OK;
+}

@@ -383,3 +383,58 @@ def test_tally_positions_rejects_out_of_range():
         oracle.tally_positions(np.array([[0, 65535]], np.int32))
     with pytest.raises(oracle.OracleError):
         oracle.tally_positions(np.array([[-1, 0]], np.int32))
+
+
+# ------------------------------------- top-k ranking by iterated removal
+
+def _levels_brute_force(d, k_top, margin=False):
+    """Levels from the definition: brute-force widest paths (simple-path
+    enumeration) on the weights of the remaining candidates, winners by
+    Sect. 2.1, removed, repeated."""
+    d = np.asarray(d, np.int64)
+    m = d.shape[0]
+    level = np.zeros(m, np.int32)
+    t = placed = 0
+    while placed < min(m, k_top):
+        rem = np.flatnonzero(level == 0)
+        ds = d[np.ix_(rem, rem)]
+        w = np.where(ds > ds.T, ds - ds.T if margin else ds, 0)
+        np.fill_diagonal(w, 0)
+        p = brute_force_widths(w)
+        t += 1
+        for a, c in enumerate(rem):
+            if all(p[a, b] >= p[b, a] for b in range(len(rem)) if b != a):
+                level[c] = t
+                placed += 1
+    return level, t
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_ranking_iterated_matches_brute_force(seed):
+    rs = np.random.Generator(np.random.PCG64(500 + seed))
+    m = int(rs.integers(2, 8))
+    n = int(rs.integers(1, 12))
+    k = int(rs.integers(1, m + 1))
+    r = W.mallows(700 + seed, n, m, k, 0.7 + 0.3 * rs.random(), W.permutation(seed, m))
+    d = oracle.tally(r, m)
+    for k_top in (1, 2, m):
+        for margin in (False, True):
+            got = oracle.ranking_iterated(d, k_top, margin)
+            want = _levels_brute_force(d, k_top, margin)
+            np.testing.assert_array_equal(got[0], want[0])
+            assert got[1] == want[1]
+
+
+def test_ranking_iterated_identical_voters_and_fig1():
+    """Identical full ballots: one candidate per level, in ballot order. Fig. 1:
+    a alone on the first level (the paper's winner)."""
+    m = 9
+    ballot = np.random.Generator(np.random.PCG64(1)).permutation(m).astype(np.int32)
+    d = oracle.tally(np.tile(ballot, (5, 1)), m)
+    level, nl = oracle.ranking_iterated(d)
+    assert nl == m
+    np.testing.assert_array_equal(level[ballot], np.arange(1, m + 1))
+    _, mu, _, win = fig1()
+    level, _ = oracle.ranking_iterated(oracle.tally(mcgarvey_ballots(mu), 4), 1)
+    assert np.flatnonzero(level == 1).tolist() == win
+    assert np.count_nonzero(level) == 1
