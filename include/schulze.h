@@ -180,6 +180,25 @@ int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* orde
                     schulze_stream_t stream);
 
 /*
+ * Top-k ranking by iterated winner removal (Sect. 4, closing remark: run the
+ * method again after removing the Schulze winners). Level t is the winner
+ * set of the profile restricted to the candidates not placed in levels
+ * 1 .. t-1 (pairwise counts do not depend on the other candidates).
+ *   d       [m, m] int32 device tally (read only); bound as for
+ *           schulze_strongest_paths; flags may add SCHULZE_F_MARGIN.
+ *   k_top   levels are assigned until at least min(k_top, m) candidates are
+ *           placed (k_top >= 1).
+ *   level   [m] int32 device output: the level (>= 1) of each placed
+ *           candidate, 0 for the others.
+ *   levels  host int32, may be NULL: number of levels assigned.
+ * Synchronous on `stream` (one host round trip per level; not for capture).
+ * Each level runs the closure on a working copy of d in which the placed
+ * candidates are isolated.
+ */
+int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t k_top,
+                             int32_t* level, int32_t* levels, uint32_t flags, schulze_stream_t stream);
+
+/*
  * The whole path for one election: tally, widest paths, winners and ranking
  * in one call (device buffers). d and p are written as by the calls above;
  * winners, order and beaten_by may each be NULL. `flags` combines the tally

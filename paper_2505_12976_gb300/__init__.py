@@ -46,6 +46,7 @@ SIGNATURES = [
     ("schulze_get_status", _c.c_int, [_vp, _c.POINTER(_i32), _vp]),
     ("schulze_tally", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _u32, _vp]),
     ("schulze_tally_positions", _c.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    ("schulze_ranking_iterated", _c.c_int, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _u32, _vp]),
     ("schulze_strongest_paths", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _u32, _vp]),
     ("schulze_winners", _c.c_int, [_vp, _vp, _i32, _vp, _vp]),
     ("schulze_ranking", _c.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
@@ -293,6 +294,22 @@ def schulze_strongest_paths_static(d: torch.Tensor, bound: int, p: torch.Tensor 
         _check(load().schulze_strongest_paths_static(_ptr(d), m, int(bound), _ptr(p), flags, _ptr(status),
                                                      _stream(stream, d.device)), "schulze_strongest_paths_static")
     return p
+
+
+def schulze_ranking_iterated(d: torch.Tensor, bound: int, k_top: int | None = None, flags: int = 0,
+                             level: torch.Tensor | None = None, ctx: Context | None = None, stream=None):
+    """Top-k ranking by iterated winner removal: (level int32 [m] on the
+    GPU, 0 = not placed; number of levels)."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    _dev_i32(d, "d", (m, m))
+    ctx = ctx or context(d.device)
+    level = _out(level, (m,), d.device, "level")
+    nl = _c.c_int32(0)
+    _check(load().schulze_ranking_iterated(ctx.handle, _ptr(d), m, int(bound), m if k_top is None else int(k_top),
+                                           _ptr(level), _c.byref(nl), flags, _stream(stream, ctx.device)),
+           "schulze_ranking_iterated")
+    return level, int(nl.value)
 
 
 NPARAM = 5313  # MLP parameters: W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64], b3

@@ -180,6 +180,39 @@ int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* orde
   return extract_launch(ctx, p, m, nullptr, order, beaten_by, ctx->ws.base, stream);
 }
 
+int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t k_top,
+                             int32_t* level, int32_t* levels, uint32_t flags, schulze_stream_t stream) {
+  if (!ctx || !d || !level || m < 1 || m > kMaxM || bound < 0 || k_top < 1) return SCHULZE_EINVAL;
+  if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || bound > 32767)) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  const size_t mm = align_up(size_t(m) * size_t(m) * 4, 256), mv = align_up(size_t(m + 1) * 4, 256);
+  const size_t cws = align_up(closure_workspace_bytes(m, bound, flags), 256);
+  if (int rc = ensure_workspace(ctx, cws + 2 * mm + 2 * mv + 256, stream)) return rc;
+  char* base = static_cast<char*>(ctx->ws.base);
+  int32_t* dw = reinterpret_cast<int32_t*>(base + cws);
+  int32_t* p = reinterpret_cast<int32_t*>(base + cws + mm);
+  int32_t* bb = reinterpret_cast<int32_t*>(base + cws + 2 * mm);
+  int32_t* placed = reinterpret_cast<int32_t*>(base + cws + 2 * mm + mv);
+  if (cudaMemsetAsync(level, 0, size_t(m) * 4, stream) != cudaSuccess ||
+      cudaMemcpyAsync(dw, d, size_t(m) * size_t(m) * 4, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  const int32_t target = std::min(k_top, m);
+  int32_t total = 0, t = 0;
+  while (total < target) {
+    ++t;
+    if (int rc = closure_launch(ctx, dw, m, bound, p, flags, ctx->ws.base, stream, bb)) return rc;
+    if (int rc = iterated_level(ctx, bb, m, t, level, placed, dw, stream)) return rc;
+    int32_t now = 0;
+    if (cudaMemcpyAsync(&now, placed, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    if (now <= 0) return SCHULZE_EDATA;  // a nonempty winner set is guaranteed for valid data
+    total += now;
+  }
+  if (levels) *levels = t;
+  return SCHULZE_OK;
+}
+
 int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d, int32_t* p,
                 int32_t* winners, int32_t* order, int32_t* beaten_by, uint32_t flags, schulze_stream_t stream) {
   if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 ||

@@ -101,6 +101,30 @@ int finish(schulze_ctx* ctx, const int32_t* bb, int32_t* pos, int32_t m, int32_t
   return check_launch();
 }
 
+// Iterated winner removal, one level: every candidate not yet placed
+// (level 0) that no remaining candidate beats gets level t and is appended
+// to placed[1 + ...] (placed[0] counts them). Placed candidates are isolated
+// in the working d, so they neither beat nor are beaten.
+__global__ void iter_level_kernel(const int32_t* __restrict__ bb, int32_t m, int32_t t, int32_t* __restrict__ level,
+                                  int32_t* __restrict__ placed) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
+    if (level[c] == 0 && bb[c] == 0) {
+      level[c] = t;
+      placed[1 + atomicAdd(&placed[0], 1)] = c;
+    }
+}
+
+// Zeroes row c and column c of the working d for every c placed in this level.
+__global__ void iter_isolate_kernel(int32_t* __restrict__ dw, int32_t m, const int32_t* __restrict__ placed) {
+  const int32_t cnt = placed[0];
+  const int64_t total = int64_t(cnt) * m;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t c = placed[1 + int32_t(e / m)], x = int32_t(e % m);
+    dw[int64_t(c) * m + x] = 0;
+    dw[int64_t(x) * m + c] = 0;
+  }
+}
+
 }  // namespace
 
 size_t extract_workspace_bytes(int32_t m) { return 2 * align_up(size_t(m) * 4, 256) + 4096; }
@@ -125,6 +149,19 @@ int extract_from_beaten_by(schulze_ctx* ctx, const int32_t* beaten_by, int32_t m
   Carver cv(ws);
   int32_t* pos = cv.take<int32_t>(size_t(m));
   return finish(ctx, beaten_by, pos, m, winners, order, stream);
+}
+
+int iterated_level(schulze_ctx* ctx, const int32_t* bb, int32_t m, int32_t t, int32_t* level, int32_t* placed,
+                   int32_t* dw, cudaStream_t stream) {
+  if (cudaMemsetAsync(placed, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+  const int g = std::max(1, std::min((m + 255) / 256, 1024));
+  {
+    Launch L(ctx, stream, "iterated_level", double(m) * 8.0);
+    iter_level_kernel<<<g, 256, 0, stream>>>(bb, m, t, level, placed);
+  }
+  Launch L(ctx, stream, "iterated_isolate", 0.0);
+  iter_isolate_kernel<<<std::max(1, std::min(m, 2048)), 256, 0, stream>>>(dw, m, placed);
+  return check_launch();
 }
 
 }  // namespace schulze

@@ -106,6 +106,11 @@ int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound,
                    const int32_t* hint_valid = nullptr);
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream);
+// One level of the iterated-removal ranking: candidates with level 0 and
+// beaten_by 0 get level t (listed in placed[1..], counted in placed[0]) and
+// are isolated in the working tally dw.
+int iterated_level(schulze_ctx* ctx, const int32_t* bb, int32_t m, int32_t t, int32_t* level, int32_t* placed,
+                   int32_t* dw, cudaStream_t stream);
 // Winners (beaten_by == 0) and the ranking from a filled beaten_by.
 int extract_from_beaten_by(schulze_ctx* ctx, const int32_t* beaten_by, int32_t m, int32_t* winners, int32_t* order,
                            void* ws, cudaStream_t stream);

@@ -482,3 +482,25 @@ def test_spotify_like_workload_full_size():
     order = host(out["order"])
     assert sorted(order.tolist()) == list(range(m))
     assert np.all(np.diff(bb[order]) >= 0)
+
+
+# ------------------------------------- top-k ranking by iterated removal
+
+@pytest.mark.parametrize("m,n,k,phi,k_top", [(9, 30, 9, 0.9, 9), (70, 400, 70, 0.95, 70), (130, 300, 20, 0.9, 130),
+                                             (700, 2000, 30, 0.9, 12), (300, 40, 300, 1.0, 25)])
+def test_ranking_iterated(m, n, k, phi, k_top):
+    r = W.mallows(m * 3 + n, n, m, k, phi, W.permutation(m + 5, m))
+    d = oracle.tally(r, m)
+    for margin in (False, True):
+        level, nl = S.schulze_ranking_iterated(cu(d), n, k_top, flags=S.F_MARGIN if margin else 0)
+        want, want_nl = oracle.ranking_iterated(d, k_top, margin)
+        eq(host(level), want, f"levels m={m} margin={margin}")
+        assert nl == want_nl
+
+
+def test_ranking_iterated_degenerate():
+    """No ballots: every candidate wins the first level. One candidate."""
+    level, nl = S.schulze_ranking_iterated(torch.zeros((5, 5), dtype=torch.int32, device="cuda"), 0, 3)
+    assert host(level).tolist() == [1] * 5 and nl == 1
+    level, nl = S.schulze_ranking_iterated(torch.zeros((1, 1), dtype=torch.int32, device="cuda"), 0)
+    assert host(level).tolist() == [1] and nl == 1
