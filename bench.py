@@ -40,6 +40,8 @@ WORKLOADS = {
                          "32 evaluation elections m=8192, n=20000, top-50, phi=0.9"),
     "spotify_like": dict(desc="m=18407, n=15553, top-200 Plackett-Luce Zipf(1.1): the shape of the paper's "
                               "largest Spotify profile, synthetic"),
+    "iterated_topk": dict(desc="top-10 ranking by iterated winner removal on the m=4096, n=20000, top-50 "
+                               "Mallows(0.9) election (tally first, outside the timed region)"),
     "weak_orders": dict(desc="m=1024, n=20000 weak orders in position form: Mallows(0.97) rankings cut into "
                              "tiers of 16 tied places; position-compare tally, closure, winners, ranking"),
 }
@@ -297,6 +299,72 @@ def run_weak(args, world, rank, local):
     return 0
 
 
+def run_iterated(args, world, rank, local):
+    """Top-10 levels by iterated winner removal from the default election's
+    tally: one step = one schulze_ranking_iterated call (host round trip per
+    level, so timed on the host around a synchronized call)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2505_12976_gb300 as S
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    e = W.large_topk(seed=W.SEED_BASE + 1 + 1000 * rank, **{k: v for k, v in (("m", args.m), ("n", args.n)) if v})
+    ctx = S.context(local)
+    d = S.schulze_tally(torch.from_numpy(e.ranks).to(dev), e.m, ctx=ctx)
+    flags = S.F_MARGIN if args.margin else 0
+    level = torch.empty(e.m, dtype=torch.int32, device=dev)
+    k_top = 10
+    for _ in range(args.warmup):
+        S.schulze_ranking_iterated(d, e.n, k_top, flags=flags, level=level, ctx=ctx)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    times, nl = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, nl = S.schulze_ranking_iterated(d, e.n, k_top, flags=flags, level=level, ctx=ctx)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clock_info = clocks.stop()
+    sec = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([sec], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    placed = int((level > 0).sum().item())
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ce = W.large_topk(seed=W.SEED_BASE + 77, m=1536)
+        dc = oracle.tally(ce.ranks, ce.m)
+        t0 = time.perf_counter()
+        oracle.ranking_iterated(dc, k_top, args.margin)
+        csec = time.perf_counter() - t0
+        cpu = {"value": float(ce.m) ** 3 / csec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"top-{k_top} iterated ranking of one m=1536 election of the same model in {csec:.2f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * float(e.m) ** 3 / sec, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
+                "config": {"workload": "iterated_topk", "detail": WORKLOADS["iterated_topk"]["desc"], "m": e.m,
+                           "n": e.n, "k": e.k, "k_top": k_top, "levels": nl, "placed": placed,
+                           "weights": "margin" if args.margin else "winning votes",
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "ms_per_level": sec * 1e3 / max(nl, 1), "roofline": None, "cpu_baseline": cpu,
+                "e2e": {"value": world * float(e.m) ** 3 / sec, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 4 * nl},
+                "timed_as": "host wall time of one synchronized call (device-resident tally)",
+                "device_status": ctx.status(), "clocks": clock_info}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_oracle_weak(pos, margin: bool, nthreads: int):
     """Wall time of the oracle's whole path on weak-order ballots."""
     import oracle
@@ -541,6 +609,8 @@ def main():
         return run_learned(args, world, rank, local)
     if args.workload == "weak_orders":
         return run_weak(args, world, rank, local)
+    if args.workload == "iterated_topk":
+        return run_iterated(args, world, rank, local)
     e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)
