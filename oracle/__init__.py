@@ -53,6 +53,8 @@ def _load():
             lib.oracle_validate.restype = ctypes.c_int
             lib.oracle_tally.argtypes = [i32p, i64, i32, i32, i32p]
             lib.oracle_tally.restype = ctypes.c_int
+            lib.oracle_winners_pregel.argtypes = [i32p, i32, i32p, i32p, i32p]
+            lib.oracle_winners_pregel.restype = ctypes.c_int
             lib.oracle_ranking_iterated.argtypes = [i32p, i32, i32, ctypes.c_int, i32p, i32p]
             lib.oracle_ranking_iterated.restype = ctypes.c_int
             lib.oracle_tally_positions.argtypes = [i32p, i64, i32, i32p]
@@ -230,3 +232,17 @@ def ranking_iterated(d, k_top: int | None = None, margin: bool = False):
     if rc:
         raise OracleError(rc)
     return level, int(nl[0])
+
+
+def winners_pregel(w):
+    """Winners by the paper's vertex-centric algorithm (Sect. 4, Alg. 1-4) on
+    edge weights w: (win [m] 0/1, while-loop iterations, propagation rounds)."""
+    w = _i32(w)
+    m = w.shape[0]
+    win = np.zeros(m, dtype=np.int32)
+    it = np.zeros(1, dtype=np.int32)
+    rd = np.zeros(1, dtype=np.int32)
+    rc = _load().oracle_winners_pregel(_p(w), m, _p(win), _p(it), _p(rd))
+    if rc:
+        raise OracleError(rc)
+    return win, int(it[0]), int(rd[0])

@@ -295,3 +295,125 @@ int oracle_ranking_iterated(const int32_t* d, int32_t m, int32_t k_top, int marg
   free(idx), free(sd), free(sw), free(sp), free(win);
   return ORACLE_OK;
 }
+
+/*
+ * Winners only, by the paper's vertex-centric algorithm (Sect. 4, Alg. 1-4),
+ * simulated with synchronous rounds. w: edge weights [m, m] (w > 0 is an
+ * edge). Ids are the candidate indices. Readings: a status, once decided,
+ * does not change (every mark below only turns 'unknown' into 'loser' or
+ * 'winner'); the optional zeroing of edges into dominated SCCs is left out
+ * (the graph stays as it is). win[c] = 1 for the winners; *iterations = the
+ * number of while-loop iterations, *rounds = propagation rounds in total.
+ * Returns ORACLE_EDATA if an iteration decides nothing (never expected).
+ */
+#define PREGEL_INF 0x7fffffff
+#define ST_UNKNOWN 0
+#define ST_LOSER 1
+#define ST_WINNER 2
+int oracle_winners_pregel(const int32_t* w, int32_t m, int32_t* win, int32_t* iterations, int32_t* rounds) {
+  if (m < 1 || !w || !win || !iterations || !rounds) return ORACLE_EINVAL;
+  int32_t* st = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * 8);
+  if (!st || !s) {
+    free(st), free(s);
+    return ORACLE_ENOMEM;
+  }
+  int32_t *ws = s + m, *t = s + 2 * m, *wt = s + 3 * m;
+  int32_t *ns = s + 4 * m, *nws = s + 5 * m, *nt = s + 6 * m, *nwt = s + 7 * m;
+  int32_t* lose = (int32_t*)calloc((size_t)m + 1, sizeof(int32_t)); /* loser marks */
+  int32_t* scc_lose = (int32_t*)calloc((size_t)m + 1, sizeof(int32_t)); /* SCC labels marked */
+  /* Initialisation-of-vertices: heaviest incoming edge above the heaviest
+   * outgoing one means some vertex beats c. */
+  for (int32_t c = 0; c < m; ++c) {
+    int32_t in = 0, out = 0;
+    for (int32_t a = 0; a < m; ++a) {
+      if (a == c) continue;
+      in = imax(in, w[(int64_t)a * m + c]);
+      out = imax(out, w[(int64_t)c * m + a]);
+    }
+    st[c] = in > out ? ST_LOSER : ST_UNKNOWN;
+  }
+  *iterations = 0, *rounds = 0;
+  int rc = ORACLE_OK;
+  for (;;) {
+    int32_t unknown = 0;
+    for (int32_t c = 0; c < m; ++c) unknown += st[c] == ST_UNKNOWN;
+    if (!unknown) break;
+    ++*iterations;
+    /* Preprocessing (Alg. 2) */
+    for (int32_t c = 0; c < m; ++c) {
+      if (st[c] == ST_UNKNOWN)
+        s[c] = t[c] = c, ws[c] = wt[c] = PREGEL_INF;
+      else
+        s[c] = t[c] = PREGEL_INF, ws[c] = wt[c] = 0;
+    }
+    /* Forward-Backward-Propagation (Alg. 3): a vertex keeps the smallest id
+     * it receives and, for that id, the widest width; rounds until nothing
+     * changes. Forward messages travel along edges (u, c), backward ones
+     * against them. */
+    for (;;) {
+      int changed = 0;
+      ++*rounds;
+      for (int32_t c = 0; c < m; ++c) {
+        int32_t bs = s[c], bw = ws[c], bt = t[c], bwt = wt[c];
+        for (int32_t u = 0; u < m; ++u) {
+          if (u == c) continue;
+          const int32_t win_uc = w[(int64_t)u * m + c], w_cu = w[(int64_t)c * m + u];
+          if (win_uc > 0 && s[u] != PREGEL_INF) {
+            const int32_t cw = imin(ws[u], win_uc);
+            if (s[u] < bs) bs = s[u], bw = cw;
+            else if (s[u] == bs) bw = imax(bw, cw);
+          }
+          if (w_cu > 0 && t[u] != PREGEL_INF) {
+            const int32_t cw = imin(wt[u], w_cu);
+            if (t[u] < bt) bt = t[u], bwt = cw;
+            else if (t[u] == bt) bwt = imax(bwt, cw);
+          }
+        }
+        ns[c] = bs, nws[c] = bw, nt[c] = bt, nwt[c] = bwt;
+        changed |= bs != s[c] || bw != ws[c] || bt != t[c] || bwt != wt[c];
+      }
+      for (int32_t c = 0; c < m; ++c) s[c] = ns[c], ws[c] = nws[c], t[c] = nt[c], wt[c] = nwt[c];
+      if (!changed) break;
+    }
+    /* Postprocessing (Alg. 4): collect the loser marks of every vertex, then
+     * apply them, then the winner rule. SCC labels are ids (or PREGEL_INF,
+     * mapped to slot m). */
+    memset(lose, 0, sizeof(int32_t) * ((size_t)m + 1));
+    memset(scc_lose, 0, sizeof(int32_t) * ((size_t)m + 1));
+    for (int32_t c = 0; c < m; ++c) {
+      if (s[c] < t[c]) {
+        lose[c] = 1;
+      } else if (s[c] > t[c]) {
+        lose[t[c]] = 1; /* t[c] is an id here: t < s <= PREGEL_INF */
+      } else if (s[c] != PREGEL_INF) {
+        if (ws[c] > wt[c]) lose[c] = 1;
+        else if (ws[c] < wt[c]) lose[s[c]] = 1;
+      }
+      for (int32_t v = 0; v < m; ++v) {
+        if (v == c || w[(int64_t)v * m + c] <= 0) continue;
+        if (s[c] != s[v] || t[c] != t[v]) {
+          if (s[c] == t[c])
+            scc_lose[s[c] == PREGEL_INF ? m : s[c]] = 1;
+          else
+            lose[c] = 1;
+        }
+      }
+    }
+    int32_t decided = 0;
+    for (int32_t c = 0; c < m; ++c) {
+      if (st[c] != ST_UNKNOWN) continue;
+      const int in_lost_scc = s[c] == t[c] && scc_lose[s[c] == PREGEL_INF ? m : s[c]];
+      if (lose[c] || in_lost_scc) st[c] = ST_LOSER, ++decided;
+    }
+    for (int32_t c = 0; c < m; ++c)
+      if (st[c] == ST_UNKNOWN && s[c] == c && t[c] == c) st[c] = ST_WINNER, ++decided;
+    if (!decided) {
+      rc = ORACLE_EDATA;
+      break;
+    }
+  }
+  for (int32_t c = 0; c < m; ++c) win[c] = st[c] == ST_WINNER;
+  free(st), free(s), free(lose), free(scc_lose);
+  return rc;
+}

@@ -22,6 +22,8 @@ MUTANTS = {
     "tally_unlisted_on_top": ("for (int32_t c = 0; c < m; ++c) pos[c] = k;",
                               "for (int32_t c = 0; c < m; ++c) pos[c] = -1;"),
     "weights_ties_are_edges": ("(i != j && a > b) ? a : 0", "(i != j && a >= b) ? a : 0"),
+    "pregel_no_width_merge": ("else if (s[u] == bs) bw = imax(bw, cw);", "else if (s[u] == bs) bw = bw;"),
+    "pregel_no_incoming_rule": ("if (s[c] != s[v] || t[c] != t[v]) {", "if (0) {"),
     "iterated_not_restricted": ("if (level[c] == 0) idx[r++] = c;", "idx[r++] = c;"),
     "iterated_level_off_by_one": ("if (win[a]) level[idx[a]] = t, ++placed;",
                                   "if (win[a]) level[idx[a]] = t + 1, ++placed;"),

@@ -438,3 +438,46 @@ def test_ranking_iterated_identical_voters_and_fig1():
     level, _ = oracle.ranking_iterated(oracle.tally(mcgarvey_ballots(mu), 4), 1)
     assert np.flatnonzero(level == 1).tolist() == win
     assert np.count_nonzero(level) == 1
+
+
+# ---------------------------- the paper's vertex-centric winners algorithm
+
+@pytest.mark.parametrize("seed", range(40))
+def test_pregel_winners_match_closure(seed):
+    """Alg. 1-4 (Sect. 4) find exactly the winners of the widest-path
+    definition (Sect. 2.1), on tallies (both edge weights) and on random
+    weighted digraphs with ties and 2-cycles; every while-loop iteration
+    decides at least one vertex."""
+    rs = np.random.Generator(np.random.PCG64(900 + seed))
+    m = int(rs.integers(1, 30))
+    r = W.mallows(900 + seed, int(rs.integers(1, 50)), m, int(rs.integers(1, m + 1)), 0.5 + 0.5 * rs.random(),
+                  W.permutation(seed, m))
+    d = oracle.tally(r, m)
+    g = rs.integers(1, int(rs.integers(1, 6)) + 1, size=(m, m)).astype(np.int32) * (rs.random((m, m)) < rs.random())
+    np.fill_diagonal(g, 0)
+    for w in (oracle.weights(d), oracle.weights_margin(d), g.astype(np.int32)):
+        win, it, _ = oracle.winners_pregel(w)
+        np.testing.assert_array_equal(win, oracle.winners(oracle.closure(w)))
+        assert it <= m
+
+
+def test_pregel_fig1_and_nl_family():
+    """Fig. 1: a alone, in one iteration. The NL-hardness family of Sect. 3:
+    a is the unique winner iff b is reachable from a."""
+    _, mu, _, win = fig1()
+    got, it, _ = oracle.winners_pregel(mu)
+    assert np.flatnonzero(got).tolist() == win and it == 1
+    for seed in range(30):
+        rs = np.random.Generator(np.random.PCG64(300 + seed))
+        nv = int(rs.integers(2, 7))
+        edges = random_digraph(rs, nv, float(rs.uniform(0.15, 0.6)))
+        a, b = (int(x) for x in rs.choice(nv, 2, replace=False))
+        mu = nl_reduction(nv, edges, a, b)
+        got, _, _ = oracle.winners_pregel(oracle.weights(mu))
+        adj = {}
+        for u, v in edges:
+            adj.setdefault(u, []).append(v)
+        if reachable(adj, a, b):
+            assert np.flatnonzero(got).tolist() == [a]
+        else:
+            assert got[a] == 0
