@@ -199,6 +199,23 @@ int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int6
                              int32_t* level, int32_t* levels, uint32_t flags, schulze_stream_t stream);
 
 /*
+ * Winners only, by the paper's vertex-centric algorithm (Sect. 4, Alg. 1-4:
+ * initial loser filter, then while some candidate is undecided: forward and
+ * backward propagation of the smallest source / target id with the widest
+ * width, and the SCC rules of the postprocessing), restated on the dense
+ * tally. The same winner set as schulze_winners on the closure; provided as
+ * a comparator for the paper's own method.
+ *   d        [m, m] int32 device tally (read only); flags: 0 or
+ *            SCHULZE_F_MARGIN (edge weights as in schulze_strongest_paths).
+ *   winners  [m] int32 device output, 1 for a winner.
+ *   stats    host int32 [2], may be NULL: while-loop iterations, propagation
+ *            rounds in total.
+ * Synchronous on `stream` (host round trips per round; not for capture).
+ */
+int schulze_winners_propagation(schulze_ctx* ctx, const int32_t* d, int32_t m, uint32_t flags, int32_t* winners,
+                                int32_t* stats, schulze_stream_t stream);
+
+/*
  * The whole path for one election: tally, widest paths, winners and ranking
  * in one call (device buffers). d and p are written as by the calls above;
  * winners, order and beaten_by may each be NULL. `flags` combines the tally

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("schulze_tally", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _u32, _vp]),
     ("schulze_tally_positions", _c.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("schulze_ranking_iterated", _c.c_int, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _u32, _vp]),
+    ("schulze_winners_propagation", _c.c_int, [_vp, _vp, _i32, _u32, _vp, _vp, _vp]),
     ("schulze_strongest_paths", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _u32, _vp]),
     ("schulze_winners", _c.c_int, [_vp, _vp, _i32, _vp, _vp]),
     ("schulze_ranking", _c.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
@@ -310,6 +311,21 @@ def schulze_ranking_iterated(d: torch.Tensor, bound: int, k_top: int | None = No
                                            _ptr(level), _c.byref(nl), flags, _stream(stream, ctx.device)),
            "schulze_ranking_iterated")
     return level, int(nl.value)
+
+
+def schulze_winners_propagation(d: torch.Tensor, flags: int = 0, winners: torch.Tensor | None = None,
+                                ctx: Context | None = None, stream=None):
+    """Winners by the paper's vertex-centric algorithm (Alg. 1-4) on the
+    tally: (winners int32 [m] on the GPU, [iterations, rounds])."""
+    d = _dev_i32(d, "d")
+    m = d.shape[0]
+    _dev_i32(d, "d", (m, m))
+    ctx = ctx or context(d.device)
+    winners = _out(winners, (m,), d.device, "winners")
+    stats = (_i32 * 2)()
+    _check(load().schulze_winners_propagation(ctx.handle, _ptr(d), m, flags, _ptr(winners), stats,
+                                              _stream(stream, ctx.device)), "schulze_winners_propagation")
+    return winners, list(stats)
 
 
 NPARAM = 5313  # MLP parameters: W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64], b3

@@ -213,6 +213,15 @@ int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int6
   return SCHULZE_OK;
 }
 
+int schulze_winners_propagation(schulze_ctx* ctx, const int32_t* d, int32_t m, uint32_t flags, int32_t* winners,
+                                int32_t* stats, schulze_stream_t stream) {
+  if (!ctx || !d || !winners || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  if (int rc = ensure_workspace(ctx, propagation_workspace_bytes(m), stream)) return rc;
+  return winners_propagation_launch(ctx, d, m, (flags & SCHULZE_F_MARGIN) != 0, winners, stats, ctx->ws.base,
+                                    stream);
+}
+
 int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d, int32_t* p,
                 int32_t* winners, int32_t* order, int32_t* beaten_by, uint32_t flags, schulze_stream_t stream) {
   if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 ||

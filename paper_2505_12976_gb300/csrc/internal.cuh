@@ -106,6 +106,11 @@ int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound,
                    const int32_t* hint_valid = nullptr);
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream);
+// Winners by the paper's vertex-centric algorithm on the dense tally;
+// stats (host, may be null): [0] while-loop iterations, [1] rounds.
+size_t propagation_workspace_bytes(int32_t m);
+int winners_propagation_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, bool margin, int32_t* winners,
+                               int32_t* stats, void* ws, cudaStream_t stream);
 // One level of the iterated-removal ranking: candidates with level 0 and
 // beaten_by 0 get level t (listed in placed[1..], counted in placed[0]) and
 // are isolated in the working tally dw.

@@ -504,3 +504,34 @@ def test_ranking_iterated_degenerate():
     assert host(level).tolist() == [1] * 5 and nl == 1
     level, nl = S.schulze_ranking_iterated(torch.zeros((1, 1), dtype=torch.int32, device="cuda"), 0)
     assert host(level).tolist() == [1] and nl == 1
+
+
+# ---------------------- the paper's vertex-centric algorithm (Alg. 1-4)
+
+@pytest.mark.parametrize("m,n,k,phi", [(1, 3, 1, 1.0), (2, 5, 2, 0.5), (33, 200, 10, 0.9), (130, 400, 130, 0.97),
+                                       (700, 2000, 30, 0.9), (300, 50, 300, 1.0)])
+def test_winners_propagation_elections(m, n, k, phi):
+    """Same winners as the closure, and the same while-loop iterations and
+    propagation rounds as the oracle's synchronous simulation."""
+    r = W.mallows(m + 2 * n, n, m, k, phi, W.permutation(m + 9, m))
+    d = oracle.tally(r, m)
+    for margin in (False, True):
+        w = oracle.weights_margin(d) if margin else oracle.weights(d)
+        win, stats = S.schulze_winners_propagation(cu(d), flags=S.F_MARGIN if margin else 0)
+        eq(host(win), oracle.winners(oracle.closure(w, nthreads=8)), f"winners m={m} margin={margin}")
+        _, it, rounds = oracle.winners_pregel(w)
+        assert stats == [it, rounds]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_winners_propagation_random_weights(seed):
+    """Arbitrary count matrices with many ties and 2-cycles."""
+    rs = np.random.Generator(np.random.PCG64(4000 + seed))
+    m = int(rs.integers(20, 200))
+    d = rs.integers(0, 6, size=(m, m)).astype(np.int32) * (rs.random((m, m)) < rs.random())
+    np.fill_diagonal(d, 0)
+    win, stats = S.schulze_winners_propagation(cu(d.astype(np.int32)))
+    w = oracle.weights(d)
+    eq(host(win), oracle.winners(oracle.closure(w, nthreads=8)), "winners")
+    _, it, rounds = oracle.winners_pregel(w)
+    assert stats == [it, rounds]
