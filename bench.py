@@ -42,6 +42,8 @@ WORKLOADS = {
                               "largest Spotify profile, synthetic"),
     "iterated_topk": dict(desc="top-10 ranking by iterated winner removal on the m=4096, n=20000, top-50 "
                                "Mallows(0.9) election (tally first, outside the timed region)"),
+    "propagation": dict(desc="winners from the tally by the paper's Alg. 1-4 restated on the GPU, against "
+                             "the closure + winners, on the default election and the Spotify-shaped one"),
     "weak_orders": dict(desc="m=1024, n=20000 weak orders in position form: Mallows(0.97) rankings cut into "
                              "tiers of 16 tied places; position-compare tally, closure, winners, ranking"),
 }
@@ -365,6 +367,71 @@ def run_iterated(args, world, rank, local):
     return 0
 
 
+def run_propagation(args, world, rank, local):
+    """Winners only, from a device-resident tally: the paper's vertex-centric
+    algorithm (schulze_winners_propagation) against the closure path
+    (schulze_strongest_paths + schulze_winners), on the default top-k
+    election and on the Spotify-shaped one; winner sets compared."""
+    import torch
+    import paper_2505_12976_gb300 as S
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    ctx = S.context(local)
+    flags = S.F_MARGIN if args.margin else 0
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    rows = {}
+    for name, e in (("large_topk", W.large_topk(seed=W.SEED_BASE + 1 + 1000 * rank)),
+                    ("spotify_like", W.spotify_like(seed=W.SEED_BASE + 8 + 1000 * rank))):
+        d = S.schulze_tally(torch.from_numpy(e.ranks).to(dev), e.m, ctx=ctx)
+        p = torch.empty_like(d)
+        win_c = torch.empty(e.m, dtype=torch.int32, device=dev)
+        win_p = torch.empty(e.m, dtype=torch.int32, device=dev)
+
+        def closure():
+            S.schulze_strongest_paths(d, e.n, p=p, flags=flags, ctx=ctx)
+            S.schulze_winners(p, winners=win_c, ctx=ctx)
+
+        def propagation():
+            return S.schulze_winners_propagation(d, flags=flags, winners=win_p, ctx=ctx)[1]
+
+        def timed(fn, steps):
+            out, ts = None, []
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                out = fn()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            return sum(ts) / len(ts), out
+
+        steps = max(1, min(args.steps, 5 if e.m > 8192 else args.steps))
+        closure(), propagation()
+        tc, _ = timed(closure, steps)
+        tp, stats = timed(propagation, steps)
+        rows[name] = {"m": e.m, "n": e.n, "k": e.k, "closure_ms": tc * 1e3, "propagation_ms": tp * 1e3,
+                      "iterations": stats[0], "rounds": stats[1], "same_winners": bool(torch.equal(win_c, win_p)),
+                      "winners": int(win_c.sum().item())}
+    if rank == 0:
+        main_row = rows["large_topk"]
+        line = {"metric": METRIC + " (winners only: the paper's Alg. 1-4 restated on the GPU)",
+                "value": world * 1e3 / main_row["propagation_ms"], "unit": "elections/s", "n_gpus": world,
+                "steps": args.steps, "warmup": 1, "ms_per_step": main_row["propagation_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": "propagation", "detail": WORKLOADS["propagation"]["desc"],
+                           "weights": "margin" if args.margin else "winning votes",
+                           "l2": "flushed (512 MiB write) before every timed call"},
+                "comparison": rows, "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": world * 1e3 / main_row["propagation_ms"], "unit": "elections/s",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "timed_as": "host wall time of synchronized calls on a device-resident tally",
+                "device_status": ctx.status()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_oracle_weak(pos, margin: bool, nthreads: int):
     """Wall time of the oracle's whole path on weak-order ballots."""
     import oracle
@@ -611,6 +678,8 @@ def main():
         return run_weak(args, world, rank, local)
     if args.workload == "iterated_topk":
         return run_iterated(args, world, rank, local)
+    if args.workload == "propagation":
+        return run_propagation(args, world, rank, local)
     e = make_election(args.workload, rank, args.m, args.n)
     n, k, m = e.n, e.k, e.m
     ranks_d = torch.from_numpy(e.ranks).to(dev)
