@@ -534,7 +534,32 @@ struct CTile;
 template <>
 struct CTile<int16_t> {
   using Word = uint32_t;
+  using Pair = uint2;  // two consecutive Words of a row
   static __device__ __forceinline__ uint32_t dup(uint32_t h) { return (h & 0xFFFFu) | (h << 16); }
+  static __device__ __forceinline__ Pair zero() { return make_uint2(0u, 0u); }
+  static __device__ __forceinline__ Pair pmax(Pair a, Pair b) {
+    return make_uint2(__vmaxs2(a.x, b.x), __vmaxs2(a.y, b.y));
+  }
+  // acc = max(acc, S(ti, tr) (x) S(tr, tj)) over the pivot entries k0 ..
+  // k0 + 7 for rows 2 rp + {0, 1}, Words 2 cp + {0, 1} of the tile
+  static __device__ __forceinline__ void product8(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
+                                                  int rp, int cp, int k0, Pair (&acc)[2]) {
+    const uint4 a0 = *reinterpret_cast<const uint4*>(S + (ti * nt + tr) * 512 + (2 * rp) * 16 + k0 / 2);
+    const uint4 a1 = *reinterpret_cast<const uint4*>(S + (ti * nt + tr) * 512 + (2 * rp + 1) * 16 + k0 / 2);
+    const uint2* bp = reinterpret_cast<const uint2*>(S + (tr * nt + tj) * 512) + cp;  // row k at bp[8 k]
+    const uint32_t w0[4] = {a0.x, a0.y, a0.z, a0.w}, w1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int k = k0 + 2 * w;
+      const uint2 b0 = bp[8 * k], b1 = bp[8 * (k + 1)];
+      const uint32_t l0 = __byte_perm(w0[w], 0, 0x1010), h0 = __byte_perm(w0[w], 0, 0x3232);
+      const uint32_t l1 = __byte_perm(w1[w], 0, 0x1010), h1 = __byte_perm(w1[w], 0, 0x3232);
+      acc[0].x = __vimax3_s16x2(acc[0].x, __vmins2(l0, b0.x), __vmins2(h0, b1.x));
+      acc[0].y = __vimax3_s16x2(acc[0].y, __vmins2(l0, b0.y), __vmins2(h0, b1.y));
+      acc[1].x = __vimax3_s16x2(acc[1].x, __vmins2(l1, b0.x), __vmins2(h1, b1.x));
+      acc[1].y = __vimax3_s16x2(acc[1].y, __vmins2(l1, b0.y), __vmins2(h1, b1.y));
+    }
+  }
   // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): the new word of thread t
   static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
                                                  int t) {
@@ -573,6 +598,35 @@ struct CTile<int16_t> {
 template <>
 struct CTile<int32_t> {
   using Word = int2;
+  using Pair = int4;
+  static __device__ __forceinline__ Pair zero() { return make_int4(0, 0, 0, 0); }
+  static __device__ __forceinline__ Pair pmax(Pair a, Pair b) {
+    return make_int4(max(a.x, b.x), max(a.y, b.y), max(a.z, b.z), max(a.w, b.w));
+  }
+  static __device__ __forceinline__ void product8(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
+                                                  int rp, int cp, int k0, Pair (&acc)[2]) {
+    const int4* a0p = reinterpret_cast<const int4*>(S + (ti * nt + tr) * 512 + (2 * rp) * 16 + k0 / 2);
+    const int4* a1p = reinterpret_cast<const int4*>(S + (ti * nt + tr) * 512 + (2 * rp + 1) * 16 + k0 / 2);
+    const int4* bp = reinterpret_cast<const int4*>(S + (tr * nt + tj) * 512) + cp;  // row k at bp[8 k]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int4 a0 = a0p[h], a1 = a1p[h];  // entries k0 + 4 h .. + 3 of the two rows
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int k = k0 + 4 * h + 2 * w;
+        const int4 b0 = bp[8 * k], b1 = bp[8 * (k + 1)];
+        const int32_t e0 = w ? a0.z : a0.x, f0 = w ? a0.w : a0.y, e1 = w ? a1.z : a1.x, f1 = w ? a1.w : a1.y;
+        acc[0].x = __vimax3_s32(acc[0].x, min(e0, b0.x), min(f0, b1.x));
+        acc[0].y = __vimax3_s32(acc[0].y, min(e0, b0.y), min(f0, b1.y));
+        acc[0].z = __vimax3_s32(acc[0].z, min(e0, b0.z), min(f0, b1.z));
+        acc[0].w = __vimax3_s32(acc[0].w, min(e0, b0.w), min(f0, b1.w));
+        acc[1].x = __vimax3_s32(acc[1].x, min(e1, b0.x), min(f1, b1.x));
+        acc[1].y = __vimax3_s32(acc[1].y, min(e1, b0.y), min(f1, b1.y));
+        acc[1].z = __vimax3_s32(acc[1].z, min(e1, b0.z), min(f1, b1.z));
+        acc[1].w = __vimax3_s32(acc[1].w, min(e1, b0.w), min(f1, b1.w));
+      }
+    }
+  }
   static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
                                                  int t) {
     const Word* arow = S + (ti * nt + tr) * 512 + (t >> 4) * 16;
@@ -625,7 +679,6 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   const int t = threadIdx.x;
   const unsigned q = cl.block_rank();
   constexpr int kPer16 = 16 / sizeof(E);       // entries per 16-byte piece
-  constexpr int kChunks = kCB * kCB / kPer16;  // 16-byte pieces per tile
   // element (i, j) of S lives at tile (i / 32, j / 32), row i % 32, column j % 32
   auto at = [&](int32_t i, int32_t j) { return ((i / kCB) * nt + j / kCB) * (kCB * kCB) + (i % kCB) * kCB + j % kCB; };
   for (int32_t e = t; e < n * (n / kPer16); e += blockDim.x) {
@@ -634,18 +687,46 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   }
   if (t < 16) tnz[t >> 2][t & 3] = 0u;
   cl.sync();  // every copy loaded before any remote write
-  uint4* remote[kClusterCtas];
+  using Pair = typename T::Pair;
+  Pair* rpair[kClusterCtas];
 #pragma unroll
-  for (int c = 0; c < kClusterCtas; ++c) remote[c] = reinterpret_cast<uint4*>(cl.map_shared_rank(S, c));
-  // tile (ti, tj) is final in this CTA's copy: copy it into the others
-  auto broadcast = [&](int32_t tile) {
-    if (t < kChunks) {
-      const int32_t off = tile * kChunks + t;
-      const uint4 v = reinterpret_cast<const uint4*>(S)[off];
-#pragma unroll
-      for (int c = 0; c < kClusterCtas; ++c)
-        if (c != int(q)) remote[c][off] = v;
+  for (int c = 0; c < kClusterCtas; ++c) rpair[c] = reinterpret_cast<Pair*>(cl.map_shared_rank(S, c));
+  Pair* lpair = reinterpret_cast<Pair*>(S);
+  // partial products of slots 1..3, two buffers used by alternate tiles
+  Pair* part = reinterpret_cast<Pair*>(cluster_smem + size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E));
+  const int slot = t >> 7, st = t & 127, rp = st >> 3, cp = st & 7;
+  int buf = 0;
+  // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): slot s takes pivot entries
+  // 8 s .. 8 s + 7 for its 2 x 2 Words, slot 0 combines the four partial
+  // maxima after one barrier (every read of the operands is done by then, so
+  // X may be one of them) and writes X, here and, with bcast, in every copy.
+  auto update = [&](int32_t ti, int32_t tj, int32_t tr, bool bcast) {
+    const int32_t tile = ti * nt + tj;
+    const int32_t i0 = (tile * 512 + (2 * rp) * 16) / 2 + cp, i1 = i0 + 8;  // Pair indices of the two rows
+    Pair acc[2];
+    if (slot == 0) {
+      acc[0] = lpair[i0], acc[1] = lpair[i1];
+    } else {
+      acc[0] = acc[1] = T::zero();
     }
+    T::product8(S, nt, ti, tj, tr, rp, cp, 8 * slot, acc);
+    Pair* pb = part + buf * (3 * 256);
+    if (slot > 0) pb[(slot - 1) * 256 + 2 * st] = acc[0], pb[(slot - 1) * 256 + 2 * st + 1] = acc[1];
+    __syncthreads();
+    if (slot == 0) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        acc[0] = T::pmax(acc[0], pb[u * 256 + 2 * st]);
+        acc[1] = T::pmax(acc[1], pb[u * 256 + 2 * st + 1]);
+      }
+      lpair[i0] = acc[0], lpair[i1] = acc[1];
+      if (bcast) {
+#pragma unroll
+        for (int c = 0; c < kClusterCtas; ++c)
+          if (c != int(q)) rpair[c][i0] = acc[0], rpair[c][i1] = acc[1];
+      }
+    }
+    buf ^= 1;
   };
   unsigned long long ops = 0;
   for (int32_t r = 0; r < ntw; ++r) {
@@ -659,11 +740,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
         tj = p + (p >= r);
       else
         ti = (p - (nt - 1)) + ((p - (nt - 1)) >= r);
-      const Word v = T::product(S, nt, ti, tj, r, t);
-      __syncthreads();  // the tile is its own operand: read it all before writing
-      S[(ti * nt + tj) * 512 + t] = v;
-      __syncthreads();
-      broadcast(ti * nt + tj);
+      update(ti, tj, r, true);
       ++ops;
     }
     cl.sync();
@@ -671,10 +748,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     const int32_t nr = (ntw - 1) * (nt - 1);
     for (int32_t p = q; p < nr; p += kClusterCtas) {
       const int32_t a = p / (nt - 1), b = p % (nt - 1);
-      const int32_t ti = a + (a >= r), tj = b + (b >= r);
-      S[(ti * nt + tj) * 512 + t] = T::product(S, nt, ti, tj, r, t);  // operands are other tiles
-      __syncthreads();
-      broadcast(ti * nt + tj);
+      update(a + (a >= r), b + (b >= r), r, true);  // operands are panels
       ++ops;
     }
     cl.sync();
@@ -946,7 +1020,8 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   }
   if (int rc = check_launch()) return rc;
   {
-    const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E);
+    const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E) +
+                        2 * 3 * 256 * sizeof(typename CTile<E>::Pair);
     cudaFuncSetAttribute(closure_cluster_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     Launch L(ctx, stream, "closure_cluster", 0.0);
     closure_cluster_kernel<E><<<kClusterCtas, kClusterThreads, smem, stream>>>(W, mp, nb, bf.warm, bf.prog,
