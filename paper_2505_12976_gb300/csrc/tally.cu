@@ -544,7 +544,65 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
     const int64_t vper = (n + gridDim.x - 1) / gridDim.x;
     const int64_t v0 = min(n, int64_t(blockIdx.x) * vper), v1 = min(n, v0 + vper);
     const int cw = wib - kFillWarps;  // counting warp
-    {
+    if (k <= 64) {
+      // Ballots of at most 64 positions: the slots stay in registers (p =
+      // lane, lane + 32) and the next ballot's ids are loaded while this one
+      // is counted.
+      const int ncw = nwarp - kFillWarps;
+      constexpr uint32_t kAll = 0xFFFFFFFFu;
+      auto slot_of = [&](int32_t c) -> uint32_t {
+        const int32_t sc = (c >= 0 && c < m) ? slot[c] : -1;
+        return sc < 0 ? uint32_t(kNoSlot) : uint32_t(sc);
+      };
+      const int32_t qlo = min(k, 32), qhi = k;
+      // two ballots ahead: ids of ballot v + 2 ncw in flight, slots of
+      // ballot v + ncw being gathered, while ballot v is counted
+      auto ids = [&](int64_t u, int32_t& a, int32_t& b) {
+        a = (u < v1 && lane < k) ? ranks[u * k + lane] : -1;
+        b = (u < v1 && lane + 32 < k) ? ranks[u * k + lane + 32] : -1;
+      };
+      int64_t v = v0 + cw;
+      int32_t c0, c1, n0, n1;
+      ids(v, c0, c1);
+      ids(v + ncw, n0, n1);
+      uint32_t s0 = lane < k ? slot_of(c0) : uint32_t(kNoSlot);
+      uint32_t s1 = lane + 32 < k ? slot_of(c1) : uint32_t(kNoSlot);
+      for (; v < v1; v += ncw) {
+        const uint32_t r0 = s0, r1 = s1;
+        s0 = lane < k ? slot_of(n0) : uint32_t(kNoSlot);
+        s1 = lane + 32 < k ? slot_of(n1) : uint32_t(kNoSlot);
+        ids(v + 2 * ncw, n0, n1);
+        const bool clean = (lane >= k || r0 != kNoSlot) && (lane + 32 >= k || r1 != kNoSlot);
+        if (__all_sync(kAll, clean)) {  // every id valid (the usual case): no per-entry checks
+          const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
+          const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+#pragma unroll 4
+          for (int32_t q = 1; q < qlo; ++q) {
+            const uint32_t sq = __shfl_sync(kAll, r0, q);
+            if (lane < q) atomicAdd(C + int32_t(sq) * wpr + w0, i0);
+          }
+#pragma unroll 4
+          for (int32_t q = 32; q < qhi; ++q) {
+            uint32_t* crow = C + int32_t(__shfl_sync(kAll, r1, q - 32)) * wpr;
+            atomicAdd(crow + w0, i0);
+            if (lane + 32 < q) atomicAdd(crow + w1, i1);
+          }
+          continue;
+        }
+        for (int32_t q = 1; q < qlo; ++q) {  // rows 1..31: lanes p < q
+          const uint32_t sq = __shfl_sync(kAll, r0, q);
+          if (sq == kNoSlot) continue;  // uniform over the warp
+          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0);
+        }
+        for (int32_t q = 32; q < qhi; ++q) {  // rows 32..63: all low lanes, high lanes p < q
+          const uint32_t sq = __shfl_sync(kAll, r1, q - 32);
+          if (sq == kNoSlot) continue;
+          uint32_t* crow = C + int32_t(sq) * wpr;
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
+          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+        }
+      }
+    } else {
       uint16_t* st = stage + cw * stage_len;
       const int ncw = nwarp - kFillWarps;
       for (int64_t v = v0 + cw; v < v1; v += ncw) {

@@ -108,6 +108,17 @@ def test_tally_compact_and_grouped_agree(m, n, k, phi):
         eq(host(S.schulze_tally(cu(r), m, flags=flags)), want, f"tally flags={flags}")
 
 
+@pytest.mark.parametrize("k", [1, 2, 16, 31, 32, 33, 47, 63, 64, 65])
+def test_tally_compact_ballot_lengths(k):
+    """The compact pair count packs the rows of each ballot's triangles two
+    to an atomic (p < q < 32 and 32 <= p < q): every ballot length around
+    those edges, against the oracle."""
+    m, n = 220, 1500
+    r = W.mallows(900 + k, n, m, k, 0.9, W.permutation(901 + k, m))
+    assert len(np.unique(r)) <= 256
+    eq(host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE)), oracle.tally(r, m), f"k={k}")
+
+
 def test_tally_compact_wide_counters():
     """More ballots per slice than 16-bit counters hold: the compact pair
     count switches to 32-bit counters. Sampled entries against the
