@@ -16,8 +16,9 @@
 // first. The closure has two parts:
 //   * the warm square (nw x nw): paths between warm candidates never pass a
 //     cold one (no outgoing edges), so it is the closure of W restricted to
-//     them: one CTA for up to kSmallTiles tile rows, else the persistent
-//     kernel below;
+//     them: repeated squaring on one thread-block cluster for up to
+//     kClusterMaxWarm warm candidates, else the persistent blocked
+//     Floyd-Warshall kernel below;
 //   * the cold columns: p[i][c] = max(w[i][c], max_x min(p[i][x], w[x][c]))
 //     over warm x, one (max, min) product with the closed warm square.
 //
@@ -28,7 +29,7 @@
 // product then reduces to one column u[i] = max(w[i][c], max_x min(p[i][x],
 // w[x][c])), which p, W's cold columns and beaten_by take from there.
 //
-// The warm-square closure runs in rounds of B = 64 candidates; round r
+// The persistent warm-square closure runs in rounds of B = 64 candidates; round r
 //   1. closes the diagonal tile (r, r) by plain Floyd-Warshall,
 //   2. updates the row and column panels: X = max(X, D (x) X) / max(X, X (x) D)
 //      with D the closed diagonal tile,
@@ -505,270 +506,155 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
   }
 }
 
-// Warm squares of at most kClusterMaxWarm candidates: blocked Floyd-Warshall
-// with 32 x 32 tiles on a cluster of kClusterCtas CTAs (one per SM). Every
-// CTA holds a copy of the whole square S (n = nw rounded up to 64, so that it
-// covers whole 64-wide tiles of W) in shared memory, stored tile by tile
-// (each 32 x 32 tile contiguous). Round r:
-//   1. every CTA closes the diagonal tile (r, r) of its own copy (one warp,
-//      the tile in registers; the same result everywhere);
-//   2. the panel tiles (r, j) and (i, r) are dealt out among the CTAs; each
-//      updates its tiles and copies them into every other copy (distributed
-//      shared memory, 16 bytes per store); cluster barrier;
-//   3. the other tiles likewise; cluster barrier.
-// A tile is written by one CTA per phase and read by no other CTA in that
-// phase, so the copies stay identical. Rows of cold candidates are zero, so
-// rounds and tile rows stop at the warm ones; columns run over all of S.
-// CTA q then writes tiles q, q + kClusterCtas, ... back into W and sets the
-// nonzero bits of the 64 x 64 tiles of W for cold_product_kernel.
-constexpr int kCB = 32;               // tile size of the cluster closure
+// Warm squares of at most kClusterMaxWarm candidates: the closure by
+// repeated (max, min) squaring, in place, on a cluster of kClusterCtas CTAs
+// (one per SM). Every CTA holds a copy of the square S (n = nw rounded up to
+// 64, row-major) in shared memory; CTA q owns the warm rows q, q + 8, ... A
+// sweep sets, for every owned row i and column j,
+//   S[i][j] = max(S[i][j], max_{k < nw} min(S[i][k], S[k][j])),
+// reading whatever the copy holds: widths only grow and every value is the
+// width of a real path, so a mix of older and newer entries is still a lower
+// bound of the closure. Each changed 16-byte piece is copied into the other
+// CTAs (distributed shared memory). Sweep t covers at least the paths of up
+// to 2^t edges, so at most ceil(log2 nw) + 1 sweeps run: the cluster stops
+// after the first sweep in which no CTA changed anything, when S (x) S <= S
+// held for the whole square, i.e. S is closed. Rows of cold candidates are
+// zero and stay zero; columns run over all of S. Each CTA then writes its
+// rows back into W and sets the nonzero bits of the 64 x 64 tiles of W for
+// cold_product_kernel.
 constexpr int kClusterCtas = 8;
-constexpr int kClusterThreads = 512;  // one 16-bit pair (or two int32 entries) of a tile per thread
+constexpr int kClusterThreads = 512;
+constexpr int kMaxSweeps = 40;  // > ceil(log2 256) + 1: never reached
 
-// Thread t of a 32 x 32 tile owns row t / 16, entries 2 (t % 16) and
-// 2 (t % 16) + 1: one 32-bit word of 16-bit lanes, or two int32 entries
-// (a Word). Tiles are contiguous: tile (ti, tj) of the nt x nt grid starts
-// at Word (ti * nt + tj) * 512.
-template <typename E>
-struct CTile;
-template <>
-struct CTile<int16_t> {
-  using Word = uint32_t;
-  using Pair = uint2;  // two consecutive Words of a row
-  static __device__ __forceinline__ uint32_t dup(uint32_t h) { return (h & 0xFFFFu) | (h << 16); }
-  static __device__ __forceinline__ Pair zero() { return make_uint2(0u, 0u); }
-  static __device__ __forceinline__ Pair pmax(Pair a, Pair b) {
-    return make_uint2(__vmaxs2(a.x, b.x), __vmaxs2(a.y, b.y));
-  }
-  // acc = max(acc, S(ti, tr) (x) S(tr, tj)) over the pivot entries k0 ..
-  // k0 + 7 for rows 2 rp + {0, 1}, Words 2 cp + {0, 1} of the tile
-  static __device__ __forceinline__ void product8(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
-                                                  int rp, int cp, int k0, Pair (&acc)[2]) {
-    const uint4 a0 = *reinterpret_cast<const uint4*>(S + (ti * nt + tr) * 512 + (2 * rp) * 16 + k0 / 2);
-    const uint4 a1 = *reinterpret_cast<const uint4*>(S + (ti * nt + tr) * 512 + (2 * rp + 1) * 16 + k0 / 2);
-    const uint2* bp = reinterpret_cast<const uint2*>(S + (tr * nt + tj) * 512) + cp;  // row k at bp[8 k]
-    const uint32_t w0[4] = {a0.x, a0.y, a0.z, a0.w}, w1[4] = {a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const int k = k0 + 2 * w;
-      const uint2 b0 = bp[8 * k], b1 = bp[8 * (k + 1)];
-      const uint32_t l0 = __byte_perm(w0[w], 0, 0x1010), h0 = __byte_perm(w0[w], 0, 0x3232);
-      const uint32_t l1 = __byte_perm(w1[w], 0, 0x1010), h1 = __byte_perm(w1[w], 0, 0x3232);
-      acc[0].x = __vimax3_s16x2(acc[0].x, __vmins2(l0, b0.x), __vmins2(h0, b1.x));
-      acc[0].y = __vimax3_s16x2(acc[0].y, __vmins2(l0, b0.y), __vmins2(h0, b1.y));
-      acc[1].x = __vimax3_s16x2(acc[1].x, __vmins2(l1, b0.x), __vmins2(h1, b1.x));
-      acc[1].y = __vimax3_s16x2(acc[1].y, __vmins2(l1, b0.y), __vmins2(h1, b1.y));
-    }
-  }
-  // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): the new word of thread t
-  static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
-                                                 int t) {
-    const Word* arow = S + (ti * nt + tr) * 512 + (t >> 4) * 16;
-    const Word* bcol = S + (tr * nt + tj) * 512 + (t & 15);
-    uint32_t acc = S[(ti * nt + tj) * 512 + t];
-#pragma unroll 4
-    for (int kk = 0; kk < kCB; kk += 2) {
-      const uint32_t a = arow[kk >> 1];
-      const uint32_t b0 = bcol[kk * 16], b1 = bcol[(kk + 1) * 16];
-      acc = __vimax3_s16x2(acc, __vmins2(dup(a), b0), __vmins2(dup(a >> 16), b1));
-    }
-    return acc;
-  }
-  // Floyd-Warshall of diagonal tile (r, r) by one warp: lane i keeps row i
-  // (16 words) in registers, row k comes by shuffles from lane k. Row k and
-  // column k do not change in step k.
-  static __device__ __forceinline__ void diag_warp(Word* S, int32_t nt, int32_t r, int lane) {
-    uint4* row = reinterpret_cast<uint4*>(S + (r * nt + r) * 512 + lane * 16);
-    uint32_t v[16];
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) {
-      const uint4 x = row[q4];
-      v[4 * q4] = x.x, v[4 * q4 + 1] = x.y, v[4 * q4 + 2] = x.z, v[4 * q4 + 3] = x.w;
-    }
-#pragma unroll
-    for (int k = 0; k < kCB; ++k) {
-      const uint32_t a = dup((k & 1) ? v[k >> 1] >> 16 : v[k >> 1]);
-#pragma unroll
-      for (int w = 0; w < 16; ++w) v[w] = __vmaxs2(v[w], __vmins2(a, __shfl_sync(0xFFFFFFFFu, v[w], k)));
-    }
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) row[q4] = make_uint4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
-  }
-};
-template <>
-struct CTile<int32_t> {
-  using Word = int2;
-  using Pair = int4;
-  static __device__ __forceinline__ Pair zero() { return make_int4(0, 0, 0, 0); }
-  static __device__ __forceinline__ Pair pmax(Pair a, Pair b) {
-    return make_int4(max(a.x, b.x), max(a.y, b.y), max(a.z, b.z), max(a.w, b.w));
-  }
-  static __device__ __forceinline__ void product8(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
-                                                  int rp, int cp, int k0, Pair (&acc)[2]) {
-    const int4* a0p = reinterpret_cast<const int4*>(S + (ti * nt + tr) * 512 + (2 * rp) * 16 + k0 / 2);
-    const int4* a1p = reinterpret_cast<const int4*>(S + (ti * nt + tr) * 512 + (2 * rp + 1) * 16 + k0 / 2);
-    const int4* bp = reinterpret_cast<const int4*>(S + (tr * nt + tj) * 512) + cp;  // row k at bp[8 k]
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int4 a0 = a0p[h], a1 = a1p[h];  // entries k0 + 4 h .. + 3 of the two rows
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const int k = k0 + 4 * h + 2 * w;
-        const int4 b0 = bp[8 * k], b1 = bp[8 * (k + 1)];
-        const int32_t e0 = w ? a0.z : a0.x, f0 = w ? a0.w : a0.y, e1 = w ? a1.z : a1.x, f1 = w ? a1.w : a1.y;
-        acc[0].x = __vimax3_s32(acc[0].x, min(e0, b0.x), min(f0, b1.x));
-        acc[0].y = __vimax3_s32(acc[0].y, min(e0, b0.y), min(f0, b1.y));
-        acc[0].z = __vimax3_s32(acc[0].z, min(e0, b0.z), min(f0, b1.z));
-        acc[0].w = __vimax3_s32(acc[0].w, min(e0, b0.w), min(f0, b1.w));
-        acc[1].x = __vimax3_s32(acc[1].x, min(e1, b0.x), min(f1, b1.x));
-        acc[1].y = __vimax3_s32(acc[1].y, min(e1, b0.y), min(f1, b1.y));
-        acc[1].z = __vimax3_s32(acc[1].z, min(e1, b0.z), min(f1, b1.z));
-        acc[1].w = __vimax3_s32(acc[1].w, min(e1, b0.w), min(f1, b1.w));
-      }
-    }
-  }
-  static __device__ __forceinline__ Word product(const Word* S, int32_t nt, int32_t ti, int32_t tj, int32_t tr,
-                                                 int t) {
-    const Word* arow = S + (ti * nt + tr) * 512 + (t >> 4) * 16;
-    const Word* bcol = S + (tr * nt + tj) * 512 + (t & 15);
-    int2 acc = S[(ti * nt + tj) * 512 + t];
-#pragma unroll 4
-    for (int kk = 0; kk < kCB; kk += 2) {
-      const int2 a = arow[kk >> 1];
-      const int2 b0 = bcol[kk * 16], b1 = bcol[(kk + 1) * 16];
-      acc.x = __vimax3_s32(acc.x, min(a.x, b0.x), min(a.y, b1.x));
-      acc.y = __vimax3_s32(acc.y, min(a.x, b0.y), min(a.y, b1.y));
-    }
-    return acc;
-  }
-  static __device__ __forceinline__ void diag_warp(Word* S, int32_t nt, int32_t r, int lane) {
-    int4* row = reinterpret_cast<int4*>(S + (r * nt + r) * 512 + lane * 16);
-    int32_t v[32];
-#pragma unroll
-    for (int q4 = 0; q4 < 8; ++q4) {
-      const int4 x = row[q4];
-      v[4 * q4] = x.x, v[4 * q4 + 1] = x.y, v[4 * q4 + 2] = x.z, v[4 * q4 + 3] = x.w;
-    }
-#pragma unroll
-    for (int k = 0; k < kCB; ++k) {
-      const int32_t a = v[k];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) v[c] = max(v[c], min(a, __shfl_sync(0xFFFFFFFFu, v[c], k)));
-    }
-#pragma unroll
-    for (int q4 = 0; q4 < 8; ++q4) row[q4] = make_int4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
-  }
-};
+// acc (16 bytes of a row) = max(acc, min(a(k), b0), min(a(k + 1), b1)) with
+// b0, b1 the same 16 bytes of rows k and k + 1 and a the row's entries k,
+// k + 1 (one 32-bit word of 16-bit lanes, or an int2)
+__device__ __forceinline__ void sweep_step(uint4& acc, uint32_t a, const uint4& b0, const uint4& b1) {
+  const uint32_t l = __byte_perm(a, 0, 0x1010), h = __byte_perm(a, 0, 0x3232);
+  acc.x = __vimax3_s16x2(acc.x, __vmins2(l, b0.x), __vmins2(h, b1.x));
+  acc.y = __vimax3_s16x2(acc.y, __vmins2(l, b0.y), __vmins2(h, b1.y));
+  acc.z = __vimax3_s16x2(acc.z, __vmins2(l, b0.z), __vmins2(h, b1.z));
+  acc.w = __vimax3_s16x2(acc.w, __vmins2(l, b0.w), __vmins2(h, b1.w));
+}
+__device__ __forceinline__ void sweep_step(uint4& acc, int2 a, const uint4& b0, const uint4& b1) {
+  auto f = [&](uint32_t x, uint32_t u, uint32_t v) {
+    return uint32_t(__vimax3_s32(int32_t(x), min(a.x, int32_t(u)), min(a.y, int32_t(v))));
+  };
+  acc.x = f(acc.x, b0.x, b1.x);
+  acc.y = f(acc.y, b0.y, b1.y);
+  acc.z = f(acc.z, b0.z, b1.z);
+  acc.w = f(acc.w, b0.w, b1.w);
+}
+
+__device__ __forceinline__ bool differs(const uint4& a, const uint4& b) {
+  return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) != 0u;
+}
 
 template <typename E>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 1)
     closure_cluster_kernel(E* __restrict__ W, int32_t ld, int32_t nb, const int32_t* __restrict__ warm,
                            uint32_t* __restrict__ prog, unsigned long long* counters) {
-  using T = CTile<E>;
-  using Word = typename T::Word;
+  using AW = typename std::conditional<sizeof(E) == 2, uint32_t, int2>::type;  // a row's entries k, k + 1
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int32_t nw = *warm;
   if (nw == 0 || nw > kClusterMaxWarm<E>) return;  // the same branch in every CTA
   extern __shared__ __align__(16) unsigned char cluster_smem[];
-  Word* S = reinterpret_cast<Word*>(cluster_smem);
-  E* Se = reinterpret_cast<E*>(cluster_smem);
-  __shared__ uint32_t tnz[4][4];  // 64 x 64 tiles of W holding a nonzero
-  const int32_t n = (nw + kB - 1) / kB * kB;  // square side: whole 64-wide tiles
-  const int32_t nt = n / kCB, ntw = (nw + kCB - 1) / kCB;  // tiles, tiles with warm rows
+  uint4* S4 = reinterpret_cast<uint4*>(cluster_smem);
+  const AW* A = reinterpret_cast<const AW*>(cluster_smem);  // row i, entries k, k + 1: A[i * n / 2 + k / 2]
+  __shared__ uint32_t tnz[4][4];                  // 64 x 64 tiles of W holding a nonzero
+  __shared__ uint32_t flags[2][kClusterCtas];     // CTA o changed something in the sweep (two buffers)
+  const int32_t n = (nw + kB - 1) / kB * kB;      // square side: whole 64-wide tiles
+  constexpr int kPer16 = 16 / sizeof(E);          // entries per 16-byte piece
+  const int32_t Q = n / kPer16;                   // pieces per row
+  const int32_t nwe = (nw + 1) & ~1;              // pivots, in pairs (row nw, if read, is zero)
   const int t = threadIdx.x;
   const unsigned q = cl.block_rank();
-  constexpr int kPer16 = 16 / sizeof(E);       // entries per 16-byte piece
-  // element (i, j) of S lives at tile (i / 32, j / 32), row i % 32, column j % 32
-  auto at = [&](int32_t i, int32_t j) { return ((i / kCB) * nt + j / kCB) * (kCB * kCB) + (i % kCB) * kCB + j % kCB; };
-  for (int32_t e = t; e < n * (n / kPer16); e += blockDim.x) {
-    const int32_t i = e / (n / kPer16), j = (e % (n / kPer16)) * kPer16;
-    *reinterpret_cast<uint4*>(Se + at(i, j)) = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(i) * ld + j));
+  {
+    // rows 0 .. nwe - 1 of W, eight 16-byte loads in flight per thread
+    const int32_t total = nwe * Q;
+    constexpr int kU = 8;
+    for (int32_t e0 = t; e0 < total; e0 += kU * kClusterThreads) {
+      uint4 v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int32_t e = e0 + u * kClusterThreads;
+        if (e < total) v[u] = __ldcg(reinterpret_cast<const uint4*>(W + int64_t(e / Q) * ld) + e % Q);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int32_t e = e0 + u * kClusterThreads;
+        if (e < total) S4[e] = v[u];
+      }
+    }
   }
   if (t < 16) tnz[t >> 2][t & 3] = 0u;
-  cl.sync();  // every copy loaded before any remote write
-  using Pair = typename T::Pair;
-  Pair* rpair[kClusterCtas];
-#pragma unroll
-  for (int c = 0; c < kClusterCtas; ++c) rpair[c] = reinterpret_cast<Pair*>(cl.map_shared_rank(S, c));
-  Pair* lpair = reinterpret_cast<Pair*>(S);
-  // partial products of slots 1..3, two buffers used by alternate tiles
-  Pair* part = reinterpret_cast<Pair*>(cluster_smem + size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E));
-  const int slot = t >> 7, st = t & 127, rp = st >> 3, cp = st & 7;
-  int buf = 0;
-  // X(ti, tj) = max(X, S(ti, tr) (x) S(tr, tj)): slot s takes pivot entries
-  // 8 s .. 8 s + 7 for its 2 x 2 Words, slot 0 combines the four partial
-  // maxima after one barrier (every read of the operands is done by then, so
-  // X may be one of them) and writes X, here and, with bcast, in every copy.
-  auto update = [&](int32_t ti, int32_t tj, int32_t tr, bool bcast) {
-    const int32_t tile = ti * nt + tj;
-    const int32_t i0 = (tile * 512 + (2 * rp) * 16) / 2 + cp, i1 = i0 + 8;  // Pair indices of the two rows
-    Pair acc[2];
-    if (slot == 0) {
-      acc[0] = lpair[i0], acc[1] = lpair[i1];
-    } else {
-      acc[0] = acc[1] = T::zero();
-    }
-    T::product8(S, nt, ti, tj, tr, rp, cp, 8 * slot, acc);
-    Pair* pb = part + buf * (3 * 256);
-    if (slot > 0) pb[(slot - 1) * 256 + 2 * st] = acc[0], pb[(slot - 1) * 256 + 2 * st + 1] = acc[1];
-    __syncthreads();
-    if (slot == 0) {
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        acc[0] = T::pmax(acc[0], pb[u * 256 + 2 * st]);
-        acc[1] = T::pmax(acc[1], pb[u * 256 + 2 * st + 1]);
+  if (t < 2 * kClusterCtas) flags[t / kClusterCtas][t % kClusterCtas] = 0u;
+  cl.sync();  // every copy loaded, every flag clear, before any remote write
+  const int32_t own = int32_t(q) < nw ? (nw - int32_t(q) + kClusterCtas - 1) / kClusterCtas : 0;
+  const int32_t items = (own + 1) / 2 * Q;  // (pair of owned rows, piece)
+  int sweeps = 0;
+  while (sweeps < kMaxSweeps) {
+    bool changed = false;
+    for (int32_t it = t; it < items; it += kClusterThreads) {
+      const int32_t rp = it / Q, c = it % Q;
+      const int32_t i0 = int32_t(q) + kClusterCtas * (2 * rp), i1 = i0 + kClusterCtas;
+      const bool has1 = i1 < nw;
+      const uint4 x0 = S4[i0 * Q + c], x1 = has1 ? S4[i1 * Q + c] : x0;
+      uint4 acc0 = x0, acc1 = x1;
+      const AW* a0p = A + i0 * (n / 2);
+      const AW* a1p = A + (has1 ? i1 : i0) * (n / 2);
+#pragma unroll 4
+      for (int32_t k = 0; k < nwe; k += 2) {
+        const uint4 b0 = S4[k * Q + c], b1 = S4[(k + 1) * Q + c];
+        sweep_step(acc0, a0p[k >> 1], b0, b1);
+        sweep_step(acc1, a1p[k >> 1], b0, b1);
       }
-      lpair[i0] = acc[0], lpair[i1] = acc[1];
-      if (bcast) {
+      if (differs(acc0, x0)) {
+        changed = true;
+        S4[i0 * Q + c] = acc0;
 #pragma unroll
-        for (int c = 0; c < kClusterCtas; ++c)
-          if (c != int(q)) rpair[c][i0] = acc[0], rpair[c][i1] = acc[1];
+        for (int o = 1; o < kClusterCtas; ++o)
+          *cl.map_shared_rank(S4 + i0 * Q + c, (q + o) % kClusterCtas) = acc0;
+      }
+      if (has1 && differs(acc1, x1)) {
+        changed = true;
+        S4[i1 * Q + c] = acc1;
+#pragma unroll
+        for (int o = 1; o < kClusterCtas; ++o)
+          *cl.map_shared_rank(S4 + i1 * Q + c, (q + o) % kClusterCtas) = acc1;
       }
     }
-    buf ^= 1;
-  };
-  unsigned long long ops = 0;
-  for (int32_t r = 0; r < ntw; ++r) {
-    if (t < 32) T::diag_warp(S, nt, r, t);  // 1. diagonal tile, in every CTA
-    __syncthreads();
-    // 2. panels: (r, j) for j != r, j < nt, then (i, r) for i != r, i < ntw
-    const int32_t np = (nt - 1) + (ntw - 1);
-    for (int32_t p = q; p < np; p += kClusterCtas) {
-      int32_t ti = r, tj = r;
-      if (p < nt - 1)
-        tj = p + (p >= r);
-      else
-        ti = (p - (nt - 1)) + ((p - (nt - 1)) >= r);
-      update(ti, tj, r, true);
-      ++ops;
-    }
-    cl.sync();
-    // 3. the other tiles: i != r (i < ntw), j != r (j < nt)
-    const int32_t nr = (ntw - 1) * (nt - 1);
-    for (int32_t p = q; p < nr; p += kClusterCtas) {
-      const int32_t a = p / (nt - 1), b = p % (nt - 1);
-      update(a + (a >= r), b + (b >= r), r, true);  // operands are panels
-      ++ops;
-    }
-    cl.sync();
+    ++sweeps;
+    const int any = __syncthreads_or(changed);
+    if (any && t < kClusterCtas) *cl.map_shared_rank(&flags[sweeps & 1][q], unsigned(t)) = 1u;
+    cl.sync();  // this sweep's copies and flags visible everywhere
+    const int more = __syncthreads_or(t < kClusterCtas && flags[sweeps & 1][t] != 0u);
+    if (t < kClusterCtas) flags[sweeps & 1][t] = 0u;  // rewritten two sweeps on, after the next barrier
+    if (!more) break;  // the same decision in every CTA
   }
-  // write back tiles q, q + 8, ... with a zero diagonal; nonzero bits per
-  // 64 x 64 tile of W
-  for (int32_t tile = q; tile < nt * nt; tile += kClusterCtas) {
-    const int32_t ti = tile / nt, tj = tile % nt;
-    for (int32_t e = t; e < kCB * kCB; e += blockDim.x) {
-      const int32_t i = ti * kCB + e / kCB, j = tj * kCB + e % kCB;
-      const E v = i == j ? E(0) : Se[tile * (kCB * kCB) + e];
-      W[int64_t(i) * ld + j] = v;
-      if (v) tnz[i / kB][j / kB] = 1u;
+  // each CTA writes its rows back with a zero diagonal; nonzero bits per
+  // 64 x 64 tile of W. No CTA writes into another any more.
+  for (int32_t it = t; it < own * Q; it += kClusterThreads) {
+    const int32_t r = it / Q, c = it % Q;
+    const int32_t i = int32_t(q) + kClusterCtas * r, j0 = c * kPer16;
+    uint4 v = S4[i * Q + c];
+    if (i >= j0 && i < j0 + kPer16) {
+      const int e = i - j0;
+      const int w = sizeof(E) == 2 ? e >> 1 : e;
+      const uint32_t keep = sizeof(E) == 2 ? ((e & 1) ? 0x0000FFFFu : 0xFFFF0000u) : 0u;
+      v.x = w == 0 ? v.x & keep : v.x;
+      v.y = w == 1 ? v.y & keep : v.y;
+      v.z = w == 2 ? v.z & keep : v.z;
+      v.w = w == 3 ? v.w & keep : v.w;
     }
+    *reinterpret_cast<uint4*>(W + int64_t(i) * ld + j0) = v;
+    if (v.x | v.y | v.z | v.w) tnz[i / kB][j0 / kB] = 1u;
   }
   __syncthreads();
   if (t < 16 && tnz[t >> 2][t & 3]) atomicOr(&prog[(t >> 2) * nb + (t & 3)], kNZ);
-  if (t == 0 && q == 0) atomicAdd(&counters[1], 1ull * ntw);
-  if (t == 0 && ops) atomicAdd(&counters[0], (ops + 7) / 8);  // in 64 x 64 x 64 tile units
-  cl.sync();  // no CTA leaves while others may still write into it
+  if (t == 0 && q == 0)  // entry updates, in 64 x 64 x 64 tile units
+    atomicAdd(&counters[0], (unsigned long long)sweeps * uint64_t(nw) * uint64_t(nw) * uint64_t(n) / 262144ull);
 }
 
 // Uniform cold columns: u[i] = max(ucol[i], max_x min(W[i][x], ucol[x]))
@@ -1020,8 +906,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   }
   if (int rc = check_launch()) return rc;
   {
-    const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E) +
-                        2 * 3 * 256 * sizeof(typename CTile<E>::Pair);
+    const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E);
     cudaFuncSetAttribute(closure_cluster_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     Launch L(ctx, stream, "closure_cluster", 0.0);
     closure_cluster_kernel<E><<<kClusterCtas, kClusterThreads, smem, stream>>>(W, mp, nb, bf.warm, bf.prog,

@@ -239,6 +239,26 @@ def test_closure_many_rounds_with_edgeless_candidates(m, cold_frac):
         eq(host(S.schulze_strongest_paths(cu(d), 20000, flags=flags)), want, f"m={m} cold={cold_frac}")
 
 
+@pytest.mark.parametrize("nw", [2, 3, 17, 64, 151, 192, 256])
+def test_closure_long_widest_paths(nw):
+    """Warm squares whose widest paths are long: a heavy Hamiltonian chain
+    through the warm candidates in a shuffled order under light random
+    edges, so that p(a, b) for distant a, b needs every edge of the chain.
+    The small-square closure then needs about log2(nw) + 1 sweeps."""
+    m = 400
+    rs = np.random.Generator(np.random.PCG64(5000 + nw))
+    warm = rs.permutation(m)[:nw]
+    d = np.zeros((m, m), np.int32)
+    d[np.ix_(warm, warm)] = rs.integers(0, 100, size=(nw, nw)) * (rs.random((nw, nw)) < 0.3)
+    heavy = rs.integers(20000, 30000, size=nw)
+    for a in range(nw):  # chain warm[0] -> warm[1] -> ... -> warm[nw - 1] -> warm[0]
+        d[warm[a], warm[(a + 1) % nw]] = heavy[a]
+    np.fill_diagonal(d, 0)
+    want = oracle.strongest_paths(d, nthreads=16)
+    for flags in (S.F_FORCE_S16, S.F_FORCE_S32):
+        eq(host(S.schulze_strongest_paths(cu(d), 30000, flags=flags)), want, f"nw={nw} flags={flags}")
+
+
 @pytest.mark.parametrize("nw", [1, 31, 32, 33, 64, 65, 151, 192, 193, 255, 256, 257, 300])
 def test_closure_warm_set_sizes(nw):
     """nw candidates with outgoing edges spread over m = 600 ids, the rest
