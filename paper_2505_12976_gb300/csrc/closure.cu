@@ -157,9 +157,11 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
                                                        const int32_t* __restrict__ hint,
                                                        const int32_t* __restrict__ hint_valid) {
   __shared__ uint32_t part[32];
+  extern __shared__ uint32_t relabel_smem[];  // m words when m <= kScanSmem
   if (hint_valid && *hint_valid) rowflag = hint;
-  // inv[c] = 1 for warm c, scanned in place into the warm rank
-  uint32_t* rank = reinterpret_cast<uint32_t*>(inv);
+  // rank[c] = 1 for warm c, scanned into the warm rank (in shared memory, or
+  // in place in inv for long candidate lists)
+  uint32_t* rank = m <= kScanSmem ? relabel_smem : reinterpret_cast<uint32_t*>(inv);
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) rank[c] = rowflag[c] ? 1u : 0u;
   __syncthreads();
   const int32_t warm = int32_t(block_exclusive_scan(rank, m, part));
@@ -235,49 +237,59 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
   const int32_t nw = *warm;
   const int32_t rows = (nw + kB - 1) / kB * kB;
   const bool uc = hint_valid && *hint_valid && rows < m;  // cold columns beyond the square: ucold[ix]
-  for (int32_t x = blockIdx.x; x < m; x += gridDim.x) {
-    const int32_t ix = inv[x];
-    int32_t* prow = p + int64_t(x) * m;
-    if (ix >= nw) {
+  // kR rows per pass: their relabeled indices are loaded together (lane r of
+  // each warp holds row r's) instead of one dependent load per row
+  constexpr int kR = 8;
+  const int lane = threadIdx.x & 31;
+  for (int32_t xb = blockIdx.x; xb < m; xb += kR * gridDim.x) {
+    const int32_t xl = xb + lane * int32_t(gridDim.x);
+    const int32_t ixl = (lane < kR && xl < m) ? inv[xl] : 0;
+    for (int r = 0; r < kR; ++r) {
+      const int32_t x = xb + r * int32_t(gridDim.x);
+      if (x >= m) break;
+      const int32_t ix = __shfl_sync(0xFFFFFFFFu, ixl, r);
+      int32_t* prow = p + int64_t(x) * m;
+      if (ix >= nw) {
+        if ((m & 3) == 0) {
+          for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x)
+            *reinterpret_cast<int4*>(prow + y) = make_int4(0, 0, 0, 0);
+        } else {
+          for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = 0;
+        }
+        continue;
+      }
+      const E* wrow = W + int64_t(ix) * mp;
       if ((m & 3) == 0) {
-        for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x)
-          *reinterpret_cast<int4*>(prow + y) = make_int4(0, 0, 0, 0);
-      } else {
-        for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = 0;
-      }
-      continue;
-    }
-    const E* wrow = W + int64_t(ix) * mp;
-    if ((m & 3) == 0) {
-      constexpr int kU = 4;  // int4 groups per thread and pass, loads issued together
-      for (int32_t y0 = 0; y0 < m; y0 += 4 * kU * blockDim.x) {
-        int4 iv[kU];
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
-          iv[q] = y < m ? *reinterpret_cast<const int4*>(inv + y) : make_int4(0, 0, 0, 0);
-        }
-        int4 v[kU];
-        const int32_t uv = uc ? ucold[ix] : 0;
-        auto at = [&](int32_t iy) { return (uc && iy >= rows) ? uv : int32_t(wrow[iy]); };
-#pragma unroll
-        for (int q = 0; q < kU; ++q) v[q] = make_int4(at(iv[q].x), at(iv[q].y), at(iv[q].z), at(iv[q].w));
-#pragma unroll
-        for (int q = 0; q < kU; ++q) {
-          const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
-          if (y >= m) continue;
-          if (x >= y && x < y + 4) {
-            const int32_t t = x - y;
-            v[q].x = t == 0 ? 0 : v[q].x, v[q].y = t == 1 ? 0 : v[q].y;
-            v[q].z = t == 2 ? 0 : v[q].z, v[q].w = t == 3 ? 0 : v[q].w;
+        constexpr int kU = 4;  // int4 groups per thread and pass, loads issued together
+        for (int32_t y0 = 0; y0 < m; y0 += 4 * kU * blockDim.x) {
+          int4 iv[kU];
+  #pragma unroll
+          for (int q = 0; q < kU; ++q) {
+            const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
+            iv[q] = y < m ? *reinterpret_cast<const int4*>(inv + y) : make_int4(0, 0, 0, 0);
           }
-          *reinterpret_cast<int4*>(prow + y) = v[q];
+          int4 v[kU];
+          const int32_t uv = uc ? ucold[ix] : 0;
+          auto at = [&](int32_t iy) { return (uc && iy >= rows) ? uv : int32_t(wrow[iy]); };
+  #pragma unroll
+          for (int q = 0; q < kU; ++q) v[q] = make_int4(at(iv[q].x), at(iv[q].y), at(iv[q].z), at(iv[q].w));
+  #pragma unroll
+          for (int q = 0; q < kU; ++q) {
+            const int32_t y = y0 + 4 * (q * blockDim.x + threadIdx.x);
+            if (y >= m) continue;
+            if (x >= y && x < y + 4) {
+              const int32_t t = x - y;
+              v[q].x = t == 0 ? 0 : v[q].x, v[q].y = t == 1 ? 0 : v[q].y;
+              v[q].z = t == 2 ? 0 : v[q].z, v[q].w = t == 3 ? 0 : v[q].w;
+            }
+            *reinterpret_cast<int4*>(prow + y) = v[q];
+          }
         }
-      }
-    } else {
-      for (int32_t y = threadIdx.x; y < m; y += blockDim.x) {
-        const int32_t iy = inv[y];
-        prow[y] = (y == x) ? 0 : (uc && iy >= rows) ? ucold[ix] : int32_t(wrow[iy]);
+      } else {
+        for (int32_t y = threadIdx.x; y < m; y += blockDim.x) {
+          const int32_t iy = inv[y];
+          prow[y] = (y == x) ? 0 : (uc && iy >= rows) ? ucold[ix] : int32_t(wrow[iy]);
+        }
       }
     }
   }
@@ -896,7 +908,8 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    relabel_kernel<<<1, 1024, 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm, bf.hint, bf.hint_valid);
+    relabel_kernel<<<1, 1024, m <= kScanSmem ? size_t(m) * 4 : 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm,
+                                                                          bf.hint, bf.hint_valid);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 512, 0, mp);

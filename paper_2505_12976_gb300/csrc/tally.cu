@@ -278,9 +278,12 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
                                                            int32_t* __restrict__ act, int32_t* __restrict__ meta,
                                                            int32_t* __restrict__ hint,
                                                            int32_t* __restrict__ hint_valid) {
-  __shared__ uint32_t part[1024];
+  __shared__ uint32_t part[32];
+  extern __shared__ uint32_t plan_smem[];  // m words when m <= kScanSmem
   {
-    uint32_t* flag = reinterpret_cast<uint32_t*>(slot);
+    // listed flags scanned into the slots (in shared memory, or in place in
+    // slot for long candidate lists)
+    uint32_t* flag = m <= kScanSmem ? plan_smem : reinterpret_cast<uint32_t*>(slot);
     for (int32_t c = threadIdx.x; c < m; c += blockDim.x) flag[c] = cnt[c] > 0 ? 1u : 0u;
     __syncthreads();
     const uint32_t na = block_exclusive_scan(flag, m, part);
@@ -918,7 +921,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   }
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
-    sparse_plan_kernel<<<1, 1024, 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot,
+    sparse_plan_kernel<<<1, 1024, m <= kScanSmem ? size_t(m) * 4 : 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot,
                                                act, meta, hint, hint_valid);
   }
   if (cp.cmax > 0) {

@@ -119,6 +119,16 @@ def test_tally_compact_ballot_lengths(k):
     eq(host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE)), oracle.tally(r, m), f"k={k}")
 
 
+def test_tally_compact_many_ballots_per_warp():
+    """Each warp of the compact pair count takes many ballots in turn from
+    its slice (ids and slots fetched ahead): the whole tally against the
+    oracle."""
+    m, n, k = 300, 60000, 8
+    r = W.mallows(911, n, m, k, 0.9, W.permutation(912, m))
+    assert len(np.unique(r)) <= 256
+    eq(host(S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE)), oracle.tally(r, m), "many ballots")
+
+
 def test_tally_compact_wide_counters():
     """More ballots per slice than 16-bit counters hold: the compact pair
     count switches to 32-bit counters. Sampled entries against the
