@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const int32_t* __restrict__ d
 template <typename E>
 __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int32_t mp, int32_t m,
                                                     const int32_t* __restrict__ inv,
+                                                    const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ warm, int32_t* __restrict__ p,
                                                     const int32_t* __restrict__ hint_valid,
                                                     const int32_t* __restrict__ ucold) {
@@ -249,13 +250,21 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
       if (x >= m) break;
       const int32_t ix = __shfl_sync(0xFFFFFFFFu, ixl, r);
       int32_t* prow = p + int64_t(x) * m;
-      if (ix >= nw) {
+      // a cold row is zero; with uniform cold columns a warm row is
+      // ucold[ix] outside the square, whose columns (relabeled b < rows,
+      // candidate perm[b]) come from W after the fill
+      if (ix >= nw || uc) {
+        const int32_t fill = ix >= nw ? 0 : ucold[ix];
         if ((m & 3) == 0) {
           for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x)
-            *reinterpret_cast<int4*>(prow + y) = make_int4(0, 0, 0, 0);
+            *reinterpret_cast<int4*>(prow + y) = make_int4(fill, fill, fill, fill);
         } else {
-          for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = 0;
+          for (int32_t y = threadIdx.x; y < m; y += blockDim.x) prow[y] = fill;
         }
+        if (ix >= nw) continue;
+        __syncthreads();  // the square's columns after the fill (the branch is the same in the whole CTA)
+        const E* wrow = W + int64_t(ix) * mp;
+        for (int32_t b = threadIdx.x; b < rows; b += blockDim.x) prow[perm[b]] = b == ix ? 0 : int32_t(wrow[b]);
         continue;
       }
       const E* wrow = W + int64_t(ix) * mp;
@@ -962,7 +971,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   {
     const int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
     Launch L(ctx, stream, "closure_widen", mm * 4.0);
-    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.warm, p, bf.hint_valid, bf.ucold);
+    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.perm, bf.warm, p, bf.hint_valid, bf.ucold);
   }
   if (bb_out) {
     Launch L(ctx, stream, "closure_beaten_by", 0.0);
