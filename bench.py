@@ -14,6 +14,7 @@ collective on the data path) and rank 0 prints the whole-job rate.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -23,6 +24,33 @@ import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def profiled_traffic() -> dict:
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    the kernels captured with ncu, from the table in profiles/dram_traffic.md:
+    {(kernel class, workload): bytes}, kept only for kernels whose source file
+    still has the digest recorded at capture time (a changed kernel has no
+    traffic figure until it is captured again)."""
+    out = {}
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "dram_traffic.md")).read().splitlines()
+    except OSError:
+        return out
+    for line in lines:
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) != 6:
+            continue
+        cls, _kernel, workload, nbytes, src, digest = cells
+        try:
+            value = float(nbytes.replace(",", ""))
+            with open(os.path.join(ROOT, src), "rb") as f:
+                current = hashlib.sha256(f.read()).hexdigest()[:16]
+        except (ValueError, OSError):
+            continue
+        if current == digest:
+            out[(cls, workload)] = value
+    return out
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
@@ -793,18 +821,21 @@ def main():
         "extract_beaten_by": ("hbm", 2 * mm4, "p and p^T read"),
     }
 
+    traffic = profiled_traffic()
+
     def roofline(name, st):
         per_launch_ms = st["ms"] / max(1, st["launches"])
         bound, units, what = work.get(name, ("hbm", st["work"], "library estimate"))
         achieved = units / (per_launch_ms * 1e-3)
+        dram = traffic.get((name, args.workload)) if not (args.m or args.n or args.margin) else None
         if bound == "alu":
             return {"bound": "alu", "kernel": name, "achieved": achieved / 1e9, "peak": alu_peak / 1e9,
-                    "unit": "Gupdates/s", "frac": achieved / alu_peak, "traffic": None,
+                    "unit": "Gupdates/s", "frac": achieved / alu_peak, "traffic": dram,
                     "lane_format": "s16x2" if s16 else "s32", "work_per_launch": units, "work": what,
                     "per_launch_ms": per_launch_ms, "launches": st["launches"],
                     "peak_source": "schulze_probe_minmax measured in this run (best same-format variant)"}
         return {"bound": "hbm", "kernel": name, "achieved": achieved / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / 1e9 / hbm_peak, "traffic": None, "bytes_per_launch": units, "work": what,
+                "frac": achieved / 1e9 / hbm_peak, "traffic": dram, "bytes_per_launch": units, "work": what,
                 "per_launch_ms": per_launch_ms, "launches": st["launches"],
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 

@@ -499,6 +499,15 @@ __global__ void __launch_bounds__(512)
 // [0, m) are skipped (the count pass reports them).
 constexpr int kFillWarps = 4;
 
+// *addr += v at a shared-memory byte address when p holds (predicated
+// reduction, no branch)
+__device__ __forceinline__ void red_shared_if(bool p, uint32_t addr, uint32_t v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], %2;\n\t}" ::"r"(uint32_t(p)),
+      "r"(addr), "r"(v)
+      : "memory");
+}
+
 template <bool kPacked>
 __device__ __forceinline__ void count_pair(uint32_t* crow, uint32_t sp) {
   if (kPacked)
@@ -577,18 +586,22 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         ids(v + 2 * ncw, n0, n1);
         const bool clean = (lane >= k || r0 != kNoSlot) && (lane + 32 >= k || r1 != kNoSlot);
         if (__all_sync(kAll, clean)) {  // every id valid (the usual case): no per-entry checks
+          // shared-memory byte addresses of this lane's counters in row 0 and
+          // the row stride; each add is a predicated reduction (no branch)
           const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
           const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+          const uint32_t cbase = uint32_t(__cvta_generic_to_shared(C)), rstride = uint32_t(wpr) * 4u;
+          const uint32_t a0 = cbase + w0 * 4u, a1 = cbase + w1 * 4u;
 #pragma unroll 4
           for (int32_t q = 1; q < qlo; ++q) {
             const uint32_t sq = __shfl_sync(kAll, r0, q);
-            if (lane < q) atomicAdd(C + int32_t(sq) * wpr + w0, i0);
+            red_shared_if(lane < q, a0 + sq * rstride, i0);
           }
 #pragma unroll 4
           for (int32_t q = 32; q < qhi; ++q) {
-            uint32_t* crow = C + int32_t(__shfl_sync(kAll, r1, q - 32)) * wpr;
-            atomicAdd(crow + w0, i0);
-            if (lane + 32 < q) atomicAdd(crow + w1, i1);
+            const uint32_t row = __shfl_sync(kAll, r1, q - 32) * rstride;
+            red_shared_if(true, a0 + row, i0);
+            red_shared_if(lane + 32 < q, a1 + row, i1);
           }
           continue;
         }
