@@ -229,6 +229,10 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
  * path on workspace memory and copies winners and order (each may be NULL)
  * back to the host. Synchronous on `stream`. Device d and p stay inside the
  * context. Returns SCHULZE_EDATA directly when the ballots are invalid.
+ * When every host buffer is page-locked, the call's work (copies included)
+ * is captured once as a CUDA graph and replayed by later calls with the same
+ * buffers and sizes (the ballots are read afresh each call); pageable
+ * buffers run the same work eagerly.
  */
 int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
                      int32_t* winners_host, int32_t* order_host, uint32_t flags, schulze_stream_t stream);

@@ -47,6 +47,52 @@ static int set_device(schulze_ctx* ctx) {
 
 using namespace schulze;
 
+// Page-locked host memory (or no buffer): graph copy nodes need it; calls
+// with pageable buffers run eagerly.
+static bool pinned(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Makes ctx->host_exec the graph of schulze_run_host's work for `key`,
+// capturing enqueue(cap_stream, host_status) when the key changed; false
+// when the call cannot be a graph (pageable host buffers, a failed capture)
+// and must run eagerly.
+template <class Enqueue>
+static bool host_graph(schulze_ctx* ctx, const schulze_ctx::HostKey& key, Enqueue&& enqueue) {
+  if (!ctx->cap_stream || !ctx->host_status) return false;
+  if (ctx->host_exec && ctx->host_key == key) return true;
+  if (!pinned(key.ranks) || !pinned(key.winners) || !pinned(key.order)) return false;
+  if (ctx->host_exec) {
+    cudaGraphExecDestroy(ctx->host_exec);
+    ctx->host_exec = nullptr;
+    ctx->host_key = schulze_ctx::HostKey{};
+  }
+  if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int rc = enqueue(ctx->cap_stream, ctx->host_status);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = rc == SCHULZE_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  ctx->host_exec = exec;
+  ctx->host_key = key;
+  return true;
+}
+
 extern "C" {
 
 const char* schulze_strerror(int code) {
@@ -87,6 +133,13 @@ int schulze_ctx_create(int device, schulze_ctx** out) {
     return SCHULZE_ENOMEM;
   }
   c->counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->status) + 8);
+  // schulze_run_host's graph: its capture stream and page-locked status word
+  // (without them that call runs eagerly)
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&c->host_status, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    c->host_status = nullptr;
+  }
   *out = c;
   return SCHULZE_OK;
 }
@@ -97,6 +150,9 @@ int schulze_ctx_destroy(schulze_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->ws.base) cudaFree(ctx->ws.base);
   if (ctx->status) cudaFree(ctx->status);
+  if (ctx->host_exec) cudaGraphExecDestroy(ctx->host_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->host_status) cudaFreeHost(ctx->host_status);
   delete ctx;
   return SCHULZE_OK;
 }
@@ -274,23 +330,32 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   int32_t* hint = cv.take<int32_t>(size_t(m));
   int32_t* hint_valid = cv.take<int32_t>(1);
   void* rest = cv.take<char>(0);
-  if (rbytes && cudaMemcpyAsync(ranks, ranks_host, rbytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-    return SCHULZE_ECUDA;
-  if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, stream, hint, hint_valid)) return rc;
-  const bool ext = winners_host || order_host;
-  if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, stream, ext ? bb : nullptr, hint, hint_valid))
-    return rc;
-  if (ext)
-    if (int rc = extract_from_beaten_by(ctx, bb, m, win, ord, rest, stream)) return rc;
-  if (winners_host &&
-      cudaMemcpyAsync(winners_host, win, size_t(m) * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-    return SCHULZE_ECUDA;
-  if (order_host && cudaMemcpyAsync(order_host, ord, size_t(m) * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-    return SCHULZE_ECUDA;
+  // the call's work on stream s, the status word copied to *st
+  auto enqueue = [&](cudaStream_t s, int32_t* st) -> int {
+    if (rbytes && cudaMemcpyAsync(ranks, ranks_host, rbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, s, hint, hint_valid)) return rc;
+    const bool ext = winners_host || order_host;
+    if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, s, ext ? bb : nullptr, hint, hint_valid)) return rc;
+    if (ext)
+      if (int rc = extract_from_beaten_by(ctx, bb, m, win, ord, rest, s)) return rc;
+    if (winners_host && cudaMemcpyAsync(winners_host, win, size_t(m) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    if (order_host && cudaMemcpyAsync(order_host, ord, size_t(m) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    if (cudaMemcpyAsync(st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    return SCHULZE_OK;
+  };
   int32_t st = 0;
-  if (cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-    return SCHULZE_ECUDA;
-  if (cudaStreamSynchronize(stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (host_graph(ctx, {ranks_host, winners_host, order_host, ctx->ws.base, n, m, k, flags}, enqueue)) {
+    if (cudaGraphLaunch(ctx->host_exec, stream) != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    st = *ctx->host_status;
+  } else {
+    if (int rc = enqueue(stream, &st)) return rc;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return SCHULZE_ECUDA;
+  }
   if (st != 0) {
     cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), stream);
     cudaStreamSynchronize(stream);

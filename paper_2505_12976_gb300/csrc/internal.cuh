@@ -52,6 +52,25 @@ struct schulze_ctx {
   std::vector<schulze::ProfRecord> prof_pending;
   std::vector<schulze::ProfClass> prof_classes;
   std::vector<cudaEvent_t> prof_free_events;
+  // schulze_run_host: the whole call (copies in, path, copies out) captured
+  // once as a CUDA graph on cap_stream and replayed while the arguments,
+  // the workspace and the host buffers (page-locked) stay the same
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t host_exec = nullptr;
+  int32_t* host_status = nullptr;  // page-locked word receiving the device status
+  struct HostKey {
+    const void* ranks = nullptr;
+    const void* winners = nullptr;
+    const void* order = nullptr;
+    const void* ws = nullptr;
+    int64_t n = -1;
+    int32_t m = -1, k = -1;
+    uint32_t flags = 0;
+    bool operator==(const HostKey& o) const {
+      return ranks == o.ranks && winners == o.winners && order == o.order && ws == o.ws && n == o.n && m == o.m &&
+             k == o.k && flags == o.flags;
+    }
+  } host_key;
 };
 
 namespace schulze {

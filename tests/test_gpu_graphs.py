@@ -1,10 +1,11 @@
-"""schulze_run captured as a CUDA graph. Several stages choose on the device
-among kernel sequences (compact or grouped tally, the closure's own warm-row
-pass, cluster or persistent closure, uniform or general cold columns): the
-graph holds every alternative and the kernels whose case it is not return at
-once. A replay must give the oracle's results whichever way the device
-decides, including when the data of a replay decides differently from the
-data the graph was captured on."""
+"""schulze_run captured as a CUDA graph, and schulze_run_host (which caches
+its own graph). Several stages choose on the device among kernel sequences
+(compact or grouped tally, the closure's own warm-row pass, cluster or
+persistent closure, uniform or general cold columns): the graph holds every
+alternative and the kernels whose case it is not return at once. A replay
+must give the oracle's results whichever way the device decides, including
+when the data of a replay decides differently from the data the graph was
+captured on."""
 import numpy as np
 import pytest
 import torch
@@ -149,4 +150,42 @@ def test_closure_graph_without_tally_flags():
         torch.cuda.synchronize()
         want = oracle.strongest_paths(d, nthreads=8)
         assert np.array_equal(p.cpu().numpy(), want), (seed, m, nw)
+    assert ctx.status() == S.OK
+
+
+def test_host_call_graph_replays():
+    """schulze_run_host with page-locked buffers runs as a cached graph: new
+    ballots in the same buffer, a second buffer (captured anew), pageable
+    buffers (eager), and invalid ballots (status reported, then cleared),
+    each against the oracle."""
+    m, n, k = 500, 2000, 20
+    dev = torch.device("cuda", 0)
+    ctx = S.context(0)
+    ballots = [W.mallows(401 + i, n, m, k, 0.9, W.permutation(402 + i, m)) for i in range(3)]
+    r_pin = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    win = torch.empty(m, dtype=torch.int32).pin_memory()
+    order = torch.empty(m, dtype=torch.int32).pin_memory()
+
+    def check(ranks, got_win, got_order, what):
+        _, _, w_want, o_want, _ = oracle.schulze(ranks, m, nthreads=8)
+        assert np.array_equal(np.asarray(got_win), w_want), what
+        assert np.array_equal(np.asarray(got_order), o_want), what
+
+    for i in (0, 1, 0, 2):  # same buffers, new contents each call
+        r_pin.copy_(torch.from_numpy(ballots[i]))
+        S.schulze_run_host(r_pin, m, winners=win, order=order, device=0)
+        check(ballots[i], win.numpy(), order.numpy(), f"pinned call on ballots {i}")
+    r_pin2 = torch.from_numpy(ballots[1]).pin_memory()  # another buffer: a new capture
+    S.schulze_run_host(r_pin2, m, winners=win, order=order, device=0)
+    check(ballots[1], win.numpy(), order.numpy(), "second pinned buffer")
+    w_np, o_np = S.schulze_run_host(ballots[2], m, device=0)  # pageable: eager
+    check(ballots[2], w_np, o_np, "pageable buffers")
+    bad = ballots[0].copy()
+    bad[7, 3] = m + 5
+    r_pin.copy_(torch.from_numpy(bad))
+    with pytest.raises(S.SchulzeError):
+        S.schulze_run_host(r_pin, m, winners=win, order=order, device=0)
+    r_pin.copy_(torch.from_numpy(ballots[0]))
+    S.schulze_run_host(r_pin, m, winners=win, order=order, device=0)
+    check(ballots[0], win.numpy(), order.numpy(), "after invalid ballots")
     assert ctx.status() == S.OK
