@@ -37,7 +37,6 @@ constexpr int kMaxTies = 16;
 struct Acc {  // per-candidate accumulators of the features pass
   int32_t* wins;
   int32_t* losses;
-  int32_t* ties;
   unsigned long long* rowsum;
   unsigned long long* colsum;
   int32_t* maxw_out;
@@ -51,7 +50,7 @@ struct Acc {  // per-candidate accumulators of the features pass
 
 __global__ void acc_init_kernel(Acc a, int32_t m) {
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-    a.wins[c] = a.losses[c] = a.ties[c] = 0;
+    a.wins[c] = a.losses[c] = 0;
     a.rowsum[c] = a.colsum[c] = a.sumw_out[c] = a.sumw_in[c] = 0ull;
     a.maxw_out[c] = a.maxw_in[c] = a.max_drow[c] = 0;
     a.min_margin[c] = INT32_MAX;
@@ -76,53 +75,95 @@ __device__ __forceinline__ int32_t warp_min(int32_t v) {
   return v;
 }
 
-// Row statistics of rows `rows0 + r` against columns `cols0 + lane` of one
-// 32 x 32 block: x = d[row][col] (from `x`), y = d[col][row] (from `y`, the
-// transposed block). One warp per row; one atomic per row and statistic.
-__device__ void row_stats(const int32_t (*x)[33], const int32_t (*y)[33], int32_t rows0, int32_t cols0, int32_t m,
-                          const Acc& a) {
-  const int lane = threadIdx.x;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int32_t i = rows0 + r, j = cols0 + lane;
-    const bool v = i < m && j < m && i != j;
-    const int32_t dij = v ? x[r][lane] : 0, dji = v ? y[lane][r] : 0;
-    const int32_t win = v && dij > dji, loss = v && dji > dij, tie = v && dij == dji;
-    const int32_t wout = win ? dij : 0, win_w = loss ? dji : 0;
-    int32_t s_win = warp_sum(win), s_loss = warp_sum(loss), s_tie = warp_sum(tie);
-    long long s_row = warp_sum64(dij), s_col = warp_sum64(dji), s_wo = warp_sum64(wout), s_wi = warp_sum64(win_w);
-    int32_t mx_wo = warp_max(wout), mx_wi = warp_max(win_w), mx_d = warp_max(dij);
-    int32_t mn_mg = warp_min(v ? dij - dji : INT32_MAX), mx_mg = warp_max(v ? dij - dji : INT32_MIN);
-    if (lane == 0 && i < m) {
-      if (s_win) atomicAdd(&a.wins[i], s_win);
-      if (s_loss) atomicAdd(&a.losses[i], s_loss);
-      if (s_tie) atomicAdd(&a.ties[i], s_tie);
-      if (s_row) atomicAdd(&a.rowsum[i], (unsigned long long)s_row);
-      if (s_col) atomicAdd(&a.colsum[i], (unsigned long long)s_col);
-      if (s_wo) atomicAdd(&a.sumw_out[i], (unsigned long long)s_wo);
-      if (s_wi) atomicAdd(&a.sumw_in[i], (unsigned long long)s_wi);
-      atomicMax(&a.maxw_out[i], mx_wo);
-      atomicMax(&a.maxw_in[i], mx_wi);
-      atomicMax(&a.max_drow[i], mx_d);
-      atomicMin(&a.min_margin[i], mn_mg);
-      atomicMax(&a.max_margin[i], mx_mg);
+// Row statistics without per-tile atomics: CTA (s, ch) takes the strip of
+// kFR rows 32 s .. 32 s + 31 against the columns of chunk ch (kFChunks
+// chunks), tile by tile (kFC columns): d[i][j] and the transposed d[j][i]
+// staged in shared memory, thread t accumulating row t / 8's statistics over
+// every eighth column of each tile in registers. The eight threads of a row
+// combine them with shuffles at the end and one adds them to the
+// candidate's accumulators (ties follow from wins and losses). Every entry
+// is read twice (as d[i][j] for row i and as d[i][j] for row j's column).
+constexpr int kFR = 32, kFC = 64, kFChunks = 8;
+
+__global__ void __launch_bounds__(256) features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
+  __shared__ int32_t x[kFR][kFC + 1];  // d[i][j]
+  __shared__ int32_t y[kFC][kFR + 1];  // d[j][i]
+  const int32_t I = blockIdx.x * kFR;
+  const int32_t ntile = (m + kFC - 1) / kFC, per = (ntile + kFChunks - 1) / kFChunks;
+  const int32_t t0 = blockIdx.y * per, t1 = min(ntile, t0 + per);
+  const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
+  const int32_t i = I + r;
+  int32_t win = 0, loss = 0, mx_wo = 0, mx_wi = 0, mx_d = 0, mn_mg = INT32_MAX, mx_mg = INT32_MIN;
+  long long s_row = 0, s_col = 0, s_wo = 0, s_wi = 0;
+  // the next tile's entries are loaded into registers while one is counted
+  constexpr int kPer = kFR * kFC / 256;  // entries of each tile per thread
+  int32_t nx[kPer], ny[kPer];
+  auto fetch = [&](int32_t J) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int rr = e / kFC, cc = e % kFC;  // x: row rr, column cc
+      nx[u] = (J < m && I + rr < m && J + cc < m) ? d[int64_t(I + rr) * m + J + cc] : 0;
+      const int yr = e / kFR, yc = e % kFR;  // y: row yr (candidate J + yr), column yc (candidate I + yc)
+      ny[u] = (J < m && J + yr < m && I + yc < m) ? d[int64_t(J + yr) * m + I + yc] : 0;
+    }
+  };
+  fetch(t0 * kFC);
+  for (int32_t tile = t0; tile < t1; ++tile) {
+    const int32_t J = tile * kFC;
+    __syncthreads();  // the previous tile is read
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      x[e / kFC][e % kFC] = nx[u];
+      y[e / kFR][e % kFR] = ny[u];
+    }
+    __syncthreads();
+    if (tile + 1 < t1) fetch(J + kFC);
+    if (i < m) {
+#pragma unroll
+      for (int u = 0; u < kFC / 8; ++u) {
+        const int c = q + 8 * u;
+        const int32_t j = J + c;
+        if (j >= m || j == i) continue;
+        const int32_t dij = x[r][c], dji = y[c][r];
+        const bool w = dij > dji, l = dji > dij;
+        win += w, loss += l;
+        s_row += dij, s_col += dji;
+        const int32_t wo = w ? dij : 0, wi = l ? dji : 0;
+        s_wo += wo, s_wi += wi;
+        mx_wo = max(mx_wo, wo), mx_wi = max(mx_wi, wi), mx_d = max(mx_d, dij);
+        mn_mg = min(mn_mg, dij - dji), mx_mg = max(mx_mg, dij - dji);
+      }
     }
   }
-}
-
-// One CTA per 32 x 32 block pair (A, B), A <= B: each d entry is read once.
-__global__ void features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
-  const int32_t A = blockIdx.y * 32, B = blockIdx.x * 32;
-  if (A > B) return;
-  __shared__ int32_t t1[32][33], t2[32][33];  // t1 = d[A.., B..], t2 = d[B.., A..]
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int32_t i = A + r, j = B + threadIdx.x;
-    t1[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
-    i = B + r, j = A + threadIdx.x;
-    t2[r][threadIdx.x] = (i < m && j < m) ? d[int64_t(i) * m + j] : 0;
+#pragma unroll
+  for (int o = 1; o <= 4; o <<= 1) {
+    win += __shfl_xor_sync(0xFFFFFFFFu, win, o);
+    loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+    s_row += __shfl_xor_sync(0xFFFFFFFFu, s_row, o);
+    s_col += __shfl_xor_sync(0xFFFFFFFFu, s_col, o);
+    s_wo += __shfl_xor_sync(0xFFFFFFFFu, s_wo, o);
+    s_wi += __shfl_xor_sync(0xFFFFFFFFu, s_wi, o);
+    mx_wo = max(mx_wo, __shfl_xor_sync(0xFFFFFFFFu, mx_wo, o));
+    mx_wi = max(mx_wi, __shfl_xor_sync(0xFFFFFFFFu, mx_wi, o));
+    mx_d = max(mx_d, __shfl_xor_sync(0xFFFFFFFFu, mx_d, o));
+    mn_mg = min(mn_mg, __shfl_xor_sync(0xFFFFFFFFu, mn_mg, o));
+    mx_mg = max(mx_mg, __shfl_xor_sync(0xFFFFFFFFu, mx_mg, o));
   }
-  __syncthreads();
-  row_stats(t1, t2, A, B, m, a);
-  if (A != B) row_stats(t2, t1, B, A, m, a);
+  if (q == 0 && i < m) {
+    if (win) atomicAdd(&a.wins[i], win);
+    if (loss) atomicAdd(&a.losses[i], loss);
+    if (s_row) atomicAdd(&a.rowsum[i], (unsigned long long)s_row);
+    if (s_col) atomicAdd(&a.colsum[i], (unsigned long long)s_col);
+    if (s_wo) atomicAdd(&a.sumw_out[i], (unsigned long long)s_wo);
+    if (s_wi) atomicAdd(&a.sumw_in[i], (unsigned long long)s_wi);
+    if (mx_wo) atomicMax(&a.maxw_out[i], mx_wo);
+    if (mx_wi) atomicMax(&a.maxw_in[i], mx_wi);
+    if (mx_d) atomicMax(&a.max_drow[i], mx_d);
+    if (mn_mg != INT32_MAX) atomicMin(&a.min_margin[i], mn_mg);
+    if (mx_mg != INT32_MIN) atomicMax(&a.max_margin[i], mx_mg);
+  }
 }
 
 // f[c][0..13] from the accumulators; ranks (14, 15) are counted afterwards.
@@ -134,7 +175,7 @@ __global__ void features_finalize_kernel(Acc a, int32_t m, int64_t n, float* __r
     const double nn = double(n > 0 ? n : 1), mm = double(m - 1);
     f[0] = float(double(a.wins[c]) / mm);
     f[1] = float(double(a.losses[c]) / mm);
-    f[2] = float(double(a.ties[c]) / mm);
+    f[2] = float(double(int64_t(m - 1) - a.wins[c] - a.losses[c]) / mm);  // every other candidate: win, loss or tie
     f[3] = float(double(a.rowsum[c]) / (nn * mm));
     f[4] = float(double(a.colsum[c]) / (nn * mm));
     f[5] = float(double(a.maxw_out[c]) / nn);
@@ -392,39 +433,73 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m1, f
 
 // --------------------------------------------------------- proposals
 
-// The `top` best scores (ties: smaller id first), one CTA of 1024 threads.
+// (s, c) ranks before (s2, c2): higher score, then smaller id
+__device__ __forceinline__ bool ranks_before(float s, int32_t c, float s2, int32_t c2) {
+  return s > s2 || (s == s2 && c < c2);
+}
+
+// Pops the head of a sorted register list (static indices only).
+__device__ __forceinline__ void pop_head(float (&ls)[kMaxProposals], int32_t (&li)[kMaxProposals]) {
+#pragma unroll
+  for (int q = 0; q + 1 < kMaxProposals; ++q) ls[q] = ls[q + 1], li[q] = li[q + 1];
+  ls[kMaxProposals - 1] = -INFINITY, li[kMaxProposals - 1] = INT32_MAX;
+}
+
+// Repeated warp-wide selection of the best list head: the `top` best of the
+// 32 lanes' sorted lists, in order (lane 0 holds them in bs/bi per round).
+__device__ __forceinline__ void warp_merge(float (&ls)[kMaxProposals], int32_t (&li)[kMaxProposals], int32_t top,
+                                           float* out_s, int32_t* out_i) {
+  for (int r = 0; r < top; ++r) {
+    float bs = ls[0];
+    int32_t bi = li[0];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xFFFFFFFFu, bs, o);
+      const int32_t i2 = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+      if (ranks_before(s2, i2, bs, bi)) bs = s2, bi = i2;
+    }
+    if (bi != INT32_MAX && li[0] == bi) pop_head(ls, li);  // ids are unique: one lane pops
+    if ((threadIdx.x & 31) == 0) out_s[r] = bs, out_i[r] = bi;
+  }
+}
+
+// The `top` best scores (ties: smaller id first), -1 past the candidates;
+// one CTA: each thread keeps the best `top` of its scores in registers,
+// each warp merges its lanes' lists, warp 0 merges the warps'.
 __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ score, int32_t m, int32_t top,
                                                     int32_t* __restrict__ out) {
-  __shared__ float bs[1024];
-  __shared__ int32_t bi[1024];
-  __shared__ int32_t chosen[kMaxProposals];
-  for (int r = 0; r < top; ++r) {
-    float best = -INFINITY;
-    int32_t arg = INT32_MAX;
-    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
-      bool taken = false;
-      for (int q = 0; q < r; ++q) taken |= chosen[q] == c;
-      if (taken) continue;
-      const float s = score[c];
-      if (s > best || (s == best && c < arg)) best = s, arg = c;
-    }
-    bs[threadIdx.x] = best;
-    bi[threadIdx.x] = arg;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-      if (threadIdx.x < o) {
-        const float s2 = bs[threadIdx.x + o];
-        const int32_t i2 = bi[threadIdx.x + o];
-        if (s2 > bs[threadIdx.x] || (s2 == bs[threadIdx.x] && i2 < bi[threadIdx.x]))
-          bs[threadIdx.x] = s2, bi[threadIdx.x] = i2;
+  __shared__ float ws[32][kMaxProposals];
+  __shared__ int32_t wi[32][kMaxProposals];
+  float ls[kMaxProposals];
+  int32_t li[kMaxProposals];
+#pragma unroll
+  for (int q = 0; q < kMaxProposals; ++q) ls[q] = -INFINITY, li[q] = INT32_MAX;
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+    float s = score[c];
+    int32_t id = c;
+#pragma unroll
+    for (int q = 0; q < kMaxProposals; ++q)  // insertion: the displaced entry moves down
+      if (ranks_before(s, id, ls[q], li[q])) {
+        const float ts = ls[q];
+        const int32_t ti = li[q];
+        ls[q] = s, li[q] = id, s = ts, id = ti;
       }
-      __syncthreads();
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  warp_merge(ls, li, top, ws[wid], wi[wid]);
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < kMaxProposals; ++q) {
+      const bool ok = lane < nwarps && q < top;
+      ls[q] = ok ? ws[lane][q] : -INFINITY;
+      li[q] = ok ? wi[lane][q] : INT32_MAX;
     }
-    if (threadIdx.x == 0) {
-      chosen[r] = bi[0] == INT32_MAX ? -1 : bi[0];
-      out[r] = chosen[r];
-    }
-    __syncthreads();
+    __shared__ float fs[kMaxProposals];
+    __shared__ int32_t fi[kMaxProposals];
+    warp_merge(ls, li, top, fs, fi);
+    __syncwarp();
+    if (lane < top) out[lane] = fi[lane] == INT32_MAX ? -1 : fi[lane];
   }
 }
 
@@ -621,7 +696,6 @@ LearnedWs carve_learned(void* ws, int32_t m) {
   LearnedWs w;
   w.acc.wins = cv.take<int32_t>(m);
   w.acc.losses = cv.take<int32_t>(m);
-  w.acc.ties = cv.take<int32_t>(m);
   w.acc.rowsum = cv.take<unsigned long long>(m);
   w.acc.colsum = cv.take<unsigned long long>(m);
   w.acc.maxw_out = cv.take<int32_t>(m);
@@ -651,8 +725,7 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
   {
     Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
     acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m);
-    const int32_t nb32 = (m + 31) / 32;
-    features_pass_kernel<<<dim3(nb32, nb32), dim3(32, 8), 0, stream>>>(d, m, w.acc);
+    features_pass_kernel<<<dim3(unsigned((m + kFR - 1) / kFR), kFChunks), 256, 0, stream>>>(d, m, w.acc);
     features_finalize_kernel<<<g, 256, 0, stream>>>(w.acc, m, n, feat);
   }
   if (cudaMemsetAsync(w.cnt14, 0, size_t(m) * 4, stream) != cudaSuccess ||
