@@ -82,6 +82,7 @@ constexpr int kFlagT = 64;
 __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int64_t bound,
                                                       int32_t* __restrict__ rowflag, int32_t* status,
                                                       const int32_t* __restrict__ hint_valid) {
+  pdl_enter();
   if (hint_valid && *hint_valid) return;  // the caller's tally already knows the flags
   __shared__ int32_t t1[kFlagT][kFlagT + 1], t2[kFlagT][kFlagT + 1];  // t1 = d[A.., B..], t2 = d[B.., A..]
   const int32_t nbt = (m + kFlagT - 1) / kFlagT;
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
                                                        int32_t* __restrict__ warm_out,
                                                        const int32_t* __restrict__ hint,
                                                        const int32_t* __restrict__ hint_valid) {
+  pdl_enter();
   __shared__ uint32_t part[32];
   extern __shared__ uint32_t relabel_smem[];  // m words when m <= kScanSmem
   if (hint_valid && *hint_valid) rowflag = hint;
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const int32_t* __restrict__ d
                                                    const int32_t* __restrict__ hint,
                                                    const int32_t* __restrict__ hint_valid, int32_t* __restrict__ ucol,
                                                    int margin) {
+  pdl_enter();
   const bool hv = hint_valid && *hint_valid;
   const int32_t rows = (*warm + kB - 1) / kB * kB;  // W rows to write
   const bool uc = hv && rows < m;                    // uniform cold columns beyond the square
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
                                                     const int32_t* __restrict__ warm, int32_t* __restrict__ p,
                                                     const int32_t* __restrict__ hint_valid,
                                                     const int32_t* __restrict__ ucold) {
+  pdl_enter();
   const int32_t nw = *warm;
   const int32_t rows = (nw + kB - 1) / kB * kB;
   const bool uc = hint_valid && *hint_valid && rows < m;  // cold columns beyond the square: ucold[ix]
@@ -464,6 +468,7 @@ constexpr int32_t kClusterMaxWarm = sizeof(E) == 2 ? 256 : 192;
 template <typename E>
 __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
                                                                        Sync sy) {
+  pdl_enter();
   __shared__ __align__(16) typename Ops<E>::Smem sm;
   __shared__ __align__(16) int32_t rowbuf[2][kB];
   __shared__ int32_t s_item[4];
@@ -575,6 +580,7 @@ template <typename E>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 1)
     closure_cluster_kernel(E* __restrict__ W, int32_t ld, int32_t nb, const int32_t* __restrict__ warm,
                            uint32_t* __restrict__ prog, unsigned long long* counters) {
+  pdl_enter();
   using AW = typename std::conditional<sizeof(E) == 2, uint32_t, int2>::type;  // a row's entries k, k + 1
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -687,6 +693,7 @@ __global__ void __launch_bounds__(256) uniform_cold_kernel(const E* __restrict__
                                                            const int32_t* __restrict__ hint_valid,
                                                            const int32_t* __restrict__ ucol, int32_t* __restrict__ u,
                                                            int32_t* __restrict__ ucount) {
+  pdl_enter();
   const int32_t nw = *warm;
   const int32_t rows = (nw + kB - 1) / kB * kB;
   if (!(hint_valid && *hint_valid && rows < m)) return;
@@ -722,6 +729,7 @@ __global__ void __launch_bounds__(512, 1) cold_strip_kernel(E* __restrict__ W, i
                                                             const int32_t* __restrict__ warm,
                                                             unsigned long long* counters,
                                                             const int32_t* __restrict__ hint_valid) {
+  pdl_enter();
   using Wd = typename std::conditional<sizeof(E) == 2, uint32_t, int32_t>::type;  // one word
   constexpr int kPer = sizeof(Wd) / sizeof(E);                                  // entries per word
   const int32_t nw = *warm;
@@ -807,6 +815,7 @@ __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ 
                                                                  const uint32_t* __restrict__ prog,
                                                                  unsigned long long* counters,
                                                                  const int32_t* __restrict__ hint_valid) {
+  pdl_enter();
   __shared__ __align__(16) typename Ops<E>::Smem sm;
   if (*warm <= kClusterMaxWarm<E>) return;  // cold_strip_kernel's case
   if (hint_valid && *hint_valid && (*warm + kB - 1) / kB * kB < m) return;  // uniform cold columns
@@ -838,6 +847,7 @@ __global__ void __launch_bounds__(512) wextract_kernel(const E* __restrict__ W, 
                                                        const int32_t* __restrict__ warm, int32_t* __restrict__ bb,
                                                        const int32_t* __restrict__ hint_valid,
                                                        const int32_t* __restrict__ ucount) {
+  pdl_enter();
   constexpr int kG = 16;  // row groups
   __shared__ int32_t part[kG][33];
   const int32_t nw = *warm;
@@ -900,6 +910,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   uint32_t* abort_flag = head + 1;
   if (cudaMemsetAsync(bf.prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   if (cudaMemsetAsync(bf.rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  if (bf.ucount && cudaMemsetAsync(bf.ucount, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
   const double mm = double(m) * double(m);
   auto grid_for = [&](const void* fn, int threads, size_t smem, int64_t cap) {
     int per_sm = 1;
@@ -913,26 +924,27 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     const int64_t nbt = (m + kFlagT - 1) / kFlagT;
     const int g = grid_for(reinterpret_cast<const void*>(rowflag_kernel), 256, 0, nbt * (nbt + 1) / 2);
     Launch L(ctx, stream, "closure_rowflags", mm * 4.0);
-    rowflag_kernel<<<g, 256, 0, stream>>>(d, m, bound, bf.rowflag, status, bf.hint_valid);
+    launch_pdl(rowflag_kernel, dim3(g), dim3(256), 0, stream, false, d, m, bound, bf.rowflag, status, bf.hint_valid);
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    relabel_kernel<<<1, 1024, m <= kScanSmem ? size_t(m) * 4 : 0, stream>>>(bf.rowflag, m, bf.perm, bf.inv, bf.warm,
-                                                                          bf.hint, bf.hint_valid);
+    launch_pdl(relabel_kernel, dim3(1), dim3(1024), m <= kScanSmem ? size_t(m) * 4 : 0, stream, false,
+               static_cast<const int32_t*>(bf.rowflag), m, bf.perm, bf.inv, bf.warm, bf.hint, bf.hint_valid);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 512, 0, mp);
     Launch L(ctx, stream, "closure_pack", 0.0);
-    pack_kernel<E><<<g, 512, 0, stream>>>(d, m, mp, bf.perm, bf.warm, W, bf.prog, nb, bf.hint, bf.hint_valid,
-                                          bf.ucol, bf.margin ? 1 : 0);
+    launch_pdl(pack_kernel<E>, dim3(g), dim3(512), 0, stream, false, d, m, mp,
+               static_cast<const int32_t*>(bf.perm), static_cast<const int32_t*>(bf.warm), W, bf.prog, nb, bf.hint,
+               bf.hint_valid, bf.ucol, bf.margin ? 1 : 0);
   }
   if (int rc = check_launch()) return rc;
   {
     const size_t smem = size_t(kClusterMaxWarm<E>) * kClusterMaxWarm<E> * sizeof(E);
     cudaFuncSetAttribute(closure_cluster_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     Launch L(ctx, stream, "closure_cluster", 0.0);
-    closure_cluster_kernel<E><<<kClusterCtas, kClusterThreads, smem, stream>>>(W, mp, nb, bf.warm, bf.prog,
-                                                                               bf.counters);
+    launch_pdl(closure_cluster_kernel<E>, dim3(kClusterCtas), dim3(kClusterThreads), smem, stream, false, W, mp, nb,
+               static_cast<const int32_t*>(bf.warm), bf.prog, bf.counters);
   }
   if (int rc = check_launch()) return rc;
   {
@@ -942,10 +954,9 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     Sync sy{bf.prog, head, abort_flag, status, bf.warm, bf.counters};
     E* Wp = W;
     int32_t ldp = mp, nbp = nb;
-    void* args[] = {&Wp, &ldp, &nbp, &sy};
     Launch L(ctx, stream, "closure_persistent", double(m) * mm);
-    if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(closure_persistent_kernel<E>), dim3(grid),
-                                    dim3(kThreads), args, 0, stream) != cudaSuccess) {
+    if (launch_pdl(closure_persistent_kernel<E>, dim3(grid), dim3(kThreads), 0, stream, true, Wp, ldp, nbp, sy) !=
+        cudaSuccess) {
       cudaGetLastError();
       return SCHULZE_ECUDA;
     }
@@ -955,28 +966,34 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     const size_t smem = (cw * (cw * sizeof(E) / 4 + 1) + cw * kStripWords) * 4;
     cudaFuncSetAttribute(cold_strip_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     Launch L(ctx, stream, "closure_cold_strips", 0.0);
-    cold_strip_kernel<E><<<sms, 512, smem, stream>>>(W, mp, m, bf.warm, bf.counters, bf.hint_valid);
+    launch_pdl(cold_strip_kernel<E>, dim3(sms), dim3(512), smem, stream, false, W, mp, m,
+               static_cast<const int32_t*>(bf.warm), bf.counters, bf.hint_valid);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(cold_product_kernel<E>), kThreads, 0, int64_t(nb) * nb);
     Launch L(ctx, stream, "closure_cold", 0.0);
-    cold_product_kernel<E><<<g, kThreads, 0, stream>>>(W, mp, nb, m, bf.warm, bf.prog, bf.counters, bf.hint_valid);
+    launch_pdl(cold_product_kernel<E>, dim3(g), dim3(kThreads), 0, stream, false, W, mp, nb, m,
+               static_cast<const int32_t*>(bf.warm), static_cast<const uint32_t*>(bf.prog), bf.counters,
+               bf.hint_valid);
   }
   if (bf.hint_valid) {
-    if (cudaMemsetAsync(bf.ucount, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
     Launch L(ctx, stream, "closure_cold_uniform", 0.0);
-    uniform_cold_kernel<E><<<std::max(1, std::min(sms, (m + 7) / 8)), 256, 0, stream>>>(
-        W, mp, m, bf.warm, bf.hint_valid, bf.ucol, bf.ucold, bf.ucount);
+    launch_pdl(uniform_cold_kernel<E>, dim3(std::max(1, std::min(sms, (m + 7) / 8))), dim3(256), 0, stream, false,
+               static_cast<const E*>(W), mp, m, static_cast<const int32_t*>(bf.warm), bf.hint_valid,
+               static_cast<const int32_t*>(bf.ucol), bf.ucold, bf.ucount);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
     Launch L(ctx, stream, "closure_widen", mm * 4.0);
-    widen_kernel<E><<<g, 256, 0, stream>>>(W, mp, m, bf.inv, bf.perm, bf.warm, p, bf.hint_valid, bf.ucold);
+    launch_pdl(widen_kernel<E>, dim3(g), dim3(256), 0, stream, false, static_cast<const E*>(W), mp, m,
+               static_cast<const int32_t*>(bf.inv), static_cast<const int32_t*>(bf.perm),
+               static_cast<const int32_t*>(bf.warm), p, bf.hint_valid, static_cast<const int32_t*>(bf.ucold));
   }
   if (bb_out) {
     Launch L(ctx, stream, "closure_beaten_by", 0.0);
-    wextract_kernel<E><<<(m + 31) / 32, 512, 0, stream>>>(W, mp, m, bf.perm, bf.warm, bb_out, bf.hint_valid,
-                                                           bf.ucount);
+    launch_pdl(wextract_kernel<E>, dim3((m + 31) / 32), dim3(512), 0, stream, false, static_cast<const E*>(W), mp, m,
+               static_cast<const int32_t*>(bf.perm), static_cast<const int32_t*>(bf.warm), bb_out, bf.hint_valid,
+               static_cast<const int32_t*>(bf.ucount));
   }
   return check_launch();
 }

@@ -60,6 +60,7 @@ __global__ void winners_kernel(const int32_t* __restrict__ bb, int32_t m, int32_
 // (chunks of i, chunks of j), pos zeroed before.
 __global__ void __launch_bounds__(256) rank_count_kernel(const int32_t* __restrict__ bb, int32_t m,
                                                          int32_t* __restrict__ pos) {
+  pdl_enter();
   __shared__ int64_t keys[kRankChunk];
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t mine = i < m ? (int64_t(bb[i]) << 32) | uint32_t(i) : INT64_MAX;
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(256) rank_count_kernel(const int32_t* __restri
 // order[pos[i]] = i; with winners, also winners[i] = (bb[i] == 0).
 __global__ void rank_scatter_kernel(const int32_t* __restrict__ pos, const int32_t* __restrict__ bb, int32_t m,
                                     int32_t* __restrict__ order, int32_t* __restrict__ winners) {
+  pdl_enter();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     order[pos[i]] = i;
     if (winners) winners[i] = bb[i] == 0;
@@ -90,10 +92,12 @@ int finish(schulze_ctx* ctx, const int32_t* bb, int32_t* pos, int32_t m, int32_t
     if (cudaMemsetAsync(pos, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
     {
       Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
-      rank_count_kernel<<<dim3(g, (m + kRankChunk - 1) / kRankChunk), 256, 0, stream>>>(bb, m, pos);
+      launch_pdl(rank_count_kernel, dim3(g, (m + kRankChunk - 1) / kRankChunk), dim3(256), 0, stream, false, bb, m,
+                 pos);
     }
     Launch L(ctx, stream, "extract_order", double(m) * 8.0);
-    rank_scatter_kernel<<<g, 256, 0, stream>>>(pos, bb, m, order, winners);
+    launch_pdl(rank_scatter_kernel, dim3(g), dim3(256), 0, stream, false, static_cast<const int32_t*>(pos), bb, m,
+               order, winners);
   } else if (winners) {
     Launch L(ctx, stream, "extract_winners", double(m) * 8.0);
     winners_kernel<<<g, 256, 0, stream>>>(bb, m, winners);

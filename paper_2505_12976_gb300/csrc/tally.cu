@@ -218,6 +218,7 @@ __global__ void mirror_kernel(int32_t* __restrict__ d, int32_t m, int32_t tile, 
 template <bool kLocal>
 __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
                                     int32_t* __restrict__ cnt, int32_t* status) {
+  pdl_enter();
   extern __shared__ uint32_t smem_count[];  // [m] histogram if kLocal, then warps_per_block * words
   const int words = (m + 31) / 32;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
                                                            int32_t* __restrict__ act, int32_t* __restrict__ meta,
                                                            int32_t* __restrict__ hint,
                                                            int32_t* __restrict__ hint_valid) {
+  pdl_enter();
   __shared__ uint32_t part[32];
   extern __shared__ uint32_t plan_smem[];  // m words when m <= kScanSmem
   {
@@ -323,6 +325,7 @@ template <bool kLocal>
 __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
                                       const int32_t* __restrict__ meta) {
+  pdl_enter();
   if (meta[1]) return;  // compact form
   if (!kLocal) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -362,6 +365,7 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
 __global__ void sparse_init_split_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb, int32_t jw,
                                          const uint32_t* __restrict__ uoff, int32_t* __restrict__ d,
                                          const int32_t* __restrict__ meta) {
+  pdl_enter();
   const int32_t b = blockIdx.x, jc = blockIdx.y;
   if (meta[1] || uoff[b + 1] - uoff[b] <= 1) return;
   const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
@@ -385,6 +389,7 @@ __global__ void __launch_bounds__(512)
                         const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries,
                         const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
                         int32_t* __restrict__ d, const int32_t* __restrict__ meta) {
+  pdl_enter();
   extern __shared__ uint32_t C[];
   __shared__ uint32_t so[kMaxRowsPerBlock + 1];  // off[R0 .. R1]
   const uint32_t unit = blockIdx.x;
@@ -522,6 +527,7 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
                          const int32_t* __restrict__ cnt, const int32_t* __restrict__ slot,
                          const int32_t* __restrict__ meta, uint32_t* __restrict__ partial, int32_t stage_len,
                          int32_t* __restrict__ d) {
+  pdl_enter();
   if (!meta[1]) return;
   extern __shared__ __align__(16) uint32_t smem_pairs[];
   const int32_t na = meta[0];
@@ -697,6 +703,7 @@ template <bool kPacked>
 __global__ void __launch_bounds__(512)
     compact_fix_kernel(const uint32_t* __restrict__ partial, int32_t G, int32_t m, const int32_t* __restrict__ cnt,
                        const int32_t* __restrict__ act, const int32_t* __restrict__ meta, int32_t* __restrict__ d) {
+  pdl_enter();
   if (!meta[1]) return;
   __shared__ uint32_t red[512][2];
   const int32_t na = meta[0];
@@ -930,23 +937,28 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
     // about one ballot per warp: the pass is bound by load latency
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 15) / 16, int64_t(sms) * per_sm)));
     Launch L(ctx, stream, "tally_count", double(total) * 4.0);
-    kern<<<blocks, threads, smem, stream>>>(ranks, n, m, k, cnt, ctx->status);
+    launch_pdl(kern, dim3(blocks), dim3(threads), smem, stream, false, ranks, n, m, k, cnt, ctx->status);
   }
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
-    sparse_plan_kernel<<<1, 1024, m <= kScanSmem ? size_t(m) * 4 : 0, stream>>>(cnt, m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot,
-                                               act, meta, hint, hint_valid);
+    launch_pdl(sparse_plan_kernel, dim3(1), dim3(1024), m <= kScanSmem ? size_t(m) * 4 : 0, stream, false,
+               static_cast<const int32_t*>(cnt), m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot, act,
+               meta, hint, hint_valid);
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_pairs", double(m) * double(m) * 4.0 + double(total) * 4.0);
     auto kern = cp.packed ? compact_pairs_kernel<true> : compact_pairs_kernel<false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.smem));
-    kern<<<cp.G, kCompactThreads, cp.smem, stream>>>(ranks, n, m, k, cnt, slot, meta, partial, cp.stage, d);
+    launch_pdl(kern, dim3(cp.G), dim3(kCompactThreads), cp.smem, stream, false, ranks, n, m, k,
+               static_cast<const int32_t*>(cnt), static_cast<const int32_t*>(slot), static_cast<const int32_t*>(meta),
+               partial, int32_t(cp.stage), d);
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_fix", 0.0);
     auto kern = cp.packed ? compact_fix_kernel<true> : compact_fix_kernel<false>;
-    kern<<<std::min(cp.cmax, 2 * sms), 512, 0, stream>>>(partial, cp.G, m, cnt, act, meta, d);
+    launch_pdl(kern, dim3(std::min(cp.cmax, 2 * sms)), dim3(512), 0, stream, false,
+               static_cast<const uint32_t*>(partial), int32_t(cp.G), m, static_cast<const int32_t*>(cnt),
+               static_cast<const int32_t*>(act), static_cast<const int32_t*>(meta), d);
   }
   {
     Launch L(ctx, stream, "tally_group", double(total) * 8.0);
@@ -954,27 +966,35 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
       const size_t smem = size_t(m) * 8;
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 4095) / 4096, uint64_t(sms)));
       cudaFuncSetAttribute(sparse_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      sparse_scatter_kernel<true><<<blocks, 1024, smem, stream>>>(ranks, total, m, cursor, entries, meta);
+      launch_pdl(sparse_scatter_kernel<true>, dim3(blocks), dim3(1024), smem, stream, false, ranks, total, m, cursor,
+                 entries, static_cast<const int32_t*>(meta));
     } else {
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
-      sparse_scatter_kernel<false><<<blocks, 256, 0, stream>>>(ranks, total, m, cursor, entries, meta);
+      launch_pdl(sparse_scatter_kernel<false>, dim3(blocks), dim3(256), 0, stream, false, ranks, total, m, cursor,
+                 entries, static_cast<const int32_t*>(meta));
     }
   }
   {
     Launch L(ctx, stream, "tally_split_init", 0.0);
-    sparse_init_split_kernel<<<dim3(sp.nblocks, sp.njc), 256, 0, stream>>>(cnt, m, sp.rb, sp.jw, uoff, d, meta);
+    launch_pdl(sparse_init_split_kernel, dim3(sp.nblocks, sp.njc), dim3(256), 0, stream, false,
+               static_cast<const int32_t*>(cnt), m, sp.rb, sp.jw, static_cast<const uint32_t*>(uoff), d,
+               static_cast<const int32_t*>(meta));
   }
   if (int rc = check_launch()) return rc;
   dim3 grid(sp.max_units, sp.njc);
   Launch L(ctx, stream, "tally_rows", double(m) * double(m) * 4.0 + double(total) * 4.0);
   if (sp.packed) {
     cudaFuncSetAttribute(sparse_units_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    sparse_units_kernel<true><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
-                                                               sp.emax, sp.rb, sp.jw, d, meta);
+    launch_pdl(sparse_units_kernel<true>, grid, dim3(512), sp.smem, stream, false, ranks, m, k,
+               static_cast<const int32_t*>(cnt), static_cast<const uint32_t*>(off),
+               static_cast<const uint32_t*>(entries), static_cast<const uint32_t*>(uoff), int32_t(sp.nblocks), sp.emax,
+               int32_t(sp.rb), int32_t(sp.jw), d, static_cast<const int32_t*>(meta));
   } else {
     cudaFuncSetAttribute(sparse_units_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    sparse_units_kernel<false><<<grid, 512, sp.smem, stream>>>(ranks, m, k, cnt, off, entries, uoff, sp.nblocks,
-                                                                sp.emax, sp.rb, sp.jw, d, meta);
+    launch_pdl(sparse_units_kernel<false>, grid, dim3(512), sp.smem, stream, false, ranks, m, k,
+               static_cast<const int32_t*>(cnt), static_cast<const uint32_t*>(off),
+               static_cast<const uint32_t*>(entries), static_cast<const uint32_t*>(uoff), int32_t(sp.nblocks), sp.emax,
+               int32_t(sp.rb), int32_t(sp.jw), d, static_cast<const int32_t*>(meta));
   }
   return check_launch();
 }
