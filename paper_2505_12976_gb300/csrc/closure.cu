@@ -908,9 +908,14 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   E* W = static_cast<E*>(bf.W);
   uint32_t* head = bf.prog + size_t(nb) * size_t(nb);
   uint32_t* abort_flag = head + 1;
-  if (cudaMemsetAsync(bf.prog, 0, (size_t(nb) * nb + 2) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  if (cudaMemsetAsync(bf.rowflag, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  if (bf.ucount && cudaMemsetAsync(bf.ucount, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+  {
+    // progress words, queue head and abort flag; row flags; the uniform count
+    ZeroSpans z;
+    z.p[0] = bf.prog, z.words[0] = int64_t(nb) * nb + 2;
+    z.p[1] = reinterpret_cast<uint32_t*>(bf.rowflag), z.words[1] = m;
+    z.p[2] = reinterpret_cast<uint32_t*>(bf.ucount), z.words[2] = 1;
+    if (int rc = zero_async(ctx, z, stream)) return rc;
+  }
   const double mm = double(m) * double(m);
   auto grid_for = [&](const void* fn, int threads, size_t smem, int64_t cap) {
     int per_sm = 1;

@@ -89,7 +89,9 @@ int finish(schulze_ctx* ctx, const int32_t* bb, int32_t* pos, int32_t m, int32_t
            cudaStream_t stream) {
   const int g = (m + 255) / 256;
   if (order) {
-    if (cudaMemsetAsync(pos, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+    ZeroSpans z;
+    z.p[0] = reinterpret_cast<uint32_t*>(pos), z.words[0] = m;
+    if (int rc = zero_async(ctx, z, stream)) return rc;
     {
       Launch L(ctx, stream, "extract_rank", double(m) * 8.0);
       launch_pdl(rank_count_kernel, dim3(g, (m + kRankChunk - 1) / kRankChunk), dim3(256), 0, stream, false, bb, m,

@@ -181,6 +181,15 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Zeroes up to four spans of 32-bit words in one kernel launched with
+// launch_pdl (where a memset would end the programmatic chain); spans with a
+// null pointer or no words are skipped.
+struct ZeroSpans {
+  uint32_t* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t words[4] = {0, 0, 0, 0};
+};
+int zero_async(schulze_ctx* ctx, const ZeroSpans& z, cudaStream_t stream);
+
 inline int check_launch() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;

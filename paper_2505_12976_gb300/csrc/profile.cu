@@ -1,6 +1,9 @@
-// Launch accounting, optional per-kernel event timing, and the integer
-// min/max issue-rate probe (include/schulze_profile.h).
+// Launch accounting, optional per-kernel event timing, the zeroing kernel
+// of the path's scratch, and the integer min/max issue-rate probe
+// (include/schulze_profile.h).
 #include <string.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -68,6 +71,36 @@ static void drain(schulze_ctx* ctx) {
     ctx->prof_free_events.push_back(r.stop);
   }
   ctx->prof_pending.clear();
+}
+
+// ----------------------------------------------------------- zeroing
+
+namespace {
+__global__ void __launch_bounds__(256) zero_kernel(ZeroSpans z) {
+  pdl_enter();
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < z.words[s]; i += stride) z.p[s][i] = 0u;
+}
+}  // namespace
+
+int zero_async(schulze_ctx* ctx, const ZeroSpans& z, cudaStream_t stream) {
+  int64_t most = 0;
+  for (int s = 0; s < 4; ++s)
+    if (z.p[s]) most = std::max(most, z.words[s]);
+  if (most == 0) return SCHULZE_OK;
+  const int sms = ctx && ctx->sm_count > 0 ? ctx->sm_count : 148;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>((most + 255) / 256, int64_t(sms) * 4)));
+  ZeroSpans zz = z;
+  for (int s = 0; s < 4; ++s)
+    if (!zz.p[s]) zz.words[s] = 0;
+  Launch L(ctx, stream, "zero", double(most) * 4.0);
+  if (launch_pdl(zero_kernel, dim3(grid), dim3(256), 0, stream, false, zz) != cudaSuccess) {
+    cudaGetLastError();
+    return SCHULZE_ECUDA;
+  }
+  return SCHULZE_OK;
 }
 
 // ----------------------------------------------------------- probe

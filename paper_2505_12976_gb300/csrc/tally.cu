@@ -896,7 +896,10 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
                  uint32_t flags, void* ws, cudaStream_t stream, int32_t* hint, int32_t* hint_valid) {
   const size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
-  if (hint && cudaMemsetAsync(hint_valid, 0, sizeof(int32_t), stream) != cudaSuccess) return SCHULZE_ECUDA;
+  const bool sparse_path = n > 0 && k > 0 && !choose_dense(n, m, k, flags);
+  // (the sparse path clears hint_valid with its counters)
+  if (hint && !sparse_path && cudaMemsetAsync(hint_valid, 0, sizeof(int32_t), stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
   if (n == 0 || k == 0) {
     return cudaMemsetAsync(d, 0, mm, stream) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
   }
@@ -924,7 +927,12 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   int32_t* meta = cv.take<int32_t>(2);
   const CompactPlan cp = compact_plan(n, m, k, sms, flags);
   uint32_t* partial = cv.take<uint32_t>(cp.partial_words);
-  if (cudaMemsetAsync(cnt, 0, size_t(m) * 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  {
+    ZeroSpans z;
+    z.p[0] = reinterpret_cast<uint32_t*>(cnt), z.words[0] = m;
+    z.p[1] = reinterpret_cast<uint32_t*>(hint_valid), z.words[1] = hint ? 1 : 0;
+    if (int rc = zero_async(ctx, z, stream)) return rc;
+  }
   const bool local_hist = m <= kLocalHistMax;
   {
     const int threads = 512;
