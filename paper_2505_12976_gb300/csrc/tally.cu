@@ -526,9 +526,22 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
     compact_pairs_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
                          const int32_t* __restrict__ cnt, const int32_t* __restrict__ slot,
                          const int32_t* __restrict__ meta, uint32_t* __restrict__ partial, int32_t stage_len,
-                         int32_t* __restrict__ d) {
+                         int32_t* __restrict__ d, int32_t rb, int32_t nblocks, const uint32_t* __restrict__ uoff) {
   pdl_enter();
-  if (!meta[1]) return;
+  if (!meta[1]) {
+    // the grouped form runs instead: this launch starts its split row blocks
+    // (the work of sparse_init_split_kernel, whole rows per CTA pass)
+    for (int32_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+      if (uoff[b + 1] - uoff[b] <= 1) continue;
+      const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
+      for (int32_t r = R0; r < R1; ++r) {
+        const int32_t base = cnt[r];
+        int32_t* drow = d + int64_t(r) * m;
+        for (int32_t j = threadIdx.x; j < m; j += blockDim.x) drow[j] = (j == r) ? 0 : base;
+      }
+    }
+    return;
+  }
   extern __shared__ __align__(16) uint32_t smem_pairs[];
   const int32_t na = meta[0];
   const int32_t wpr = kPacked ? (na + 1) >> 1 : na;
@@ -959,7 +972,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.smem));
     launch_pdl(kern, dim3(cp.G), dim3(kCompactThreads), cp.smem, stream, false, ranks, n, m, k,
                static_cast<const int32_t*>(cnt), static_cast<const int32_t*>(slot), static_cast<const int32_t*>(meta),
-               partial, int32_t(cp.stage), d);
+               partial, int32_t(cp.stage), d, int32_t(sp.rb), int32_t(sp.nblocks), static_cast<const uint32_t*>(uoff));
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_fix", 0.0);
@@ -982,7 +995,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
                  entries, static_cast<const int32_t*>(meta));
     }
   }
-  {
+  if (cp.cmax == 0) {  // else the compact kernel starts the split rows when the grouped form runs
     Launch L(ctx, stream, "tally_split_init", 0.0);
     launch_pdl(sparse_init_split_kernel, dim3(sp.nblocks, sp.njc), dim3(256), 0, stream, false,
                static_cast<const int32_t*>(cnt), m, sp.rb, sp.jw, static_cast<const uint32_t*>(uoff), d,
