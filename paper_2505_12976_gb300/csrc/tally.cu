@@ -271,7 +271,12 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
 //    emax of its entries; uoff[b] is the exclusive scan of nu_b.
 //  * slot[c]: index of c among the listed candidates (-1 if unlisted), act
 //    the inverse, meta[0] = |A| and meta[1] = 1 when the compact form runs
-//    (|A| <= compact_max).
+//    (|A| <= compact_max). For the compact form the slots follow decreasing
+//    cnt (ties by id): ballots drawn around a common order then list, in
+//    their first positions, candidates whose slots lie close together, and
+//    the pair counts of one position land in distinct shared-memory banks
+//    (each slot of a 16-bit-packed row takes its own word in the first half
+//    of the slots, see compact_pairs_kernel).
 __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb,
                                                            int32_t nblocks, uint32_t emax, uint32_t* __restrict__ off,
                                                            uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff,
@@ -282,27 +287,67 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
   pdl_enter();
   __shared__ uint32_t part[32];
   extern __shared__ uint32_t plan_smem[];  // m words when m <= kScanSmem
+  // the counts are read once: the first kHeld per thread stay in registers,
+  // the rest (lists longer than kHeld * 1024 candidates) are re-read
+  constexpr int kHeld = 8;
+  int32_t held[kHeld];
+#pragma unroll
+  for (int h = 0; h < kHeld; ++h) {
+    const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
+    held[h] = c < m ? cnt[c] : 0;
+  }
+  auto each = [&](auto&& f) {  // f(c, cnt[c]) for this thread's candidates
+#pragma unroll
+    for (int h = 0; h < kHeld; ++h) {
+      const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
+      if (c < m) f(c, held[h]);
+    }
+    for (int32_t c = int32_t(threadIdx.x) + kHeld * int32_t(blockDim.x); c < m; c += blockDim.x) f(c, cnt[c]);
+  };
   {
     // listed flags scanned into the slots (in shared memory, or in place in
     // slot for long candidate lists)
     uint32_t* flag = m <= kScanSmem ? plan_smem : reinterpret_cast<uint32_t*>(slot);
-    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) flag[c] = cnt[c] > 0 ? 1u : 0u;
+    each([&](int32_t c, int32_t x) { flag[c] = x > 0 ? 1u : 0u; });
     __syncthreads();
     const uint32_t na = block_exclusive_scan(flag, m, part);
-    for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
-      const int32_t s = cnt[c] > 0 ? int32_t(flag[c]) : -1;
-      slot[c] = s;
-      if (s >= 0) act[s] = c;
+    const bool compact = int32_t(na) <= compact_max;
+    // compact: listed ids in id order, and their order keys (count, then
+    // the complement of the index, so that a larger key goes first)
+    __shared__ int32_t lid[kCompactMaxPacked];
+    __shared__ unsigned long long lkey[kCompactMaxPacked];
+    // slots, and the closure's warm flags (the listed candidates, valid when
+    // one is never listed)
+    each([&](int32_t c, int32_t x) {
+      const int32_t s = x > 0 ? int32_t(flag[c]) : -1;
+      if (compact && s >= 0) {
+        lid[s] = c, lkey[s] = (static_cast<unsigned long long>(x) << 32) | uint32_t(~s);  // slot, act below
+      } else {
+        slot[c] = s;
+        if (s >= 0) act[s] = c;
+      }
+      if (hint) hint[c] = x > 0 ? 1 : 0;
+    });
+    if (threadIdx.x == 0) {
+      meta[0] = int32_t(na), meta[1] = compact ? 1 : 0;
+      if (hint) *hint_valid = int32_t(na) < m ? 1 : 0;
     }
-    if (threadIdx.x == 0) meta[0] = int32_t(na), meta[1] = int32_t(na) <= compact_max ? 1 : 0;
-    if (hint) {  // warm flags for the closure: the listed candidates, when one is never listed
-      for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hint[c] = cnt[c] > 0 ? 1 : 0;
-      if (threadIdx.x == 0) *hint_valid = int32_t(na) < m ? 1 : 0;
+    if (compact) {  // the compact form needs no grouping plan, only its slot order
+      static_assert(kCompactMaxPacked >= kCompactMaxWide && kCompactMaxPacked * 4 <= 1024, "4 threads per slot");
+      __syncthreads();
+      const int32_t s = int32_t(threadIdx.x >> 2), q = int32_t(threadIdx.x & 3);
+      const unsigned long long ks = s < int32_t(na) ? lkey[s] : ~0ull;
+      int32_t r = 0;  // listed candidates ahead of lid[s]: larger count, or equal count and smaller id
+#pragma unroll 8
+      for (int32_t j = q; j < int32_t(na); j += 4) r += lkey[j] > ks ? 1 : 0;
+      r += __shfl_xor_sync(0xFFFFFFFFu, r, 1);
+      r += __shfl_xor_sync(0xFFFFFFFFu, r, 2);
+      if (s < int32_t(na) && q == 0) slot[lid[s]] = r, act[r] = lid[s];
+      return;
     }
-    if (int32_t(na) <= compact_max) return;  // the compact form needs no grouping plan
     __syncthreads();
   }
-  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) off[c] = uint32_t(cnt[c]);
+  each([&](int32_t c, int32_t x) { off[c] = uint32_t(x); });
   __syncthreads();
   const uint32_t total = block_exclusive_scan(off, m, part);
   if (threadIdx.x == 0) off[m] = total;
@@ -495,8 +540,10 @@ __global__ void __launch_bounds__(512)
 //     cnt[i] for listed i and j != i, else 0 (stores, bound by HBM);
 // (b) the others count C over A x A for the slice in shared memory (cell
 //     [slot i][slot j], 16-bit lanes packed two per word when a slice has at
-//     most 65535 ballots, else 32-bit; bound by shared-memory atomics) and
-//     store it as this CTA's partial.
+//     most 65535 ballots, slot j < hw in the low half of word j and slot
+//     j >= hw in the high half of word j - hw, hw = ceil(|A| / 2) words per
+//     row; else 32-bit; bound by shared-memory atomics) and store it as this
+//     CTA's partial.
 // Counting: a warp per ballot, its slots staged in shared memory; for every
 // position q the lanes add 1 to C[slot at q][slot at p] for p < q, so the
 // lanes of one atomic always hit distinct counters (ballots drawn around a
@@ -513,12 +560,20 @@ __device__ __forceinline__ void red_shared_if(bool p, uint32_t addr, uint32_t v)
       : "memory");
 }
 
+// Counter of slot sp in a row: 16-bit packed, slot sp < hw in the low half
+// of word sp, slot sp >= hw in the high half of word sp - hw (hw = words per
+// row), so that nearby slots take distinct words; else word sp.
 template <bool kPacked>
-__device__ __forceinline__ void count_pair(uint32_t* crow, uint32_t sp) {
-  if (kPacked)
-    atomicAdd(crow + (sp >> 1), 1u << ((sp & 1u) * 16u));
-  else
-    atomicAdd(crow + sp, 1u);
+__device__ __forceinline__ uint32_t slot_word(uint32_t sp, uint32_t hw) {
+  return kPacked ? (sp < hw ? sp : sp - hw) : sp;
+}
+template <bool kPacked>
+__device__ __forceinline__ uint32_t slot_inc(uint32_t sp, uint32_t hw) {
+  return kPacked ? (sp < hw ? 1u : 0x10000u) : 1u;
+}
+template <bool kPacked>
+__device__ __forceinline__ void count_pair(uint32_t* crow, uint32_t sp, uint32_t hw) {
+  atomicAdd(crow + slot_word<kPacked>(sp, hw), slot_inc<kPacked>(sp, hw));
 }
 
 template <bool kPacked>
@@ -545,6 +600,7 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
   extern __shared__ __align__(16) uint32_t smem_pairs[];
   const int32_t na = meta[0];
   const int32_t wpr = kPacked ? (na + 1) >> 1 : na;
+  const uint32_t hw = uint32_t(wpr);
   const int32_t words = na * wpr;
   uint32_t* C = smem_pairs;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -607,8 +663,8 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         if (__all_sync(kAll, clean)) {  // every id valid (the usual case): no per-entry checks
           // shared-memory byte addresses of this lane's counters in row 0 and
           // the row stride; each add is a predicated reduction (no branch)
-          const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
-          const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+          const uint32_t w0 = slot_word<kPacked>(r0, hw), w1 = slot_word<kPacked>(r1, hw);
+          const uint32_t i0 = slot_inc<kPacked>(r0, hw), i1 = slot_inc<kPacked>(r1, hw);
           const uint32_t cbase = uint32_t(__cvta_generic_to_shared(C)), rstride = uint32_t(wpr) * 4u;
           const uint32_t a0 = cbase + w0 * 4u, a1 = cbase + w1 * 4u;
 #pragma unroll 4
@@ -627,14 +683,14 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         for (int32_t q = 1; q < qlo; ++q) {  // rows 1..31: lanes p < q
           const uint32_t sq = __shfl_sync(kAll, r0, q);
           if (sq == kNoSlot) continue;  // uniform over the warp
-          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0);
+          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0, hw);
         }
         for (int32_t q = 32; q < qhi; ++q) {  // rows 32..63: all low lanes, high lanes p < q
           const uint32_t sq = __shfl_sync(kAll, r1, q - 32);
           if (sq == kNoSlot) continue;
           uint32_t* crow = C + int32_t(sq) * wpr;
-          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
-          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0, hw);
+          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1, hw);
         }
       }
     } else {
@@ -655,8 +711,8 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         bool clean = (lane >= k || r0 != kNoSlot) && (lane + 32 >= k || r1 != kNoSlot);
         for (int32_t q = 64 + lane; q < k; q += 32) clean &= st[q] != kNoSlot;
         if (__all_sync(0xFFFFFFFFu, clean)) {  // every id valid (the usual case): no per-entry checks
-          const uint32_t w0 = kPacked ? r0 >> 1 : r0, w1 = kPacked ? r1 >> 1 : r1;
-          const uint32_t i0 = kPacked ? 1u << ((r0 & 1u) * 16u) : 1u, i1 = kPacked ? 1u << ((r1 & 1u) * 16u) : 1u;
+          const uint32_t w0 = slot_word<kPacked>(r0, hw), w1 = slot_word<kPacked>(r1, hw);
+          const uint32_t i0 = slot_inc<kPacked>(r0, hw), i1 = slot_inc<kPacked>(r1, hw);
 #pragma unroll 4
           for (int32_t q = 1; q < qlo; ++q) {
             const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
@@ -672,7 +728,7 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
             uint32_t* crow = C + int32_t(st[q]) * wpr;
             atomicAdd(crow + w0, i0);
             atomicAdd(crow + w1, i1);
-            for (int32_t p = 64 + lane; p < q; p += 32) count_pair<kPacked>(crow, st[p]);
+            for (int32_t p = 64 + lane; p < q; p += 32) count_pair<kPacked>(crow, st[p], hw);
           }
           __syncwarp();
           continue;
@@ -680,24 +736,24 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         for (int32_t q = 1; q < qlo; ++q) {  // rows 1..31: lanes p < q
           const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r0, q);
           if (sq == kNoSlot) continue;  // uniform over the warp
-          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0);
+          if (lane < q && r0 != kNoSlot) count_pair<kPacked>(C + int32_t(sq) * wpr, r0, hw);
         }
         for (int32_t q = 32; q < qhi; ++q) {  // rows 32..63: all low lanes, high lanes p < q
           const uint32_t sq = __shfl_sync(0xFFFFFFFFu, r1, q - 32);
           if (sq == kNoSlot) continue;
           uint32_t* crow = C + int32_t(sq) * wpr;
-          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
-          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0, hw);
+          if (lane + 32 < q && r1 != kNoSlot) count_pair<kPacked>(crow, r1, hw);
         }
         for (int32_t q = 64; q < k; ++q) {  // long ballots
           const uint32_t sq = st[q];
           if (sq == kNoSlot) continue;
           uint32_t* crow = C + int32_t(sq) * wpr;
-          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0);
-          if (r1 != kNoSlot) count_pair<kPacked>(crow, r1);
+          if (r0 != kNoSlot) count_pair<kPacked>(crow, r0, hw);
+          if (r1 != kNoSlot) count_pair<kPacked>(crow, r1, hw);
           for (int32_t p = 64 + lane; p < q; p += 32) {
             const uint32_t sp = st[p];
-            if (sp != kNoSlot) count_pair<kPacked>(crow, sp);
+            if (sp != kNoSlot) count_pair<kPacked>(crow, sp, hw);
           }
         }
         __syncwarp();
@@ -760,9 +816,9 @@ __global__ void __launch_bounds__(512)
       const int32_t i = act[a];
       const int32_t base = cnt[i];
       int32_t* drow = d + int64_t(i) * m;
-      const int32_t b0 = kPacked ? 2 * int32_t(threadIdx.x) : int32_t(threadIdx.x);
+      const int32_t b0 = int32_t(threadIdx.x), b1 = b0 + wpr;  // word w: slots w and w + wpr (packed)
       if (b0 != a) drow[act[b0]] = base - int32_t(lo);
-      if (kPacked && b0 + 1 < na && b0 + 1 != a) drow[act[b0 + 1]] = base - int32_t(hi);
+      if (kPacked && b1 < na && b1 != a) drow[act[b1]] = base - int32_t(hi);
     }
     __syncthreads();
   }
