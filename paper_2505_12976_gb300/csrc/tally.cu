@@ -551,13 +551,11 @@ __global__ void __launch_bounds__(512)
 // [0, m) are skipped (the count pass reports them).
 constexpr int kFillWarps = 4;
 
-// *addr += v at a shared-memory byte address when p holds (predicated
-// reduction, no branch)
-__device__ __forceinline__ void red_shared_if(bool p, uint32_t addr, uint32_t v) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], %2;\n\t}" ::"r"(uint32_t(p)),
-      "r"(addr), "r"(v)
-      : "memory");
+// *addr += v at a shared-memory byte address. Always issued: a predicated
+// shared-memory reduction costs about two extra branch-unit instructions,
+// so lanes with nothing to count add to a word of their own instead.
+__device__ __forceinline__ void red_shared(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
 // Counter of slot sp in a row: 16-bit packed, slot sp < hw in the low half
@@ -662,21 +660,24 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
         const bool clean = (lane >= k || r0 != kNoSlot) && (lane + 32 >= k || r1 != kNoSlot);
         if (__all_sync(kAll, clean)) {  // every id valid (the usual case): no per-entry checks
           // shared-memory byte addresses of this lane's counters in row 0 and
-          // the row stride; each add is a predicated reduction (no branch)
+          // the row stride; a lane not above position q adds to its own word
+          // of the (here unused) staging area instead (distinct banks, no
+          // branch)
           const uint32_t w0 = slot_word<kPacked>(r0, hw), w1 = slot_word<kPacked>(r1, hw);
           const uint32_t i0 = slot_inc<kPacked>(r0, hw), i1 = slot_inc<kPacked>(r1, hw);
           const uint32_t cbase = uint32_t(__cvta_generic_to_shared(C)), rstride = uint32_t(wpr) * 4u;
           const uint32_t a0 = cbase + w0 * 4u, a1 = cbase + w1 * 4u;
+          const uint32_t sink = uint32_t(__cvta_generic_to_shared(stage)) + uint32_t(lane) * 4u;
 #pragma unroll 4
           for (int32_t q = 1; q < qlo; ++q) {
             const uint32_t sq = __shfl_sync(kAll, r0, q);
-            red_shared_if(lane < q, a0 + sq * rstride, i0);
+            red_shared(lane < q ? a0 + sq * rstride : sink, i0);
           }
 #pragma unroll 4
           for (int32_t q = 32; q < qhi; ++q) {
             const uint32_t row = __shfl_sync(kAll, r1, q - 32) * rstride;
-            red_shared_if(true, a0 + row, i0);
-            red_shared_if(lane + 32 < q, a1 + row, i1);
+            red_shared(a0 + row, i0);
+            red_shared(lane + 32 < q ? a1 + row : sink, i1);
           }
           continue;
         }
