@@ -231,6 +231,39 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
   __syncthreads();
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  if (k <= 64) {
+    // ballots of at most 64 positions: a lane holds positions lane and
+    // lane + 32 in registers (also for clearing the bitmap), and the next
+    // ballot's ids are loaded while this one is checked and counted
+    auto ids = [&](int64_t u, int32_t& a, int32_t& b) {
+      a = (u < n && lane < k) ? ranks[u * k + lane] : -1;
+      b = (u < n && lane + 32 < k) ? ranks[u * k + lane + 32] : -1;
+    };
+    int32_t xa, xb;
+    ids(warp, xa, xb);
+    for (int64_t v = warp; v < n; v += nwarps) {
+      const int32_t ca = xa, cb = xb;
+      ids(v + nwarps, xa, xb);
+      const bool pa = lane < k, pb = lane + 32 < k;
+      const bool oka = pa && ca >= 0 && ca < m, okb = pb && cb >= 0 && cb < m;
+      const uint32_t bita = 1u << (ca & 31), bitb = 1u << (cb & 31);
+      const uint32_t olda = oka ? atomicOr(&bm[ca >> 5], bita) : 0u;
+      const uint32_t oldb = okb ? atomicOr(&bm[cb >> 5], bitb) : 0u;
+      const bool fa = oka && !(olda & bita), fb = okb && !(oldb & bitb);  // first occurrences
+      if ((pa && !fa) || (pb && !fb)) set_status(status, SCHULZE_EDATA);  // out of range or repeated
+      if (kLocal) {
+        if (fa) atomicAdd(&hist[ca], 1u);
+        if (fb) atomicAdd(&hist[cb], 1u);
+      } else {
+        if (fa) atomicAdd(&cnt[ca], 1);
+        if (fb) atomicAdd(&cnt[cb], 1);
+      }
+      __syncwarp();
+      if (oka) bm[ca >> 5] = 0u;  // clear what this ballot set
+      if (okb) bm[cb >> 5] = 0u;
+      __syncwarp();
+    }
+  } else
   for (int64_t v = warp; v < n; v += nwarps) {
     const int32_t* row = ranks + v * k;
     for (int32_t q0 = 0; q0 < k; q0 += kWarp) {

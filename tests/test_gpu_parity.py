@@ -483,6 +483,35 @@ def test_tally_positions_many_ballots_and_order_form():
     eq(host(S.schulze_tally_positions(cu(pos))), host(S.schulze_tally(cu(r), m)), "positions vs order form")
 
 
+def test_tally_rejects_bad_ids_in_long_ballots():
+    """Repeated or out-of-range ids anywhere in ballots of 33 to 64
+    positions (each lane of the count pass holds two positions): a repeat
+    inside the first 32 positions, across the two halves, inside the second
+    half, and an out-of-range id in the second half are each reported; the
+    clean ballots around them tally as the oracle says."""
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    m, n = 300, 3000
+    for k in (33, 50, 64):
+        good = W.mallows(600 + k, n, m, k, 0.9)
+        S.schulze_tally(cu(good), m, flags=S.F_TALLY_SPARSE)
+        assert ctx.status() == S.OK, k
+        eq(host(S.schulze_tally(cu(good), m, flags=S.F_TALLY_SPARSE)), oracle.tally(good, m), f"clean k={k}")
+        for a, b in ((3, 17), (5, 40), (35, k - 1), (0, 32)):
+            if max(a, b) >= k:
+                continue
+            bad = good.copy()
+            bad[n // 2, b] = bad[n // 2, a]
+            S.schulze_tally(cu(bad), m, flags=S.F_TALLY_SPARSE)
+            assert ctx.status() == S.EDATA, (k, a, b)
+        bad = good.copy()
+        bad[n - 1, k - 1] = m + 1
+        S.schulze_tally(cu(bad), m, flags=S.F_TALLY_SPARSE)
+        assert ctx.status() == S.EDATA, k
+        S.schulze_tally(cu(good), m, flags=S.F_TALLY_SPARSE)
+        assert ctx.status() == S.OK, k
+
+
 def test_tally_positions_rejects_out_of_range():
     ctx = S.context()
     assert ctx.status() == S.OK
