@@ -150,17 +150,16 @@ __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict_
 }
 
 // Stable partition: perm[new] = old, candidates with edges first; inv[old] = new.
-// The flags come from rowflag_kernel, or from the tally (hint) when it set
-// *hint_valid.
+// The flags come from rowflag_kernel; when the tally set *hint_valid it has
+// written the relabeling of its own flags already, and this launch returns.
 __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict__ rowflag, int32_t m,
                                                        int32_t* __restrict__ perm, int32_t* __restrict__ inv,
                                                        int32_t* __restrict__ warm_out,
-                                                       const int32_t* __restrict__ hint,
                                                        const int32_t* __restrict__ hint_valid) {
   pdl_enter();
   __shared__ uint32_t part[32];
   extern __shared__ uint32_t relabel_smem[];  // m words when m <= kScanSmem
-  if (hint_valid && *hint_valid) rowflag = hint;
+  if (hint_valid && *hint_valid) return;
   // rank[c] = 1 for warm c, scanned into the warm rank (in shared memory, or
   // in place in inv for long candidate lists)
   uint32_t* rank = m <= kScanSmem ? relabel_smem : reinterpret_cast<uint32_t*>(inv);
@@ -934,7 +933,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
     launch_pdl(relabel_kernel, dim3(1), dim3(1024), m <= kScanSmem ? size_t(m) * 4 : 0, stream, false,
-               static_cast<const int32_t*>(bf.rowflag), m, bf.perm, bf.inv, bf.warm, bf.hint, bf.hint_valid);
+               static_cast<const int32_t*>(bf.rowflag), m, bf.perm, bf.inv, bf.warm, bf.hint_valid);
   }
   {
     const int g = grid_for(reinterpret_cast<const void*>(pack_kernel<E>), 512, 0, mp);
@@ -1005,7 +1004,7 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
 
 template <typename E>
 int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
-                cudaStream_t stream, int32_t* bb_out, const int32_t* hint, const int32_t* hint_valid,
+                cudaStream_t stream, int32_t* bb_out, int32_t* hint, const int32_t* hint_valid,
                 bool margin) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
@@ -1017,6 +1016,11 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   bf.perm = cv.take<int32_t>(size_t(m));
   bf.inv = cv.take<int32_t>(size_t(m));
   bf.warm = cv.take<int32_t>(1);
+  if (hint) {  // the relabeling lives with the tally's flags (written there when they are valid)
+    bf.perm = hint + m;
+    bf.inv = hint + 2 * size_t(m);
+    bf.warm = hint + 3 * size_t(m);
+  }
   bf.ucol = cv.take<int32_t>(size_t(m));
   bf.ucold = cv.take<int32_t>(size_t(m));
   bf.ucount = cv.take<int32_t>(1);
@@ -1038,7 +1042,7 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
 }
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
-                   void* ws, cudaStream_t stream, int32_t* beaten_by, const int32_t* hint,
+                   void* ws, cudaStream_t stream, int32_t* beaten_by, int32_t* hint,
                    const int32_t* hint_valid) {
   const bool margin = (flags & SCHULZE_F_MARGIN) != 0;
   if (use_s16(bound, flags))

@@ -167,12 +167,14 @@ int schulze_reserve(schulze_ctx* ctx, int32_t m_max, int64_t n_max, int32_t k_ma
                                tally_workspace_bytes(n_max, m_max, k_max, SCHULZE_F_TALLY_SPARSE)));
   size_t c = std::max(closure_workspace_bytes(m_max, n_max, 0), closure_workspace_bytes(m_max, 1, 0));
   size_t x = extract_workspace_bytes(m_max);
-  // schulze_run keeps the tally's warm flags and beaten_by after the stages
-  const size_t mv = align_up(size_t(m_max) * 4, 256);
-  size_t need = std::max(align_up(std::max(t, c), 256) + 2 * mv + 256, x);
-  // schulze_run_host keeps ranks, d, p and four vectors next to the stages
+  // schulze_run keeps the tally's warm flags (with their relabeling) and
+  // beaten_by after the stages
+  const size_t mv = align_up(size_t(m_max) * 4, 256), hv = align_up(hint_words(m_max) * 4, 256);
+  size_t need = std::max(align_up(std::max(t, c), 256) + hv + mv + 256, x);
+  // schulze_run_host keeps ranks, d, p, three vectors and the hint words
+  // next to the stages
   size_t host_path = align_up(size_t(n_max) * size_t(k_max) * 4, 256) +
-                     2 * align_up(size_t(m_max) * size_t(m_max) * 4, 256) + 4 * mv + 256 + need + 4096;
+                     2 * align_up(size_t(m_max) * size_t(m_max) * 4, 256) + 3 * mv + hv + 512 + need + 4096;
   need = std::max(need, host_path);
   int rc = ensure_workspace(ctx, need, nullptr);
   if (rc) return rc;
@@ -290,15 +292,15 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
   // closure's scratch when the caller does not want it
   // warm flags from the tally and the closure's beaten_by live after both
   // stages' scratch
-  const size_t mv = align_up(size_t(m) * 4, 256);
+  const size_t mv = align_up(size_t(m) * 4, 256), hv = align_up(hint_words(m) * 4, 256);
   const size_t keep = std::max(align_up(tally_workspace_bytes(n, m, k, flags), 256),
                                align_up(closure_workspace_bytes(m, n, flags), 256));
-  size_t need = std::max(keep + 2 * mv + 256, extract_workspace_bytes(m));
+  size_t need = std::max(keep + hv + mv + 256, extract_workspace_bytes(m));
   if (int rc = ensure_workspace(ctx, need, stream)) return rc;
   char* tail = static_cast<char*>(ctx->ws.base) + keep;
   int32_t* hint = reinterpret_cast<int32_t*>(tail);
-  int32_t* hint_valid = reinterpret_cast<int32_t*>(tail + mv);
-  int32_t* bb = beaten_by ? beaten_by : reinterpret_cast<int32_t*>(tail + mv + 256);
+  int32_t* hint_valid = reinterpret_cast<int32_t*>(tail + hv);
+  int32_t* bb = beaten_by ? beaten_by : reinterpret_cast<int32_t*>(tail + hv + 256);
   if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream, hint, hint_valid)) return rc;
   const bool ext = winners || order || beaten_by;
   if (int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream, ext ? bb : nullptr, hint, hint_valid))
@@ -318,7 +320,8 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
   size_t stage = std::max(tally_workspace_bytes(n, m, k, flags),
                           std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
-  size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + 4 * align_up(size_t(m) * 4, 256) + 256;
+  size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + 3 * align_up(size_t(m) * 4, 256) +
+                align_up(hint_words(m) * 4, 256) + 512;
   if (int rc = ensure_workspace(ctx, head + stage + 4096, stream)) return rc;
   Carver cv(ctx->ws.base);
   int32_t* ranks = cv.take<int32_t>(size_t(n) * size_t(k));
@@ -327,7 +330,7 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   int32_t* win = cv.take<int32_t>(size_t(m));
   int32_t* ord = cv.take<int32_t>(size_t(m));
   int32_t* bb = cv.take<int32_t>(size_t(m));
-  int32_t* hint = cv.take<int32_t>(size_t(m));
+  int32_t* hint = cv.take<int32_t>(hint_words(m));
   int32_t* hint_valid = cv.take<int32_t>(1);
   void* rest = cv.take<char>(0);
   // the call's work on stream s, the status word copied to *st

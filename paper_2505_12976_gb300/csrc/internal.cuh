@@ -104,11 +104,15 @@ size_t extract_workspace_bytes(int32_t m);
 size_t tally_positions_workspace_bytes(int64_t n, int32_t m);
 
 // Stage launchers operating on caller-provided workspace (no allocation).
-// With hint / hint_valid (int32 [m] and one word, outside ws), a top-k
-// tally also reports which candidates have an outgoing edge: when some
-// candidate is listed on no ballot, exactly the listed ones do (each beats
-// every unlisted one, and an unlisted one prefers nobody). *hint_valid is
-// set to 1 when hint holds them, else 0.
+// With hint / hint_valid (hint_words(m) int32 words and one word, outside
+// ws), a top-k tally also reports which candidates have an outgoing edge:
+// when some candidate is listed on no ballot, exactly the listed ones do
+// (each beats every unlisted one, and an unlisted one prefers nobody).
+// *hint_valid is set to 1 when hint holds them, else 0. Layout of hint:
+// flags [m], then the closure's warm-first relabeling of those flags, perm
+// [m] (new -> old), inv [m] (old -> new) and the warm count [1], which the
+// tally's plan pass writes so that the closure need not scan the flags.
+inline size_t hint_words(int32_t m) { return 3 * size_t(m) + 1; }
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
                  uint32_t flags, void* ws, cudaStream_t stream, int32_t* hint = nullptr,
                  int32_t* hint_valid = nullptr);
@@ -119,10 +123,12 @@ int tally_positions_launch(schulze_ctx* ctx, const int32_t* pos, int64_t n, int3
 // With beaten_by non-null the closure also fills it (int32 [m]) from its
 // warm rows, so extract_from_beaten_by can finish without reading p. With
 // hint / hint_valid (from tally_launch, outside ws) the closure takes the
-// warm flags from the tally when *hint_valid is set, skipping its own pass
-// over d (and that pass's bound check, which the tally's d meets).
+// warm flags and their relabeling from the tally when *hint_valid is set,
+// skipping its own pass over d (and that pass's bound check, which the
+// tally's d meets); otherwise it writes its relabeling into hint's perm,
+// inv and warm words.
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
-                   void* ws, cudaStream_t stream, int32_t* beaten_by = nullptr, const int32_t* hint = nullptr,
+                   void* ws, cudaStream_t stream, int32_t* beaten_by = nullptr, int32_t* hint = nullptr,
                    const int32_t* hint_valid = nullptr);
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream);

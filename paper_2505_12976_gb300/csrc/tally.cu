@@ -350,9 +350,18 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
     __shared__ int32_t lid[kCompactMaxPacked];
     __shared__ unsigned long long lkey[kCompactMaxPacked];
     // slots, and the closure's warm flags (the listed candidates, valid when
-    // one is never listed)
+    // one is never listed) with their warm-first relabeling: listed c keeps
+    // rank flag[c] (listed candidates before it), unlisted c follows all
+    // listed ones in id order
+    int32_t* rperm = hint ? hint + m : nullptr;
+    int32_t* rinv = hint ? hint + 2 * int64_t(m) : nullptr;
     each([&](int32_t c, int32_t x) {
-      const int32_t s = x > 0 ? int32_t(flag[c]) : -1;
+      const int32_t f = int32_t(flag[c]);  // read before slot[c] (its storage for long lists) is written
+      const int32_t s = x > 0 ? f : -1;
+      if (hint) {
+        const int32_t nw = x > 0 ? f : int32_t(na) + (c - f);
+        rperm[nw] = c, rinv[c] = nw;
+      }
       if (compact && s >= 0) {
         lid[s] = c, lkey[s] = (static_cast<unsigned long long>(x) << 32) | uint32_t(~s);  // slot, act below
       } else {
@@ -363,7 +372,7 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
     });
     if (threadIdx.x == 0) {
       meta[0] = int32_t(na), meta[1] = compact ? 1 : 0;
-      if (hint) *hint_valid = int32_t(na) < m ? 1 : 0;
+      if (hint) *hint_valid = int32_t(na) < m ? 1 : 0, hint[3 * int64_t(m)] = int32_t(na);
     }
     if (compact) {  // the compact form needs no grouping plan, only its slot order
       static_assert(kCompactMaxPacked >= kCompactMaxWide && kCompactMaxPacked * 4 <= 1024, "4 threads per slot");
