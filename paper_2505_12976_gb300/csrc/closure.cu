@@ -82,7 +82,7 @@ constexpr int kFlagT = 64;
 __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int64_t bound,
                                                       int32_t* __restrict__ rowflag, int32_t* status,
                                                       const int32_t* __restrict__ hint_valid) {
-  pdl_enter();
+  pdl_enter_early();
   if (hint_valid && *hint_valid) return;  // the caller's tally already knows the flags
   __shared__ int32_t t1[kFlagT][kFlagT + 1], t2[kFlagT][kFlagT + 1];  // t1 = d[A.., B..], t2 = d[B.., A..]
   const int32_t nbt = (m + kFlagT - 1) / kFlagT;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
                                                        int32_t* __restrict__ perm, int32_t* __restrict__ inv,
                                                        int32_t* __restrict__ warm_out,
                                                        const int32_t* __restrict__ hint_valid) {
-  pdl_enter();
+  pdl_enter_early();
   __shared__ uint32_t part[32];
   extern __shared__ uint32_t relabel_smem[];  // m words when m <= kScanSmem
   if (hint_valid && *hint_valid) return;
@@ -467,7 +467,7 @@ constexpr int32_t kClusterMaxWarm = sizeof(E) == 2 ? 256 : 192;
 template <typename E>
 __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
                                                                        Sync sy) {
-  pdl_enter();
+  pdl_enter_early();
   __shared__ __align__(16) typename Ops<E>::Smem sm;
   __shared__ __align__(16) int32_t rowbuf[2][kB];
   __shared__ int32_t s_item[4];
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(512, 1) cold_strip_kernel(E* __restrict__ W, i
                                                             const int32_t* __restrict__ warm,
                                                             unsigned long long* counters,
                                                             const int32_t* __restrict__ hint_valid) {
-  pdl_enter();
+  pdl_enter_early();
   using Wd = typename std::conditional<sizeof(E) == 2, uint32_t, int32_t>::type;  // one word
   constexpr int kPer = sizeof(Wd) / sizeof(E);                                  // entries per word
   const int32_t nw = *warm;
@@ -814,7 +814,7 @@ __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ 
                                                                  const uint32_t* __restrict__ prog,
                                                                  unsigned long long* counters,
                                                                  const int32_t* __restrict__ hint_valid) {
-  pdl_enter();
+  pdl_enter_early();
   __shared__ __align__(16) typename Ops<E>::Smem sm;
   if (*warm <= kClusterMaxWarm<E>) return;  // cold_strip_kernel's case
   if (hint_valid && *hint_valid && (*warm + kB - 1) / kB * kB < m) return;  // uniform cold columns

@@ -168,6 +168,14 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// The same for kernels that usually return at once (the alternatives the
+// device decides against): the successor may start launching before the
+// wait, so a returning kernel adds little to the chain. The successor still
+// waits for this kernel's completion, which follows the predecessor's.
+__device__ __forceinline__ void pdl_enter_early() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,

@@ -412,7 +412,7 @@ template <bool kLocal>
 __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
                                       const int32_t* __restrict__ meta) {
-  pdl_enter();
+  pdl_enter_early();
   if (meta[1]) return;  // compact form
   if (!kLocal) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(512)
                         const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries,
                         const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
                         int32_t* __restrict__ d, const int32_t* __restrict__ meta) {
-  pdl_enter();
+  pdl_enter_early();
   extern __shared__ uint32_t C[];
   __shared__ uint32_t so[kMaxRowsPerBlock + 1];  // off[R0 .. R1]
   const uint32_t unit = blockIdx.x;
