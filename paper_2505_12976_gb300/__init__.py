@@ -166,8 +166,14 @@ def context(device=None) -> Context:
     return _ctx[dev]
 
 
+# the current stream's raw handle without building a torch Stream object
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream, device):
     if stream is None:
+        if _raw_stream is not None and isinstance(device, int):
+            return _vp(_raw_stream(device))
         stream = torch.cuda.current_stream(device)
     return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
@@ -500,6 +506,6 @@ def schulze_run_host(ranks: np.ndarray, m: int, flags: int = 0, winners: np.ndar
     order = np.empty(m, np.int32) if order is None else order
     wptr = winners.data_ptr() if isinstance(winners, torch.Tensor) else winners.ctypes.data
     optr = order.data_ptr() if isinstance(order, torch.Tensor) else order.ctypes.data
-    _check(load().schulze_run_host(ctx.handle, _vp(rptr), n, m, k, _vp(wptr), _vp(optr), flags,
-                                   _stream(stream, ctx.device)), "schulze_run_host")
+    _check(ctx._lib.schulze_run_host(ctx.handle, _vp(rptr), n, m, k, _vp(wptr), _vp(optr), flags,
+                                     _stream(stream, ctx.device)), "schulze_run_host")
     return winners, order
