@@ -66,6 +66,25 @@ def test_argument_checks_without_gpu(lib):
     assert lib.schulze_ctx_create(-1, ctypes.byref(v())) == -1
 
 
+def test_host_call_argument_checks_without_gpu(lib):
+    """schulze_run_host: the C entry point rejects a missing context with
+    SCHULZE_EINVAL, and the binding rejects ballots of the wrong type or
+    layout, both before any CUDA call."""
+    v = ctypes.c_void_p
+    lib.schulze_run_host.argtypes = [v, v, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, v, v, ctypes.c_uint32, v]
+    buf = (ctypes.c_int32 * 16)()
+    assert lib.schulze_run_host(None, ctypes.cast(buf, v), 2, 4, 2, None, None, 0, None) == -1  # no context
+    import numpy as np
+    import paper_2505_12976_gb300 as S
+    with pytest.raises(ValueError):
+        S.schulze_run_host(np.zeros((2, 3), np.int64), 4)  # not int32
+    with pytest.raises(ValueError):
+        S.schulze_run_host(np.zeros((3, 2), np.int32).T, 4)  # not C-contiguous
+    import torch
+    with pytest.raises(ValueError):
+        S.schulze_run_host(torch.zeros((2, 3), dtype=torch.int64), 4)
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding refuses to run when the library is missing, and nothing in
     the package imports the oracle."""
