@@ -68,8 +68,9 @@ def _load():
             lib.oracle_beaten_by.argtypes = [i32p, i32, i32p]
             lib.oracle_ranking.argtypes = [i32p, i32, i32p, i32p]
             lib.oracle_widest_one.argtypes = [i32p, i32, i32, ctypes.c_int, i32p]
+            lib.oracle_widest_many.argtypes = [i32p, i32, i32p, i32, ctypes.c_int, i32p, ctypes.c_int]
             for f in (lib.oracle_weights, lib.oracle_weights_margin, lib.oracle_closure, lib.oracle_winners,
-                      lib.oracle_beaten_by, lib.oracle_ranking, lib.oracle_widest_one):
+                      lib.oracle_beaten_by, lib.oracle_ranking, lib.oracle_widest_one, lib.oracle_widest_many):
                 f.restype = None
             _lib = lib
     return _lib
@@ -208,6 +209,18 @@ def widest_to(w, t: int) -> np.ndarray:
     m = w.shape[0]
     out = np.empty(m, dtype=np.int32)
     _load().oracle_widest_one(_p(w), m, int(t), 1, _p(out))
+    return out
+
+
+def widest_many(w, sources, transpose: bool = False, nthreads: int = 1) -> np.ndarray:
+    """Rows p(s, .) for every s in sources (columns p(., s) with transpose),
+    by max-min Dijkstra, sources spread over nthreads: [len(sources), m]."""
+    w = _i32(w)
+    m = w.shape[0]
+    src = np.ascontiguousarray(sources, dtype=np.int32).reshape(-1)
+    out = np.empty((src.size, m), dtype=np.int32)
+    if src.size:
+        _load().oracle_widest_many(_p(w), m, _p(src), int(src.size), int(bool(transpose)), _p(out), int(nthreads))
     return out
 
 

@@ -252,6 +252,19 @@ void oracle_widest_one(const int32_t* w, int32_t m, int32_t s, int transpose, in
 }
 
 /*
+ * Several rows (or, with `transpose`, columns) of the closure at once:
+ * out[t * m + v] = p(src[t], v) (or p(v, src[t])), each computed by
+ * oracle_widest_one; the sources are independent, so they are spread over
+ * `nthreads` OpenMP threads. Used for exact checks of single candidates of
+ * profiles too large for the full closure.
+ */
+void oracle_widest_many(const int32_t* w, int32_t m, const int32_t* src, int32_t count, int transpose,
+                        int32_t* out, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int32_t t = 0; t < count; ++t) oracle_widest_one(w, m, src[t], transpose, out + (int64_t)t * m);
+}
+
+/*
  * Top-k ranking by iterated winner removal (Sect. 4, closing remark: run the
  * method again after removing the Schulze winners). Level t is the winner
  * set of the profile restricted to the candidates not placed in levels

@@ -43,6 +43,8 @@ MUTANTS = {
     "beaten_by_reversed": ("if (j != i && p[(int64_t)j * m + i] > p[(int64_t)i * m + j]) ++c;",
                            "if (j != i && p[(int64_t)j * m + i] < p[(int64_t)i * m + j]) ++c;"),
     "ranking_tiebreak_reversed": ("order[t - 1] > i))", "order[t - 1] < i))"),
+    "tally_entry_ties_counted": ("if (pi < pj) cnt += 1;", "if (pi <= pj) cnt += 1;"),
+    "tally_entry_unlisted_first": ("int32_t pi = k, pj = k;", "int32_t pi = 0, pj = 0;"),
     "dijkstra_max_instead_of_min": ("int64_t cand = best[u] < (int64_t)e ? best[u] : (int64_t)e;",
                                     "int64_t cand = best[u] > (int64_t)e ? best[u] : (int64_t)e;"),
 }

@@ -124,6 +124,18 @@ def test_dijkstra_rows_and_columns_match_closure():
         np.testing.assert_array_equal(oracle.widest_to(w, s), p[:, s])
 
 
+def test_dijkstra_batched_rows_and_columns():
+    """The batched form (sources spread over threads) gives the same rows and
+    columns as the closure."""
+    e = W.large_topk(seed=6, n=500, m=140, k=15)
+    w = oracle.weights(oracle.tally(e.ranks, e.m))
+    p = oracle.closure(w)
+    src = [0, 3, 70, 139, 3]
+    np.testing.assert_array_equal(oracle.widest_many(w, src, nthreads=4), p[src])
+    np.testing.assert_array_equal(oracle.widest_many(w, src, transpose=True, nthreads=4), p[:, src].T)
+    assert oracle.widest_many(w, []).shape == (0, e.m)
+
+
 def test_dijkstra_brute_force():
     rs = np.random.Generator(np.random.PCG64(12))
     for _ in range(30):
@@ -174,6 +186,51 @@ def test_topk_identities(m, n, k, seed):
     np.testing.assert_array_equal(oracle.tally(r[perm], m), d)
     h = n // 2
     np.testing.assert_array_equal(oracle.tally(r[:h], m) + oracle.tally(r[h:], m), d)
+
+
+@pytest.mark.parametrize("case", ["full", "topk", "topk_one", "no_ballots", "empty_ballots", "one_candidate"])
+def test_tally_entry_counts_like_the_tally(case):
+    """The voter-by-voter count of one entry (used for sampled checks of
+    profiles too large for the whole tally) equals the whole tally entry by
+    entry, unlisted candidates included, and vanishes where nobody votes."""
+    if case == "full":
+        m, r = 9, W.mallows(31, 70, 9, 9, 0.8, W.permutation(31, 9))
+    elif case == "topk":
+        m, r = 14, W.mallows(32, 90, 14, 4, 0.9, W.permutation(32, 14))
+    elif case == "topk_one":
+        m, r = 6, W.impartial(33, 25, 6, 1)
+    elif case == "no_ballots":
+        m, r = 5, np.zeros((0, 3), np.int32)
+    elif case == "empty_ballots":
+        m, r = 5, np.zeros((7, 0), np.int32)
+    else:
+        m, r = 1, np.zeros((4, 1), np.int32)
+    d = oracle.tally(r, m)
+    got = np.array([[oracle.tally_entry(r, m, i, j) for j in range(m)] for i in range(m)])
+    np.testing.assert_array_equal(got, d)
+    if case in ("no_ballots", "empty_ballots"):
+        assert not got.any()
+    if case.startswith("topk"):
+        unlisted = np.setdiff1d(np.arange(m), np.unique(r))
+        for a in unlisted:  # an unlisted candidate is preferred to nobody
+            assert not got[a].any()
+
+
+def test_tally_entry_hand_derived():
+    """Entries fixed by hand rather than by the tally: the tie counterexample
+    (ballots [0, 2] and [2, 1] over three candidates) and Fig. 1 realised by
+    McGarvey's construction (d[a][b] = 21 + mu(a, b) / 2 off the diagonal)."""
+    g = topk_tie_counterexample()
+    for i in range(g["m"]):
+        for j in range(g["m"]):
+            assert oracle.tally_entry(g["ballots"], g["m"], i, j) == g["d"][i][j], (i, j)
+    _, mu, _, _ = fig1()
+    ballots = mcgarvey_ballots(mu)
+    n = ballots.shape[0]
+    for i in range(4):
+        for j in range(4):
+            want = 0 if i == j else (n + int(mu[i, j]) - int(mu[j, i])) // 2
+            assert oracle.tally_entry(ballots, 4, i, j) == want, (i, j)
 
 
 def test_unlisted_candidates_tie():
