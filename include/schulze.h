@@ -12,7 +12,10 @@
  *  - All array arguments are DEVICE pointers (cudaMalloc / torch CUDA memory)
  *    owned by the caller, unless a call says "host". The library never frees
  *    them and keeps no reference after the call returns.
- *  - Matrices are dense, row-major, leading dimension m, int32.
+ *  - Matrices are dense, row-major, leading dimension m, int32. Device
+ *    pointers need only the 4-byte alignment of int32; rows that start on
+ *    16-byte boundaries (m a multiple of 4 and a 16-byte aligned base) are
+ *    moved with 16-byte accesses, others element by element.
  *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
  *    the legacy default stream). Outputs are valid once the stream reaches
  *    the end of the call's work.
@@ -84,6 +87,16 @@ size_t schulze_workspace_bytes(const schulze_ctx* ctx);
  * reset it to SCHULZE_OK. */
 int schulze_get_status(schulze_ctx* ctx, int32_t* status, schulze_stream_t stream);
 
+/* Bound on each device-side wait of the closure's persistent kernel (a CTA
+ * waiting for the tiles an item depends on), in SM clock cycles; default
+ * 4e9, about 2 s at 2 GHz. A wait that runs out records SCHULZE_ETIMEOUT in
+ * the status word and raises an abort flag that every CTA checks in its
+ * waits and before its next item, so the launch always ends; that call's
+ * outputs are then unspecified and the next call starts afresh. Applies to
+ * calls issued after it (a graph captured earlier keeps the limit it was
+ * captured with). cycles >= 1, else SCHULZE_EINVAL. */
+int schulze_set_wait_limit(schulze_ctx* ctx, int64_t cycles);
+
 /*
  * Pairwise tally (Sect. 2.1: the counts behind the majority margin
  * mu(a,b) = d[a][b] - d[b][a]).
@@ -145,13 +158,18 @@ int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64
  *          larger m returns SCHULZE_ETOOBIG.
  *   status a device int32 where data errors found by the kernels are
  *          recorded (SCHULZE_EDATA, SCHULZE_ETIMEOUT; the first one wins; the
- *          caller zeroes it), or NULL to not record them.
+ *          caller zeroes it), or NULL to not record them. When status would
+ *          hold an error, p is unspecified; with NULL such an error goes
+ *          unnoticed (the call still returns SCHULZE_OK), so pass a status
+ *          word unless d is known to be valid.
  * Scratch: one file-scope device array of about 4.1 MB (W for m <= 1024 in
  * int32, progress words, relabeling), present on every GPU that loads the
  * library until the process exits. The call runs on the calling thread's
  * current device; its first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) and caches it, so make that first call
- * before any stream capture. The call resets the parts of the array that
+ * before any stream capture. The cache assumes one primary context per
+ * device for the life of the process: after cudaDeviceReset() the cached
+ * address is stale, so do not call this entry point again in that process. The call resets the parts of the array that
  * must start at zero; all calls share the one array, so calls that overlap
  * on the GPU (other streams, other host threads) race and corrupt each
  * other's results: order them on one stream.
@@ -272,14 +290,34 @@ int schulze_batch_layout(const schulze_batch* b, int64_t* ranks_elems, int64_t* 
 int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
                       int32_t* order, int32_t* beaten_by, schulze_stream_t stream);
 
-/* Schedule knobs: tally_policy, the ballots staged per tally step (0:
- * sixteen, 1: eight); order_policy (0: longest election first, 1: the
- * caller's order). Synchronous. */
+/* Schedule knobs: tally_policy 0 stages each election's ballots in steps of
+ * its m-bucket's size (schulze_batch_set_bucket_chunk, the autotuner), 1
+ * stages eight everywhere; order_policy 0 runs the longest elections first,
+ * 1 the caller's order. Synchronous. */
 int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t order_policy);
 
-/* Autotuner: times every schedule on this batch (two runs each on `stream`),
- * keeps the fastest and reports it. With cache_path, a previous result for
- * the same batch signature and GPU is reused, and a new one appended. */
+/* Elections are grouped by m into five buckets (m <= 64, 128, 256, 512,
+ * 1024); the tally of an election stages `chunk` ballots per step as position
+ * rows in shared memory (8, 16, 32 or 64; a power of two that fits: chunk *
+ * ceil64(m) * 6 bytes within the CTA's shared memory and chunk * m <= 16384),
+ * set here per bucket (EINVAL for a size that does not fit the bucket's
+ * largest m). Synchronous. */
+int schulze_batch_set_bucket_chunk(schulze_batch* b, int32_t bucket, int32_t chunk);
+
+/* The per-bucket schedule: largest m of each bucket, its ballots per step
+ * and the number of the plan's elections in it (host int32 [5] each, any may
+ * be NULL). */
+int schulze_batch_bucket_schedule(const schulze_batch* b, int32_t* bucket_max_m, int32_t* chunks,
+                                  int32_t* elections);
+
+/* Autotuner: for every m-bucket with elections, times the bucket's elections
+ * alone (one launch over them, three runs, the best of the last two) with
+ * every ballots-per-step size that fits and keeps the fastest; then times
+ * both election orders on the whole batch. best_tally receives 0 (the
+ * per-bucket schedule), best_order the order policy. With cache_path, a
+ * result already recorded for the same GPU and bucket (election count and
+ * mean ballot count) or batch signature is reused, and new ones are
+ * appended, one "<key> <value>" line each. */
 int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tally,
                            int32_t* best_order, schulze_stream_t stream);
 
@@ -331,10 +369,14 @@ int schulze_certify(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, co
 
 /* Winners of the election with tally d: features, proposals (the MLP with
  * `params`, or the Copeland score wins - losses when params is NULL), the
- * `top` best (<= 8) certified in order, the closure as fallback. Synchronous
- * on `stream`. winners: device int32 [m]. stats (HOST int32 [4], may be
- * NULL): [0] index of the proposal that certified (-1 if none), [1] 1 if the
- * closure decided, [2] ties checked, [3] relaxation rounds. */
+ * `top` best (<= 8) certified in order. When none certifies, the full
+ * closure decides; when the warm set is too large to certify (more than
+ * 2048 candidates with outgoing edges), the paper's propagation algorithm
+ * (Sect. 4, Alg. 1-4, as schulze_winners_propagation) decides instead.
+ * Synchronous on `stream`. winners: device int32 [m]. stats (HOST int32 [4],
+ * may be NULL): [0] index of the proposal that certified (-1 if none), [1] 0
+ * if a proposal certified, 1 if the closure decided, 2 if the propagation
+ * did, [2] ties checked, [3] relaxation rounds. */
 int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const float* params, int32_t top,
                          int32_t* winners, int32_t* stats, schulze_stream_t stream);
 

@@ -51,7 +51,13 @@ int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* d
  * three-input max folding two updates, 3 instructions per 4 updates; kind 3:
  * int32 with a three-input max, 3 instructions per 2 updates; kind 4: fp32
  * lanes; kind 5: fp32 with a three-input max; kind 6: half the chains as
- * kind 3, half as kind 5). *seconds
+ * kind 3, half as kind 5; kinds 7-11 work on non-negative int32 bit patterns
+ * read as fp32 where a float unit is used, as a closure sharing one matrix
+ * between the two units would: kind 7 fp32 mins with an int32 three-input
+ * max, kind 8 int32 mins with an fp32 three-input max, kind 9 a third of the
+ * chains as kind 3 and the rest in fp32, kind 10 two thirds as kind 3, kind
+ * 11 half and half; kind 12 the tally's guard-bit compare-and-count of two
+ * 16-bit position lanes, counting lane compares as updates). *seconds
  * receives the kernel time (CUDA events) and *updates the number of
  * (max, min) lane updates done.
  * Synchronous.

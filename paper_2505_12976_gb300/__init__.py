@@ -44,6 +44,7 @@ SIGNATURES = [
     ("schulze_reserve", _c.c_int, [_vp, _i32, _i64, _i32]),
     ("schulze_workspace_bytes", _c.c_size_t, [_vp]),
     ("schulze_get_status", _c.c_int, [_vp, _c.POINTER(_i32), _vp]),
+    ("schulze_set_wait_limit", _c.c_int, [_vp, _i64]),
     ("schulze_tally", _c.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _u32, _vp]),
     ("schulze_tally_positions", _c.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("schulze_ranking_iterated", _c.c_int, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _u32, _vp]),
@@ -59,6 +60,8 @@ SIGNATURES = [
     ("schulze_batch_layout", _c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64), _vp, _vp, _vp]),
     ("schulze_batch_run", _c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("schulze_batch_set_schedule", _c.c_int, [_vp, _i32, _i32]),
+    ("schulze_batch_set_bucket_chunk", _c.c_int, [_vp, _i32, _i32]),
+    ("schulze_batch_bucket_schedule", _c.c_int, [_vp, _vp, _vp, _vp]),
     ("schulze_batch_autotune", _c.c_int, [_vp, _vp, _c.c_char_p, _c.POINTER(_i32), _c.POINTER(_i32), _vp]),
     ("schulze_features", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _vp]),
     ("schulze_mlp_forward", _c.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
@@ -128,6 +131,10 @@ class Context:
         _check(self._lib.schulze_get_status(self.handle, ctypes.byref(st), _stream(stream, self.device)),
                "schulze_get_status")
         return int(st.value)
+
+    def set_wait_limit(self, cycles: int):
+        """Clock-cycle bound on each device-side wait of the persistent closure."""
+        _check(self._lib.schulze_set_wait_limit(self.handle, int(cycles)), "schulze_set_wait_limit")
 
     def profile(self, enable: bool = True):
         """Start (clearing) or stop per-kernel event timing of this context."""
@@ -289,17 +296,29 @@ def schulze_strongest_paths_static(d: torch.Tensor, bound: int, p: torch.Tensor 
                                    status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Widest paths without any device allocation inside the library, for
     callers that cannot allocate device memory (m <= 1024; scratch is a fixed
-    array in the library). `status`: optional device int32 [1] receiving data
-    errors. Calls must not overlap on the GPU."""
+    array in the library). Calls must not overlap on the GPU.
+
+    `status`: a zeroed device int32 [1] that receives data errors (EDATA,
+    ETIMEOUT) asynchronously; the caller reads it and treats p as unspecified
+    when it is nonzero. Without one, this wrapper makes its own status word,
+    waits for the stream and raises SchulzeError on an error, so that a bad
+    count or a timed-out wait is never returned silently."""
     d = _dev_i32(d, "d")
     m = d.shape[0]
     _dev_i32(d, "d", (m, m))
     p = _out(p, (m, m), d.device, "p")
-    if status is not None:
+    own = status is None
+    if own:
+        status = torch.zeros(1, dtype=torch.int32, device=d.device)
+    else:
         _dev_i32(status, "status", (1,))
     with torch.cuda.device(d.device):
         _check(load().schulze_strongest_paths_static(_ptr(d), m, int(bound), _ptr(p), flags, _ptr(status),
                                                      _stream(stream, d.device)), "schulze_strongest_paths_static")
+    if own:
+        code = int(status.item())  # waits for the current stream
+        if code != OK:
+            raise SchulzeError(code, "schulze_strongest_paths_static (device status)")
     return p
 
 
@@ -407,7 +426,8 @@ def schulze_winners_fast(d: torch.Tensor, n: int, params: torch.Tensor | None = 
                          winners: torch.Tensor | None = None, ctx: Context | None = None, stream=None):
     """Exact winners via certified proposals (MLP, or Copeland when params is
     None); returns (winners, stats) with stats = [certified proposal index or
-    -1, closure fallback 0/1, ties checked, relaxation rounds]."""
+    -1, fallback (0 none, 1 closure, 2 the paper's propagation for warm sets
+    above 2048), ties checked, relaxation rounds]."""
     d = _dev_i32(d, "d")
     m = d.shape[0]
     if params is not None:
@@ -462,6 +482,17 @@ class SchulzeBatch:
     def set_schedule(self, tally_policy: int, order_policy: int):
         _check(self._lib.schulze_batch_set_schedule(self.handle, tally_policy, order_policy),
                "schulze_batch_set_schedule")
+
+    def set_bucket_chunk(self, bucket: int, chunk: int):
+        """Ballots staged per tally step for the elections of one m-bucket."""
+        _check(self._lib.schulze_batch_set_bucket_chunk(self.handle, int(bucket), int(chunk)),
+               "schulze_batch_set_bucket_chunk")
+
+    def bucket_schedule(self):
+        """[(largest m of the bucket, ballots per step, elections in it)] for the five m-buckets."""
+        mx, ch, el = (_i32 * 5)(), (_i32 * 5)(), (_i32 * 5)()
+        _check(self._lib.schulze_batch_bucket_schedule(self.handle, mx, ch, el), "schulze_batch_bucket_schedule")
+        return [(mx[q], ch[q], el[q]) for q in range(5)]
 
     def autotune(self, ranks: torch.Tensor, cache_path: str | None = None, stream=None):
         """Pick the fastest schedule for this batch; returns (tally_policy, order_policy)."""

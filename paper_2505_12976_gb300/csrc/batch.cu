@@ -32,7 +32,21 @@ constexpr int64_t kFlushVoters = 32768;  // 16-bit lane counters are flushed bef
 struct Job {
   int32_t n, m, k, e;
   int64_t ranks_off, mat_off, vec_off;
+  int32_t chunk;  // ballots staged per tally step (the schedule of the election's m-bucket)
+  int32_t pad;
 };
+
+// Elections are grouped by m into buckets, each with its own tally schedule
+// (ballots staged per step), which schulze_batch_autotune times and caches.
+constexpr int kBuckets = 5;
+constexpr int32_t kBucketMax[kBuckets] = {64, 128, 256, 512, 1024};
+inline int bucket_of(int32_t m) {
+  int b = 0;
+  while (b + 1 < kBuckets && m > kBucketMax[b]) ++b;
+  return b;
+}
+constexpr int kChunkChoices[4] = {8, 16, 32, 64};
+constexpr int kPrefetch = 32;  // ballot ids a thread holds for the next step
 
 struct BatchArgs {
   const Job* jobs;
@@ -48,16 +62,15 @@ struct BatchArgs {
   size_t slot_bytes;  // per CTA: W slot, then a d slot when the caller passes no d
   size_t w_bytes;
   int32_t* status;
-  int32_t tally_policy;  // ballots staged per tally step: 0 sixteen, 1 eight
 };
 
-// Dynamic shared memory of one batch CTA, reused stage by stage.
-constexpr int kChunkMax = 16;  // ballots staged per tally step (policy 0; policy 1 stages 8)
+// Dynamic shared memory of one batch CTA, reused stage by stage. The tally
+// stages `chunk` ballots as position rows of mpad (m rounded up to 64)
+// entries: dup[chunk][mpad] (position in both 16-bit halves, guard bits set)
+// then pos[chunk][mpad] (16-bit), carved from `raw`.
+constexpr size_t kStageBytes = sizeof(tiles::SmemS32) * kGroups + 2 * tiles::kB * 4;
 union BatchSmem {
-  struct {
-    uint32_t dup[kChunkMax][kBatchMaxM];  // position of every candidate, in both 16-bit halves
-    uint16_t pos[kChunkMax][kBatchMaxM];  // the same positions, one per 16-bit slot
-  } stage;
+  unsigned char raw[kStageBytes];
   struct {
     tiles::SmemS32 t[kGroups];
     int32_t rowbuf[2][tiles::kB];
@@ -83,8 +96,8 @@ constexpr int kTT = 64;  // tally tile: 64 x 64 counters per group, 8 x 4 per th
 // rest: d[j][i] = n - d[i][j]. The first round also checks the ballots: an
 // id out of range, or one whose position slot is already taken within the
 // same ballot, is reported as SCHULZE_EDATA.
-__device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, int chunk,
-                      BatchSmem& sm, int32_t* status) {
+__device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, BatchSmem& sm,
+                      int32_t* status) {
   const int32_t n = jb.n, m = jb.m, k = jb.k;
   const bool full = k >= m - 1;
   const int32_t nbt = (m + kTT - 1) / kTT;
@@ -95,6 +108,23 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   // bits of count_lt2
   const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16) | kGuard2;
   const int32_t mpad = int32_t(align_up(size_t(m), kTT));
+  const int chunk = jb.chunk;  // chunk * mpad * 6 <= sizeof(BatchSmem), chunk * k <= kBT * kPrefetch (plan)
+  uint32_t* dup = reinterpret_cast<uint32_t*>(sm.raw);                         // [chunk][mpad]
+  uint16_t* pos = reinterpret_cast<uint16_t*>(sm.raw + size_t(chunk) * mpad * 4);  // [chunk][mpad]
+  // ballot ids of a step: thread tid holds positions q0 + u * lanes of ballot
+  // vv of the step; the next step's ids are loaded before this step's counts
+  const int lanes = kBT / chunk;
+  const int vv = tid / lanes, q0 = tid % lanes;
+  int32_t cv[kPrefetch];
+  auto load_ids = [&](int64_t v0n) {
+    const bool have = v0n + vv < n;
+    const int32_t* row = ranks + (v0n + vv) * k;
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int32_t q = q0 + u * lanes;
+      cv[u] = (have && q < k) ? __ldcs(row + q) : -1;
+    }
+  };
   for (int32_t t0 = 0; t0 < ntiles; t0 += kGroups) {
     // this group's tile (bi, bj)
     const int32_t tt = t0 + g;
@@ -114,62 +144,51 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r][0] = acc[r][1] = 0u;
     bool first_flush = true;
+    load_ids(0);
     for (int64_t v0 = 0; v0 < n; v0 += chunk) {
       const int nv = int(n - v0 < chunk ? n - v0 : int64_t(chunk));
       __syncthreads();
       if (k < m || check) {  // unlisted candidates sit at position k
         for (int t = tid; t < chunk * mpad; t += kBT) {
-          const int vv = t / mpad, c = t % mpad;
-          sm.stage.dup[vv][c] = unl2;
-          sm.stage.pos[vv][c] = uint16_t(unl);
+          dup[t] = unl2;
+          pos[t] = uint16_t(unl);
         }
         __syncthreads();
       } else if (mpad > m) {  // full ballots fill 0..m-1; the padding stays unlisted
         for (int t = tid; t < chunk * (mpad - m); t += kBT) {
-          const int vv = t / (mpad - m), c = m + t % (mpad - m);
-          sm.stage.dup[vv][c] = unl2;
-          sm.stage.pos[vv][c] = uint16_t(unl);
+          const int w = t / (mpad - m), c = m + t % (mpad - m);
+          dup[w * mpad + c] = unl2;
+          pos[w * mpad + c] = uint16_t(unl);
         }
       }
-      // 32 lanes per ballot row, sixteen loads in flight per thread
-      const int lanes = kBT / chunk;  // threads per staged ballot (32 or 64)
-      const int vv = tid / lanes, q0 = tid % lanes;
-      if (vv < nv) {
-        const int32_t* row = ranks + (v0 + vv) * k;
-        for (int32_t qb = q0; qb < k; qb += lanes * 16) {
-          int32_t cv[16];
+      if (vv < nv) {  // this step's ids, loaded during the previous step
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int32_t q = qb + u * lanes;
-            cv[u] = q < k ? __ldcs(row + q) : -1;
+        for (int u = 0; u < kPrefetch; ++u) {
+          const int32_t q = q0 + u * lanes;
+          if (q >= k) break;
+          const int32_t c = cv[u];
+          if (c < 0 || c >= m) {
+            if (check) set_status(status, SCHULZE_EDATA);
+            continue;
           }
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int32_t q = qb + u * lanes;
-            if (q >= k) break;
-            const int32_t c = cv[u];
-            if (c < 0 || c >= m) {
-              if (check) set_status(status, SCHULZE_EDATA);
-              continue;
-            }
-            const uint32_t q2 = uint32_t(q) | (uint32_t(q) << 16) | kGuard2;
-            if (check) {
-              if (atomicExch(&sm.stage.dup[vv][c], q2) != unl2) set_status(status, SCHULZE_EDATA);
-            } else {
-              sm.stage.dup[vv][c] = q2;
-            }
-            sm.stage.pos[vv][c] = uint16_t(q);
+          const uint32_t q2 = uint32_t(q) | (uint32_t(q) << 16) | kGuard2;
+          if (check) {
+            if (atomicExch(&dup[vv * mpad + c], q2) != unl2) set_status(status, SCHULZE_EDATA);
+          } else {
+            dup[vv * mpad + c] = q2;
           }
+          pos[vv * mpad + c] = uint16_t(q);
         }
       }
+      if (v0 + chunk < n) load_ids(v0 + chunk);  // in flight while this step counts
       __syncthreads();
       if (tt < ntiles) {
         for (int u = 0; u < nv; ++u) {
           uint32_t a[8], b[2];
-          const uint4 a0 = *reinterpret_cast<const uint4*>(&sm.stage.dup[u][I0 + ty * 8]);
-          const uint4 a1 = *reinterpret_cast<const uint4*>(&sm.stage.dup[u][I0 + ty * 8 + 4]);
+          const uint4 a0 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8]);
+          const uint4 a1 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8 + 4]);
           a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
-          const uint2 bv = *reinterpret_cast<const uint2*>(&sm.stage.pos[u][J0 + tx * 4]);
+          const uint2 bv = *reinterpret_cast<const uint2*>(&pos[u * mpad + J0 + tx * 4]);
           b[0] = bv.x, b[1] = bv.y;
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
       for (int64_t t = threadIdx.x; t < int64_t(m) * m; t += kBT) dm[t] = 0;
       __syncthreads();
     } else {
-      tally(jb, ranks, dm, a.tally_policy == 1 ? 8 : kChunkMax, sm, a.status);
+      tally(jb, ranks, dm, sm, a.status);
     }
     const int32_t mp = int32_t(align_up(size_t(m), tiles::kB));
     pack<E>(dm, m, mp, W);
@@ -348,8 +367,9 @@ struct schulze_batch {
   unsigned char* scratch = nullptr;
   size_t slot_bytes = 0, w_bytes = 0;
   int grid = 0;
-  int32_t tally_policy = 0;
+  int32_t tally_policy = 0;  // 0: each m-bucket's ballots per step; 1: eight everywhere
   int32_t order_policy = 0;  // 0 longest first, 1 the caller's order
+  int32_t bucket_chunk[schulze::kBuckets] = {32, 32, 32, 16, 16};
   size_t smem = 0;
 };
 
@@ -363,12 +383,29 @@ double job_cost(const Job& j) {
   return tally + 1.5 * mp * mp * mp;
 }
 
+// Whether `chunk` ballots of an election with m candidates can be staged:
+// the position rows fit the shared memory, and a thread holds at most
+// kPrefetch ids of a step (chunk * m <= kBT * kPrefetch, as k <= m).
+bool chunk_fits(int32_t m, int32_t chunk) {
+  const size_t mpad = align_up(size_t(m), 64);
+  return chunk >= 1 && chunk <= kBT && size_t(chunk) * mpad * 6 <= kStageBytes &&
+         int64_t(chunk) * m <= int64_t(kBT) * kPrefetch;
+}
+
+int32_t job_chunk(const schulze_batch* b, int32_t m) {
+  if (b->tally_policy == 1) return 8;
+  int32_t c = b->bucket_chunk[bucket_of(m)];
+  while (c > 8 && !chunk_fits(m, c)) c /= 2;
+  return c;
+}
+
 void order_jobs(schulze_batch* b) {
   std::vector<Job> js(size_t(b->E));
   for (int32_t e = 0; e < b->E; ++e) js[e] = b->jobs_host[e];
   std::sort(js.begin(), js.end(), [](const Job& x, const Job& y) { return x.e < y.e; });
   if (b->order_policy == 0)
     std::stable_sort(js.begin(), js.end(), [](const Job& x, const Job& y) { return job_cost(x) > job_cost(y); });
+  for (Job& j : js) j.chunk = job_chunk(b, j.m);
   b->jobs_host = js;
 }
 
@@ -378,6 +415,30 @@ int upload_jobs(schulze_batch* b) {
       cudaSuccess)
     return SCHULZE_ECUDA;
   return SCHULZE_OK;
+}
+
+// One launch over `njobs` jobs of the uploaded table (the whole plan, or a
+// subset uploaded by the autotuner), outputs to the per-CTA scratch or the
+// caller's buffers.
+int launch_jobs(schulze_batch* b, int32_t njobs, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
+                int32_t* order, int32_t* beaten_by, cudaStream_t stream) {
+  if (cudaMemsetAsync(b->head, 0, 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
+  BatchArgs a;
+  a.jobs = b->jobs_dev;
+  a.njobs = njobs;
+  a.head = b->head;
+  a.ranks = ranks;
+  a.d = d, a.p = p, a.winners = winners, a.order = order, a.beaten_by = beaten_by;
+  a.scratch = b->scratch;
+  a.slot_bytes = b->slot_bytes;
+  a.w_bytes = b->w_bytes;
+  a.status = b->ctx->status;
+  Launch L(b->ctx, stream, "batch_elections", double(njobs));
+  if (b->s16)
+    batch_kernel<int16_t><<<b->grid, kBT, b->smem, stream>>>(a);
+  else
+    batch_kernel<int32_t><<<b->grid, kBT, b->smem, stream>>>(a);
+  return check_launch();
 }
 
 size_t batch_smem(bool s16) {
@@ -394,6 +455,7 @@ extern "C" {
 
 int schulze_batch_create(schulze_ctx* ctx, int32_t E, const int32_t* n, const int32_t* m, const int32_t* k,
                          schulze_batch** out) {
+  AbiRange abi_range("schulze_batch_create");
   if (!ctx || !out || E < 0 || (E > 0 && (!n || !m || !k))) return SCHULZE_EINVAL;
   *out = nullptr;
   for (int32_t e = 0; e < E; ++e)
@@ -478,27 +540,11 @@ int schulze_batch_layout(const schulze_batch* b, int64_t* ranks_elems, int64_t* 
 
 int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
                       int32_t* order, int32_t* beaten_by, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_batch_run");
   if (!b || (b->ranks_elems > 0 && !ranks)) return SCHULZE_EINVAL;
   if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   if (b->E == 0) return SCHULZE_OK;
-  if (cudaMemsetAsync(b->head, 0, 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
-  BatchArgs a;
-  a.jobs = b->jobs_dev;
-  a.njobs = b->E;
-  a.head = b->head;
-  a.ranks = ranks;
-  a.d = d, a.p = p, a.winners = winners, a.order = order, a.beaten_by = beaten_by;
-  a.scratch = b->scratch;
-  a.slot_bytes = b->slot_bytes;
-  a.w_bytes = b->w_bytes;
-  a.status = b->ctx->status;
-  a.tally_policy = b->tally_policy;
-  Launch L(b->ctx, stream, "batch_elections", double(b->E));
-  if (b->s16)
-    batch_kernel<int16_t><<<b->grid, kBT, b->smem, stream>>>(a);
-  else
-    batch_kernel<int32_t><<<b->grid, kBT, b->smem, stream>>>(a);
-  return check_launch();
+  return launch_jobs(b, b->E, ranks, d, p, winners, order, beaten_by, stream);
 }
 
 int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t order_policy) {
@@ -506,70 +552,151 @@ int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t o
   if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
   b->tally_policy = tally_policy;
-  if (order_policy != b->order_policy) {
-    b->order_policy = order_policy;
-    order_jobs(b);
-    if (int rc = upload_jobs(b)) return rc;
+  b->order_policy = order_policy;
+  order_jobs(b);
+  return upload_jobs(b);
+}
+
+int schulze_batch_set_bucket_chunk(schulze_batch* b, int32_t bucket, int32_t chunk) {
+  if (!b || bucket < 0 || bucket >= kBuckets || !chunk_fits(kBucketMax[bucket], chunk) || (chunk & (chunk - 1)))
+    return SCHULZE_EINVAL;
+  if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
+  b->bucket_chunk[bucket] = chunk;
+  order_jobs(b);
+  return upload_jobs(b);
+}
+
+int schulze_batch_bucket_schedule(const schulze_batch* b, int32_t* bucket_max_m, int32_t* chunks,
+                                  int32_t* elections) {
+  if (!b) return SCHULZE_EINVAL;
+  for (int q = 0; q < kBuckets; ++q) {
+    if (bucket_max_m) bucket_max_m[q] = kBucketMax[q];
+    if (chunks) chunks[q] = b->bucket_chunk[q];
+    if (elections) elections[q] = 0;
   }
+  if (elections)
+    for (const Job& j : b->jobs_host) ++elections[bucket_of(j.m)];
   return SCHULZE_OK;
 }
 
 int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tile,
                            int32_t* best_order, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_batch_autotune");
   if (!b || (b->ranks_elems > 0 && !ranks)) return SCHULZE_EINVAL;
   if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
-  // batch signature for the cache: size, totals, largest election, GPU
+  // cache keys: GPU, counter width, then per m-bucket its election count and
+  // mean ballot count (the tally schedule), per batch its totals (the order)
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, b->ctx->device);
-  char key[256];
-  snprintf(key, sizeof(key), "%.100s|E=%d|R=%lld|M=%lld|mmax=%d|s16=%d", prop.name, b->E,
-           (long long)b->ranks_elems, (long long)b->mat_elems, b->m_max, b->s16 ? 1 : 0);
-  for (char* c = key; *c; ++c)
-    if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';  // the cache line format splits on blanks
-  int32_t bt = -1, bo = -1;
-  if (cache_path) {  // line format: <key> <tally_policy> <order_policy>
+  auto clean = [](char* key) {
+    for (char* c = key; *c; ++c)
+      if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';  // the cache line format splits on blanks
+  };
+  std::vector<std::pair<std::string, int>> cached;
+  if (cache_path) {  // line format: <key> <value>
     if (FILE* f = fopen(cache_path, "r")) {
       char line[512];
       while (fgets(line, sizeof(line), f)) {
-        char k2[256];
-        int t2, o2;
-        if (sscanf(line, "%255s %d %d", k2, &t2, &o2) == 3 && strcmp(k2, key) == 0) bt = t2, bo = o2;
+        char k2[400];
+        int v2;
+        if (sscanf(line, "%399s %d", k2, &v2) == 2) cached.emplace_back(k2, v2);
       }
       fclose(f);
     }
   }
-  if (bt < 0) {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+  auto lookup = [&](const char* key) {
+    int v = -1;
+    for (const auto& kv : cached)
+      if (kv.first == key) v = kv.second;
+    return v;
+  };
+  std::vector<std::pair<std::string, int>> fresh;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // best of two timed runs after a warm-up
+  auto time_jobs = [&](int32_t njobs, float* ms_out) -> int {
     float best = 1e30f;
-    for (int32_t o = 0; o <= 1; ++o)
-      for (int32_t t = 0; t <= 1; ++t) {
-        if (int rc = schulze_batch_set_schedule(b, t, o)) return rc;
-        float total = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {
-          cudaEventRecord(e0, stream);
-          if (int rc = schulze_batch_run(b, ranks, nullptr, nullptr, nullptr, nullptr, nullptr, stream)) return rc;
-          cudaEventRecord(e1, stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) return SCHULZE_ECUDA;
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0) total += ms;  // first run warms up
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, stream);
+      if (int rc = launch_jobs(b, njobs, ranks, nullptr, nullptr, nullptr, nullptr, nullptr, stream)) return rc;
+      cudaEventRecord(e1, stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return SCHULZE_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    *ms_out = best;
+    return SCHULZE_OK;
+  };
+  int rc = SCHULZE_OK;
+  b->tally_policy = 0;
+  for (int q = 0; q < kBuckets && rc == SCHULZE_OK; ++q) {
+    std::vector<Job> sub;
+    double nsum = 0.0;
+    for (const Job& j : b->jobs_host)
+      if (bucket_of(j.m) == q) sub.push_back(j), nsum += j.n;
+    if (sub.empty()) continue;
+    char key[400];
+    snprintf(key, sizeof(key), "%.100s|s16=%d|bucket<=%d|elections=%zu|mean_n=%lld", prop.name, b->s16 ? 1 : 0,
+             kBucketMax[q], sub.size(), (long long)(nsum / double(sub.size())));
+    clean(key);
+    int best_c = lookup(key);
+    if (best_c < 0 || !chunk_fits(kBucketMax[q], best_c)) {
+      // time this bucket's elections alone for every staging size that fits
+      float best = 1e30f;
+      best_c = b->bucket_chunk[q];
+      for (int c : kChunkChoices) {
+        if (!chunk_fits(kBucketMax[q], c)) continue;
+        for (Job& j : sub) j.chunk = c;
+        if (cudaMemcpy(b->jobs_dev, sub.data(), sizeof(Job) * sub.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+          rc = SCHULZE_ECUDA;
+          break;
         }
-        if (total < best) best = total, bt = t, bo = o;
+        float ms = 0.f;
+        if ((rc = time_jobs(int32_t(sub.size()), &ms)) != SCHULZE_OK) break;
+        if (ms < best) best = ms, best_c = c;
       }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (cache_path) {
-      if (FILE* f = fopen(cache_path, "a")) {
-        fprintf(f, "%s %d %d\n", key, bt, bo);
-        fclose(f);
+      fresh.emplace_back(key, best_c);
+    }
+    b->bucket_chunk[q] = best_c;
+  }
+  int32_t bo = -1;
+  if (rc == SCHULZE_OK) {
+    char key[400];
+    snprintf(key, sizeof(key), "%.100s|s16=%d|order|E=%d|R=%lld|M=%lld|mmax=%d", prop.name, b->s16 ? 1 : 0, b->E,
+             (long long)b->ranks_elems, (long long)b->mat_elems, b->m_max);
+    clean(key);
+    bo = lookup(key);
+    if (bo < 0 || bo > 1) {
+      float best = 1e30f;
+      for (int32_t o = 0; o <= 1 && rc == SCHULZE_OK; ++o) {
+        b->order_policy = o;
+        order_jobs(b);
+        if ((rc = upload_jobs(b)) != SCHULZE_OK) break;
+        float ms = 0.f;
+        if ((rc = time_jobs(b->E, &ms)) != SCHULZE_OK) break;
+        if (ms < best) best = ms, bo = o;
       }
+      fresh.emplace_back(key, bo);
     }
   }
-  if (int rc = schulze_batch_set_schedule(b, bt, bo)) return rc;
-  if (best_tile) *best_tile = bt;
-  if (best_order) *best_order = bo;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the plan's job table back in full with the chosen schedule
+  b->order_policy = bo >= 0 ? bo : 0;
+  order_jobs(b);
+  if (int rc2 = upload_jobs(b)) return rc2;
+  if (rc != SCHULZE_OK) return rc;
+  if (cache_path && !fresh.empty()) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      for (const auto& kv : fresh) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+      fclose(f);
+    }
+  }
+  if (best_tile) *best_tile = 0;  // each m-bucket's own ballots per step
+  if (best_order) *best_order = b->order_policy;
   return SCHULZE_OK;
 }
 

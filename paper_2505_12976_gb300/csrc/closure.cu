@@ -68,7 +68,7 @@ using tiles::diag_closure;
 
 constexpr uint32_t kNZ = 1u << 30;         // progress word: tile has a nonzero entry
 constexpr uint32_t kRoundMask = kNZ - 1u;  // progress word: rounds applied
-constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz, unless the context sets another
 
 // ------------------------------------------------------------ relabel
 
@@ -81,7 +81,7 @@ constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kFlagT = 64;
 __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict__ d, int32_t m, int64_t bound,
                                                       int32_t* __restrict__ rowflag, int32_t* status,
-                                                      const int32_t* __restrict__ hint_valid) {
+                                                      const int32_t* __restrict__ hint_valid, int vec4) {
   pdl_enter_early();
   if (hint_valid && *hint_valid) return;  // the caller's tally already knows the flags
   __shared__ int32_t t1[kFlagT][kFlagT + 1], t2[kFlagT][kFlagT + 1];  // t1 = d[A.., B..], t2 = d[B.., A..]
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) rowflag_kernel(const int32_t* __restrict_
   const int64_t npairs = int64_t(nbt) * (nbt + 1) / 2;
   const int lane = threadIdx.x & 31;
   const int rq = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;  // rows rq + 16 q, columns c4 .. c4 + 3
-  const bool vec = (m & 3) == 0;
+  const bool vec = vec4 != 0;  // rows of d start on 16-byte boundaries
   int32_t a = 0;           // pairs (a, b), a <= b, numbered row by row
   int64_t rowstart = 0;    // number of the pair (a, a)
   bool bad = false;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
                                                     const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ warm, int32_t* __restrict__ p,
                                                     const int32_t* __restrict__ hint_valid,
-                                                    const int32_t* __restrict__ ucold) {
+                                                    const int32_t* __restrict__ ucold, int vec4) {
   pdl_enter();
   const int32_t nw = *warm;
   const int32_t rows = (nw + kB - 1) / kB * kB;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
       // candidate perm[b]) come from W after the fill
       if (ix >= nw || uc) {
         const int32_t fill = ix >= nw ? 0 : ucold[ix];
-        if ((m & 3) == 0) {
+        if (vec4) {
           for (int32_t y = 4 * threadIdx.x; y < m; y += 4 * blockDim.x)
             *reinterpret_cast<int4*>(prow + y) = make_int4(fill, fill, fill, fill);
         } else {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) widen_kernel(const E* __restrict__ W, int
         continue;
       }
       const E* wrow = W + int64_t(ix) * mp;
-      if ((m & 3) == 0) {
+      if (vec4) {
         constexpr int kU = 4;  // int4 groups per thread and pass, loads issued together
         for (int32_t y0 = 0; y0 < m; y0 += 4 * kU * blockDim.x) {
           int4 iv[kU];
@@ -433,6 +433,7 @@ struct Sync {
   int32_t* status;
   const int32_t* warm;           // candidates with outgoing edges
   unsigned long long* counters;  // [0] tile updates done, [1] diagonal closures done, [2] items
+  long long spin_limit;          // clock cycles a wait may take before it gives up
 };
 
 // Thread 0 waits until prog[idx] has applied at least `need` rounds; returns
@@ -444,7 +445,7 @@ __device__ uint32_t wait_round(const Sync& sy, int32_t idx, uint32_t need) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sy.prog + idx) : "memory");
     if ((v & kRoundMask) >= need) return v;
     if (*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) return 0xFFFFFFFFu;
-    if (clock64() - t0 > kSpinLimitCycles) {
+    if (clock64() - t0 > sy.spin_limit) {
       set_status(sy.status, SCHULZE_ETIMEOUT);
       atomicExch(sy.abort_flag, 1u);
       return 0xFFFFFFFFu;
@@ -464,11 +465,15 @@ __device__ __forceinline__ void publish(const Sync& sy, int32_t idx, uint32_t wo
 template <typename E>
 constexpr int32_t kClusterMaxWarm = sizeof(E) == 2 ? 256 : 192;
 
-template <typename E>
-__global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
-                                                                       Sync sy) {
+#ifdef SCHULZE_PERSIST_MIN_BLOCKS
+#define SCHULZE_PERSIST_BOUNDS __launch_bounds__(kThreads, SCHULZE_PERSIST_MIN_BLOCKS)
+#else
+#define SCHULZE_PERSIST_BOUNDS __launch_bounds__(kThreads)
+#endif
+template <typename E, int kMix>
+__global__ void SCHULZE_PERSIST_BOUNDS closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb, Sync sy) {
   pdl_enter_early();
-  __shared__ __align__(16) typename Ops<E>::Smem sm;
+  __shared__ __align__(16) typename Ops<E, kMix>::Smem sm;
   __shared__ __align__(16) int32_t rowbuf[2][kB];
   __shared__ int32_t s_item[4];
   __shared__ uint32_t s_flags;
@@ -477,9 +482,17 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
   if (*sy.warm <= kClusterMaxWarm<E>) return;  // closure_cluster_kernel's case
   const Shape sh = make_shape(nbr, nbr);  // the warm square; nb is the progress-word row stride
   const int64_t total_items = int64_t(nbr) * nbr * nbr;
+  // Thread 0 claims the next queue slot while the CTA computes the current
+  // item, so the claim's round trip does not idle the CTA between items. The
+  // schedule stays deadlock-free: a CTA holds at most one claimed item it has
+  // not started, always later in the queue than the one it computes, so the
+  // earliest unfinished item is always being computed (its dependencies are
+  // earlier, hence finished) and completes.
+  uint32_t t_next = 0;
+  if (threadIdx.x == 0) t_next = atomicAdd(sy.head, 1u);
   for (;;) {
     if (threadIdx.x == 0) {
-      const int64_t t = int64_t(atomicAdd(sy.head, 1u));
+      const int64_t t = int64_t(t_next);
       Item it{-1, 0, 0, 0};
       uint32_t flags = 0;  // bit 0: skip the update; bit 1: tile already nonzero
       if (t < total_items && !*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) {
@@ -516,12 +529,13 @@ __global__ void __launch_bounds__(kThreads) closure_persistent_kernel(E* __restr
     const uint32_t flags = s_flags;
     __syncthreads();
     if (kind < 0) return;
+    if (threadIdx.x == 0) t_next = atomicAdd(sy.head, 1u);  // in flight during this item
     bool nz = (flags & 2u) != 0;
     if (!(flags & 1u)) {
       if (kind == kDiag)
         nz = diag_closure<E>(W, ld, r, rowbuf, threadIdx.x, BlockBarrier{});
       else
-        nz = Ops<E>::update(W, ld, i, j, r, sm, threadIdx.x, BlockBarrier{});
+        nz = Ops<E, kMix>::update(W, ld, i, j, r, sm, threadIdx.x, BlockBarrier{});
     }
     if (threadIdx.x == 0) {
       publish(sy, i * nb + j, uint32_t(r + 1) | (nz ? kNZ : 0u));
@@ -808,14 +822,14 @@ __global__ void __launch_bounds__(512, 1) cold_strip_kernel(E* __restrict__ W, i
 // value either one sees is the width of a real path and the closed square
 // composes with itself without growing (p(i,x) and p(x,y) give a walk no
 // wider than p(i,y)), so the result is the exact closure either way.
-template <typename E>
+template <typename E, int kMix>
 __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ W, int32_t ld, int32_t nb,
                                                                  int32_t m, const int32_t* __restrict__ warm,
                                                                  const uint32_t* __restrict__ prog,
                                                                  unsigned long long* counters,
                                                                  const int32_t* __restrict__ hint_valid) {
   pdl_enter_early();
-  __shared__ __align__(16) typename Ops<E>::Smem sm;
+  __shared__ __align__(16) typename Ops<E, kMix>::Smem sm;
   if (*warm <= kClusterMaxWarm<E>) return;  // cold_strip_kernel's case
   if (hint_valid && *hint_valid && (*warm + kB - 1) / kB * kB < m) return;  // uniform cold columns
   const int32_t nbr = (*warm + kB - 1) / kB;
@@ -827,7 +841,7 @@ __global__ void __launch_bounds__(kThreads) cold_product_kernel(E* __restrict__ 
     for (int32_t k = 0; k < nbr; ++k) {
       const uint32_t a = prog[i * nb + k], b = prog[k * nb + j];
       if ((a & kNZ) && (b & kNZ)) {
-        Ops<E>::update(W, ld, i, j, k, sm, threadIdx.x, BlockBarrier{});
+        Ops<E, kMix>::update(W, ld, i, j, k, sm, threadIdx.x, BlockBarrier{});
         ++done;
       }
     }
@@ -898,10 +912,11 @@ struct ClosureBufs {
 };
 
 // Rowflags, relabel, pack, closure of the warm square, cold product, widen.
-// ctx may be null (no counting, no profiling).
-template <typename E>
-int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
-                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out = nullptr) {
+// ctx may be null (no counting, no profiling). kMix: the min/max units of
+// the int32 tile updates (tiles::update2_s32).
+template <typename E, int kMix>
+int closure_pipeline_mix(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                         const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   E* W = static_cast<E*>(bf.W);
@@ -928,11 +943,14 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     const int64_t nbt = (m + kFlagT - 1) / kFlagT;
     const int g = grid_for(reinterpret_cast<const void*>(rowflag_kernel), 256, 0, nbt * (nbt + 1) / 2);
     Launch L(ctx, stream, "closure_rowflags", mm * 4.0);
-    launch_pdl(rowflag_kernel, dim3(g), dim3(256), 0, stream, false, d, m, bound, bf.rowflag, status, bf.hint_valid);
+    launch_pdl(rowflag_kernel, dim3(g), dim3(256), 0, stream, false, d, m, bound, bf.rowflag, status, bf.hint_valid,
+               rows_vec16(d, m));
   }
   {
     Launch L(ctx, stream, "closure_relabel", double(m) * 12.0);
-    launch_pdl(relabel_kernel, dim3(1), dim3(1024), m <= kScanSmem ? size_t(m) * 4 : 0, stream, false,
+    const size_t smem = m <= kScanSmem ? size_t(m) * 4 : 0;
+    cudaFuncSetAttribute(relabel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    launch_pdl(relabel_kernel, dim3(1), dim3(1024), smem, stream, false,
                static_cast<const int32_t*>(bf.rowflag), m, bf.perm, bf.inv, bf.warm, bf.hint_valid);
   }
   {
@@ -953,13 +971,14 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
   if (int rc = check_launch()) return rc;
   {
     // persistent grid: every CTA resident (cooperative launch)
-    const int grid = grid_for(reinterpret_cast<const void*>(closure_persistent_kernel<E>), kThreads, 0,
+    const int grid = grid_for(reinterpret_cast<const void*>(closure_persistent_kernel<E, kMix>), kThreads, 0,
                               int64_t(nb) * nb * nb);
-    Sync sy{bf.prog, head, abort_flag, status, bf.warm, bf.counters};
+    Sync sy{bf.prog, head, abort_flag, status, bf.warm, bf.counters,
+            ctx ? ctx->wait_limit_cycles : kSpinLimitCycles};
     E* Wp = W;
     int32_t ldp = mp, nbp = nb;
     Launch L(ctx, stream, "closure_persistent", double(m) * mm);
-    if (launch_pdl(closure_persistent_kernel<E>, dim3(grid), dim3(kThreads), 0, stream, true, Wp, ldp, nbp, sy) !=
+    if (launch_pdl(closure_persistent_kernel<E, kMix>, dim3(grid), dim3(kThreads), 0, stream, true, Wp, ldp, nbp, sy) !=
         cudaSuccess) {
       cudaGetLastError();
       return SCHULZE_ECUDA;
@@ -974,9 +993,9 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
                static_cast<const int32_t*>(bf.warm), bf.counters, bf.hint_valid);
   }
   {
-    const int g = grid_for(reinterpret_cast<const void*>(cold_product_kernel<E>), kThreads, 0, int64_t(nb) * nb);
+    const int g = grid_for(reinterpret_cast<const void*>(cold_product_kernel<E, kMix>), kThreads, 0, int64_t(nb) * nb);
     Launch L(ctx, stream, "closure_cold", 0.0);
-    launch_pdl(cold_product_kernel<E>, dim3(g), dim3(kThreads), 0, stream, false, W, mp, nb, m,
+    launch_pdl(cold_product_kernel<E, kMix>, dim3(g), dim3(kThreads), 0, stream, false, W, mp, nb, m,
                static_cast<const int32_t*>(bf.warm), static_cast<const uint32_t*>(bf.prog), bf.counters,
                bf.hint_valid);
   }
@@ -991,7 +1010,8 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
     Launch L(ctx, stream, "closure_widen", mm * 4.0);
     launch_pdl(widen_kernel<E>, dim3(g), dim3(256), 0, stream, false, static_cast<const E*>(W), mp, m,
                static_cast<const int32_t*>(bf.inv), static_cast<const int32_t*>(bf.perm),
-               static_cast<const int32_t*>(bf.warm), p, bf.hint_valid, static_cast<const int32_t*>(bf.ucold));
+               static_cast<const int32_t*>(bf.warm), p, bf.hint_valid, static_cast<const int32_t*>(bf.ucold),
+               rows_vec16(p, m));
   }
   if (bb_out) {
     Launch L(ctx, stream, "closure_beaten_by", 0.0);
@@ -1000,6 +1020,19 @@ int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int
                static_cast<const int32_t*>(bf.ucount));
   }
   return check_launch();
+}
+
+// The int32 tile updates share their work between the integer and the fp32
+// min/max units (the counts' bit patterns order alike on both) unless a
+// count could reach the fp32 infinity pattern 0x7F800000.
+template <typename E>
+int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
+                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out = nullptr) {
+  if constexpr (sizeof(E) == 4 && tiles::kS32Mix != 0) {
+    if (bound < 0x7F800000LL)
+      return closure_pipeline_mix<E, tiles::kS32Mix>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out);
+  }
+  return closure_pipeline_mix<E, 0>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out);
 }
 
 template <typename E>

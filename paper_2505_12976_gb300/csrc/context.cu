@@ -95,6 +95,19 @@ static bool host_graph(schulze_ctx* ctx, const schulze_ctx::HostKey& key, Enqueu
 
 extern "C" {
 
+int schulze_set_wait_limit(schulze_ctx* ctx, int64_t cycles) {
+  if (!ctx || cycles < 1) return SCHULZE_EINVAL;
+  if (ctx->wait_limit_cycles != cycles && ctx->host_exec) {
+    // schulze_run_host's cached graph holds the old limit in its launches
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+    cudaGraphExecDestroy(ctx->host_exec);
+    ctx->host_exec = nullptr;
+    ctx->host_key = schulze_ctx::HostKey{};
+  }
+  ctx->wait_limit_cycles = cycles;
+  return SCHULZE_OK;
+}
+
 const char* schulze_strerror(int code) {
   switch (code) {
     case SCHULZE_OK: return "ok";
@@ -195,6 +208,7 @@ int schulze_get_status(schulze_ctx* ctx, int32_t* status, schulze_stream_t strea
 
 int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
                   uint32_t flags, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_tally");
   if (!ctx || !d || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 || n >= (int64_t(1) << 31) ||
       uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks))
     return SCHULZE_EINVAL;
@@ -206,6 +220,7 @@ int schulze_tally(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, 
 
 int schulze_tally_positions(schulze_ctx* ctx, const int32_t* pos, int64_t n, int32_t m, int32_t* d,
                             schulze_stream_t stream) {
+  AbiRange abi_range("schulze_tally_positions");
   if (!ctx || !d || m < 1 || m > kMaxM || n < 0 || n >= (int64_t(1) << 31) ||
       uint64_t(n) * uint64_t(m) >= (uint64_t(1) << 40) || (n > 0 && !pos))
     return SCHULZE_EINVAL;
@@ -216,6 +231,7 @@ int schulze_tally_positions(schulze_ctx* ctx, const int32_t* pos, int64_t n, int
 
 int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
                             uint32_t flags, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_strongest_paths");
   if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || bound < 0) return SCHULZE_EINVAL;
   if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || bound > 32767)) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
@@ -224,6 +240,7 @@ int schulze_strongest_paths(schulze_ctx* ctx, const int32_t* d, int32_t m, int64
 }
 
 int schulze_winners(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_winners");
   if (!ctx || !p || !winners || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
   if (int rc = ensure_workspace(ctx, extract_workspace_bytes(m), stream)) return rc;
@@ -232,6 +249,7 @@ int schulze_winners(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winn
 
 int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* order, int32_t* beaten_by,
                     schulze_stream_t stream) {
+  AbiRange abi_range("schulze_ranking");
   if (!ctx || !p || !order || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
   if (int rc = ensure_workspace(ctx, extract_workspace_bytes(m), stream)) return rc;
@@ -240,6 +258,7 @@ int schulze_ranking(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* orde
 
 int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t k_top,
                              int32_t* level, int32_t* levels, uint32_t flags, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_ranking_iterated");
   if (!ctx || !d || !level || m < 1 || m > kMaxM || bound < 0 || k_top < 1) return SCHULZE_EINVAL;
   if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || bound > 32767)) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
@@ -273,6 +292,7 @@ int schulze_ranking_iterated(schulze_ctx* ctx, const int32_t* d, int32_t m, int6
 
 int schulze_winners_propagation(schulze_ctx* ctx, const int32_t* d, int32_t m, uint32_t flags, int32_t* winners,
                                 int32_t* stats, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_winners_propagation");
   if (!ctx || !d || !winners || m < 1 || m > kMaxM) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
   if (int rc = ensure_workspace(ctx, propagation_workspace_bytes(m), stream)) return rc;
@@ -282,6 +302,7 @@ int schulze_winners_propagation(schulze_ctx* ctx, const int32_t* d, int32_t m, u
 
 int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d, int32_t* p,
                 int32_t* winners, int32_t* order, int32_t* beaten_by, uint32_t flags, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_run");
   if (!ctx || !d || !p || d == p || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 ||
       n >= (int64_t(1) << 31) || uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks))
     return SCHULZE_EINVAL;
@@ -312,6 +333,7 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
 
 int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
                      int32_t* winners_host, int32_t* order_host, uint32_t flags, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_run_host");
   if (!ctx || m < 1 || m > kMaxM || k < 0 || k > m || n < 0 || n >= (int64_t(1) << 31) ||
       uint64_t(n) * uint64_t(k) >= (uint64_t(1) << 32) || (n > 0 && k > 0 && !ranks_host))
     return SCHULZE_EINVAL;

@@ -8,12 +8,45 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/schulze.h"
 #include "../../include/schulze_profile.h"
 
 namespace schulze {
 
 constexpr int kMaxM = 65535;
+
+// Non-negative int32 values read as fp32 bit patterns keep their order
+// (sign bit clear; below 2^23 they are subnormals, which min and max without
+// flush-to-zero compare exactly), so a (max, min) update on such values may
+// run on the floating-point min/max unit instead of the integer one. Bit
+// patterns at or above 0x7F800000 would be infinities or NaNs: callers use
+// these only when every value is below that.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t fmin_bits(uint32_t a, uint32_t b) {
+  return __float_as_uint(fminf(__uint_as_float(a), __uint_as_float(b)));
+}
+__device__ __forceinline__ uint32_t fmax3_bits(uint32_t a, uint32_t b, uint32_t c) {
+  return __float_as_uint(max3f(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c)));
+}
+__device__ __forceinline__ uint32_t imax3_bits(uint32_t a, uint32_t b, uint32_t c) {
+  return uint32_t(__vimax3_s32(int32_t(a), int32_t(b), int32_t(c)));
+}
+__device__ __forceinline__ uint32_t imin_bits(uint32_t a, uint32_t b) { return uint32_t(min(int32_t(a), int32_t(b))); }
+
+// Names one C-ABI call as a range on the host timeline of profilers that
+// read NVTX annotations (header-only NVTX: a no-op when no tool is attached).
+struct AbiRange {
+  explicit AbiRange(const char* name) { nvtxRangePushA(name); }
+  ~AbiRange() { nvtxRangePop(); }
+  AbiRange(const AbiRange&) = delete;
+  AbiRange& operator=(const AbiRange&) = delete;
+};
 
 // Device status word helpers: the first error recorded wins.
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
@@ -50,6 +83,9 @@ struct schulze_ctx {
   size_t smem_optin = 0;
   int64_t launches = 0;
   bool profiling = false;
+  // bound on each device-side wait of the persistent closure, in SM clock
+  // cycles (schulze_set_wait_limit)
+  long long wait_limit_cycles = 4000000000LL;
   std::vector<schulze::ProfRecord> prof_pending;
   std::vector<schulze::ProfClass> prof_classes;
   std::vector<cudaEvent_t> prof_free_events;
@@ -81,6 +117,15 @@ namespace schulze {
 int ensure_workspace(schulze_ctx* ctx, size_t bytes, cudaStream_t stream);
 
 constexpr inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Rows of an int32 [m, m] caller matrix at `ptr` may be moved with 16-byte
+// accesses only when every row starts on a 16-byte boundary: m a multiple of
+// 4 and the base itself aligned. Caller pointers need only 4-byte alignment
+// (an int32 tensor with an odd storage offset, say), so kernels take this as
+// an argument instead of deciding from m alone.
+inline int rows_vec16(const void* ptr, int32_t m) {
+  return ((m & 3) == 0 && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0) ? 1 : 0;
+}
 
 // Carves aligned sub-buffers out of the workspace.
 struct Carver {

@@ -768,6 +768,7 @@ using namespace schulze;
 extern "C" {
 
 int schulze_features(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, float* feat, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_features");
   if (!ctx || !d || !feat || m < 1 || m > kMaxM || n < 0) return SCHULZE_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   if (int rc = ensure_workspace(ctx, learned_ws_bytes(m), stream)) return rc;
@@ -777,6 +778,7 @@ int schulze_features(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, f
 
 int schulze_mlp_forward(schulze_ctx* ctx, const float* params, const float* feat, int32_t N, float* score,
                         schulze_stream_t stream) {
+  AbiRange abi_range("schulze_mlp_forward");
   if (!ctx || !params || !feat || !score || N < 0) return SCHULZE_EINVAL;
   if (N == 0) return SCHULZE_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
@@ -788,6 +790,7 @@ int schulze_mlp_forward(schulze_ctx* ctx, const float* params, const float* feat
 int schulze_mlp_train_step(schulze_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t step,
                            const float* feat, const int32_t* label, const int32_t* seg_off, int32_t nseg, int32_t N,
                            float lr, float* loss, float* grad, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_mlp_train_step");
   if (!ctx || !params || !adam_m || !adam_v || step < 1 || !feat || !label || !seg_off || nseg < 1 || N < 1 ||
       !(lr >= 0.f))
     return SCHULZE_EINVAL;
@@ -829,6 +832,7 @@ int schulze_mlp_train_step(schulze_ctx* ctx, float* params, float* adam_m, float
 
 int schulze_certify(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const int32_t* cand, int32_t ncand,
                     int32_t* winners, int32_t* result, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_certify");
   if (!ctx || !d || !cand || !winners || !result || m < 1 || m > kMaxM || n < 0 || ncand < 0 ||
       ncand > kMaxProposals)
     return SCHULZE_EINVAL;
@@ -846,6 +850,7 @@ int schulze_certify(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, co
 
 int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, const float* params, int32_t top,
                          int32_t* winners, int32_t* stats, schulze_stream_t stream) {
+  AbiRange abi_range("schulze_winners_fast");
   if (!ctx || !d || !winners || m < 1 || m > kMaxM || n < 0 || top < 1 || top > kMaxProposals) return SCHULZE_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   const size_t lw = learned_ws_bytes(m);
@@ -870,13 +875,23 @@ int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t 
   }
   if (int rc = certify_launch(ctx, d, m, w.cand, std::min(top, m), winners, w.res, w, fwd, bwd, stream)) return rc;
   int32_t res[4] = {0, -1, 0, 0};
+  int32_t nwarm = 0;
   if (cudaMemcpyAsync(res, w.res, sizeof(res), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaMemcpyAsync(&nwarm, w.nwarm, sizeof(nwarm), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
     return SCHULZE_ECUDA;
   int32_t fallback = 0;
-  if (!res[0]) {
-    // no proposal certified (or the warm set / tie set is too large): the
-    // full closure decides, on workspace memory after the certification data
+  if (!res[0] && nwarm > kCertifyMaxWarm) {
+    // a warm set too large for the certification CTA (dense profiles): the
+    // paper's propagation (Alg. 1-4) decides exactly, with O(m^2) passes
+    // per round instead of the closure's O(nw^3)
+    fallback = 2;
+    if (int rc = ensure_workspace(ctx, propagation_workspace_bytes(m), stream)) return rc;
+    int32_t ps[2] = {0, 0};
+    if (int rc = winners_propagation_launch(ctx, d, m, false, winners, ps, ctx->ws.base, stream)) return rc;
+  } else if (!res[0]) {
+    // no proposal certified (or too many ties): the full closure decides,
+    // on workspace memory after the certification data
     fallback = 1;
     const size_t mm4 = align_up(size_t(m) * size_t(m) * 4, 256);
     const size_t stage = std::max(closure_workspace_bytes(m, n, 0), extract_workspace_bytes(m));

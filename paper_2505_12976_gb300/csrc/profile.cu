@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "count.cuh"
 #include "internal.cuh"
 
 namespace schulze {
@@ -139,12 +140,6 @@ __global__ void __launch_bounds__(256) minmax_probe_kernel(int iters, uint32_t s
   if (s == 0x12345678u) sink[0] = s;
 }
 
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float d;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-  return d;
-}
-
 // Float lanes: KIND 4 fp32 max(c, min(a, b)); KIND 5 fp32 three-input max
 // folding two updates; KIND 6 half the chains int32 three-input max, half
 // fp32 three-input max (do the two pipes add up?).
@@ -178,6 +173,70 @@ __global__ void __launch_bounds__(256) minmax_probe_f32_kernel(int iters, uint32
   uint32_t s = 0;
 #pragma unroll
   for (int q = 0; q < C; ++q) s ^= __float_as_uint(c[q]) ^ uint32_t(ci[q]);
+  if (s == 0x12345678u) sink[0] = s;
+}
+
+// Probes on non-negative int32 bit patterns, the integer and the fp32
+// min/max units sharing one set of values (see fmin_bits). KIND 7: the two
+// mins on the fp32 unit, the three-input max on the integer unit; KIND 8:
+// the reverse; KIND 9: a third of the chains all-integer, the rest
+// all-fp32; KIND 10: two thirds all-integer; KIND 11: half and half (as
+// KIND 6, on the bit patterns the closure would use).
+template <int KIND>
+__global__ void __launch_bounds__(256) minmax_probe_bits_kernel(int iters, uint32_t seed, uint32_t* sink) {
+  constexpr int C = 18;  // a multiple of 2 and 3
+  uint32_t c[C], a[C];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    c[q] = (t * 2654435761u + q * 40503u + seed) & 0xFFFFFu;
+    a[q] = (t * 97u + q * 7919u + seed * 3u) & 0xFFFFFu;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      // chains of one kind read chains of the same kind (KIND 9-11), all
+      // updated every step; q + 6, q + 12 keep the residue mod 2 and 3
+      const uint32_t b1 = c[(q + 6) % C], b2 = c[(q + 12) % C], a2 = a[(q + 6) % C];
+      bool intchain = false;
+      if (KIND == 9) intchain = (q % 3) == 0;
+      if (KIND == 10) intchain = (q % 3) != 0;
+      if (KIND == 11) intchain = (q & 1) == 0;
+      if (KIND == 7) {
+        c[q] = imax3_bits(c[q], fmin_bits(a[q], b1), fmin_bits(a2, b2));
+      } else if (KIND == 8) {
+        c[q] = fmax3_bits(c[q], imin_bits(a[q], b1), imin_bits(a2, b2));
+      } else if (intchain) {
+        c[q] = imax3_bits(c[q], imin_bits(a[q], b1), imin_bits(a2, b2));
+      } else {
+        c[q] = fmax3_bits(c[q], fmin_bits(a[q], b1), fmin_bits(a2, b2));
+      }
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < C; ++q) s ^= c[q];
+  if (s == 0x12345678u) sink[0] = s;
+}
+
+// KIND 12: the tally's guard-bit compare-and-count on two 16-bit lanes
+// (count_lt2): per chain step, two position compares.
+__global__ void __launch_bounds__(256) compare_probe_kernel(int iters, uint32_t seed, uint32_t* sink) {
+  constexpr int C = 16;
+  uint32_t acc[C], a[C];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    acc[q] = (t * 2654435761u + q * 40503u + seed) & 0x3FFF3FFFu;
+    a[q] = ((t * 97u + q * 7919u + seed * 3u) & 0x3FFF3FFFu) | kGuard2;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = count_lt2(acc[q], a[q], acc[(q + 5) % C] & 0x3FFF3FFFu);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < C; ++q) s ^= acc[q];
   if (s == 0x12345678u) sink[0] = s;
 }
 
@@ -231,7 +290,7 @@ int schulze_closure_counters(schulze_ctx* ctx, int64_t* tile_updates, int64_t* d
 }
 
 int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* seconds, double* updates) {
-  if (kind < 0 || kind > 6 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
+  if (kind < 0 || kind > 12 || blocks < 1 || iters < 1 || !seconds || !updates) return SCHULZE_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return SCHULZE_ECUDA;
   uint32_t* sink = nullptr;
   if (cudaMalloc(&sink, 4) != cudaSuccess) return SCHULZE_ENOMEM;
@@ -245,7 +304,13 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
     else if (kind == 3) minmax_probe_kernel<3><<<blocks, 256>>>(it, 1u, sink);
     else if (kind == 4) minmax_probe_f32_kernel<4><<<blocks, 256>>>(it, 1u, sink);
     else if (kind == 5) minmax_probe_f32_kernel<5><<<blocks, 256>>>(it, 1u, sink);
-    else minmax_probe_f32_kernel<6><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 6) minmax_probe_f32_kernel<6><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 7) minmax_probe_bits_kernel<7><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 8) minmax_probe_bits_kernel<8><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 9) minmax_probe_bits_kernel<9><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 10) minmax_probe_bits_kernel<10><<<blocks, 256>>>(it, 1u, sink);
+    else if (kind == 11) minmax_probe_bits_kernel<11><<<blocks, 256>>>(it, 1u, sink);
+    else compare_probe_kernel<<<blocks, 256>>>(it, 1u, sink);
   };
   launch(16);  // warm-up
   cudaEventRecord(e0);
@@ -261,9 +326,10 @@ int schulze_probe_minmax(int device, int kind, int blocks, int iters, double* se
   *seconds = double(ms) * 1e-3;
   // (max, min) updates per chain step: one, or two when a three-input max
   // folds two steps, times the lanes per word
-  static const double per_step[7] = {1.0, 2.0, 4.0, 2.0, 1.0, 2.0, 2.0};
+  static const double per_step[13] = {1.0, 2.0, 4.0, 2.0, 1.0, 2.0, 2.0, 2.0, 2.0, 2.0, 2.0, 2.0, 2.0};
   const double lanes = per_step[kind];
-  *updates = double(blocks) * 256.0 * double(iters) * 16.0 * lanes;
+  const double chains = (kind >= 7 && kind <= 11) ? 18.0 : 16.0;
+  *updates = double(blocks) * 256.0 * double(iters) * chains * lanes;
   return rc;
 }
 

@@ -6,8 +6,9 @@
 namespace schulze {
 
 // Scans of up to this many entries run in a dynamic shared-memory buffer
-// (48 KB, no opt-in needed); longer ones in place in global memory.
-constexpr int32_t kScanSmem = 12288;
+// (208 KB: the launch opts in above the 48 KB default); longer ones in place
+// in global memory.
+constexpr int32_t kScanSmem = 53248;
 
 // Block-wide exclusive scan of v[0..len) (uint32) in place; returns the total.
 // Every thread of the block must call it; part holds >= 32 words. Thread t

@@ -25,7 +25,6 @@ namespace schulze {
 namespace {
 
 constexpr int kWarp = 32;
-constexpr int kMaxRowsPerBlock = 256;  // rows of d owned by one sparse work unit
 constexpr int32_t kLocalHistMax = 16384;  // candidates counted in shared memory per CTA
 // compact pair count: |A| limits (16-bit packed / 32-bit counters), CTAs, threads
 constexpr int32_t kCompactMaxPacked = 256;
@@ -299,9 +298,8 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
 
 // Plans the sparse tally on the device (one CTA of 1024 threads):
 //  * off[c] / cursor[c]: start of candidate c's entries (exclusive scan of cnt);
-//  * the rows are cut into blocks of rb rows; block b holds E_b entries and
-//    gets nu_b = max(1, ceil(E_b / emax)) work units, each a slice of at most
-//    emax of its entries; uoff[b] is the exclusive scan of nu_b.
+//  * ord: the order in which the grouped form's rows kernel takes the rows
+//    (longest first, by floor(log2(cnt)));
 //  * slot[c]: index of c among the listed candidates (-1 if unlisted), act
 //    the inverse, meta[0] = |A| and meta[1] = 1 when the compact form runs
 //    (|A| <= compact_max). For the compact form the slots follow decreasing
@@ -310,18 +308,21 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
 //    the pair counts of one position land in distinct shared-memory banks
 //    (each slot of a 16-bit-packed row takes its own word in the first half
 //    of the slots, see compact_pairs_kernel).
-__global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb,
-                                                           int32_t nblocks, uint32_t emax, uint32_t* __restrict__ off,
-                                                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ uoff,
+__global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m,
+                                                           uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                                                           int32_t* __restrict__ ord, uint32_t S, int32_t hcap,
+                                                           int2* __restrict__ utab, int32_t utab_cap,
+                                                           int32_t* __restrict__ gmeta,
                                                            int32_t compact_max, int32_t* __restrict__ slot,
                                                            int32_t* __restrict__ act, int32_t* __restrict__ meta,
                                                            int32_t* __restrict__ hint,
                                                            int32_t* __restrict__ hint_valid) {
   pdl_enter();
   __shared__ uint32_t part[32];
-  extern __shared__ uint32_t plan_smem[];  // m words when m <= kScanSmem
+  extern __shared__ uint32_t plan_smem[];  // m words if m <= kScanSmem, then the staged counts
   // the counts are read once: the first kHeld per thread stay in registers,
-  // the rest (lists longer than kHeld * 1024 candidates) are re-read
+  // the rest (lists longer than kHeld * 1024 candidates) are staged in shared
+  // memory after the scan buffer when both fit, else re-read
   constexpr int kHeld = 8;
   int32_t held[kHeld];
 #pragma unroll
@@ -329,13 +330,21 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
     const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
     held[h] = c < m ? cnt[c] : 0;
   }
+  const int32_t held_n = kHeld * int32_t(blockDim.x);
+  const int32_t extra = m > held_n ? m - held_n : 0;
+  const bool tail_smem = extra > 0 && m + extra <= kScanSmem;
+  const int32_t* tail = tail_smem ? reinterpret_cast<const int32_t*>(plan_smem + m) : cnt + held_n;
+  if (tail_smem) {
+    for (int32_t i = threadIdx.x; i < extra; i += blockDim.x) plan_smem[m + i] = uint32_t(cnt[held_n + i]);
+    __syncthreads();
+  }
   auto each = [&](auto&& f) {  // f(c, cnt[c]) for this thread's candidates
 #pragma unroll
     for (int h = 0; h < kHeld; ++h) {
       const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
       if (c < m) f(c, held[h]);
     }
-    for (int32_t c = int32_t(threadIdx.x) + kHeld * int32_t(blockDim.x); c < m; c += blockDim.x) f(c, cnt[c]);
+    for (int32_t c = int32_t(threadIdx.x) + held_n; c < m; c += blockDim.x) f(c, tail[c - held_n]);
   };
   {
     // listed flags scanned into the slots (in shared memory, or in place in
@@ -389,19 +398,64 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
     }
     __syncthreads();
   }
-  each([&](int32_t c, int32_t x) { off[c] = uint32_t(x); });
+  // grouped form: each candidate's entries start at off[c] (the scan runs in
+  // shared memory when the list fits). The rows kernel takes its work from
+  // one queue: first the units of the heavy rows (more than S entries; the
+  // first hcap of them, each cut into units of S entries, utab[u] = (index in
+  // ord, part)), then the other rows one by one, in the order ord[]: heavy
+  // rows first, then by decreasing floor(log2(cnt)), so that long rows start
+  // early and do not end the kernel late. gmeta = {heavy rows split, units}.
+  uint32_t* offs = m <= kScanSmem ? plan_smem : off;
+  each([&](int32_t c, int32_t x) { offs[c] = uint32_t(x); });
   __syncthreads();
-  const uint32_t total = block_exclusive_scan(off, m, part);
+  const uint32_t total = block_exclusive_scan(offs, m, part);
+  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
+    const uint32_t o = offs[c];
+    if (offs != off) off[c] = o;
+    cursor[c] = o;
+  }
   if (threadIdx.x == 0) off[m] = total;
-  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) cursor[c] = off[c];
+  __shared__ uint32_t bcnt[34];
+  if (threadIdx.x < 34) bcnt[threadIdx.x] = 0u;
   __syncthreads();
-  for (int32_t b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const uint32_t e0 = off[b * rb], e1 = off[min(m, (b + 1) * rb)];
-    uoff[b] = max(1u, (e1 - e0 + emax - 1) / emax);
+  // 33: heavy; 1 .. 32: floor(log2(cnt)) + 1; 0: unlisted
+  auto bucket = [&](int32_t x) { return uint32_t(x) > S ? 33 : (x > 0 ? 32 - __clz(x) : 0); };
+  auto add_bucket = [&](int32_t b) -> uint32_t {  // warp-aggregated bcnt[b]++, returns the old count + rank
+    const uint32_t peers = __match_any_sync(__activemask(), b);
+    const int leader = __ffs(peers) - 1;
+    const uint32_t rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+    uint32_t base = 0;
+    if ((threadIdx.x & 31) == leader) base = atomicAdd(&bcnt[b], uint32_t(__popc(peers)));
+    return __shfl_sync(peers, base, leader) + rank;
+  };
+  each([&](int32_t c, int32_t x) { add_bucket(bucket(x)); });
+  __syncthreads();
+  const int32_t heavy = int32_t(bcnt[33]);
+  const int32_t hs = min(heavy, hcap);  // heavy rows split into units
+  __syncthreads();
+  if (threadIdx.x == 0) {  // bucket starts, heavy and long rows first; then counters reused as cursors
+    uint32_t run = 0;
+    for (int b = 33; b >= 0; --b) {
+      const uint32_t t = bcnt[b];
+      bcnt[b] = run;
+      run += t;
+    }
   }
   __syncthreads();
-  const uint32_t units = block_exclusive_scan(uoff, nblocks, part);
-  if (threadIdx.x == 0) uoff[nblocks] = units;
+  each([&](int32_t c, int32_t x) { ord[add_bucket(bucket(x))] = c; });
+  __syncthreads();
+  // units of the split rows: the exclusive scan of ceil(cnt / S) over
+  // ord[0 .. hs), in shared memory when the list fits, else in hcap words
+  // kept after the unit table
+  uint32_t* uo = m <= kScanSmem ? plan_smem : reinterpret_cast<uint32_t*>(utab) + 2 * size_t(utab_cap);
+  for (int32_t t = threadIdx.x; t < hs; t += blockDim.x) uo[t] = (uint32_t(cnt[ord[t]]) + S - 1) / S;
+  __syncthreads();
+  const uint32_t units = block_exclusive_scan(uo, hs, part);
+  for (int32_t t = threadIdx.x; t < hs; t += blockDim.x) {
+    const uint32_t u0 = uo[t], nu = (uint32_t(cnt[ord[t]]) + S - 1) / S;
+    for (uint32_t q = 0; q < nu; ++q) utab[u0 + q] = make_int2(t, int32_t(q));
+  }
+  if (threadIdx.x == 0) gmeta[0] = hs, gmeta[1] = int32_t(units);
 }
 
 // entries grouped by candidate: entries[cursor[c]++] = v * k + q. With kLocal
@@ -411,9 +465,19 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
 template <bool kLocal>
 __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
-                                      const int32_t* __restrict__ meta) {
+                                      const int32_t* __restrict__ meta, const int32_t* __restrict__ gmeta,
+                                      int32_t* __restrict__ hacc, uint32_t* __restrict__ hdone) {
   pdl_enter_early();
   if (meta[1]) return;  // compact form
+  {
+    // the split rows' accumulators and unit counters start at zero (the
+    // rows kernel runs after this one)
+    int4* h4 = reinterpret_cast<int4*>(hacc);  // 256-byte aligned rows of (m + 3) & ~3 words
+    const int64_t hw4 = int64_t(gmeta[0]) * ((m + 3) / 4);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < hw4; t += int64_t(gridDim.x) * blockDim.x)
+      h4[t] = make_int4(0, 0, 0, 0);
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < gmeta[0]; t += gridDim.x * blockDim.x) hdone[t] = 0u;
+  }
   if (!kLocal) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
       int32_t c = ranks[e];
@@ -447,131 +511,204 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
   }
 }
 
-// Rows of blocks split into several units start as d[c][j] = cnt[c] (0 on
-// the diagonal); their units then subtract their partial counts atomically.
-__global__ void sparse_init_split_kernel(const int32_t* __restrict__ cnt, int32_t m, int32_t rb, int32_t jw,
-                                         const uint32_t* __restrict__ uoff, int32_t* __restrict__ d,
-                                         const int32_t* __restrict__ meta) {
-  pdl_enter();
-  const int32_t b = blockIdx.x, jc = blockIdx.y;
-  if (meta[1] || uoff[b + 1] - uoff[b] <= 1) return;
-  const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
-  const int32_t J0 = jc * jw, J1 = min(m, J0 + jw);
-  for (int32_t r = R0; r < R1; ++r) {
-    const int32_t base = cnt[r];
-    int32_t* drow = d + int64_t(r) * m;
-    for (int32_t j = J0 + threadIdx.x; j < J1; j += blockDim.x) drow[j] = (j == r) ? 0 : base;
-  }
-}
+// Grouped form: d[r][j] = cnt[r] - C[r][j] row by row, each row written
+// once with streaming stores. C[r][.] is counted in shared memory as 16-bit
+// counters, two columns per word (column j in the low half of word j / 2
+// when j is even). The entries (v, q) of row r come from the grouping
+// (entries[off[r] .. off[r+1]) hold v * k + q); each adds 1 to C[r][j] for
+// every j listed above position q in ballot v. A counter never exceeds the
+// entries counted into it (at most S <= 65535 per unit).
+// A persistent CTA takes work from one queue (see sparse_plan_kernel):
+//  * a unit of a heavy row (more than S entries) counts its slice of the
+//    entries and adds its nonzero counters into the row's int32 accumulator
+//    in global memory (L2-resident, reductions without return); the unit
+//    that finishes last writes the row from the accumulator;
+//  * any other row is counted and written by one CTA (a heavy row beyond the
+//    accumulators in chunks of S entries: the first chunk writes d = cnt - C,
+//    later ones subtract their counts from the written row).
+// The write pass clears the counters it reads, ready for the next item.
+constexpr int kRowsThreads = 256;
 
-// One CTA per (work unit, column chunk [J0, J0 + jw)). C counters for the
-// unit's rows live in shared memory: 16-bit lanes packed two per word when
-// n <= 65535, else 32-bit. C[c][j] counts the unit's entries (v, q) of
-// candidate c whose ballot lists j above position q. A whole-block unit then
-// writes d[c][j] = cnt[c] - C[c][j]; a unit holding a slice of a split block
-// subtracts its nonzero counts from the pre-initialised rows.
-template <bool kPacked>
-__global__ void __launch_bounds__(512)
-    sparse_units_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
+__global__ void __launch_bounds__(kRowsThreads, 5)
+    grouped_rows_kernel(const int32_t* __restrict__ ranks, int32_t m, int32_t k, const int32_t* __restrict__ cnt,
                         const uint32_t* __restrict__ off, const uint32_t* __restrict__ entries,
-                        const uint32_t* __restrict__ uoff, int32_t nblocks, uint32_t emax, int32_t rb, int32_t jw,
-                        int32_t* __restrict__ d, const int32_t* __restrict__ meta) {
+                        const int32_t* __restrict__ ord, const int2* __restrict__ utab,
+                        const int32_t* __restrict__ gmeta, uint32_t S, int32_t* __restrict__ hacc,
+                        uint32_t* __restrict__ hdone, uint32_t* __restrict__ queue, int32_t* __restrict__ d,
+                        int vec4, const int32_t* __restrict__ meta) {
   pdl_enter_early();
-  extern __shared__ uint32_t C[];
-  __shared__ uint32_t so[kMaxRowsPerBlock + 1];  // off[R0 .. R1]
-  const uint32_t unit = blockIdx.x;
-  if (meta[1] || unit >= uoff[nblocks]) return;
-  int32_t lo = 0, hi = nblocks - 1;  // block b with uoff[b] <= unit < uoff[b + 1]
-  while (lo < hi) {
-    int32_t mid = (lo + hi + 1) >> 1;
-    if (uoff[mid] <= unit) lo = mid; else hi = mid - 1;
-  }
-  const int32_t b = lo;
-  const uint32_t u = unit - uoff[b], nu = uoff[b + 1] - uoff[b];
-  const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
-  const int32_t J0 = blockIdx.y * jw, J1 = min(m, J0 + jw);
-  const int32_t wlen = J1 - J0;
-  const int32_t wpr = kPacked ? (jw + 1) / 2 : jw;  // words per row
-  const int32_t nwords = (R1 - R0) * wpr;
-  for (int32_t t = threadIdx.x; t < nwords; t += blockDim.x) C[t] = 0u;
-  for (int32_t t = threadIdx.x; t <= R1 - R0; t += blockDim.x) so[t] = off[R0 + t];
-  __syncthreads();
-  const uint32_t eb = so[0], ee = so[R1 - R0];
-  const uint32_t s0 = eb + u * emax, s1 = min(ee, s0 + emax);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  auto count = [&](uint32_t* crow, int32_t j) {
-    if (j >= 0 && j < wlen) {
-      if (kPacked)
-        atomicAdd(&crow[j >> 1], 1u << ((j & 1) * 16));
-      else
-        atomicAdd(&crow[j], 1u);
+  if (meta[1]) return;  // compact form
+  extern __shared__ __align__(16) uint32_t rows_smem[];
+  uint32_t* C = rows_smem;
+  __shared__ int32_t s_last;
+  const int32_t wpr = (m + 1) >> 1;
+  const int32_t hld = (m + 3) & ~3;  // accumulator row stride
+  const int32_t hs = gmeta[0], units = gmeta[1];
+  const uint32_t items = uint32_t(units) + uint32_t(m - hs);
+  for (int32_t w = threadIdx.x; w < wpr; w += blockDim.x) C[w] = 0u;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  auto count = [&](int32_t j) {
+    if (uint32_t(j) < uint32_t(m)) atomicAdd(&C[j >> 1], 1u << ((j & 1) * 16));
+  };
+  // C += the prefixes of entries [c0, c1): a warp takes 32 entries (one per
+  // lane), then walks them four at a time with the lanes spread over the
+  // ballot prefix above each (four prefix loads in flight per lane)
+  auto count_range = [&](uint32_t c0, uint32_t c1) {
+    constexpr int kG = 4;
+    for (uint32_t base = c0 + 32u * wib; base < c1; base += 32u * nwarp) {
+      const uint32_t t = base + lane;
+      const uint32_t e = t < c1 ? entries[t] : 0u;
+      const int32_t q = t < c1 ? int32_t(e % uint32_t(k)) : 0;
+      const int cntv = int(min(32u, c1 - base));
+      for (int g = 0; g < cntv; g += kG) {
+        int32_t jv[kG][2], qv[kG];
+        uint32_t rowstart[kG];
+#pragma unroll
+        for (int uu = 0; uu < kG; ++uu) {
+          const int sidx = g + uu;
+          const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx & 31);
+          const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx & 31);
+          const bool ok = sidx < cntv;
+          const int32_t* prefix = ranks + (es - uint32_t(qs));
+          qv[uu] = ok ? qs : 0;
+          rowstart[uu] = es - uint32_t(qs);
+          jv[uu][0] = (ok && lane < qs) ? prefix[lane] : -1;
+          jv[uu][1] = (ok && lane + 32 < qs) ? prefix[lane + 32] : -1;
+        }
+#pragma unroll
+        for (int uu = 0; uu < kG; ++uu) {
+          count(jv[uu][0]);
+          count(jv[uu][1]);
+          for (int32_t p = 64 + lane; p < qv[uu]; p += 32) count(ranks[rowstart[uu] + p]);
+        }
+      }
     }
   };
-  // A warp takes 32 entries at a time (one per lane) and finds each entry's
-  // candidate from the CSR offsets; it then walks them four at a time with the
-  // lanes spread over the ballot prefix above each entry, so that eight
-  // prefix loads per lane are in flight before the shared-memory counts.
-  for (uint32_t base = s0 + 32u * wib; base < s1; base += 32u * nw) {
-    const uint32_t t = base + lane;
-    const bool valid = t < s1;
-    const uint32_t e = valid ? entries[t] : 0u;
-    const int32_t q = valid ? int32_t(e % uint32_t(k)) : 0;
-    int32_t c = -1;
-    if (valid) {  // row r with so[r - R0] <= t < so[r - R0 + 1]
-      int32_t a = 0, z = R1 - R0 - 1;
-      while (a < z) {
-        int32_t mid = (a + z + 1) >> 1;
-        if (so[mid] <= t) a = mid; else z = mid - 1;
+  // d[r][.] = base - C (first) or d[r][.] -= C; acc adds an int32 row of
+  // counts (the accumulator of a split row); counters cleared
+  auto write_row = [&](int32_t r, int32_t base, bool first, const int32_t* acc) {
+    int32_t* drow = d + int64_t(r) * m;
+    if (vec4) {
+      for (int32_t g = threadIdx.x; g < (m >> 2); g += blockDim.x) {
+        const int32_t j = 4 * g;
+        uint2* cw = reinterpret_cast<uint2*>(C + (j >> 1));
+        const uint2 w = *cw;
+        *cw = make_uint2(0u, 0u);
+        int4* dst = reinterpret_cast<int4*>(drow + j);
+        int4 v = first ? make_int4(base, base, base, base) : __ldcs(dst);
+        v.x -= int32_t(w.x & 0xFFFFu), v.y -= int32_t(w.x >> 16);
+        v.z -= int32_t(w.y & 0xFFFFu), v.w -= int32_t(w.y >> 16);
+        if (acc) {
+          const int4 a = __ldcg(reinterpret_cast<const int4*>(acc + j));
+          v.x -= a.x, v.y -= a.y, v.z -= a.z, v.w -= a.w;
+        }
+        if (first && r >= j && r < j + 4) {
+          const int32_t t = r - j;
+          v.x = t == 0 ? 0 : v.x, v.y = t == 1 ? 0 : v.y, v.z = t == 2 ? 0 : v.z, v.w = t == 3 ? 0 : v.w;
+        }
+        __stcs(dst, v);
       }
-      c = R0 + a;
-    }
-    const int cntv = int(min(32u, s1 - base));
-    for (int g = 0; g < cntv; g += 4) {
-      int32_t jv[4][2];
-      uint32_t* crow[4];
-      int32_t qv[4];
-      uint32_t rowstart[4];
+    } else {
+      for (int32_t w = threadIdx.x; w < wpr; w += blockDim.x) {
+        const uint32_t cw = C[w];
+        C[w] = 0u;
 #pragma unroll
-      for (int uu = 0; uu < 4; ++uu) {
-        const int sidx = g + uu;
-        const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx & 31);
-        const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx & 31);
-        const int32_t cs = __shfl_sync(0xFFFFFFFFu, c, sidx & 31);
-        const bool ok = sidx < cntv && cs >= R0 && cs < R1;
-        const int32_t* prefix = ranks + (es - uint32_t(qs));
-        qv[uu] = ok ? qs : 0;
-        rowstart[uu] = es - uint32_t(qs);
-        crow[uu] = C + (ok ? cs - R0 : 0) * wpr;
-        jv[uu][0] = (ok && lane < qs) ? prefix[lane] - J0 : -1;
-        jv[uu][1] = (ok && lane + 32 < qs) ? prefix[lane + 32] - J0 : -1;
-      }
-#pragma unroll
-      for (int uu = 0; uu < 4; ++uu) {
-        count(crow[uu], jv[uu][0]);
-        count(crow[uu], jv[uu][1]);
-        for (int32_t p = 64 + lane; p < qv[uu]; p += 32) count(crow[uu], ranks[rowstart[uu] + p] - J0);
+        for (int h = 0; h < 2; ++h) {
+          const int32_t j = 2 * w + h;
+          if (j >= m) break;
+          const int32_t c = int32_t((cw >> (16 * h)) & 0xFFFFu) + (acc ? __ldcg(acc + j) : 0);
+          if (first)
+            drow[j] = j == r ? 0 : base - c;
+          else if (c)
+            drow[j] -= c;
+        }
       }
     }
+  };
+  // Thread 0 fetches the next work item while the CTA works on the current
+  // one (queue slot at the start of the item, its row after the counting,
+  // the row's offsets and count after the write), so that the dependent
+  // global round trips of the queue do not stall the CTA between items. The
+  // item is handed over through a double buffer: the buffer written during
+  // item i is read at the start of item i + 1 and rewritten only during
+  // item i + 2, after every thread has passed the barrier that starts i + 1.
+  __shared__ int32_t s_next[2][6];  // row, part, index in ord, e0, e1, cnt (row -1: no more work)
+  auto resolve = [&](uint32_t u, int32_t& r, int32_t& part, int32_t& t) {
+    r = -1, part = -1, t = -1;
+    if (u < uint32_t(units)) {
+      const int2 ut = utab[u];
+      t = ut.x, part = ut.y, r = ord[t];
+    } else if (u < items) {
+      t = hs + int32_t(u - uint32_t(units)), r = ord[t];
+    }
+  };
+  auto publish = [&](int buf, int32_t r, int32_t part, int32_t t) {
+    s_next[buf][0] = r, s_next[buf][1] = part, s_next[buf][2] = t;
+    if (r >= 0) {
+      s_next[buf][3] = int32_t(off[r]), s_next[buf][4] = int32_t(off[r + 1]), s_next[buf][5] = cnt[r];
+    }
+  };
+  if (threadIdx.x == 0) {
+    int32_t r, part, t;
+    resolve(atomicAdd(queue, 1u), r, part, t);
+    publish(0, r, part, t);
   }
-  __syncthreads();
-  if (nu == 1) {
-    for (int32_t r = R0; r < R1; ++r) {
-      const int32_t cb = cnt[r];
-      const uint32_t* crow = C + (r - R0) * wpr;
-      int32_t* drow = d + int64_t(r) * m + J0;
-      for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
-        uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
-        drow[j] = (J0 + j == r) ? 0 : cb - int32_t(cv);
+  for (int it = 0;; ++it) {
+    __syncthreads();  // the item is published; counters cleared (first pass) / by the last write
+    const int cur = it & 1;
+    const int32_t r = s_next[cur][0], part = s_next[cur][1], t = s_next[cur][2];
+    if (r < 0) return;
+    const uint32_t e0 = uint32_t(s_next[cur][3]), e1 = uint32_t(s_next[cur][4]);
+    const int32_t cb = s_next[cur][5];
+    uint32_t u_next = 0;
+    int32_t r_n = -1, part_n = -1, t_n = -1;
+    if (threadIdx.x == 0) u_next = atomicAdd(queue, 1u);
+    auto after_count = [&]() {
+      if (threadIdx.x == 0) resolve(u_next, r_n, part_n, t_n);
+    };
+    auto after_write = [&]() {
+      if (threadIdx.x == 0) publish(cur ^ 1, r_n, part_n, t_n);
+    };
+    if (part >= 0) {
+      // a unit of a split row
+      const uint32_t c0 = e0 + uint32_t(part) * S, c1 = min(e1, c0 + S);
+      count_range(c0, c1);
+      __syncthreads();
+      after_count();
+      int32_t* acc = hacc + int64_t(t) * hld;
+      for (int32_t w = threadIdx.x; w < wpr; w += blockDim.x) {
+        const uint32_t cw = C[w];
+        if (!cw) continue;
+        C[w] = 0u;
+        if (cw & 0xFFFFu) atomicAdd(acc + 2 * w, int32_t(cw & 0xFFFFu));
+        if (cw >> 16) atomicAdd(acc + 2 * w + 1, int32_t(cw >> 16));
       }
-    }
-  } else {
-    for (int32_t r = R0; r < R1; ++r) {
-      const uint32_t* crow = C + (r - R0) * wpr;
-      int32_t* drow = d + int64_t(r) * m + J0;
-      for (int32_t j = threadIdx.x; j < wlen; j += blockDim.x) {
-        uint32_t cv = kPacked ? ((crow[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu) : crow[j];
-        if (cv && J0 + j != r) atomicSub(&drow[j], int32_t(cv));
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t nu = (uint32_t(cb) + S - 1) / S;
+        s_last = atomicAdd(hdone + t, 1u) == nu - 1 ? 1 : 0;
       }
+      __syncthreads();
+      if (s_last) {  // every unit's counts are in the accumulator
+        __threadfence();
+        write_row(r, cb, true, acc);
+      }
+      after_write();
+    } else {
+      // a whole row (chunks of S entries for a heavy row beyond the accumulators)
+      uint32_t c0 = e0;
+      bool fetched = false;
+      do {
+        const uint32_t c1 = min(e1, c0 + S);
+        count_range(c0, c1);
+        __syncthreads();
+        if (!fetched) after_count(), fetched = true;
+        write_row(r, cb, c0 == e0, nullptr);
+        c0 = c1;
+        if (c0 < e1) __syncthreads();  // the next chunk counts into cleared counters
+      } while (c0 < e1);
+      after_write();
     }
   }
 }
@@ -621,22 +758,9 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
     compact_pairs_kernel(const int32_t* __restrict__ ranks, int64_t n, int32_t m, int32_t k,
                          const int32_t* __restrict__ cnt, const int32_t* __restrict__ slot,
                          const int32_t* __restrict__ meta, uint32_t* __restrict__ partial, int32_t stage_len,
-                         int32_t* __restrict__ d, int32_t rb, int32_t nblocks, const uint32_t* __restrict__ uoff) {
+                         int32_t* __restrict__ d, int vec4) {
   pdl_enter();
-  if (!meta[1]) {
-    // the grouped form runs instead: this launch starts its split row blocks
-    // (the work of sparse_init_split_kernel, whole rows per CTA pass)
-    for (int32_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-      if (uoff[b + 1] - uoff[b] <= 1) continue;
-      const int32_t R0 = b * rb, R1 = min(m, R0 + rb);
-      for (int32_t r = R0; r < R1; ++r) {
-        const int32_t base = cnt[r];
-        int32_t* drow = d + int64_t(r) * m;
-        for (int32_t j = threadIdx.x; j < m; j += blockDim.x) drow[j] = (j == r) ? 0 : base;
-      }
-    }
-    return;
-  }
+  if (!meta[1]) return;  // the grouped form runs instead
   extern __shared__ __align__(16) uint32_t smem_pairs[];
   const int32_t na = meta[0];
   const int32_t wpr = kPacked ? (na + 1) >> 1 : na;
@@ -656,7 +780,7 @@ __global__ void __launch_bounds__(kCompactThreads, 1)
     for (int32_t i = i0; i < i1; ++i) {
       const int32_t b = slot[i] < 0 ? 0 : cnt[i];
       int32_t* drow = d + int64_t(i) * m;
-      if ((m & 3) == 0) {
+      if (vec4) {  // rows of d start on 16-byte boundaries
         for (int32_t j = 4 * ft; j < m; j += 4 * nft) {
           const int32_t t = i - j;  // diagonal lane inside the 4 entries, if any
           *reinterpret_cast<int4*>(drow + j) =
@@ -867,43 +991,6 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-struct SparsePlan {
-  int32_t rb, jw, njc, nblocks;
-  bool packed;
-  size_t smem;
-  uint32_t emax, max_units;
-};
-
-SparsePlan sparse_plan(int64_t n, int32_t m, int32_t k, int sms) {
-  const size_t smem_budget = 96 * 1024;
-  SparsePlan s;
-  s.packed = n <= 65535;
-  const size_t bytes_per = s.packed ? 2 : 4;
-  // whole rows when at least one fits, else split the columns
-  size_t row_bytes = align_up(size_t(m) * bytes_per, 4);
-  if (row_bytes <= smem_budget) {
-    s.jw = m;
-    s.njc = 1;
-    s.rb = int32_t(std::max<size_t>(1, smem_budget / row_bytes));
-    s.rb = std::min(std::min(s.rb, m), kMaxRowsPerBlock);
-  } else {
-    s.njc = int32_t((row_bytes + smem_budget - 1) / smem_budget);
-    s.jw = (m + s.njc - 1) / s.njc;
-    s.jw = (s.jw + 1) & ~1;
-    s.njc = (m + s.jw - 1) / s.jw;
-    s.rb = 1;
-  }
-  s.nblocks = (m + s.rb - 1) / s.rb;
-  size_t wpr = s.packed ? size_t(s.jw + 1) / 2 : size_t(s.jw);
-  s.smem = size_t(s.rb) * wpr * 4;
-  // about eight units per SM over all entries, but no slice below 512 entries
-  const uint64_t total = uint64_t(n) * uint64_t(k);
-  uint64_t emax = (total + uint64_t(sms) * 8 - 1) / (uint64_t(sms) * 8);
-  s.emax = uint32_t(std::max<uint64_t>(512, emax));
-  s.max_units = uint32_t(s.nblocks + (total + s.emax - 1) / s.emax);
-  return s;
-}
-
 // Compact form limits for a launch over G CTAs: cmax = the largest |A| it
 // takes (0: never), stage = per-warp staging entries (>= k), smem bytes.
 struct CompactPlan {
@@ -991,6 +1078,34 @@ int dense_tally(schulze_ctx* ctx, int64_t n, int32_t m, bool full, bool guard_ok
 
 }  // namespace
 
+// Grouped form geometry: S entries per unit of a heavy row (about eight
+// units per SM over all entries, 512 .. 65535 so that a unit's 16-bit
+// counters cannot overflow), hcap rows with accumulators (every row with
+// more than S entries, within 256 MB), the unit table's capacity.
+constexpr int kSmsForSizing = 160;  // at least the SM count of the GPUs this runs on (GB300: 152)
+
+struct GroupedPlan {
+  uint32_t S;
+  int32_t hcap, hld;
+  int64_t utab_cap;
+};
+
+GroupedPlan grouped_plan(int64_t n, int32_t m, int32_t k, int sms) {
+  GroupedPlan g;
+  const uint64_t total = uint64_t(n) * uint64_t(k);
+  g.S = uint32_t(std::min<uint64_t>(65535, std::max<uint64_t>(512, total / (uint64_t(std::max(sms, 1)) * 8))));
+  g.hld = (m + 3) & ~3;
+  const int64_t fit = std::max<int64_t>(1, (int64_t(1) << 26) / g.hld);
+  g.hcap = int32_t(std::min<int64_t>(std::min<int64_t>(m, int64_t(total / g.S) + 1), fit));
+  g.utab_cap = int64_t(total / g.S) + g.hcap + 1;
+  return g;
+}
+
+size_t grouped_bytes(const GroupedPlan& g) {
+  return align_up(size_t(g.utab_cap) * 8 + size_t(g.hcap) * 4, 256) + 256 +
+         align_up(size_t(g.hcap) * size_t(g.hld) * 4, 256) + align_up(size_t(g.hcap) * 4, 256);
+}
+
 size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
   if (choose_dense(n, m, k, flags)) {
     int32_t tile = dense_tile(m);
@@ -1001,8 +1116,9 @@ size_t tally_workspace_bytes(int64_t n, int32_t m, int32_t k, uint32_t flags) {
   // partial counts for up to kCompactMaxCtas slices, either counter width
   const size_t cp = size_t(std::min(m, kCompactMaxPacked)), cw = size_t(std::min(m, kCompactMaxWide));
   const size_t partial_words = size_t(kCompactMaxCtas) * std::max(cp * ((cp + 1) / 2), cw * cw);
-  return align_up(size_t(m) * 4, 256) + 3 * align_up((size_t(m) + 1) * 4, 256) + align_up(total * 4, 256) +
-         2 * align_up(size_t(m) * 4, 256) + 256 + align_up(partial_words * 4, 256) + 4096;
+  return align_up(size_t(m) * 4, 256) + 2 * align_up((size_t(m) + 1) * 4, 256) + align_up(size_t(m) * 4, 256) +
+         256 + align_up(total * 4, 256) + 2 * align_up(size_t(m) * 4, 256) + 256 + align_up(partial_words * 4, 256) +
+         grouped_bytes(grouped_plan(n, m, k, kSmsForSizing)) + 4096;
 }
 
 int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, int32_t k, int32_t* d,
@@ -1028,21 +1144,27 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   }
   // sparse
   const uint32_t total = uint32_t(uint64_t(n) * uint64_t(k));
-  const SparsePlan sp = sparse_plan(n, m, k, sms);
   int32_t* cnt = cv.take<int32_t>(size_t(m));
   uint32_t* off = cv.take<uint32_t>(size_t(m) + 1);
   uint32_t* cursor = cv.take<uint32_t>(size_t(m) + 1);
-  uint32_t* uoff = cv.take<uint32_t>(size_t(sp.nblocks) + 1);
+  int32_t* ord = cv.take<int32_t>(size_t(m));
+  uint32_t* queue = cv.take<uint32_t>(1);
   uint32_t* entries = cv.take<uint32_t>(total);
   int32_t* slot = cv.take<int32_t>(size_t(m));
   int32_t* act = cv.take<int32_t>(size_t(m));
   int32_t* meta = cv.take<int32_t>(2);
   const CompactPlan cp = compact_plan(n, m, k, sms, flags);
   uint32_t* partial = cv.take<uint32_t>(cp.partial_words);
+  const GroupedPlan gp = grouped_plan(n, m, k, std::min(sms, kSmsForSizing));  // within the sized workspace
+  int2* utab = reinterpret_cast<int2*>(cv.take<char>(size_t(gp.utab_cap) * 8 + size_t(gp.hcap) * 4));
+  int32_t* gmeta = cv.take<int32_t>(2);
+  int32_t* hacc = cv.take<int32_t>(size_t(gp.hcap) * size_t(gp.hld));
+  uint32_t* hdone = cv.take<uint32_t>(size_t(gp.hcap));
   {
     ZeroSpans z;
     z.p[0] = reinterpret_cast<uint32_t*>(cnt), z.words[0] = m;
     z.p[1] = reinterpret_cast<uint32_t*>(hint_valid), z.words[1] = hint ? 1 : 0;
+    z.p[2] = queue, z.words[2] = 1;
     if (int rc = zero_async(ctx, z, stream)) return rc;
   }
   const bool local_hist = m <= kLocalHistMax;
@@ -1061,9 +1183,14 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   }
   {
     Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
-    launch_pdl(sparse_plan_kernel, dim3(1), dim3(1024), m <= kScanSmem ? size_t(m) * 4 : 0, stream, false,
-               static_cast<const int32_t*>(cnt), m, sp.rb, sp.nblocks, sp.emax, off, cursor, uoff, cp.cmax, slot, act,
-               meta, hint, hint_valid);
+    // the scan buffer (m words), then the counts beyond the 8 x 1024 held in
+    // registers when both fit (the kernel makes the same choice)
+    const int32_t extra = std::max(0, m - 8 * 1024);
+    const size_t smem = m > kScanSmem ? 0 : size_t(m + (extra > 0 && m + extra <= kScanSmem ? extra : 0)) * 4;
+    cudaFuncSetAttribute(sparse_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    launch_pdl(sparse_plan_kernel, dim3(1), dim3(1024), smem, stream, false, static_cast<const int32_t*>(cnt), m, off,
+               cursor, ord, gp.S, gp.hcap, utab, int32_t(gp.utab_cap), gmeta, cp.cmax, slot, act, meta, hint,
+               hint_valid);
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_pairs", double(m) * double(m) * 4.0 + double(total) * 4.0);
@@ -1071,7 +1198,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.smem));
     launch_pdl(kern, dim3(cp.G), dim3(kCompactThreads), cp.smem, stream, false, ranks, n, m, k,
                static_cast<const int32_t*>(cnt), static_cast<const int32_t*>(slot), static_cast<const int32_t*>(meta),
-               partial, int32_t(cp.stage), d, int32_t(sp.rb), int32_t(sp.nblocks), static_cast<const uint32_t*>(uoff));
+               partial, int32_t(cp.stage), d, rows_vec16(d, m));
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_fix", 0.0);
@@ -1087,34 +1214,33 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 4095) / 4096, uint64_t(sms)));
       cudaFuncSetAttribute(sparse_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       launch_pdl(sparse_scatter_kernel<true>, dim3(blocks), dim3(1024), smem, stream, false, ranks, total, m, cursor,
-                 entries, static_cast<const int32_t*>(meta));
+                 entries, static_cast<const int32_t*>(meta), static_cast<const int32_t*>(gmeta), hacc, hdone);
     } else {
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));
       launch_pdl(sparse_scatter_kernel<false>, dim3(blocks), dim3(256), 0, stream, false, ranks, total, m, cursor,
-                 entries, static_cast<const int32_t*>(meta));
+                 entries, static_cast<const int32_t*>(meta), static_cast<const int32_t*>(gmeta), hacc, hdone);
     }
   }
-  if (cp.cmax == 0) {  // else the compact kernel starts the split rows when the grouped form runs
-    Launch L(ctx, stream, "tally_split_init", 0.0);
-    launch_pdl(sparse_init_split_kernel, dim3(sp.nblocks, sp.njc), dim3(256), 0, stream, false,
-               static_cast<const int32_t*>(cnt), m, sp.rb, sp.jw, static_cast<const uint32_t*>(uoff), d,
-               static_cast<const int32_t*>(meta));
-  }
   if (int rc = check_launch()) return rc;
-  dim3 grid(sp.max_units, sp.njc);
-  Launch L(ctx, stream, "tally_rows", double(m) * double(m) * 4.0 + double(total) * 4.0);
-  if (sp.packed) {
-    cudaFuncSetAttribute(sparse_units_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    launch_pdl(sparse_units_kernel<true>, grid, dim3(512), sp.smem, stream, false, ranks, m, k,
+  {
+    // persistent rows kernel: every CTA resident, rows from the plan's queue
+    const size_t smem = align_up(size_t((m + 1) / 2) * 4, 16);
+    cudaFuncSetAttribute(grouped_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(grouped_rows_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_rows_kernel, kRowsThreads, smem) !=
+            cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    const int grid = int(std::min<int64_t>(int64_t(per_sm) * sms, m));
+    Launch L(ctx, stream, "tally_rows", double(m) * double(m) * 4.0 + double(total) * 4.0);
+    launch_pdl(grouped_rows_kernel, dim3(grid), dim3(kRowsThreads), smem, stream, false, ranks, m, k,
                static_cast<const int32_t*>(cnt), static_cast<const uint32_t*>(off),
-               static_cast<const uint32_t*>(entries), static_cast<const uint32_t*>(uoff), int32_t(sp.nblocks), sp.emax,
-               int32_t(sp.rb), int32_t(sp.jw), d, static_cast<const int32_t*>(meta));
-  } else {
-    cudaFuncSetAttribute(sparse_units_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sp.smem));
-    launch_pdl(sparse_units_kernel<false>, grid, dim3(512), sp.smem, stream, false, ranks, m, k,
-               static_cast<const int32_t*>(cnt), static_cast<const uint32_t*>(off),
-               static_cast<const uint32_t*>(entries), static_cast<const uint32_t*>(uoff), int32_t(sp.nblocks), sp.emax,
-               int32_t(sp.rb), int32_t(sp.jw), d, static_cast<const int32_t*>(meta));
+               static_cast<const uint32_t*>(entries), static_cast<const int32_t*>(ord),
+               static_cast<const int2*>(utab), static_cast<const int32_t*>(gmeta), gp.S, hacc, hdone, queue, d,
+               rows_vec16(d, m), static_cast<const int32_t*>(meta));
   }
   return check_launch();
 }

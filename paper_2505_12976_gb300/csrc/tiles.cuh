@@ -5,6 +5,8 @@
 // when a block runs several groups side by side.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace schulze {
@@ -125,9 +127,30 @@ struct SmemS16 {
   uint16_t B[kB][kB];  // B[k][j]
 };
 
+// Which min/max unit an int32 update of the micro-tile runs on (kMix):
+// 0 all integer; 1 every second entry on the fp32 unit; 2 the mins on the
+// fp32 unit and the three-input max on the integer unit; 3 a third of the
+// entries integer, the rest fp32; 4 two thirds integer. The fp32 forms read
+// the same bits (fmin_bits): exact for every count below 0x7F800000.
+#ifndef SCHULZE_S32_MIX
+#define SCHULZE_S32_MIX 0
+#endif
+constexpr int kS32Mix = SCHULZE_S32_MIX;
+
+template <int kMix, int kE>
+__device__ __forceinline__ int32_t update2_s32(int32_t c, int32_t a0, int32_t b0, int32_t a1, int32_t b1) {
+  const uint32_t uc = uint32_t(c), ua0 = uint32_t(a0), ub0 = uint32_t(b0), ua1 = uint32_t(a1), ub1 = uint32_t(b1);
+  constexpr bool kInt = kMix == 0 || (kMix == 1 && (kE & 1) == 0) || (kMix == 3 && kE % 3 == 0) ||
+                        (kMix == 4 && kE % 3 != 0);
+  if (kMix == 2) return int32_t(imax3_bits(uc, fmin_bits(ua0, ub0), fmin_bits(ua1, ub1)));
+  if (kInt) return __vimax3_s32(c, min(a0, b0), min(a1, b1));
+  return int32_t(fmax3_bits(uc, fmin_bits(ua0, ub0), fmin_bits(ua1, ub1)));
+}
+
 // X(ti, tj) = max(X, W(ti, r) (x) W(r, tj)), int32 lanes. Returns whether
-// the updated tile holds a nonzero.
-template <class Bar>
+// the updated tile holds a nonzero. kMix: see update2_s32 (0 whenever a
+// count may reach 0x7F800000).
+template <int kMix, class Bar>
 __device__ bool tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
                                 SmemS32& sm, int tid, const Bar& bar) {
   const int tx = tid % kTX, ty = tid / kTX;
@@ -171,11 +194,18 @@ __device__ bool tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti,
       a[h][4] = a1.x, a[h][5] = a1.y, a[h][6] = a1.z, a[h][7] = a1.w;
       bb[h][0] = b.x, bb[h][1] = b.y, bb[h][2] = b.z, bb[h][3] = b.w;
     }
-#pragma unroll
-    for (int rr = 0; rr < kRM; ++rr)
-#pragma unroll
-      for (int cc = 0; cc < kRN; ++cc)
-        acc[rr][cc] = __vimax3_s32(acc[rr][cc], min(a[0][rr], bb[0][cc]), min(a[1][rr], bb[1][cc]));
+    auto row = [&](auto rrc) {
+      constexpr int rr = decltype(rrc)::value;
+      acc[rr][0] = update2_s32<kMix, rr * kRN + 0>(acc[rr][0], a[0][rr], bb[0][0], a[1][rr], bb[1][0]);
+      acc[rr][1] = update2_s32<kMix, rr * kRN + 1>(acc[rr][1], a[0][rr], bb[0][1], a[1][rr], bb[1][1]);
+      acc[rr][2] = update2_s32<kMix, rr * kRN + 2>(acc[rr][2], a[0][rr], bb[0][2], a[1][rr], bb[1][2]);
+      acc[rr][3] = update2_s32<kMix, rr * kRN + 3>(acc[rr][3], a[0][rr], bb[0][3], a[1][rr], bb[1][3]);
+    };
+    static_assert(kRM == 8 && kRN == 4, "micro-tile shape");
+    row(std::integral_constant<int, 0>{}), row(std::integral_constant<int, 1>{});
+    row(std::integral_constant<int, 2>{}), row(std::integral_constant<int, 3>{});
+    row(std::integral_constant<int, 4>{}), row(std::integral_constant<int, 5>{});
+    row(std::integral_constant<int, 6>{}), row(std::integral_constant<int, 7>{});
   }
   int32_t any = 0;
 #pragma unroll
@@ -249,19 +279,20 @@ __device__ bool tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti,
   return bar.sync_or(any != 0u);
 }
 
-template <typename E>
+// Tile update by lane format; kMix (int32 only) as for tile_update_s32.
+template <typename E, int kMix = 0>
 struct Ops;
-template <>
-struct Ops<int32_t> {
+template <int kMix>
+struct Ops<int32_t, kMix> {
   using Smem = SmemS32;
   template <class Bar>
   static __device__ bool update(int32_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,
                                 const Bar& bar) {
-    return tile_update_s32(W, ld, ti, tj, r, sm, tid, bar);
+    return tile_update_s32<kMix>(W, ld, ti, tj, r, sm, tid, bar);
   }
 };
-template <>
-struct Ops<int16_t> {
+template <int kMix>
+struct Ops<int16_t, kMix> {
   using Smem = SmemS16;
   template <class Bar>
   static __device__ bool update(int16_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,

@@ -64,6 +64,8 @@ def test_argument_checks_without_gpu(lib):
     lib.schulze_ctx_create.argtypes = [ctypes.c_int, ctypes.POINTER(v)]
     assert lib.schulze_tally(None, None, 1, 4, 4, None, 0, None) == -1
     assert lib.schulze_ctx_create(-1, ctypes.byref(v())) == -1
+    lib.schulze_set_wait_limit.argtypes = [v, ctypes.c_int64]
+    assert lib.schulze_set_wait_limit(None, 1000) == -1
 
 
 def test_host_call_argument_checks_without_gpu(lib):

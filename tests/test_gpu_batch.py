@@ -128,18 +128,55 @@ def test_batch_workload_sample_and_graph_replay():
 
 
 def test_batch_autotune_keeps_results_exact(tmp_path):
-    bw = W.batch_mixed(E=12, seed=5, m_range=(8, 200), n_range=(50, 800))
+    """The autotuner picks ballots per tally step for every m-bucket of the
+    batch and the election order; the cached choices are reused by a second
+    call, and the tuned plan stays exact."""
+    bw = W.batch_mixed(E=40, seed=5, m_range=(8, 700), n_range=(50, 800))
     b = S.SchulzeBatch(bw.n, bw.m, bw.k)
     ranks = torch.from_numpy(bw.ranks).cuda()
     cache = str(tmp_path / "autotune.txt")
     t1, o1 = b.autotune(ranks, cache)
-    assert 0 <= t1 <= 1 and 0 <= o1 <= 1
-    t2, o2 = b.autotune(ranks, cache)  # second call reads the cache
-    assert (t1, o1) == (t2, o2)
+    sched1 = b.bucket_schedule()
+    assert t1 == 0 and 0 <= o1 <= 1
+    used = [q for q, (_, _, e) in enumerate(sched1) if e > 0]
+    assert len(used) >= 4
+    lines = open(cache).read().splitlines()
+    assert sum("bucket<=" in ln for ln in lines) == len(used) and sum("|order|" in ln for ln in lines) == 1
+    for q in used:  # every choice is a staging size that fits the bucket
+        mx, ch, _ = sched1[q]
+        assert ch in (8, 16, 32, 64) and ch * (-(-mx // 64) * 64) * 6 <= 131584 and ch * mx <= 16384
+    b2 = S.SchulzeBatch(bw.n, bw.m, bw.k)
+    t2, o2 = b2.autotune(ranks, cache)  # a new plan of the same batch reads the cache
+    assert (t1, o1) == (t2, o2) and b2.bucket_schedule() == sched1
+    assert open(cache).read().splitlines() == lines  # nothing re-timed
     outs = _outputs(b)
     b.run(ranks, *outs)
     torch.cuda.synchronize()
     _check(b, [(bw.election(e).ranks, int(bw.m[e])) for e in range(bw.E)], outs)
+
+
+def test_batch_every_bucket_schedule_is_exact():
+    """Every ballots-per-step size each m-bucket accepts (8 to 64 where the
+    position rows fit) gives the oracle's results; sizes that do not fit are
+    refused."""
+    els = _mixed_elections(seed=8) + [(W.mallows(41, 900, 700, 700, 0.9, W.permutation(41, 700)), 700),
+                                      (W.impartial(42, 300, 1000, 60), 1000)]
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k)
+    ranks = torch.from_numpy(flat).cuda()
+    bucket_max = [mx for mx, _, _ in b.bucket_schedule()]
+    for chunk in (8, 16, 32, 64):
+        fits = [c * (-(-mx // 64) * 64) * 6 <= 131584 and c * mx <= 16384 for mx in bucket_max for c in [chunk]]
+        for q, ok in enumerate(fits):
+            if ok:
+                b.set_bucket_chunk(q, chunk)
+            else:
+                with pytest.raises(S.SchulzeError):
+                    b.set_bucket_chunk(q, chunk)
+        outs = _outputs(b)
+        b.run(ranks, *outs)
+        torch.cuda.synchronize()
+        _check(b, els, outs)
 
 
 def test_batch_reports_bad_ballots():

@@ -164,3 +164,104 @@ def test_winners_fast_large_election_against_closure():
     w, stats = S.schulze_winners_fast(out["d"], e.n, None, top=4)
     assert torch.equal(w, out["winners"])
     assert stats[1] == 0  # the Copeland proposal certified: no closure needed
+
+
+@pytest.fixture(scope="module")
+def trained_params():
+    """A proposal network trained by the library on 192 GPU-solved elections
+    drawn like the training set of the learned-proposal workload (m in
+    [256, 2048], top-k Mallows), eight epochs: small, but trained."""
+    from paper_2505_12976_gb300 import learned as L
+    data = L.Dataset("cuda")
+    tb = W.learned_train(E=192, seed=4242)
+    for e in range(tb.E):
+        data.add(cu(tb.election(e).ranks), int(tb.m[e]))
+    tr = L.Trainer(W.mlp_init(11), seed=12)
+    hist = tr.train(data, epochs=8, elections_per_step=32, lr=3e-3)
+    assert hist[-1] < hist[0]
+    return tr.params
+
+
+def test_learned_eval_elections_match_oracle(trained_params):
+    """Evaluation elections of the learned-proposal workload at full size
+    (m = 8192, n = 20000, top-50 Mallows(0.9)), eight of them: the winners
+    from trained proposals equal the oracle's. The oracle works on the
+    listed candidates A only: an unlisted candidate is preferred to nobody,
+    so it has no outgoing edge, every listed one beats it, and paths between
+    listed candidates never leave A (Sect. 2.1 definitions); the tally of
+    the ballots relabeled to A is d[A, A], checked against the GPU's."""
+    ev = W.learned_eval(E=8)
+    for e in range(ev.E):
+        r, m, n = ev.election(e).ranks, int(ev.m[e]), int(ev.n[e])
+        d = S.schulze_tally(cu(r), m)
+        A = np.unique(r)
+        idx = np.full(m, -1, np.int32)
+        idx[A] = np.arange(A.size, dtype=np.int32)
+        dA = oracle.tally(idx[r], A.size)
+        np.testing.assert_array_equal(d.cpu().numpy()[np.ix_(A, A)], dA)
+        want = np.zeros(m, np.int32)
+        want[A] = oracle.winners(oracle.strongest_paths(dA, nthreads=8))
+        for params in (trained_params, None):
+            w, stats = S.schulze_winners_fast(d, n, params, top=4)
+            np.testing.assert_array_equal(w.cpu().numpy(), want)
+            assert stats[1] in (0, 1)
+
+
+def test_winners_fast_dense_profile_uses_propagation():
+    """A dense profile whose warm set is too large to certify (every one of
+    2200 candidates has an outgoing edge): the paper's propagation decides,
+    exactly, instead of the closure."""
+    m, n, k = 2200, 1500, 2200
+    r = W.impartial(77, n, m, k)
+    d = S.schulze_tally(cu(r), m)
+    want = oracle.winners(oracle.strongest_paths(d.cpu().numpy(), nthreads=8))
+    w, stats = S.schulze_winners_fast(d, n, None, top=4)
+    assert stats[1] == 2, stats
+    np.testing.assert_array_equal(w.cpu().numpy(), want)
+
+
+def test_trained_proposals_gain_over_copeland():
+    """What the trained network gains over the method without it (the
+    Copeland score wins - losses as the proposer). Trained by the library on
+    2000 GPU-solved elections of the learned workload's training model,
+    twenty epochs (training is deterministic, so the counts below repeat).
+    Evaluated on near-uniform profiles (Mallows phi 0.99, 0.995, 1.0; m 300
+    and 1000; 2000 top-30 ballots), where the top of the majority graph has
+    cycles and Copeland's first choice is sometimes not a Schulze winner:
+    the network's first choice must be a winner at least as often, and must
+    be right on some elections where Copeland's is not. Winner sets from both
+    proposers stay exact (the closure judges; the oracle judges the m = 300
+    ones). The counts are printed."""
+    from paper_2505_12976_gb300 import learned as L
+    data = L.Dataset("cuda")
+    for c0 in range(0, 2000, 256):
+        tb = W.learned_train(E=min(256, 2000 - c0), seed=W.SEED_BASE + 4 + 7919 * c0)
+        for e in range(tb.E):
+            data.add(cu(tb.election(e).ranks), int(tb.m[e]))
+    tr = L.Trainer(W.mlp_init(), seed=W.SEED_BASE + 6)
+    tr.train(data, epochs=20, elections_per_step=64, lr=3e-3)
+    tally = {"E": 0, "mlp_hit1": 0, "cop_hit1": 0, "cop_miss": 0, "mlp_hit1_where_cop_misses": 0}
+    for phi in (0.99, 0.995, 1.0):
+        for s in range(32):
+            m = 300 if s % 2 else 1000
+            r = W.mallows(5000 + s, 2000, m, 30, phi, W.permutation(77 + s, m))
+            out = S.schulze_run(cu(r), m)
+            win = out["winners"].cpu().numpy()
+            if m == 300:
+                np.testing.assert_array_equal(win, oracle.winners(oracle.strongest_paths(oracle.tally(r, m))))
+            d, n = out["d"], r.shape[0]
+            mlp = S.schulze_mlp_forward(tr.params, S.schulze_features(d, n)).cpu().numpy()
+            dn = d.cpu().numpy()
+            cop = ((dn > dn.T).sum(1) - (dn < dn.T).sum(1)).astype(np.float64)
+            hit_m, hit_c = bool(win[np.argmax(mlp)]), bool(win[np.argmax(cop)])
+            tally["E"] += 1
+            tally["mlp_hit1"] += hit_m
+            tally["cop_hit1"] += hit_c
+            tally["cop_miss"] += not hit_c
+            tally["mlp_hit1_where_cop_misses"] += hit_m and not hit_c
+            for params in (tr.params, None):
+                w, _ = S.schulze_winners_fast(d, n, params, top=4)
+                np.testing.assert_array_equal(w.cpu().numpy(), win)
+    print("proposal first-choice hits on near-uniform profiles:", tally)
+    assert tally["mlp_hit1"] >= tally["cop_hit1"]
+    assert tally["cop_miss"] == 0 or tally["mlp_hit1_where_cop_misses"] >= 1

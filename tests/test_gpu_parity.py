@@ -1,5 +1,7 @@
 """CUDA path against the CPU oracle, element by element (bit-exact: every
 quantity is an integer)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -309,6 +311,142 @@ def test_closure_bound_violation_flagged():
 
 # ------------------------------------------------------- end to end
 
+def test_unaligned_caller_buffers():
+    """Caller matrices need only the 4-byte alignment of int32: d and p one
+    element past a 16-byte boundary (m a multiple of 4, so aligned buffers
+    would take 16-byte row accesses) give the oracle's results through the
+    tally's streaming fill, the closure's reads of d and its writes of p."""
+    def unaligned(m):
+        buf = torch.full((m * m + 1,), -9, dtype=torch.int32, device="cuda")
+        t = buf[1:].view(m, m)
+        assert t.data_ptr() % 16 != 0 and t.is_contiguous()
+        return t
+    m, n, k = 300, 2000, 20
+    r = W.mallows(77, n, m, k, 0.9, W.permutation(77, m))
+    d_o, p_o, win_o, order_o, bb_o = oracle.schulze(r, m)
+    d, p = unaligned(m), unaligned(m)
+    eq(host(S.schulze_tally(cu(r), m, d=d, flags=S.F_TALLY_SPARSE)), d_o, "compact tally, unaligned d")
+    eq(host(S.schulze_tally(cu(r), m, d=d, flags=S.F_TALLY_SPARSE | S.F_TALLY_GROUPED)), d_o, "grouped, unaligned d")
+    eq(host(S.schulze_strongest_paths(d, n, p=p)), p_o, "closure, unaligned d and p")
+    out = S.schulze_run(cu(r), m, out={"d": unaligned(m), "p": unaligned(m)})
+    eq(host(out["d"]), d_o)
+    eq(host(out["p"]), p_o)
+    eq(host(out["winners"]), win_o)
+    eq(host(out["order"]), order_o)
+    # a dense square above the cluster kernel's size (persistent closure)
+    rs = np.random.Generator(np.random.PCG64(78))
+    m = 516
+    dd = rs.integers(0, 30000, size=(m, m)).astype(np.int32)
+    np.fill_diagonal(dd, 0)
+    d = unaligned(m)
+    d.copy_(cu(dd))
+    want = oracle.strongest_paths(dd, nthreads=NT)
+    for flags in (0, S.F_FORCE_S32):
+        eq(host(S.schulze_strongest_paths(d, 30000, p=unaligned(m), flags=flags)), want, f"persistent flags={flags}")
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_closure_wait_limit_runs_out_and_recovers(flags):
+    """The persistent closure's bounded waits, made to run out (a limit of
+    one clock cycle on a square of 11 x 11 tiles, where items wait for the
+    tiles of the round before): the call returns, the status word reports
+    SCHULZE_ETIMEOUT, and the next call at the normal limit is exact."""
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    rs = np.random.Generator(np.random.PCG64(91 + flags))
+    m = 700
+    d = rs.integers(0, 30000, size=(m, m)).astype(np.int32)
+    np.fill_diagonal(d, 0)
+    want = oracle.strongest_paths(d, nthreads=NT)
+    dd = cu(d)
+    try:
+        ctx.set_wait_limit(1)
+        S.schulze_strongest_paths(dd, 30000, flags=flags, ctx=ctx)
+        assert ctx.status() == S.ETIMEOUT
+    finally:
+        ctx.set_wait_limit(4_000_000_000)
+    eq(host(S.schulze_strongest_paths(dd, 30000, flags=flags, ctx=ctx)), want, "after a timed-out call")
+    assert ctx.status() == S.OK
+
+
+CANARY = -0x5A5A5A5B  # 0xA5A5A5A5
+PAD = 64  # canary words before and after each buffer (256 bytes: the buffer itself stays 16-byte aligned)
+
+
+def guarded(shape, dtype=torch.int32):
+    """An output buffer with canary words on both sides; returns (view, check)
+    where check() asserts that no canary word changed."""
+    n = int(np.prod(shape))
+    fill = CANARY if dtype == torch.int32 else float("nan")
+    buf = torch.full((n + 2 * PAD,), fill, dtype=dtype, device="cuda")
+
+    def check(what=""):
+        torch.cuda.synchronize()
+        edge = torch.cat([buf[:PAD], buf[PAD + n:]]).cpu()
+        ok = (edge == CANARY).all() if dtype == torch.int32 else torch.isnan(edge).all()
+        assert bool(ok), f"canary overwritten around {what} {tuple(shape)}"
+    return buf[PAD:PAD + n].view(*shape), check
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 5, 1), (63, 300, 63), (65, 500, 20), (200, 1000, 12), (300, 900, 300),
+                                   (517, 800, 40), (1029, 400, 30)])
+def test_outputs_stay_within_their_buffers(m, n, k):
+    """A stand-in for a device memory checker: canary words before and after
+    every output buffer must survive every call that writes it (the whole
+    path, each tally form, both closures and margin weights, winners,
+    ranking, weak-order tally, the allocation-free closure, the learned
+    calls), and the outputs still equal the oracle's."""
+    r = W.mallows(m * 3 + k, n, m, k, 0.9, W.permutation(m, m))
+    d_o, p_o, win_o, order_o, bb_o = oracle.schulze(r, m)
+    rr = cu(r)
+    outs = {key: guarded(shape) for key, shape in (("d", (m, m)), ("p", (m, m)), ("winners", (m,)),
+                                                   ("order", (m,)), ("beaten_by", (m,)))}
+    S.schulze_run(rr, m, out={key: v for key, (v, _) in outs.items()})
+    for key, want in (("d", d_o), ("p", p_o), ("winners", win_o), ("order", order_o), ("beaten_by", bb_o)):
+        outs[key][1](f"schulze_run {key}")
+        eq(host(outs[key][0]), want, key)
+    for flags in (S.F_TALLY_DENSE, S.F_TALLY_SPARSE, S.F_TALLY_SPARSE | S.F_TALLY_GROUPED):
+        d, chk = guarded((m, m))
+        S.schulze_tally(rr, m, d=d, flags=flags)
+        chk(f"tally {flags}")
+        eq(host(d), d_o, f"tally {flags}")
+    dd = cu(d_o)
+    for flags in (0, S.F_FORCE_S32, S.F_MARGIN):
+        p, chk = guarded((m, m))
+        S.schulze_strongest_paths(dd, n, p=p, flags=flags)
+        chk(f"strongest_paths {flags}")
+        if not flags & S.F_MARGIN:
+            eq(host(p), p_o, f"closure {flags}")
+    pp = cu(p_o)
+    w, chk = guarded((m,))
+    S.schulze_winners(pp, winners=w)
+    chk("winners")
+    o, chk_o = guarded((m,))
+    b, chk_b = guarded((m,))
+    S.schulze_ranking(pp, order=o, beaten_by=b)
+    chk_o("order"), chk_b("beaten_by")
+    eq(host(o), order_o, "order")
+    pos = np.full((n, m), k, np.int32)
+    for v in range(n):
+        pos[v, r[v]] = np.arange(k)
+    d, chk = guarded((m, m))
+    S.schulze_tally_positions(cu(pos), d=d)
+    chk("tally_positions")
+    eq(host(d), d_o, "positions")
+    if m <= 1024:
+        p, chk = guarded((m, m))
+        S.schulze_strongest_paths_static(dd, n, p=p)
+        chk("strongest_paths_static")
+        eq(host(p), p_o, "static")
+    f, chk = guarded((m, 16), torch.float32)
+    S.schulze_features(dd, n, feat=f)
+    chk("features")
+    w, chk = guarded((m,))
+    S.schulze_winners_fast(dd, n, None, top=4, winners=w)
+    chk("winners_fast")
+    eq(host(w), win_o, "winners_fast")
+
+
 def test_degenerate_elections():
     for m in (1, 2, 9):
         for r in (np.zeros((0, m), np.int32), np.zeros((5, 0), np.int32)):
@@ -343,10 +481,50 @@ def test_host_buffers_path_matches_device_path():
         S.schulze_run_host(np.array([[0, 0]], np.int32), 3)
 
 
-def _sampled_closure_checks(w, p_gpu, rows):
-    for s in rows:
-        eq(p_gpu[s], oracle.widest_from(w, s), f"row {s}")
-        eq(p_gpu[:, s], oracle.widest_to(w, s), f"col {s}")
+NT = os.cpu_count() or 1
+
+
+def _sampled_closure_checks(w, p_gpu, rows, wT=None):
+    """Rows and columns of p by max-min Dijkstra (columns on the transposed
+    graph, whose rows are the columns of p)."""
+    wT = np.ascontiguousarray(w.T) if wT is None else wT
+    eq(p_gpu[rows], oracle.widest_many(w, rows, nthreads=NT), f"rows {rows}")
+    eq(p_gpu[:, rows].T, oracle.widest_many(wT, rows, nthreads=NT), f"columns {rows}")
+
+
+def _exact_winners_and_beaten_by(w, win_gpu, bb_gpu, seed, extra=64, wT=None):
+    """Completeness of the winner set on a profile too large for the oracle's
+    whole closure (Sect. 2.1). One reported winner c gets its row and column
+    of p by max-min Dijkstra: it must beat or tie everyone. Any other winner y
+    would need p(y, c) >= p(c, y) and, c being a winner, p(c, y) >= p(y, c):
+    a tie. So the exact winner set is c plus the candidates tied with c that
+    no one beats, each checked by its own row and column; it must equal the
+    reported set. beaten_by is then checked exactly on every candidate
+    reported with beaten_by <= 1 and on `extra` seeded others."""
+    m = w.shape[0]
+    wT = np.ascontiguousarray(w.T) if wT is None else wT
+    reported = np.flatnonzero(win_gpu)
+    assert reported.size >= 1, "empty winner set"
+    c = int(reported[0])
+    fc = oracle.widest_many(w, [c], nthreads=1)[0]
+    bc = oracle.widest_many(wT, [c], nthreads=1)[0]
+    assert np.all(fc >= bc), f"reported winner {c} is beaten"
+    tied = np.flatnonzero(fc == bc)
+    tied = tied[tied != c]
+    assert tied.size <= 512, f"{tied.size} candidates tied with the winner: too many to check one by one"
+    exact = {c}
+    if tied.size:
+        F = oracle.widest_many(w, tied, nthreads=NT)
+        B = oracle.widest_many(wT, tied, nthreads=NT)
+        exact |= {int(x) for x, f, b in zip(tied, F, B) if np.all(f >= b)}
+    assert sorted(exact) == reported.tolist(), f"winner set: reported {reported.tolist()}, exact {sorted(exact)}"
+    rs = np.random.Generator(np.random.PCG64(seed))
+    check = np.unique(np.concatenate([np.flatnonzero(bb_gpu <= 1), rs.integers(0, m, extra)])).astype(np.int32)
+    F = oracle.widest_many(w, check, nthreads=NT)
+    B = oracle.widest_many(wT, check, nthreads=NT)
+    for x, f, b in zip(check, F, B):
+        assert bb_gpu[x] == int(np.sum(b > f)), f"beaten_by[{x}]"
+    return len(exact), check.size
 
 
 def test_large_topk_workload_full_size():
@@ -364,19 +542,29 @@ def test_large_topk_workload_full_size():
     # have no outgoing edge), so p on A x A is the oracle closure of d[A, A]
     A = np.unique(e.ranks)
     dA = np.ascontiguousarray(d[np.ix_(A, A)])
-    eq(p[np.ix_(A, A)], oracle.strongest_paths(dA, nthreads=16), "closure on the listed candidates")
+    eq(p[np.ix_(A, A)], oracle.strongest_paths(dA, nthreads=NT), "closure on the listed candidates")
+    # the rest of p, whole: an unlisted candidate is preferred to nobody, so
+    # its row is zero, and every unlisted column equals p[., c] of the
+    # closure of the listed candidates plus that column (paths into c run
+    # through listed candidates only); the oracle's closure over A and eight
+    # unlisted columns gives those values, the same in every unlisted column
+    cold = np.setdiff1d(np.arange(e.m), A)
+    assert cold.size > 0
+    eq(p[cold], np.zeros((cold.size, e.m), np.int32), "rows of unlisted candidates")
+    C8 = cold[rs.choice(cold.size, min(8, cold.size), replace=False)]
+    AC = np.concatenate([A, C8])
+    pAC = oracle.strongest_paths(np.ascontiguousarray(d[np.ix_(AC, AC)]), nthreads=NT)
+    ucol = pAC[:A.size, A.size]
+    for t in range(1, C8.size):
+        eq(pAC[:A.size, A.size + t], ucol, "uniform unlisted columns in the oracle closure")
+    eq(p[np.ix_(A, cold)], np.repeat(ucol[:, None], cold.size, axis=1), "unlisted columns, listed rows")
+    # p is now checked entry by entry: winners, order and beaten_by follow
+    # from it by the oracle's own definitions
+    eq(host(out["winners"]), oracle.winners(p), "winners")
+    order_o, bb_o = oracle.ranking(p)
+    eq(host(out["order"]), order_o, "order")
+    eq(host(out["beaten_by"]), bb_o, "beaten_by")
     _sampled_closure_checks(w, p, [0, e.m - 1] + rs.integers(0, e.m, 4).tolist() + rs.choice(A, 4).tolist())
-    win = host(out["winners"])
-    bb = host(out["beaten_by"])
-    for c in np.flatnonzero(win):
-        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
-        assert np.all(fwd >= bwd), "certified winner"
-    for c in rs.integers(0, e.m, 6).tolist() + np.argsort(bb)[:4].tolist():
-        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
-        assert bb[c] == int(np.sum(bwd > fwd)), f"beaten_by[{c}]"
-    order = host(out["order"])
-    assert sorted(order.tolist()) == list(range(e.m))
-    assert np.all(np.diff(bb[order]) >= 0)
 
 
 def test_huge_pl_workload_full_size():
@@ -396,16 +584,19 @@ def test_huge_pl_workload_full_size():
             assert d[i, j] == oracle.tally_entry(e.ranks, m, i, j)
     dS = np.ascontiguousarray(d[np.ix_(sub, sub)])
     pS = S.schulze_strongest_paths(cu(dS), bound=e.n)
-    pS_want = oracle.strongest_paths(dS, nthreads=16)
+    pS_want = oracle.strongest_paths(dS, nthreads=NT)
     eq(host(pS), pS_want, "subsample closure")
     eq(host(S.schulze_winners(pS)), oracle.winners(pS_want), "subsample winners")
     eq(host(S.schulze_ranking(pS)[0]), oracle.ranking(pS_want)[0], "subsample ranking")
     w = oracle.weights(d)
+    wT = np.ascontiguousarray(w.T)
     p = host(out["p"])
-    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1]), 5])
-    for c in np.flatnonzero(host(out["winners"])):
-        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
-        assert np.all(fwd >= bwd)
+    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1]), 5], wT)
+    bb = host(out["beaten_by"])
+    _exact_winners_and_beaten_by(w, host(out["winners"]), bb, seed=16384, wT=wT)
+    order = host(out["order"])
+    assert sorted(order.tolist()) == list(range(m))
+    assert np.all(np.diff(bb[order]) >= 0)
 
 
 # ------------------------------------------ margins and weak-order ballots
@@ -541,14 +732,13 @@ def test_spotify_like_workload_full_size():
             assert d[i, j] == oracle.tally_entry(e.ranks, m, i, j)
     dS = np.ascontiguousarray(d[np.ix_(sub, sub)])
     pS = S.schulze_strongest_paths(cu(dS), bound=e.n)
-    eq(host(pS), oracle.strongest_paths(dS, nthreads=16), "subsample closure")
+    eq(host(pS), oracle.strongest_paths(dS, nthreads=NT), "subsample closure")
     w = oracle.weights(d)
+    wT = np.ascontiguousarray(w.T)
     p = host(out["p"])
-    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1000]), m - 1])
-    for c in np.flatnonzero(host(out["winners"])):
-        fwd, bwd = oracle.widest_from(w, c), oracle.widest_to(w, c)
-        assert np.all(fwd >= bwd)
+    _sampled_closure_checks(w, p, [int(sub[0]), int(sub[1000]), m - 1], wT)
     bb = host(out["beaten_by"])
+    _exact_winners_and_beaten_by(w, host(out["winners"]), bb, seed=18407, wT=wT)
     order = host(out["order"])
     assert sorted(order.tolist()) == list(range(m))
     assert np.all(np.diff(bb[order]) >= 0)

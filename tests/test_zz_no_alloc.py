@@ -8,6 +8,7 @@ The file is named to be collected last: if it fails, a run that stops at the
 first failure has already run every other test.
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -60,7 +61,7 @@ def _inputs():
 
 def test_static_matches_allocating_entry_point_twice(lib):
     S, f = lib
-    for flags in (0, S.F_FORCE_S32):
+    for flags in (0, S.F_FORCE_S32, S.F_MARGIN, S.F_MARGIN | S.F_FORCE_S32):
         for d_np, bound in _inputs():
             d = torch.from_numpy(d_np).cuda()
             status = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -92,3 +93,33 @@ def test_static_reports_data_errors_in_caller_status(lib):
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc, _ = _call(f, d, 30000, 0, status)
     assert rc == S.OK and int(status.item()) == S.EDATA
+
+
+def test_static_matches_oracle(lib):
+    """Not only the other entry point: both elections, both edge weights,
+    against the oracle's Floyd-Warshall (Sect. 2.1 definitions), each input
+    run twice in a row on the shared array."""
+    S, f = lib
+    for margin in (False, True):
+        for d_np, bound in _inputs():
+            w = oracle.weights_margin(d_np) if margin else oracle.weights(d_np)
+            want = oracle.closure(w, nthreads=os.cpu_count() or 1)
+            d = torch.from_numpy(d_np).cuda()
+            for _ in range(2):
+                status = torch.zeros(1, dtype=torch.int32, device="cuda")
+                rc, p = _call(f, d, bound, S.F_MARGIN if margin else 0, status)
+                assert rc == S.OK and int(status.item()) == S.OK
+                np.testing.assert_array_equal(p.cpu().numpy(), want)
+
+
+def test_static_binding_raises_on_device_error_without_status(lib):
+    """With no status word of the caller's, the binding checks its own and
+    raises instead of returning an unspecified p."""
+    S, _ = lib
+    d = torch.tensor([[0, 40000], [0, 0]], dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SchulzeError):
+        S.schulze_strongest_paths_static(d, 30000)
+    # and a valid call afterwards is exact again
+    d2 = torch.tensor([[0, 5, 1], [2, 0, 7], [3, 1, 0]], dtype=torch.int32, device="cuda")
+    want = oracle.strongest_paths(d2.cpu().numpy())
+    np.testing.assert_array_equal(S.schulze_strongest_paths_static(d2, 10).cpu().numpy(), want)
