@@ -769,6 +769,55 @@ def run_sharded(args, world, rank, local):
     return 0
 
 
+def run_kernel_case(args, local):
+    """Small single-kernel cases for profiling (one GPU): `closure_s32` /
+    `closure_s16` close a seeded dense random count matrix (m = --m, default
+    4096) twice as warm-up and once timed; `tally_grouped` tallies the
+    default m = 16384, n = 200000 top-20 election (the grouped form) three
+    times and once timed; `batch_sample` runs a 256-election sample of the
+    mixed batch twice and once timed. Prints the timed call's milliseconds."""
+    import torch
+    import paper_2505_12976_gb300 as S
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    if args.kernel_case in ("closure_s32", "closure_s16"):
+        m = args.m or 4096
+        hi = 1000000 if args.kernel_case == "closure_s32" else 30000
+        flags = S.F_FORCE_S32 if args.kernel_case == "closure_s32" else S.F_FORCE_S16
+        rs = np.random.Generator(np.random.PCG64(5))
+        d = rs.integers(0, hi, size=(m, m), dtype=np.int32)
+        np.fill_diagonal(d, 0)
+        dd = torch.from_numpy(d).to(dev)
+        p = torch.empty_like(dd)
+        call = lambda: S.schulze_strongest_paths(dd, hi, p=p, flags=flags)
+        reps = 2
+    elif args.kernel_case == "tally_grouped":
+        e = W.huge_pl()
+        r = torch.from_numpy(e.ranks).to(dev)
+        d = torch.empty((e.m, e.m), dtype=torch.int32, device=dev)
+        call = lambda: S.schulze_tally(r, e.m, d=d)
+        reps = 3
+    else:
+        bw = W.batch_mixed(E=256, seed=123)
+        plan = S.SchulzeBatch(bw.n, bw.m, bw.k)
+        r = torch.from_numpy(bw.ranks).to(dev)
+        w = torch.empty(plan.vec_elems, dtype=torch.int32, device=dev)
+        call = lambda: plan.run(r, winners=w)
+        reps = 2
+    for _ in range(reps):
+        call()
+    torch.cuda.synchronize()
+    ev[0].record()
+    call()
+    ev[1].record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "ms": ev[0].elapsed_time(ev[1]),
+                      "device_status": S.context().status()}), flush=True)
+    return 0
+
+
 def run_reference(args, world, rank):
     """The CPU oracle as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -816,6 +865,9 @@ def main():
     ap.add_argument("--eval-elections", type=int, default=256, help="evaluation elections (learned workload)")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs (learned workload)")
     ap.add_argument("--margin", action="store_true", help="margin edge weights instead of winning votes")
+    ap.add_argument("--kernel-case", default=None, choices=["closure_s32", "closure_s16", "tally_grouped",
+                                                             "batch_sample"],
+                    help="run one small single-kernel case for profiling instead of the benchmark")
     ap.add_argument("--shard-voters", action="store_true",
                     help="one election, voters split over the ranks (tally + all-reduce of d; strong scaling)")
     args = ap.parse_args()
@@ -836,6 +888,8 @@ def main():
     __graft_entry__.build()
     import paper_2505_12976_gb300 as S
 
+    if args.kernel_case:
+        return run_kernel_case(args, local)
     if args.shard_voters:
         return run_sharded(args, world, rank, local)
     if args.workload == "batch_mixed":

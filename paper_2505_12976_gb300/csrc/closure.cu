@@ -65,6 +65,7 @@ using tiles::kThreads;  // threads per CTA
 using tiles::BlockBarrier;
 using tiles::Ops;
 using tiles::diag_closure;
+using tiles::diag_closure_local;
 
 constexpr uint32_t kNZ = 1u << 30;         // progress word: tile has a nonzero entry
 constexpr uint32_t kRoundMask = kNZ - 1u;  // progress word: rounds applied
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(1024) relabel_kernel(const int32_t* __restrict
                                                        int32_t* __restrict__ warm_out,
                                                        const int32_t* __restrict__ hint_valid) {
   pdl_enter_early();
-  __shared__ uint32_t part[32];
+  __shared__ uint32_t part[33];
   extern __shared__ uint32_t relabel_smem[];  // m words when m <= kScanSmem
   if (hint_valid && *hint_valid) return;
   // rank[c] = 1 for warm c, scanned into the warm rank (in shared memory, or
@@ -465,82 +466,146 @@ __device__ __forceinline__ void publish(const Sync& sy, int32_t idx, uint32_t wo
 template <typename E>
 constexpr int32_t kClusterMaxWarm = sizeof(E) == 2 ? 256 : 192;
 
-#ifdef SCHULZE_PERSIST_MIN_BLOCKS
-#define SCHULZE_PERSIST_BOUNDS __launch_bounds__(kThreads, SCHULZE_PERSIST_MIN_BLOCKS)
-#else
-#define SCHULZE_PERSIST_BOUNDS __launch_bounds__(kThreads)
-#endif
+// CTAs per SM: five for int32 lanes (at most 96 registers a thread; the
+// tile update needs 92), which measured fastest against four and six; seven
+// for packed int16 lanes (72 registers, as the unbounded build took)
+#define SCHULZE_PERSIST_BOUNDS __launch_bounds__(kThreads, sizeof(E) == 2 ? 7 : 5)
+// The next work item of a persistent CTA, as thread 0 prepares it while the
+// CTA computes the current one: the item, the progress words it waits for
+// (own tile: `need` rounds applied; panel: the closed diagonal; tile: both
+// panels) and their values as first loaded.
+struct Pending {
+  Item it;
+  int32_t dep[3];
+  uint32_t need[3];
+  uint32_t val[3];
+};
+
+__device__ __forceinline__ uint32_t load_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 template <typename E, int kMix>
 __global__ void SCHULZE_PERSIST_BOUNDS closure_persistent_kernel(E* __restrict__ W, int32_t ld, int32_t nb, Sync sy) {
   pdl_enter_early();
   __shared__ __align__(16) typename Ops<E, kMix>::Smem sm;
   __shared__ __align__(16) int32_t rowbuf[2][kB];
-  __shared__ int32_t s_item[4];
-  __shared__ uint32_t s_flags;
+  __shared__ int32_t s_item[2][4];  // kind, round, tile row, tile column (double-buffered)
+  __shared__ uint32_t s_flags[2];   // bit 0: skip the update; bit 1: tile already nonzero
+  __shared__ int32_t s_slow[2];     // the next item still has to wait (double-buffered)
   constexpr uint32_t kFail = 0xFFFFFFFFu;
   const int32_t nbr = (*sy.warm + kB - 1) / kB;
   if (*sy.warm <= kClusterMaxWarm<E>) return;  // closure_cluster_kernel's case
   const Shape sh = make_shape(nbr, nbr);  // the warm square; nb is the progress-word row stride
   const int64_t total_items = int64_t(nbr) * nbr * nbr;
-  // Thread 0 claims the next queue slot while the CTA computes the current
-  // item, so the claim's round trip does not idle the CTA between items. The
-  // schedule stays deadlock-free: a CTA holds at most one claimed item it has
-  // not started, always later in the queue than the one it computes, so the
-  // earliest unfinished item is always being computed (its dependencies are
-  // earlier, hence finished) and completes.
-  uint32_t t_next = 0;
-  if (threadIdx.x == 0) t_next = atomicAdd(sy.head, 1u);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int64_t t = int64_t(t_next);
-      Item it{-1, 0, 0, 0};
-      uint32_t flags = 0;  // bit 0: skip the update; bit 1: tile already nonzero
-      if (t < total_items && !*reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) {
-        it = decode_item(t, sh);
-        const uint32_t r = uint32_t(it.r);
-        const uint32_t own = wait_round(sy, it.i * nb + it.j, r);  // rounds 0 .. r-1 applied
-        uint32_t ok = own;
-        if (own != kFail) {
-          if (it.kind == kDiag) {
-            if (!(own & kNZ)) flags |= 1u;
-          } else if (it.kind == kPanel) {
-            const uint32_t dg = wait_round(sy, it.r * nb + it.r, r + 1);
-            ok = dg;
-            if (dg != kFail && (!(dg & kNZ) || !(own & kNZ))) flags |= 1u;
-          } else {
-            const uint32_t pa = wait_round(sy, it.i * nb + it.r, r + 1);
-            const uint32_t pb = pa != kFail ? wait_round(sy, it.r * nb + it.j, r + 1) : kFail;
-            ok = pb;
-            if (pb != kFail && (!(pa & kNZ) || !(pb & kNZ))) flags |= 1u;
-          }
-        }
-        if (ok == kFail) {
-          it.kind = -1;
-        } else {
-          __threadfence();
-          if (own & kNZ) flags |= 2u;
-        }
-      }
-      s_item[0] = it.kind, s_item[1] = it.r, s_item[2] = it.i, s_item[3] = it.j;
-      s_flags = flags;
+  // Thread 0 runs the schedule. While the CTA computes item i it claims the
+  // next queue slot, decodes it and loads the progress words it depends on.
+  // After its own part of item i it looks at them again without waiting:
+  // when all are there, it writes the next item into the other half of the
+  // double buffer, which the barrier ending item i makes visible, so one
+  // barrier per item is left besides the operand barrier inside the update.
+  // When one is not there yet, nothing waits before item i is published (the
+  // missing tile may itself wait, through other CTAs, for item i): thread 0
+  // publishes, then waits (bounded) and hands the item over behind one more
+  // barrier. The schedule stays deadlock-free: a CTA holds at most one
+  // claimed, unstarted item, later in the queue than its current one, and
+  // only waits once its current item is published, so the earliest
+  // unfinished item is always being computed (its dependencies are earlier,
+  // hence finished) and completes.
+  __shared__ Pending nx;  // thread 0's alone (kept out of every thread's registers)
+  auto issue = [&](uint32_t t) {  // thread 0: claim decoded, dependencies' words loaded
+    nx.it = Item{-1, 0, 0, 0};
+    nx.dep[0] = nx.dep[1] = nx.dep[2] = -1;
+    if (int64_t(t) >= total_items || *reinterpret_cast<volatile uint32_t*>(sy.abort_flag)) return;
+    nx.it = decode_item(int64_t(t), sh);
+    const Item& it = nx.it;
+    const uint32_t r = uint32_t(it.r);
+    nx.dep[0] = it.i * nb + it.j, nx.need[0] = r;  // rounds 0 .. r-1 applied
+    if (it.kind == kPanel) {
+      nx.dep[1] = it.r * nb + it.r, nx.need[1] = r + 1;
+    } else if (it.kind == kTile) {
+      nx.dep[1] = it.i * nb + it.r, nx.need[1] = r + 1;
+      nx.dep[2] = it.r * nb + it.j, nx.need[2] = r + 1;
     }
-    __syncthreads();
-    const int32_t kind = s_item[0], r = s_item[1], i = s_item[2], j = s_item[3];
-    const uint32_t flags = s_flags;
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (nx.dep[q] >= 0) nx.val[q] = load_acquire(sy.prog + nx.dep[q]);
+  };
+  // thread 0, no waiting: every dependency of the next item there (those not
+  // seen yet are loaded once more)
+  auto ready = [&]() -> bool {
+    if (nx.it.kind < 0) return true;
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (nx.dep[q] < 0 || (nx.val[q] & kRoundMask) >= nx.need[q]) continue;
+      nx.val[q] = load_acquire(sy.prog + nx.dep[q]);
+      all = all && (nx.val[q] & kRoundMask) >= nx.need[q];
+    }
+    return all;
+  };
+  // thread 0: wait for what is still missing (bounded), decide the flags,
+  // write the next item into s_item[buf]
+  auto decide = [&](int buf) {
+    if (nx.it.kind >= 0) {
+      bool ok = true;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (nx.dep[q] < 0 || !ok || (nx.val[q] & kRoundMask) >= nx.need[q]) continue;
+        nx.val[q] = wait_round(sy, nx.dep[q], nx.need[q]);
+        ok = nx.val[q] != kFail;
+      }
+      if (!ok) nx.it.kind = -1;
+    }
+    uint32_t flags = 0;
+    if (nx.it.kind >= 0) {
+      __threadfence();
+      const uint32_t own = nx.val[0];
+      if (nx.it.kind == kDiag) {
+        if (!(own & kNZ)) flags |= 1u;
+      } else if (nx.it.kind == kPanel) {
+        if (!(nx.val[1] & kNZ) || !(own & kNZ)) flags |= 1u;
+      } else if (!(nx.val[1] & kNZ) || !(nx.val[2] & kNZ)) {
+        flags |= 1u;
+      }
+      if (own & kNZ) flags |= 2u;
+    }
+    s_item[buf][0] = nx.it.kind, s_item[buf][1] = nx.it.r, s_item[buf][2] = nx.it.i, s_item[buf][3] = nx.it.j;
+    s_flags[buf] = flags;
+  };
+  if (threadIdx.x == 0) {
+    issue(atomicAdd(sy.head, 1u));
+    decide(0);  // nothing computed yet: waiting here delays no one
+  }
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
+    const int32_t kind = s_item[buf][0], r = s_item[buf][1], i = s_item[buf][2], j = s_item[buf][3];
+    const uint32_t flags = s_flags[buf];
     if (kind < 0) return;
-    if (threadIdx.x == 0) t_next = atomicAdd(sy.head, 1u);  // in flight during this item
+    if (threadIdx.x == 0) issue(atomicAdd(sy.head, 1u));  // loads in flight during this item
     bool nz = (flags & 2u) != 0;
     if (!(flags & 1u)) {
       if (kind == kDiag)
-        nz = diag_closure<E>(W, ld, r, rowbuf, threadIdx.x, BlockBarrier{});
+        nz = diag_closure_local<E>(W, ld, r, rowbuf, threadIdx.x, BlockBarrier{});
       else
-        nz = Ops<E, kMix>::update(W, ld, i, j, r, sm, threadIdx.x, BlockBarrier{});
+        nz = Ops<E, kMix>::update_local(W, ld, i, j, r, sm, threadIdx.x, BlockBarrier{});
     }
+    if (threadIdx.x == 0) {
+      const bool fast = ready();
+      if (fast) decide(buf ^ 1);
+      s_slow[buf] = fast ? 0 : 1;
+    }
+    nz = __syncthreads_or(nz) != 0;  // every store of the tile done; next item or s_slow[buf] visible
     if (threadIdx.x == 0) {
       publish(sy, i * nb + j, uint32_t(r + 1) | (nz ? kNZ : 0u));
       if (!(flags & 1u)) atomicAdd(&sy.counters[kind == kDiag ? 1 : 0], 1ull);
       atomicAdd(&sy.counters[2], 1ull);
+    }
+    if (s_slow[buf]) {  // the next item's tiles were not all there: wait now that this one is published
+      if (threadIdx.x == 0) decide(buf ^ 1);
+      __syncthreads();
     }
   }
 }

@@ -226,13 +226,52 @@ __global__ void features_rank_finalize_kernel(const int32_t* __restrict__ cnt14,
 // ----------------------------------------------------------------- MLP
 
 // Forward pass, one thread per candidate; parameters staged in shared
-// memory. h1, h2 (ReLU outputs) are stored when given (training).
+// memory. h1, h2 (ReLU outputs) are stored when given (training). Launched
+// with kMlpThreads per CTA so that a list of a few thousand candidates
+// spreads over most SMs; every thread reads the same weight at a time
+// (a broadcast), four weights per 16-byte load, each sum taken in the
+// parameters' order.
+constexpr int kMlpThreads = 64;
 __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restrict__ theta,
                                                           const float* __restrict__ feat, int32_t N,
                                                           float* __restrict__ score, float* __restrict__ h1out,
                                                           float* __restrict__ h2out) {
-  __shared__ float p[kNP];
-  for (int t = threadIdx.x; t < kNP; t += blockDim.x) p[t] = theta[t];
+  __shared__ __align__(16) float p[kNP + 3];
+  // stage the parameters with eight loads in flight per thread (16-byte
+  // loads when the caller's array is 16-byte aligned)
+  if ((reinterpret_cast<uintptr_t>(theta) & 15u) == 0) {
+    const float4* t4 = reinterpret_cast<const float4*>(theta);
+    float4* p4 = reinterpret_cast<float4*>(p);
+    constexpr int kN4 = kNP / 4;
+    for (int t0 = threadIdx.x; t0 < kN4; t0 += 8 * blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < kN4) v[u] = __ldg(t4 + t);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < kN4) p4[t] = v[u];
+      }
+    }
+    for (int t = 4 * kN4 + threadIdx.x; t < kNP; t += blockDim.x) p[t] = theta[t];
+  } else {
+    for (int t0 = threadIdx.x; t0 < kNP; t0 += 8 * blockDim.x) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < kNP) v[u] = __ldg(theta + t);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < kNP) p[t] = v[u];
+      }
+    }
+  }
   __syncthreads();
   const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
@@ -240,18 +279,29 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restric
 #pragma unroll
   for (int q = 0; q < kNF; ++q) x[q] = feat[int64_t(c) * kNF + q];
   float h1[kH];
+  static_assert(kOffW1 % 4 == 0 && kOffW2 % 4 == 0 && kNF % 4 == 0 && kH % 4 == 0, "16-byte weight rows");
 #pragma unroll
   for (int o = 0; o < kH; ++o) {
     float s = p[kOffB1 + o];
+    const float4* w = reinterpret_cast<const float4*>(p + kOffW1 + o * kNF);
 #pragma unroll
-    for (int q = 0; q < kNF; ++q) s = fmaf(p[kOffW1 + o * kNF + q], x[q], s);
+    for (int q4 = 0; q4 < kNF / 4; ++q4) {
+      const float4 v = w[q4];
+      s = fmaf(v.x, x[4 * q4], s), s = fmaf(v.y, x[4 * q4 + 1], s);
+      s = fmaf(v.z, x[4 * q4 + 2], s), s = fmaf(v.w, x[4 * q4 + 3], s);
+    }
     h1[o] = fmaxf(s, 0.f);
   }
   float out = p[kOffB3];
   for (int o = 0; o < kH; ++o) {
     float s = p[kOffB2 + o];
+    const float4* w = reinterpret_cast<const float4*>(p + kOffW2 + o * kH);
 #pragma unroll
-    for (int q = 0; q < kH; ++q) s = fmaf(p[kOffW2 + o * kH + q], h1[q], s);
+    for (int q4 = 0; q4 < kH / 4; ++q4) {
+      const float4 v = w[q4];
+      s = fmaf(v.x, h1[4 * q4], s), s = fmaf(v.y, h1[4 * q4 + 1], s);
+      s = fmaf(v.z, h1[4 * q4 + 2], s), s = fmaf(v.w, h1[4 * q4 + 3], s);
+    }
     const float h = fmaxf(s, 0.f);
     if (h2out) h2out[int64_t(c) * kH + o] = h;
     out = fmaf(p[kOffW3 + o], h, out);
@@ -783,7 +833,8 @@ int schulze_mlp_forward(schulze_ctx* ctx, const float* params, const float* feat
   if (N == 0) return SCHULZE_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
   Launch L(ctx, stream, "mlp_forward", double(N) * 5248.0 * 2.0);
-  mlp_forward_kernel<<<(N + 255) / 256, 256, 0, stream>>>(params, feat, N, score, nullptr, nullptr);
+  mlp_forward_kernel<<<(N + kMlpThreads - 1) / kMlpThreads, kMlpThreads, 0, stream>>>(params, feat, N, score, nullptr,
+                                                                                        nullptr);
   return check_launch();
 }
 
@@ -810,7 +861,7 @@ int schulze_mlp_train_step(schulze_ctx* ctx, float* params, float* adam_m, float
   float* g = grad ? grad : cv.take<float>(kNP);
   {
     Launch L(ctx, stream, "mlp_train_forward", double(N) * 5248.0 * 2.0);
-    mlp_forward_kernel<<<(N + 255) / 256, 256, 0, stream>>>(params, feat, N, score, h1, h2);
+    mlp_forward_kernel<<<(N + kMlpThreads - 1) / kMlpThreads, kMlpThreads, 0, stream>>>(params, feat, N, score, h1, h2);
   }
   {
     Launch L(ctx, stream, "mlp_train_loss", double(N) * 8.0);
@@ -865,7 +916,8 @@ int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t 
   {
     Launch L(ctx, stream, "proposal_scores", double(m) * 5248.0 * 2.0);
     if (params)
-      mlp_forward_kernel<<<(m + 255) / 256, 256, 0, stream>>>(params, feat, m, w.score, nullptr, nullptr);
+      mlp_forward_kernel<<<(m + kMlpThreads - 1) / kMlpThreads, kMlpThreads, 0, stream>>>(params, feat, m, w.score,
+                                                                                          nullptr, nullptr);
     else
       copeland_score_kernel<<<std::max(1, std::min((m + 255) / 256, 1024)), 256, 0, stream>>>(w.acc, m, w.score);
   }

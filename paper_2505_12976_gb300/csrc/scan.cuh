@@ -11,41 +11,47 @@ namespace schulze {
 constexpr int32_t kScanSmem = 53248;
 
 // Block-wide exclusive scan of v[0..len) (uint32) in place; returns the total.
-// Every thread of the block must call it; part holds >= 32 words. Thread t
-// sums a contiguous run of v, the runs are scanned with warp shuffles and
-// one pass over the warp totals, then each thread rewrites its run.
+// Every thread of the block must call it; part holds >= 33 words. Warp w
+// owns the contiguous segment [w * seg, (w + 1) * seg): its lanes read 32
+// consecutive words at a time (no shared-memory bank conflicts), a first
+// pass sums the segment, one warp scans the segment totals, and a second
+// pass scans each run of 32 with warp shuffles, carrying the running sum.
 __device__ inline uint32_t block_exclusive_scan(uint32_t* v, int32_t len, uint32_t* part) {
-  const int T = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int per = (len + T - 1) / T;
-  const int b = min(len, threadIdx.x * per), e = min(len, b + per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int32_t seg = (len + nw - 1) / nw;
+  const int32_t b = min(len, wid * seg), e = min(len, b + seg);
   uint32_t s = 0;
-  for (int c = b; c < e; ++c) s += v[c];
-  uint32_t x = s;  // inclusive scan within the warp
+  for (int32_t c = b + lane; c < e; c += 32) s += v[c];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) part[wid] = x;
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) part[wid] = s;
   __syncthreads();
   if (wid == 0) {
-    const int nw = T >> 5;
-    uint32_t w = lane < nw ? part[lane] : 0u;
+    const uint32_t x = lane < nw ? part[lane] : 0u;
+    uint32_t inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-      if (lane >= o) w += y;
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += y;
     }
-    if (lane < nw) part[lane] = w;  // inclusive warp totals
+    if (lane < nw) part[lane] = inc - x;  // exclusive prefix of each segment
+    if (lane == 31) part[32] = inc;        // the total
   }
   __syncthreads();
-  uint32_t run = (wid ? part[wid - 1] : 0u) + x - s;
-  for (int c = b; c < e; ++c) {
-    const uint32_t y = v[c];
-    v[c] = run;
-    run += y;
+  uint32_t carry = part[wid];
+  for (int32_t c0 = b; c0 < e; c0 += 32) {
+    const int32_t c = c0 + lane;
+    const uint32_t x = c < e ? v[c] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (c < e) v[c] = carry + inc - x;
+    carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
   }
-  const uint32_t total = part[(T >> 5) - 1];
+  const uint32_t total = part[32];
   __syncthreads();
   return total;
 }

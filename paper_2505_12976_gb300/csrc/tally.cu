@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __rest
                                                            int32_t* __restrict__ hint,
                                                            int32_t* __restrict__ hint_valid) {
   pdl_enter();
-  __shared__ uint32_t part[32];
+  __shared__ uint32_t part[33];
   extern __shared__ uint32_t plan_smem[];  // m words if m <= kScanSmem, then the staged counts
   // the counts are read once: the first kHeld per thread stay in registers,
   // the rest (lists longer than kHeld * 1024 candidates) are staged in shared

@@ -48,8 +48,8 @@ struct GroupBarrier {
 // tile's diagonal may pick up cycle widths; it never changes an off-diagonal
 // entry and is zeroed on output. Returns whether the tile holds a nonzero.
 template <typename E, class Bar>
-__device__ bool diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t (*rowbuf)[kB], int tid,
-                             const Bar& bar) {
+__device__ bool diag_closure_local(E* __restrict__ W, int32_t ld, int32_t r, int32_t (*rowbuf)[kB], int tid,
+                                   const Bar& bar) {
   const int i = tid >> 1, half = tid & 1;
   E* base = W + (int64_t(r) * kB + i) * ld + int64_t(r) * kB + half * 32;
   int32_t v[32];
@@ -114,7 +114,16 @@ __device__ bool diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t (
       any |= v[4 * q] | v[4 * q + 1] | v[4 * q + 2] | v[4 * q + 3];
     }
   }
-  return bar.sync_or(any != 0);
+  return any != 0;
+}
+
+// The closure above, then one barrier that also reports whether the tile
+// holds a nonzero anywhere. The _local form leaves that barrier to the
+// caller (it returns this thread's part of the answer).
+template <typename E, class Bar>
+__device__ bool diag_closure(E* __restrict__ W, int32_t ld, int32_t r, int32_t (*rowbuf)[kB], int tid,
+                             const Bar& bar) {
+  return bar.sync_or(diag_closure_local<E>(W, ld, r, rowbuf, tid, bar));
 }
 
 // Shared-memory operand layouts of one tile update.
@@ -151,8 +160,8 @@ __device__ __forceinline__ int32_t update2_s32(int32_t c, int32_t a0, int32_t b0
 // the updated tile holds a nonzero. kMix: see update2_s32 (0 whenever a
 // count may reach 0x7F800000).
 template <int kMix, class Bar>
-__device__ bool tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
-                                SmemS32& sm, int tid, const Bar& bar) {
+__device__ bool tile_update_s32_local(int32_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
+                                      SmemS32& sm, int tid, const Bar& bar) {
   const int tx = tid % kTX, ty = tid / kTX;
   const int32_t* Ag = W + int64_t(ti) * kB * ld + int64_t(r) * kB;
   const int32_t* Bg = W + int64_t(r) * kB * ld + int64_t(tj) * kB;
@@ -214,13 +223,13 @@ __device__ bool tile_update_s32(int32_t* __restrict__ W, int32_t ld, int32_t ti,
     __stcg(reinterpret_cast<int4*>(Cg + int64_t(ty * kRM + rr) * ld + tx * kRN), v);
     any |= v.x | v.y | v.z | v.w;
   }
-  return bar.sync_or(any != 0);  // also frees the shared operands
+  return any != 0;  // the caller's barrier also frees the shared operands
 }
 
 // X(ti, tj) = max(X, W(ti, r) (x) W(r, tj)), two 16-bit lanes per word.
 template <class Bar>
-__device__ bool tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
-                                SmemS16& sm, int tid, const Bar& bar) {
+__device__ bool tile_update_s16_local(int16_t* __restrict__ W, int32_t ld, int32_t ti, int32_t tj, int32_t r,
+                                      SmemS16& sm, int tid, const Bar& bar) {
   const int tx = tid % kTX, ty = tid / kTX;
   const int16_t* Ag = W + int64_t(ti) * kB * ld + int64_t(r) * kB;
   const int16_t* Bg = W + int64_t(r) * kB * ld + int64_t(tj) * kB;
@@ -276,28 +285,41 @@ __device__ bool tile_update_s16(int16_t* __restrict__ W, int32_t ld, int32_t ti,
     __stcg(reinterpret_cast<uint2*>(Cg + int64_t(ty * kRM + rr) * ld + tx * kRN), make_uint2(acc[rr][0], acc[rr][1]));
     any |= acc[rr][0] | acc[rr][1];
   }
-  return bar.sync_or(any != 0u);
+  return any != 0u;
 }
 
-// Tile update by lane format; kMix (int32 only) as for tile_update_s32.
+// Tile update by lane format; kMix (int32 only) as for tile_update_s32_local.
+// update() ends with the barrier that also reports whether the updated tile
+// holds a nonzero (and frees the shared operands); update_local() leaves
+// that barrier to the caller and returns this thread's part of the answer.
 template <typename E, int kMix = 0>
 struct Ops;
 template <int kMix>
 struct Ops<int32_t, kMix> {
   using Smem = SmemS32;
   template <class Bar>
+  static __device__ bool update_local(int32_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,
+                                      const Bar& bar) {
+    return tile_update_s32_local<kMix>(W, ld, ti, tj, r, sm, tid, bar);
+  }
+  template <class Bar>
   static __device__ bool update(int32_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,
                                 const Bar& bar) {
-    return tile_update_s32<kMix>(W, ld, ti, tj, r, sm, tid, bar);
+    return bar.sync_or(update_local(W, ld, ti, tj, r, sm, tid, bar));
   }
 };
 template <int kMix>
 struct Ops<int16_t, kMix> {
   using Smem = SmemS16;
   template <class Bar>
+  static __device__ bool update_local(int16_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,
+                                      const Bar& bar) {
+    return tile_update_s16_local(W, ld, ti, tj, r, sm, tid, bar);
+  }
+  template <class Bar>
   static __device__ bool update(int16_t* W, int32_t ld, int32_t ti, int32_t tj, int32_t r, Smem& sm, int tid,
                                 const Bar& bar) {
-    return tile_update_s16(W, ld, ti, tj, r, sm, tid, bar);
+    return bar.sync_or(update_local(W, ld, ti, tj, r, sm, tid, bar));
   }
 };
 
