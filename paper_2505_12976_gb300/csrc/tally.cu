@@ -550,37 +550,47 @@ __global__ void __launch_bounds__(kRowsThreads, 5)
   auto count = [&](int32_t j) {
     if (uint32_t(j) < uint32_t(m)) atomicAdd(&C[j >> 1], 1u << ((j & 1) * 16));
   };
-  // C += the prefixes of entries [c0, c1): a warp takes 32 entries (one per
-  // lane), then walks them four at a time with the lanes spread over the
-  // ballot prefix above each (four prefix loads in flight per lane)
+  // C += the prefixes of entries [c0, c1). A warp takes 32 entries (one per
+  // lane; entry e is position q = e mod k of its ballot, whose q prefix
+  // positions are counted) and numbers their (entry, prefix position) pairs
+  // consecutively with an inclusive scan of q over the lanes; each lane then
+  // takes every 32nd pair, finding its entry by a binary search over the
+  // scan. Every lane does useful work whatever the mix of q (the lanes of a
+  // short prefix would otherwise idle), and a long prefix is still read by
+  // consecutive lanes. kU pairs per lane are in flight at a time.
   auto count_range = [&](uint32_t c0, uint32_t c1) {
-    constexpr int kG = 4;
+    constexpr int kU = 4;
     for (uint32_t base = c0 + 32u * wib; base < c1; base += 32u * nwarp) {
       const uint32_t t = base + lane;
       const uint32_t e = t < c1 ? entries[t] : 0u;
       const int32_t q = t < c1 ? int32_t(e % uint32_t(k)) : 0;
-      const int cntv = int(min(32u, c1 - base));
-      for (int g = 0; g < cntv; g += kG) {
-        int32_t jv[kG][2], qv[kG];
-        uint32_t rowstart[kG];
+      const uint32_t first = e - uint32_t(q);  // the ballot's first position
+      int32_t incl = q;
 #pragma unroll
-        for (int uu = 0; uu < kG; ++uu) {
-          const int sidx = g + uu;
-          const uint32_t es = __shfl_sync(0xFFFFFFFFu, e, sidx & 31);
-          const int32_t qs = __shfl_sync(0xFFFFFFFFu, q, sidx & 31);
-          const bool ok = sidx < cntv;
-          const int32_t* prefix = ranks + (es - uint32_t(qs));
-          qv[uu] = ok ? qs : 0;
-          rowstart[uu] = es - uint32_t(qs);
-          jv[uu][0] = (ok && lane < qs) ? prefix[lane] : -1;
-          jv[uu][1] = (ok && lane + 32 < qs) ? prefix[lane + 32] : -1;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int32_t excl = incl - q, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      for (int32_t f0 = 0; f0 < total; f0 += 32 * kU) {
+        int32_t jv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int32_t f = f0 + 32 * u + lane;
+          // s = the number of lanes whose pairs all lie below f (at most 31
+          // when f < total): pair f belongs to lane s's entry
+          int s = 0;
+#pragma unroll
+          for (int step = 16; step; step >>= 1) {
+            const int32_t v = __shfl_sync(0xFFFFFFFFu, incl, s + step - 1);
+            if (v <= f) s += step;
+          }
+          const int32_t ex = __shfl_sync(0xFFFFFFFFu, excl, s);
+          const uint32_t st = __shfl_sync(0xFFFFFFFFu, first, s);
+          jv[u] = f < total ? ranks[st + uint32_t(f - ex)] : -1;
         }
 #pragma unroll
-        for (int uu = 0; uu < kG; ++uu) {
-          count(jv[uu][0]);
-          count(jv[uu][1]);
-          for (int32_t p = 64 + lane; p < qv[uu]; p += 32) count(ranks[rowstart[uu] + p]);
-        }
+        for (int u = 0; u < kU; ++u) count(jv[u]);
       }
     }
   };
