@@ -19,7 +19,6 @@
 
 #include "count.cuh"
 #include "internal.cuh"
-#include "scan.cuh"
 
 namespace schulze {
 namespace {
@@ -230,7 +229,32 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
   __syncthreads();
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  if (k <= 64) {
+  if (k <= 32) {
+    // ballots of at most 32 positions: a lane per position, the next two
+    // ballots' ids in flight while this one is checked and counted
+    auto id = [&](int64_t u) { return (u < n && lane < k) ? ranks[u * k + lane] : -1; };
+    int32_t x0 = id(warp), x1 = id(warp + nwarps);
+    const bool pa = lane < k;
+    for (int64_t v = warp; v < n; v += nwarps) {
+      const int32_t ca = x0;
+      x0 = x1;
+      x1 = id(v + 2 * nwarps);
+      const bool oka = pa && ca >= 0 && ca < m;
+      const uint32_t bita = 1u << (ca & 31);
+      const uint32_t olda = oka ? atomicOr(&bm[ca >> 5], bita) : 0u;
+      const bool fa = oka && !(olda & bita);  // first occurrence
+      if (pa && !fa) set_status(status, SCHULZE_EDATA);  // out of range or repeated
+      if (fa) {
+        if (kLocal)
+          atomicAdd(&hist[ca], 1u);
+        else
+          atomicAdd(&cnt[ca], 1);
+      }
+      __syncwarp();
+      if (oka) bm[ca >> 5] = 0u;  // clear what this ballot set
+      __syncwarp();
+    }
+  } else if (k <= 64) {
     // ballots of at most 64 positions: a lane holds positions lane and
     // lane + 32 in registers (also for clearing the bitmap), and the next
     // ballot's ids are loaded while this one is checked and counted
@@ -296,7 +320,8 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
   }
 }
 
-// Plans the sparse tally on the device (one CTA of 1024 threads):
+// Plans the sparse tally on the device, in two passes over tiles of
+// kPlanTile candidates (one CTA per tile, a thread per candidate):
 //  * off[c] / cursor[c]: start of candidate c's entries (exclusive scan of cnt);
 //  * ord: the order in which the grouped form's rows kernel takes the rows
 //    (longest first, by floor(log2(cnt)));
@@ -308,162 +333,250 @@ __global__ void sparse_count_kernel(const int32_t* __restrict__ ranks, int64_t n
 //    the pair counts of one position land in distinct shared-memory banks
 //    (each slot of a 16-bit-packed row takes its own word in the first half
 //    of the slots, see compact_pairs_kernel).
-__global__ void __launch_bounds__(1024) sparse_plan_kernel(const int32_t* __restrict__ cnt, int32_t m,
-                                                           uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
-                                                           int32_t* __restrict__ ord, uint32_t S, int32_t hcap,
-                                                           int2* __restrict__ utab, int32_t utab_cap,
-                                                           int32_t* __restrict__ gmeta,
-                                                           int32_t compact_max, int32_t* __restrict__ slot,
-                                                           int32_t* __restrict__ act, int32_t* __restrict__ meta,
-                                                           int32_t* __restrict__ hint,
-                                                           int32_t* __restrict__ hint_valid) {
+// The first pass sums each tile (listed candidates, entries, units of the
+// heavy rows, rows per length bucket) into agg; the second combines the
+// sums of the tiles before its own with its local scans and writes its
+// candidates' entries of every table directly.
+constexpr int kPlanTile = 1024;
+constexpr int kAggWords = 40;  // listed, entries, heavy units, 34 bucket counts (padded)
+constexpr int kBuckets = 34;   // 33: heavy (more than S entries); 1 .. 32: floor(log2(cnt)) + 1; 0: unlisted
+
+__device__ __forceinline__ int plan_bucket(int32_t x, uint32_t S) {
+  return uint32_t(x) > S ? 33 : (x > 0 ? 32 - __clz(x) : 0);
+}
+
+// ctr[key] += 1 for every lane, aggregated over the lanes with the same key
+// (all 32 lanes call it); returns the old value plus the lane's rank among them
+__device__ __forceinline__ uint32_t warp_bump(uint32_t* ctr, int key) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&ctr[key], uint32_t(__popc(peers)));
+  return __shfl_sync(0xFFFFFFFFu, base, leader) + uint32_t(__popc(peers & ((1u << lane) - 1u)));
+}
+
+// sum over the block (kPlanTile threads) of v; valid in every thread
+__device__ __forceinline__ uint32_t plan_block_sum(uint32_t v, uint32_t* ws) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  __syncthreads();  // ws free
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t t = ws[threadIdx.x & 31];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+  return t;
+}
+
+// exclusive scans over the block (kPlanTile threads, in thread order) of a and b
+__device__ __forceinline__ void plan_block_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb,
+                                                 uint32_t (*ws)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ya = __shfl_up_sync(0xFFFFFFFFu, ia, o), yb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+    if (lane >= o) ia += ya, ib += yb;
+  }
+  __syncthreads();  // ws free
+  if (lane == 31) ws[0][wid] = ia, ws[1][wid] = ib;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t xa = ws[0][lane], xb = ws[1][lane];
+    uint32_t sa = xa, sb = xb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t ya = __shfl_up_sync(0xFFFFFFFFu, sa, o), yb = __shfl_up_sync(0xFFFFFFFFu, sb, o);
+      if (lane >= o) sa += ya, sb += yb;
+    }
+    ws[0][lane] = sa - xa, ws[1][lane] = sb - xb;
+  }
+  __syncthreads();
+  ea = ws[0][wid] + ia - a, eb = ws[1][wid] + ib - b;
+}
+
+__global__ void __launch_bounds__(kPlanTile) plan_tiles_kernel(const int32_t* __restrict__ cnt, int32_t m, uint32_t S,
+                                                               uint32_t* __restrict__ agg) {
   pdl_enter();
-  __shared__ uint32_t part[33];
-  extern __shared__ uint32_t plan_smem[];  // m words if m <= kScanSmem, then the staged counts
-  // the counts are read once: the first kHeld per thread stay in registers,
-  // the rest (lists longer than kHeld * 1024 candidates) are staged in shared
-  // memory after the scan buffer when both fit, else re-read
-  constexpr int kHeld = 8;
-  int32_t held[kHeld];
-#pragma unroll
-  for (int h = 0; h < kHeld; ++h) {
-    const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
-    held[h] = c < m ? cnt[c] : 0;
-  }
-  const int32_t held_n = kHeld * int32_t(blockDim.x);
-  const int32_t extra = m > held_n ? m - held_n : 0;
-  const bool tail_smem = extra > 0 && m + extra <= kScanSmem;
-  const int32_t* tail = tail_smem ? reinterpret_cast<const int32_t*>(plan_smem + m) : cnt + held_n;
-  if (tail_smem) {
-    for (int32_t i = threadIdx.x; i < extra; i += blockDim.x) plan_smem[m + i] = uint32_t(cnt[held_n + i]);
-    __syncthreads();
-  }
-  auto each = [&](auto&& f) {  // f(c, cnt[c]) for this thread's candidates
-#pragma unroll
-    for (int h = 0; h < kHeld; ++h) {
-      const int32_t c = int32_t(threadIdx.x) + h * int32_t(blockDim.x);
-      if (c < m) f(c, held[h]);
+  __shared__ uint32_t sb[kBuckets + 1];  // + a slot for the threads past m
+  __shared__ uint32_t ws[32];
+  if (threadIdx.x <= kBuckets) sb[threadIdx.x] = 0u;
+  __syncthreads();
+  const int32_t c = int32_t(blockIdx.x) * kPlanTile + int32_t(threadIdx.x);
+  const int32_t x = c < m ? cnt[c] : 0;
+  const int bk = c < m ? plan_bucket(x, S) : kBuckets;
+  warp_bump(sb, bk);
+  uint32_t* a = agg + size_t(blockIdx.x) * kAggWords;
+  const uint32_t listed = plan_block_sum(x > 0 ? 1u : 0u, ws);
+  const uint32_t entries = plan_block_sum(uint32_t(x), ws);
+  const uint32_t units = plan_block_sum(bk == 33 ? (uint32_t(x) + S - 1) / S : 0u, ws);
+  if (threadIdx.x == 0) a[0] = listed, a[1] = entries, a[2] = units;
+  if (threadIdx.x < kBuckets) a[3 + threadIdx.x] = sb[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kPlanTile)
+    plan_place_kernel(const int32_t* __restrict__ cnt, int32_t m, const uint32_t* __restrict__ agg, int32_t tiles,
+                      uint32_t S, int32_t hcap, uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                      int32_t* __restrict__ ord, int2* __restrict__ utab, int32_t* __restrict__ gmeta,
+                      int32_t compact_max, int32_t* __restrict__ slot, int32_t* __restrict__ act,
+                      int32_t* __restrict__ meta, int32_t* __restrict__ hint, int32_t* __restrict__ hint_valid) {
+  pdl_enter();
+  constexpr int kQ = 3 + kBuckets;   // quantities summed per tile
+  __shared__ uint32_t before[kQ];    // over the tiles before this one
+  __shared__ uint32_t all[kQ];       // over every tile
+  __shared__ uint32_t bcur[kBuckets + 1];  // this tile's next ord position per bucket (+ a slot past m)
+  __shared__ uint32_t ws[2][32];
+  __shared__ uint32_t hnu[kPlanTile];  // units of this tile's heavy rows, by their order in ord
+  const int32_t tile = int32_t(blockIdx.x);
+  if (threadIdx.x < kQ) {
+    uint32_t bf = 0, al = 0;
+    for (int32_t t = 0; t < tiles; ++t) {
+      const uint32_t v = agg[size_t(t) * kAggWords + threadIdx.x];
+      bf += t < tile ? v : 0u;
+      al += v;
     }
-    for (int32_t c = int32_t(threadIdx.x) + held_n; c < m; c += blockDim.x) f(c, tail[c - held_n]);
-  };
-  {
-    // listed flags scanned into the slots (in shared memory, or in place in
-    // slot for long candidate lists)
-    uint32_t* flag = m <= kScanSmem ? plan_smem : reinterpret_cast<uint32_t*>(slot);
-    each([&](int32_t c, int32_t x) { flag[c] = x > 0 ? 1u : 0u; });
-    __syncthreads();
-    const uint32_t na = block_exclusive_scan(flag, m, part);
-    const bool compact = int32_t(na) <= compact_max;
-    // compact: listed ids in id order, and their order keys (count, then
-    // the complement of the index, so that a larger key goes first)
-    __shared__ int32_t lid[kCompactMaxPacked];
-    __shared__ unsigned long long lkey[kCompactMaxPacked];
-    // slots, and the closure's warm flags (the listed candidates, valid when
-    // one is never listed) with their warm-first relabeling: listed c keeps
-    // rank flag[c] (listed candidates before it), unlisted c follows all
-    // listed ones in id order
-    int32_t* rperm = hint ? hint + m : nullptr;
-    int32_t* rinv = hint ? hint + 2 * int64_t(m) : nullptr;
-    each([&](int32_t c, int32_t x) {
-      const int32_t f = int32_t(flag[c]);  // read before slot[c] (its storage for long lists) is written
-      const int32_t s = x > 0 ? f : -1;
-      if (hint) {
-        const int32_t nw = x > 0 ? f : int32_t(na) + (c - f);
-        rperm[nw] = c, rinv[c] = nw;
-      }
-      if (compact && s >= 0) {
-        lid[s] = c, lkey[s] = (static_cast<unsigned long long>(x) << 32) | uint32_t(~s);  // slot, act below
-      } else {
-        slot[c] = s;
-        if (s >= 0) act[s] = c;
-      }
-      if (hint) hint[c] = x > 0 ? 1 : 0;
-    });
-    if (threadIdx.x == 0) {
-      meta[0] = int32_t(na), meta[1] = compact ? 1 : 0;
-      if (hint) *hint_valid = int32_t(na) < m ? 1 : 0, hint[3 * int64_t(m)] = int32_t(na);
-    }
-    if (compact) {  // the compact form needs no grouping plan, only its slot order
-      static_assert(kCompactMaxPacked >= kCompactMaxWide && kCompactMaxPacked * 4 <= 1024, "4 threads per slot");
-      __syncthreads();
-      const int32_t s = int32_t(threadIdx.x >> 2), q = int32_t(threadIdx.x & 3);
-      const unsigned long long ks = s < int32_t(na) ? lkey[s] : ~0ull;
-      int32_t r = 0;  // listed candidates ahead of lid[s]: larger count, or equal count and smaller id
-#pragma unroll 8
-      for (int32_t j = q; j < int32_t(na); j += 4) r += lkey[j] > ks ? 1 : 0;
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, 1);
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, 2);
-      if (s < int32_t(na) && q == 0) slot[lid[s]] = r, act[r] = lid[s];
-      return;
-    }
-    __syncthreads();
+    before[threadIdx.x] = bf, all[threadIdx.x] = al;
   }
-  // grouped form: each candidate's entries start at off[c] (the scan runs in
-  // shared memory when the list fits). The rows kernel takes its work from
-  // one queue: first the units of the heavy rows (more than S entries; the
-  // first hcap of them, each cut into units of S entries, utab[u] = (index in
-  // ord, part)), then the other rows one by one, in the order ord[]: heavy
-  // rows first, then by decreasing floor(log2(cnt)), so that long rows start
-  // early and do not end the kernel late. gmeta = {heavy rows split, units}.
-  uint32_t* offs = m <= kScanSmem ? plan_smem : off;
-  each([&](int32_t c, int32_t x) { offs[c] = uint32_t(x); });
   __syncthreads();
-  const uint32_t total = block_exclusive_scan(offs, m, part);
-  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
-    const uint32_t o = offs[c];
-    if (offs != off) off[c] = o;
-    cursor[c] = o;
-  }
-  if (threadIdx.x == 0) off[m] = total;
-  __shared__ uint32_t bcnt[34];
-  if (threadIdx.x < 34) bcnt[threadIdx.x] = 0u;
-  __syncthreads();
-  // 33: heavy; 1 .. 32: floor(log2(cnt)) + 1; 0: unlisted
-  auto bucket = [&](int32_t x) { return uint32_t(x) > S ? 33 : (x > 0 ? 32 - __clz(x) : 0); };
-  auto add_bucket = [&](int32_t b) -> uint32_t {  // warp-aggregated bcnt[b]++, returns the old count + rank
-    const uint32_t peers = __match_any_sync(__activemask(), b);
-    const int leader = __ffs(peers) - 1;
-    const uint32_t rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
-    uint32_t base = 0;
-    if ((threadIdx.x & 31) == leader) base = atomicAdd(&bcnt[b], uint32_t(__popc(peers)));
-    return __shfl_sync(peers, base, leader) + rank;
-  };
-  each([&](int32_t c, int32_t x) { add_bucket(bucket(x)); });
-  __syncthreads();
-  const int32_t heavy = int32_t(bcnt[33]);
-  const int32_t hs = min(heavy, hcap);  // heavy rows split into units
-  __syncthreads();
-  if (threadIdx.x == 0) {  // bucket starts, heavy and long rows first; then counters reused as cursors
+  if (threadIdx.x == 0) {  // bucket starts: heavy rows first, then decreasing length
     uint32_t run = 0;
-    for (int b = 33; b >= 0; --b) {
-      const uint32_t t = bcnt[b];
-      bcnt[b] = run;
-      run += t;
+    for (int bk = kBuckets - 1; bk >= 0; --bk) {
+      bcur[bk] = run + before[3 + bk];
+      run += all[3 + bk];
+    }
+    bcur[kBuckets] = 0u;
+  }
+  const int32_t c = tile * kPlanTile + int32_t(threadIdx.x);
+  const bool in = c < m;
+  const int32_t x = in ? cnt[c] : 0;
+  const bool listed = x > 0;
+  uint32_t fl, ol;  // listed candidates and entries before c within the tile
+  plan_block_scan2(listed ? 1u : 0u, uint32_t(x), fl, ol, ws);  // (its barriers also publish bcur)
+  const uint32_t na = all[0], total = all[1];
+  const uint32_t f = before[0] + fl;
+  const bool compact = int32_t(na) <= compact_max;
+  if (in) {
+    if (hint) {
+      // warm-first relabeling: listed c keeps rank f, unlisted c follows all
+      // listed ones in id order
+      const uint32_t nw = listed ? f : na + (uint32_t(c) - f);
+      hint[m + int64_t(nw)] = c, hint[2 * int64_t(m) + c] = int32_t(nw), hint[c] = listed ? 1 : 0;
+    }
+    if (!compact) {
+      slot[c] = listed ? int32_t(f) : -1;
+      if (listed) act[f] = c;
+    } else if (!listed) {
+      slot[c] = -1;
+    }
+  }
+  if (tile == 0 && threadIdx.x == 0) {
+    meta[0] = int32_t(na), meta[1] = compact ? 1 : 0;
+    if (hint) *hint_valid = na < uint32_t(m) ? 1 : 0, hint[3 * int64_t(m)] = int32_t(na);
+  }
+  if (compact) {
+    // the compact form needs no grouping plan, only its slot order: CTA 0
+    // collects the listed candidates and ranks them by (count desc, id asc)
+    if (tile != 0) return;
+    static_assert(kCompactMaxPacked >= kCompactMaxWide && kCompactMaxPacked * 4 <= kPlanTile, "4 threads per slot");
+    __shared__ int32_t lid[kCompactMaxPacked];
+    __shared__ int32_t lcnt[kCompactMaxPacked];
+    __shared__ uint32_t nl;
+    if (threadIdx.x == 0) nl = 0u;
+    __syncthreads();
+    for (int32_t c0 = 0; c0 < m; c0 += kPlanTile) {
+      const int32_t cc = c0 + int32_t(threadIdx.x);
+      const int32_t xc = cc < m ? cnt[cc] : 0;
+      const bool lc = xc > 0;
+      const uint32_t mask = __ballot_sync(0xFFFFFFFFu, lc);
+      uint32_t base = 0;
+      if ((threadIdx.x & 31) == 0 && mask) base = atomicAdd(&nl, uint32_t(__popc(mask)));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (lc) {
+        const uint32_t pos = base + uint32_t(__popc(mask & ((1u << (threadIdx.x & 31)) - 1u)));
+        lid[pos] = cc, lcnt[pos] = xc;  // pos < na <= compact_max
+      }
+    }
+    __syncthreads();
+    const int32_t sl = int32_t(threadIdx.x >> 2), q = int32_t(threadIdx.x & 3);
+    const bool own = sl < int32_t(na);
+    const int32_t ci = own ? lid[sl] : 0, xi = own ? lcnt[sl] : 0;
+    int32_t r = 0;  // listed candidates ahead of ci: larger count, or equal count and smaller id
+#pragma unroll 8
+    for (int32_t j = q; j < int32_t(na); j += 4) r += (lcnt[j] > xi || (lcnt[j] == xi && lid[j] < ci)) ? 1 : 0;
+    r += __shfl_xor_sync(0xFFFFFFFFu, r, 1);
+    r += __shfl_xor_sync(0xFFFFFFFFu, r, 2);
+    if (own && q == 0) slot[ci] = r, act[r] = ci;
+    return;
+  }
+  // grouped form: each candidate's entries start at off[c]. The rows kernel
+  // takes its work from one queue: first the units of the heavy rows (more
+  // than S entries; the first hcap of them in ord, each cut into units of S
+  // entries, utab[u] = (index in ord, part)), then the other rows one by
+  // one, in the order ord[]: heavy rows first, then by decreasing
+  // floor(log2(cnt)), so that long rows start early and do not end the
+  // kernel late. gmeta = {heavy rows split, units}.
+  if (in) {
+    const uint32_t o = before[1] + ol;
+    off[c] = o, cursor[c] = o;
+  }
+  if (tile == 0 && threadIdx.x == 0) off[m] = total;
+  const uint32_t hpre = bcur[33];  // this tile's first heavy row in ord (read before the bumps below)
+  __syncthreads();
+  const int bk = in ? plan_bucket(x, S) : kBuckets;
+  const uint32_t t = warp_bump(bcur, bk);  // c's position in ord
+  if (in) ord[t] = c;
+  const uint32_t heavy = all[3 + 33], hs = min(heavy, uint32_t(hcap));
+  const uint32_t nu = bk == 33 ? (uint32_t(x) + S - 1) / S : 0u;
+  if (bk == 33) hnu[t - hpre] = nu;
+  __syncthreads();
+  const uint32_t htile = bcur[33] - hpre;  // this tile's heavy rows
+  if (threadIdx.x < 32) {  // exclusive scan of hnu[0 .. htile) in place
+    uint32_t carry = 0;
+    for (uint32_t i0 = 0; i0 < htile; i0 += 32) {
+      const uint32_t i = i0 + threadIdx.x;
+      const uint32_t v = i < htile ? hnu[i] : 0u;
+      uint32_t inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (int(threadIdx.x) >= o) inc += y;
+      }
+      if (i < htile) hnu[i] = carry + inc - v;
+      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
   }
   __syncthreads();
-  each([&](int32_t c, int32_t x) { ord[add_bucket(bucket(x))] = c; });
-  __syncthreads();
-  // units of the split rows: the exclusive scan of ceil(cnt / S) over
-  // ord[0 .. hs), in shared memory when the list fits, else in hcap words
-  // kept after the unit table
-  uint32_t* uo = m <= kScanSmem ? plan_smem : reinterpret_cast<uint32_t*>(utab) + 2 * size_t(utab_cap);
-  for (int32_t t = threadIdx.x; t < hs; t += blockDim.x) uo[t] = (uint32_t(cnt[ord[t]]) + S - 1) / S;
-  __syncthreads();
-  const uint32_t units = block_exclusive_scan(uo, hs, part);
-  for (int32_t t = threadIdx.x; t < hs; t += blockDim.x) {
-    const uint32_t u0 = uo[t], nu = (uint32_t(cnt[ord[t]]) + S - 1) / S;
-    for (uint32_t q = 0; q < nu; ++q) utab[u0 + q] = make_int2(t, int32_t(q));
+  if (bk == 33 && t < hs) {
+    // the heavy rows before this tile's all lie below the cap when this one does
+    const uint32_t u0 = before[2] + hnu[t - hpre];
+    for (uint32_t q = 0; q < nu; ++q) utab[u0 + q] = make_int2(int32_t(t), int32_t(q));
+    if (t == hs - 1 && heavy > hs) gmeta[1] = int32_t(u0 + nu);  // the cap cuts the heavy rows here
   }
-  if (threadIdx.x == 0) gmeta[0] = hs, gmeta[1] = int32_t(units);
+  if (tile == 0 && threadIdx.x == 0) {
+    gmeta[0] = int32_t(hs);
+    if (heavy <= hs)
+      gmeta[1] = int32_t(all[2]);  // every heavy row split
+    else if (hs == 0)
+      gmeta[1] = 0;
+  }
 }
 
 // entries grouped by candidate: entries[cursor[c]++] = v * k + q. With kLocal
-// each CTA takes a contiguous chunk of entries, counts it per candidate in
-// shared memory, reserves each candidate's slots with one global atomic and
-// then places its entries with shared-memory cursors.
+// (m <= kLocalHistMax, 1024 threads) each CTA takes a contiguous chunk of
+// entries in rounds of kScatterHeld entries per thread (all their loads in
+// flight at once): it counts the round per candidate in shared memory,
+// reserves each candidate's slots with one global atomic (every thread
+// issues all of its candidates' atomics before it uses their results; the
+// returned base becomes the candidate's shared-memory cursor) and places
+// the entries, reading the round's ids again (from L2).
+constexpr int kScatterHeld = 28;
+constexpr int kScatterThreads = 1024;
+constexpr int kScatterResv = kLocalHistMax / kScatterThreads;  // candidates per thread in the reservations
+static_assert(kLocalHistMax % (2 * kScatterThreads) == 0, "whole reservations per thread, in two halves");
+
 template <bool kLocal>
-__global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
+__global__ void __launch_bounds__(1024) sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_t total, int32_t m,
                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
                                       const int32_t* __restrict__ meta, const int32_t* __restrict__ gmeta,
                                       int32_t* __restrict__ hacc, uint32_t* __restrict__ hdone) {
@@ -487,27 +600,58 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
     }
     return;
   }
-  extern __shared__ uint32_t smem_scatter[];  // hist[m], base[m]
+  extern __shared__ uint32_t smem_scatter[];  // hist[m], cur[m]
   uint32_t* hist = smem_scatter;
-  uint32_t* basev = smem_scatter + m;
+  uint32_t* cur = smem_scatter + m;
   const uint32_t chunk = (total + gridDim.x - 1) / gridDim.x;
   const uint32_t e0 = min(total, blockIdx.x * chunk), e1 = min(total, e0 + chunk);
   for (int32_t c = threadIdx.x; c < m; c += blockDim.x) hist[c] = 0u;
   __syncthreads();
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int32_t c = ranks[e];
-    if (c >= 0 && c < m) atomicAdd(&hist[c], 1u);
-  }
-  __syncthreads();
-  for (int32_t c = threadIdx.x; c < m; c += blockDim.x) {
-    const uint32_t h = hist[c];
-    if (h) basev[c] = atomicAdd(&cursor[c], h);
-    hist[c] = 0u;
-  }
-  __syncthreads();
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int32_t c = ranks[e];
-    if (c >= 0 && c < m) entries[basev[c] + atomicAdd(&hist[c], 1u)] = e;
+  constexpr uint32_t kRound = uint32_t(kScatterHeld) * kScatterThreads;
+  for (uint32_t r0 = e0; r0 < e1; r0 += kRound) {
+    {
+      int32_t cv[kScatterHeld];
+#pragma unroll
+      for (int h = 0; h < kScatterHeld; ++h) {
+        const uint32_t e = r0 + threadIdx.x + uint32_t(h) * kScatterThreads;
+        cv[h] = e < e1 ? ranks[e] : -1;
+      }
+#pragma unroll
+      for (int h = 0; h < kScatterHeld; ++h)
+        if (cv[h] >= 0 && cv[h] < m) atomicAdd(&hist[cv[h]], 1u);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i0 = 0; i0 < kScatterResv; i0 += kScatterResv / 2) {  // two halves: eight atomics in flight
+      uint32_t hv[kScatterResv / 2], bv[kScatterResv / 2];
+#pragma unroll
+      for (int i = 0; i < kScatterResv / 2; ++i) {
+        const int32_t c = int32_t(threadIdx.x) + (i0 + i) * kScatterThreads;
+        hv[i] = c < m ? hist[c] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < kScatterResv / 2; ++i)
+        bv[i] = hv[i] ? atomicAdd(&cursor[int32_t(threadIdx.x) + (i0 + i) * kScatterThreads], hv[i]) : 0u;
+#pragma unroll
+      for (int i = 0; i < kScatterResv / 2; ++i) {
+        const int32_t c = int32_t(threadIdx.x) + (i0 + i) * kScatterThreads;
+        if (hv[i]) cur[c] = bv[i], hist[c] = 0u;
+      }
+    }
+    __syncthreads();
+    {
+      int32_t cv[kScatterHeld];
+#pragma unroll
+      for (int h = 0; h < kScatterHeld; ++h) {
+        const uint32_t e = r0 + threadIdx.x + uint32_t(h) * kScatterThreads;
+        cv[h] = e < e1 ? __ldcg(ranks + e) : -1;
+      }
+#pragma unroll
+      for (int h = 0; h < kScatterHeld; ++h)
+        if (cv[h] >= 0 && cv[h] < m)
+          entries[atomicAdd(&cur[cv[h]], 1u)] = r0 + threadIdx.x + uint32_t(h) * kScatterThreads;
+    }
+    __syncthreads();  // cur is read before the next round's reservations overwrite it
   }
 }
 
@@ -518,7 +662,7 @@ __global__ void sparse_scatter_kernel(const int32_t* __restrict__ ranks, uint32_
 // (entries[off[r] .. off[r+1]) hold v * k + q); each adds 1 to C[r][j] for
 // every j listed above position q in ballot v. A counter never exceeds the
 // entries counted into it (at most S <= 65535 per unit).
-// A persistent CTA takes work from one queue (see sparse_plan_kernel):
+// A persistent CTA takes work from one queue (see plan_place_kernel):
 //  * a unit of a heavy row (more than S entries) counts its slice of the
 //    entries and adds its nonzero counters into the row's int32 accumulator
 //    in global memory (L2-resident, reductions without return); the unit
@@ -1112,7 +1256,7 @@ GroupedPlan grouped_plan(int64_t n, int32_t m, int32_t k, int sms) {
 }
 
 size_t grouped_bytes(const GroupedPlan& g) {
-  return align_up(size_t(g.utab_cap) * 8 + size_t(g.hcap) * 4, 256) + 256 +
+  return align_up(size_t(g.utab_cap) * 8, 256) + 256 + align_up(size_t((g.hld + kPlanTile - 1) / kPlanTile) * kAggWords * 4, 256) +
          align_up(size_t(g.hcap) * size_t(g.hld) * 4, 256) + align_up(size_t(g.hcap) * 4, 256);
 }
 
@@ -1166,8 +1310,9 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
   const CompactPlan cp = compact_plan(n, m, k, sms, flags);
   uint32_t* partial = cv.take<uint32_t>(cp.partial_words);
   const GroupedPlan gp = grouped_plan(n, m, k, std::min(sms, kSmsForSizing));  // within the sized workspace
-  int2* utab = reinterpret_cast<int2*>(cv.take<char>(size_t(gp.utab_cap) * 8 + size_t(gp.hcap) * 4));
+  int2* utab = reinterpret_cast<int2*>(cv.take<char>(size_t(gp.utab_cap) * 8));
   int32_t* gmeta = cv.take<int32_t>(2);
+  uint32_t* agg = cv.take<uint32_t>(size_t((m + kPlanTile - 1) / kPlanTile) * kAggWords);
   int32_t* hacc = cv.take<int32_t>(size_t(gp.hcap) * size_t(gp.hld));
   uint32_t* hdone = cv.take<uint32_t>(size_t(gp.hcap));
   {
@@ -1192,15 +1337,16 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
     launch_pdl(kern, dim3(blocks), dim3(threads), smem, stream, false, ranks, n, m, k, cnt, ctx->status);
   }
   {
-    Launch L(ctx, stream, "tally_plan", double(m) * 12.0);
-    // the scan buffer (m words), then the counts beyond the 8 x 1024 held in
-    // registers when both fit (the kernel makes the same choice)
-    const int32_t extra = std::max(0, m - 8 * 1024);
-    const size_t smem = m > kScanSmem ? 0 : size_t(m + (extra > 0 && m + extra <= kScanSmem ? extra : 0)) * 4;
-    cudaFuncSetAttribute(sparse_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    launch_pdl(sparse_plan_kernel, dim3(1), dim3(1024), smem, stream, false, static_cast<const int32_t*>(cnt), m, off,
-               cursor, ord, gp.S, gp.hcap, utab, int32_t(gp.utab_cap), gmeta, cp.cmax, slot, act, meta, hint,
-               hint_valid);
+    const int32_t tiles = (m + kPlanTile - 1) / kPlanTile;
+    {
+      Launch L(ctx, stream, "tally_plan", double(m) * 4.0);
+      launch_pdl(plan_tiles_kernel, dim3(tiles), dim3(kPlanTile), 0, stream, false, static_cast<const int32_t*>(cnt),
+                 m, gp.S, agg);
+    }
+    Launch L(ctx, stream, "tally_place", double(m) * 20.0);
+    launch_pdl(plan_place_kernel, dim3(tiles), dim3(kPlanTile), 0, stream, false, static_cast<const int32_t*>(cnt), m,
+               static_cast<const uint32_t*>(agg), tiles, gp.S, gp.hcap, off, cursor, ord, utab, gmeta, cp.cmax, slot,
+               act, meta, hint, hint_valid);
   }
   if (cp.cmax > 0) {
     Launch L(ctx, stream, "tally_compact_pairs", double(m) * double(m) * 4.0 + double(total) * 4.0);
@@ -1223,7 +1369,7 @@ int tally_launch(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, i
       const size_t smem = size_t(m) * 8;
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 4095) / 4096, uint64_t(sms)));
       cudaFuncSetAttribute(sparse_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      launch_pdl(sparse_scatter_kernel<true>, dim3(blocks), dim3(1024), smem, stream, false, ranks, total, m, cursor,
+      launch_pdl(sparse_scatter_kernel<true>, dim3(blocks), dim3(kScatterThreads), smem, stream, false, ranks, total, m, cursor,
                  entries, static_cast<const int32_t*>(meta), static_cast<const int32_t*>(gmeta), hacc, hdone);
     } else {
       const int blocks = int(std::min<uint64_t>((uint64_t(total) + 255) / 256, uint64_t(sms) * 16));

@@ -175,6 +175,39 @@ def test_tally_column_split():
     _check_row_col_sums(r, m, d)
 
 
+def test_tally_heavy_rows_beyond_the_accumulators():
+    """About 1100 candidates, each on more ballots than one unit of the
+    grouped rows kernel counts (S = 822 entries here), at m = 65535, where
+    only the first 1024 heavy rows get split-row accumulators: the other
+    heavy rows are counted in chunks into the written row. Only the 1100
+    are ever listed, so d restricted to them is the tally of the same
+    ballots relabelled 0..1099 (checked whole against the oracle), an
+    unlisted column holds each row's ballot count, an unlisted row is zero,
+    and every row and column sum (taken on the device) meets its closed
+    form."""
+    m, n, k, core = 65535, 100000, 10, 1100
+    ids = W.permutation(41, m)[:core].astype(np.int64)
+    small = W.impartial(42, n, core, k)
+    r = ids[small].astype(np.int32)
+    d = S.schulze_tally(cu(r), m, flags=S.F_TALLY_SPARSE | S.F_TALLY_GROUPED)
+    idx = torch.from_numpy(ids).cuda()
+    eq(host(d[idx][:, idx]), oracle.tally(small, core), "listed square")
+    listed_n = np.bincount(small.reshape(-1), minlength=core)
+    unl = np.setdiff1d(np.arange(m), ids)
+    rs = np.random.Generator(np.random.PCG64(43))
+    for j in rs.choice(unl, 4, replace=False):
+        eq(host(d[idx, int(j)]), listed_n, f"unlisted column {j}")
+        assert int(host(d[int(j)].abs().sum())) == 0
+    rows = np.zeros(m, np.int64)
+    cols = np.full(m, n * k, np.int64)
+    np.add.at(rows, r.reshape(-1), (m - 1 - np.tile(np.arange(k), n)))
+    np.add.at(cols, r.reshape(-1), np.tile(np.arange(k), n) - k)
+    eq(host(d.sum(dim=1, dtype=torch.int64)), rows, "row sums")
+    eq(host(d.sum(dim=0, dtype=torch.int64)), cols, "column sums")
+    del d
+    torch.cuda.empty_cache()
+
+
 def _check_row_col_sums(r, m, d):
     n, k = r.shape
     rows = np.zeros(m, np.int64)
