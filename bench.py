@@ -774,8 +774,10 @@ def run_kernel_case(args, local):
     `closure_s16` close a seeded dense random count matrix (m = --m, default
     4096) twice as warm-up and once timed; `tally_grouped` tallies the
     default m = 16384, n = 200000 top-20 election (the grouped form) three
-    times and once timed; `batch_sample` runs a 256-election sample of the
-    mixed batch twice and once timed. Prints the timed call's milliseconds."""
+    times and once timed; `tally_compact` does the same for the m = 4096,
+    n = 20000 top-50 election (151 listed candidates: the compact form);
+    `batch_sample` runs a 256-election sample of the mixed batch twice and
+    once timed. Prints the timed call's milliseconds."""
     import torch
     import paper_2505_12976_gb300 as S
     import workloads as W
@@ -793,8 +795,8 @@ def run_kernel_case(args, local):
         p = torch.empty_like(dd)
         call = lambda: S.schulze_strongest_paths(dd, hi, p=p, flags=flags)
         reps = 2
-    elif args.kernel_case == "tally_grouped":
-        e = W.huge_pl()
+    elif args.kernel_case in ("tally_grouped", "tally_compact"):
+        e = W.huge_pl() if args.kernel_case == "tally_grouped" else W.large_topk()
         r = torch.from_numpy(e.ranks).to(dev)
         d = torch.empty((e.m, e.m), dtype=torch.int32, device=dev)
         call = lambda: S.schulze_tally(r, e.m, d=d)
@@ -865,8 +867,8 @@ def main():
     ap.add_argument("--eval-elections", type=int, default=256, help="evaluation elections (learned workload)")
     ap.add_argument("--epochs", type=int, default=20, help="training epochs (learned workload)")
     ap.add_argument("--margin", action="store_true", help="margin edge weights instead of winning votes")
-    ap.add_argument("--kernel-case", default=None, choices=["closure_s32", "closure_s16", "tally_grouped",
-                                                             "batch_sample"],
+    ap.add_argument("--kernel-case", default=None,
+                    choices=["closure_s32", "closure_s16", "tally_grouped", "tally_compact", "batch_sample"],
                     help="run one small single-kernel case for profiling instead of the benchmark")
     ap.add_argument("--shard-voters", action="store_true",
                     help="one election, voters split over the ranks (tally + all-reduce of d; strong scaling)")

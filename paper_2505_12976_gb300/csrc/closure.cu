@@ -981,7 +981,7 @@ struct ClosureBufs {
 // the int32 tile updates (tiles::update2_s32).
 template <typename E, int kMix>
 int closure_pipeline_mix(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
-                         const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out) {
+                         const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out, bool side) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   E* W = static_cast<E*>(bf.W);
@@ -1071,12 +1071,26 @@ int closure_pipeline_mix(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m,
                static_cast<const int32_t*>(bf.ucol), bf.ucold, bf.ucount);
   }
   {
-    const int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
-    Launch L(ctx, stream, "closure_widen", mm * 4.0);
-    launch_pdl(widen_kernel<E>, dim3(g), dim3(256), 0, stream, false, static_cast<const E*>(W), mp, m,
+    // p is written from W (and the uniform cold values); with a side stream
+    // it is written there while beaten_by and the ranking come out of W on
+    // stream, with at most four CTAs per SM so that those kernels find room
+    const bool fork = side && bb_out && ctx && ctx->side_stream;
+    cudaStream_t wst = stream;
+    int g = grid_for(reinterpret_cast<const void*>(widen_kernel<E>), 256, 0, m);
+    if (fork) {
+      if (cudaEventRecord(ctx->side_fork, stream) != cudaSuccess ||
+          cudaStreamWaitEvent(ctx->side_stream, ctx->side_fork, 0) != cudaSuccess)
+        return SCHULZE_ECUDA;
+      ctx->side_pending = true;  // joined by the caller, whatever happens next
+      wst = ctx->side_stream;
+      g = std::min(g, 4 * sms);
+    }
+    Launch L(ctx, wst, "closure_widen", mm * 4.0);
+    launch_pdl(widen_kernel<E>, dim3(g), dim3(256), 0, wst, false, static_cast<const E*>(W), mp, m,
                static_cast<const int32_t*>(bf.inv), static_cast<const int32_t*>(bf.perm),
                static_cast<const int32_t*>(bf.warm), p, bf.hint_valid, static_cast<const int32_t*>(bf.ucold),
                rows_vec16(p, m));
+    if (fork && cudaEventRecord(ctx->side_join, wst) != cudaSuccess) return SCHULZE_ECUDA;
   }
   if (bb_out) {
     Launch L(ctx, stream, "closure_beaten_by", 0.0);
@@ -1092,18 +1106,19 @@ int closure_pipeline_mix(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m,
 // count could reach the fp32 infinity pattern 0x7F800000.
 template <typename E>
 int closure_pipeline(schulze_ctx* ctx, int sms, const int32_t* d, int32_t m, int64_t bound, int32_t* p,
-                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out = nullptr) {
+                     const ClosureBufs& bf, int32_t* status, cudaStream_t stream, int32_t* bb_out = nullptr,
+                     bool side = false) {
   if constexpr (sizeof(E) == 4 && tiles::kS32Mix != 0) {
     if (bound < 0x7F800000LL)
-      return closure_pipeline_mix<E, tiles::kS32Mix>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out);
+      return closure_pipeline_mix<E, tiles::kS32Mix>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out, side);
   }
-  return closure_pipeline_mix<E, 0>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out);
+  return closure_pipeline_mix<E, 0>(ctx, sms, d, m, bound, p, bf, status, stream, bb_out, side);
 }
 
 template <typename E>
 int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, void* ws,
                 cudaStream_t stream, int32_t* bb_out, int32_t* hint, const int32_t* hint_valid,
-                bool margin) {
+                bool margin, bool side) {
   const int32_t mp = int32_t(align_up(size_t(m), kB));
   const int32_t nb = mp / kB;
   Carver cv(ws);
@@ -1127,7 +1142,7 @@ int run_closure(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, in
   bf.hint_valid = hint_valid;
   bf.margin = margin;
   const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
-  return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream, bb_out);
+  return closure_pipeline<E>(ctx, sms, d, m, bound, p, bf, ctx->status, stream, bb_out, side);
 }
 
 }  // namespace
@@ -1141,11 +1156,11 @@ size_t closure_workspace_bytes(int32_t m, int64_t bound, uint32_t flags) {
 
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
                    void* ws, cudaStream_t stream, int32_t* beaten_by, int32_t* hint,
-                   const int32_t* hint_valid) {
+                   const int32_t* hint_valid, bool side) {
   const bool margin = (flags & SCHULZE_F_MARGIN) != 0;
   if (use_s16(bound, flags))
-    return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin);
-  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin);
+    return run_closure<int16_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin, side);
+  return run_closure<int32_t>(ctx, d, m, bound, p, ws, stream, beaten_by, hint, hint_valid, margin, side);
 }
 
 // ------------------------------------------------- allocation-free variant

@@ -8,6 +8,12 @@
 
 namespace schulze {
 
+int side_join(schulze_ctx* ctx, cudaStream_t stream) {
+  if (!ctx || !ctx->side_pending) return SCHULZE_OK;
+  ctx->side_pending = false;
+  return cudaStreamWaitEvent(stream, ctx->side_join, 0) == cudaSuccess ? SCHULZE_OK : SCHULZE_ECUDA;
+}
+
 int ensure_workspace(schulze_ctx* ctx, size_t bytes, cudaStream_t stream) {
   if (bytes <= ctx->ws.bytes) return SCHULZE_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -153,6 +159,17 @@ int schulze_ctx_create(int device, schulze_ctx** out) {
     cudaGetLastError();
     c->host_status = nullptr;
   }
+  // the side stream of schulze_run (without it p is written on the call's
+  // stream)
+  if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->side_fork) cudaEventDestroy(c->side_fork);
+    if (c->side_join) cudaEventDestroy(c->side_join);
+    c->side_stream = nullptr, c->side_fork = nullptr, c->side_join = nullptr;
+  }
   *out = c;
   return SCHULZE_OK;
 }
@@ -165,6 +182,9 @@ int schulze_ctx_destroy(schulze_ctx* ctx) {
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->host_exec) cudaGraphExecDestroy(ctx->host_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
+  if (ctx->side_join) cudaEventDestroy(ctx->side_join);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
   delete ctx;
   return SCHULZE_OK;
@@ -181,9 +201,9 @@ int schulze_reserve(schulze_ctx* ctx, int32_t m_max, int64_t n_max, int32_t k_ma
   size_t c = std::max(closure_workspace_bytes(m_max, n_max, 0), closure_workspace_bytes(m_max, 1, 0));
   size_t x = extract_workspace_bytes(m_max);
   // schulze_run keeps the tally's warm flags (with their relabeling) and
-  // beaten_by after the stages
+  // beaten_by after the stages, then the extraction's scratch
   const size_t mv = align_up(size_t(m_max) * 4, 256), hv = align_up(hint_words(m_max) * 4, 256);
-  size_t need = std::max(align_up(std::max(t, c), 256) + hv + mv + 256, x);
+  size_t need = align_up(std::max(t, c), 256) + hv + mv + 256 + x;
   // schulze_run_host keeps ranks, d, p, three vectors and the hint words
   // next to the stages
   size_t host_path = align_up(size_t(n_max) * size_t(k_max) * 4, 256) +
@@ -309,26 +329,27 @@ int schulze_run(schulze_ctx* ctx, const int32_t* ranks, int64_t n, int32_t m, in
   if ((flags & SCHULZE_F_TALLY_DENSE) && (flags & SCHULZE_F_TALLY_SPARSE)) return SCHULZE_EINVAL;
   if ((flags & SCHULZE_F_FORCE_S16) && ((flags & SCHULZE_F_FORCE_S32) || n > 32767)) return SCHULZE_EINVAL;
   if (int rc = set_device(ctx)) return rc;
-  // beaten_by comes out of the closure (from its warm rows), kept after the
-  // closure's scratch when the caller does not want it
-  // warm flags from the tally and the closure's beaten_by live after both
-  // stages' scratch
+  // workspace: the stages' scratch (tally, then closure, from the start),
+  // then the tally's warm flags with their relabeling and beaten_by (kept
+  // across the stages), then the extraction's scratch (the winners and the
+  // ranking are extracted while p is still being written from the closure's
+  // scratch on the side stream)
   const size_t mv = align_up(size_t(m) * 4, 256), hv = align_up(hint_words(m) * 4, 256);
   const size_t keep = std::max(align_up(tally_workspace_bytes(n, m, k, flags), 256),
                                align_up(closure_workspace_bytes(m, n, flags), 256));
-  size_t need = std::max(keep + hv + mv + 256, extract_workspace_bytes(m));
-  if (int rc = ensure_workspace(ctx, need, stream)) return rc;
+  const size_t xoff = keep + hv + mv + 256;
+  if (int rc = ensure_workspace(ctx, xoff + extract_workspace_bytes(m), stream)) return rc;
   char* tail = static_cast<char*>(ctx->ws.base) + keep;
   int32_t* hint = reinterpret_cast<int32_t*>(tail);
   int32_t* hint_valid = reinterpret_cast<int32_t*>(tail + hv);
   int32_t* bb = beaten_by ? beaten_by : reinterpret_cast<int32_t*>(tail + hv + 256);
+  void* xws = static_cast<char*>(ctx->ws.base) + xoff;
   if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, ctx->ws.base, stream, hint, hint_valid)) return rc;
   const bool ext = winners || order || beaten_by;
-  if (int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream, ext ? bb : nullptr, hint, hint_valid))
-    return rc;
-  if (ext && (winners || order))
-    if (int rc = extract_from_beaten_by(ctx, bb, m, winners, order, ctx->ws.base, stream)) return rc;
-  return SCHULZE_OK;
+  int rc = closure_launch(ctx, d, m, n, p, flags, ctx->ws.base, stream, ext ? bb : nullptr, hint, hint_valid, true);
+  if (!rc && ext && (winners || order)) rc = extract_from_beaten_by(ctx, bb, m, winners, order, xws, stream);
+  const int rj = side_join(ctx, stream);  // also after an error: a capture must end with the fork joined
+  return rc ? rc : rj;
 }
 
 int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int32_t m, int32_t k,
@@ -340,8 +361,9 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   if (int rc = set_device(ctx)) return rc;
   size_t rbytes = size_t(n) * size_t(k) * sizeof(int32_t);
   size_t mm = size_t(m) * size_t(m) * sizeof(int32_t);
-  size_t stage = std::max(tally_workspace_bytes(n, m, k, flags),
-                          std::max(closure_workspace_bytes(m, n, flags), extract_workspace_bytes(m)));
+  // (the extraction's scratch after the closure's: they run side by side)
+  size_t stage = align_up(std::max(tally_workspace_bytes(n, m, k, flags), closure_workspace_bytes(m, n, flags)), 256) +
+                 extract_workspace_bytes(m);
   size_t head = align_up(rbytes, 256) + 2 * align_up(mm, 256) + 3 * align_up(size_t(m) * 4, 256) +
                 align_up(hint_words(m) * 4, 256) + 512;
   if (int rc = ensure_workspace(ctx, head + stage + 4096, stream)) return rc;
@@ -355,15 +377,18 @@ int schulze_run_host(schulze_ctx* ctx, const int32_t* ranks_host, int64_t n, int
   int32_t* hint = cv.take<int32_t>(hint_words(m));
   int32_t* hint_valid = cv.take<int32_t>(1);
   void* rest = cv.take<char>(0);
+  void* xrest = static_cast<char*>(rest) +
+                align_up(std::max(tally_workspace_bytes(n, m, k, flags), closure_workspace_bytes(m, n, flags)), 256);
   // the call's work on stream s, the status word copied to *st
   auto enqueue = [&](cudaStream_t s, int32_t* st) -> int {
     if (rbytes && cudaMemcpyAsync(ranks, ranks_host, rbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return SCHULZE_ECUDA;
     if (int rc = tally_launch(ctx, ranks, n, m, k, d, flags, rest, s, hint, hint_valid)) return rc;
     const bool ext = winners_host || order_host;
-    if (int rc = closure_launch(ctx, d, m, n, p, flags, rest, s, ext ? bb : nullptr, hint, hint_valid)) return rc;
-    if (ext)
-      if (int rc = extract_from_beaten_by(ctx, bb, m, win, ord, rest, s)) return rc;
+    int rc = closure_launch(ctx, d, m, n, p, flags, rest, s, ext ? bb : nullptr, hint, hint_valid, true);
+    if (!rc && ext) rc = extract_from_beaten_by(ctx, bb, m, win, ord, xrest, s);
+    const int rj = side_join(ctx, s);
+    if (rc || rj) return rc ? rc : rj;
     if (winners_host && cudaMemcpyAsync(winners_host, win, size_t(m) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return SCHULZE_ECUDA;
     if (order_host && cudaMemcpyAsync(order_host, ord, size_t(m) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -93,6 +93,13 @@ struct schulze_ctx {
   // once as a CUDA graph on cap_stream and replayed while the arguments,
   // the workspace and the host buffers (page-locked) stay the same
   cudaStream_t cap_stream = nullptr;
+  // schulze_run / schulze_run_host: the closure writes p on side_stream
+  // (forked from the call's stream with side_fork) while the winners and
+  // the ranking are extracted; side_join is recorded after it and the
+  // call's stream waits on it before the call returns (side_pending)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  bool side_pending = false;
   cudaGraphExec_t host_exec = nullptr;
   int32_t* host_status = nullptr;  // page-locked word receiving the device status
   struct HostKey {
@@ -171,10 +178,15 @@ int tally_positions_launch(schulze_ctx* ctx, const int32_t* pos, int64_t n, int3
 // warm flags and their relabeling from the tally when *hint_valid is set,
 // skipping its own pass over d (and that pass's bound check, which the
 // tally's d meets); otherwise it writes its relabeling into hint's perm,
-// inv and warm words.
+// inv and warm words. With side (and beaten_by) p is written on the
+// context's side stream while beaten_by is extracted on stream; the caller
+// ends with side_join(ctx, stream) before it returns (and before anything
+// on stream reuses the closure's scratch).
 int closure_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t bound, int32_t* p, uint32_t flags,
                    void* ws, cudaStream_t stream, int32_t* beaten_by = nullptr, int32_t* hint = nullptr,
-                   const int32_t* hint_valid = nullptr);
+                   const int32_t* hint_valid = nullptr, bool side = false);
+// stream waits for the side stream's work if closure_launch forked any
+int side_join(schulze_ctx* ctx, cudaStream_t stream);
 int extract_launch(schulze_ctx* ctx, const int32_t* p, int32_t m, int32_t* winners, int32_t* order,
                    int32_t* beaten_by, void* ws, cudaStream_t stream);
 // Winners by the paper's vertex-centric algorithm on the dense tally;
