@@ -623,8 +623,9 @@ def run_batch(args, world, rank, local):
                 "config": {"workload": "batch_mixed", "detail": WORKLOADS["batch_mixed"]["desc"], "elections": E,
                            "ballot_bytes": int(bw.ranks.nbytes),
                            "schedule": {"tally_policy": tile, "order_policy": ordp,
-                                        "ballots_per_step_by_m_bucket": {f"m<={mx}": {"chunk": ch, "elections": el}
-                                                                         for mx, ch, el in sched}},
+                                        "by_m_bucket": {f"m<={mx}": {"ballots_per_step": ch, "groups_per_tile": g,
+                                                                     "elections": el}
+                                                        for (mx, ch, el), g in zip(sched, plan.bucket_tiles())}},
                            "l2": "inputs (ballots) larger than L2"},
                 "elections_per_sec": eps, "one_launch_per_election_elections_per_sec": single_eps,
                 "batch_speedup_vs_one_launch_per_election": eps / world / single_eps,

@@ -304,20 +304,31 @@ int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t o
  * largest m). Synchronous. */
 int schulze_batch_set_bucket_chunk(schulze_batch* b, int32_t bucket, int32_t chunk);
 
+/* The tally of an election covers d in 64 x 64 tiles, worked on by the four
+ * 128-thread tile groups of a CTA; groups_per_tile (1, 2 or 4) groups share
+ * one tile, each counting every groups_per_tile-th staged ballot (so an
+ * election of one or two tiles still keeps all four busy), set here per
+ * bucket (EINVAL otherwise). Synchronous. */
+int schulze_batch_set_bucket_tiles(schulze_batch* b, int32_t bucket, int32_t groups_per_tile);
+
 /* The per-bucket schedule: largest m of each bucket, its ballots per step
  * and the number of the plan's elections in it (host int32 [5] each, any may
  * be NULL). */
 int schulze_batch_bucket_schedule(const schulze_batch* b, int32_t* bucket_max_m, int32_t* chunks,
                                   int32_t* elections);
 
+/* Groups per tally tile of each bucket (host int32 [5], not NULL). */
+int schulze_batch_bucket_tiles(const schulze_batch* b, int32_t* groups_per_tile);
+
 /* Autotuner: for every m-bucket with elections, times the bucket's elections
  * alone (one launch over them, three runs, the best of the last two) with
- * every ballots-per-step size that fits and keeps the fastest; then times
- * both election orders on the whole batch. best_tally receives 0 (the
- * per-bucket schedule), best_order the order policy. With cache_path, a
- * result already recorded for the same GPU and bucket (election count and
- * mean ballot count) or batch signature is reused, and new ones are
- * appended, one "<key> <value>" line each. */
+ * every ballots-per-step size that fits times every number of groups per
+ * tally tile (1, 2, 4) and keeps the fastest pair; then times both election
+ * orders on the whole batch. best_tally receives 0 (the per-bucket
+ * schedule), best_order the order policy. With cache_path, a result already
+ * recorded for the same GPU and bucket (election count and mean ballot
+ * count; value chunk * 8 + groups per tile) or batch signature is reused,
+ * and new ones are appended, one "<key> <value>" line each. */
 int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* cache_path, int32_t* best_tally,
                            int32_t* best_order, schulze_stream_t stream);
 

@@ -62,6 +62,8 @@ SIGNATURES = [
     ("schulze_batch_set_schedule", _c.c_int, [_vp, _i32, _i32]),
     ("schulze_batch_set_bucket_chunk", _c.c_int, [_vp, _i32, _i32]),
     ("schulze_batch_bucket_schedule", _c.c_int, [_vp, _vp, _vp, _vp]),
+    ("schulze_batch_set_bucket_tiles", _c.c_int, [_vp, _i32, _i32]),
+    ("schulze_batch_bucket_tiles", _c.c_int, [_vp, _vp]),
     ("schulze_batch_autotune", _c.c_int, [_vp, _vp, _c.c_char_p, _c.POINTER(_i32), _c.POINTER(_i32), _vp]),
     ("schulze_features", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _vp]),
     ("schulze_mlp_forward", _c.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
@@ -493,6 +495,17 @@ class SchulzeBatch:
         mx, ch, el = (_i32 * 5)(), (_i32 * 5)(), (_i32 * 5)()
         _check(self._lib.schulze_batch_bucket_schedule(self.handle, mx, ch, el), "schulze_batch_bucket_schedule")
         return [(mx[q], ch[q], el[q]) for q in range(5)]
+
+    def set_bucket_tiles(self, bucket: int, groups_per_tile: int):
+        """Tile groups (1, 2 or 4) sharing one tally tile for the elections of one m-bucket."""
+        _check(self._lib.schulze_batch_set_bucket_tiles(self.handle, int(bucket), int(groups_per_tile)),
+               "schulze_batch_set_bucket_tiles")
+
+    def bucket_tiles(self):
+        """Groups per tally tile of the five m-buckets."""
+        g = (_i32 * 5)()
+        _check(self._lib.schulze_batch_bucket_tiles(self.handle, g), "schulze_batch_bucket_tiles")
+        return [g[q] for q in range(5)]
 
     def autotune(self, ranks: torch.Tensor, cache_path: str | None = None, stream=None):
         """Pick the fastest schedule for this batch; returns (tally_policy, order_policy)."""

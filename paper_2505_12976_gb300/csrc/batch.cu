@@ -33,11 +33,12 @@ struct Job {
   int32_t n, m, k, e;
   int64_t ranks_off, mat_off, vec_off;
   int32_t chunk;  // ballots staged per tally step (the schedule of the election's m-bucket)
-  int32_t pad;
+  int32_t gpt;    // tile groups that share one tally tile, splitting its ballots (1, 2 or 4)
 };
 
 // Elections are grouped by m into buckets, each with its own tally schedule
-// (ballots staged per step), which schulze_batch_autotune times and caches.
+// (ballots staged per step, tile groups per tally tile), which
+// schulze_batch_autotune times and caches.
 constexpr int kBuckets = 5;
 constexpr int32_t kBucketMax[kBuckets] = {64, 128, 256, 512, 1024};
 inline int bucket_of(int32_t m) {
@@ -46,6 +47,7 @@ inline int bucket_of(int32_t m) {
   return b;
 }
 constexpr int kChunkChoices[4] = {8, 16, 32, 64};
+constexpr int kGptChoices[3] = {1, 2, 4};
 constexpr int kPrefetch = 32;  // ballot ids a thread holds for the next step
 
 struct BatchArgs {
@@ -86,9 +88,12 @@ union BatchSmem {
 
 constexpr int kTT = 64;  // tally tile: 64 x 64 counters per group, 8 x 4 per thread
 
-// The election's d, tile by tile: each of the four 128-thread groups owns one
-// 64 x 64 tile of d per round and counts it over all ballots in 16-bit lanes
-// (two columns per word, the row operand duplicated into both halves).
+// The election's d, tile by tile: the four 128-thread groups take tiles of
+// 64 x 64 entries, jb.gpt groups per tile (4 / gpt tiles per round), and
+// count them in 16-bit lanes (two columns per word, the row operand
+// duplicated into both halves); the groups of one tile take alternate
+// staged ballots and add their counts into d (zeroed first) with atomics,
+// so an election of one or two tiles still keeps every group busy.
 // Ballots are staged `chunk` at a time as full position rows (unlisted
 // candidates at position k), so one staging serves the four tiles of a
 // round. Counters are added into d every kFlushVoters ballots. Full
@@ -109,6 +114,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16) | kGuard2;
   const int32_t mpad = int32_t(align_up(size_t(m), kTT));
   const int chunk = jb.chunk;  // chunk * mpad * 6 <= sizeof(BatchSmem), chunk * k <= kBT * kPrefetch (plan)
+  const int gpt = jb.gpt, tpr = kGroups / gpt, phase = g % gpt;  // tiles per round, this group's ballots
   uint32_t* dup = reinterpret_cast<uint32_t*>(sm.raw);                         // [chunk][mpad]
   uint16_t* pos = reinterpret_cast<uint16_t*>(sm.raw + size_t(chunk) * mpad * 4);  // [chunk][mpad]
   // ballot ids of a step: thread tid holds positions q0 + u * lanes of ballot
@@ -125,9 +131,11 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
       cv[u] = (have && q < k) ? __ldcs(row + q) : -1;
     }
   };
-  for (int32_t t0 = 0; t0 < ntiles; t0 += kGroups) {
+  if (gpt > 1)  // the groups of a tile add into d (visible after the first barrier below)
+    for (int64_t t = tid; t < int64_t(m) * m; t += kBT) dm[t] = 0;
+  for (int32_t t0 = 0; t0 < ntiles; t0 += tpr) {
     // this group's tile (bi, bj)
-    const int32_t tt = t0 + g;
+    const int32_t tt = t0 + g / gpt;
     int32_t bi = 0, bj = 0;
     if (tt < ntiles) {
       if (full) {
@@ -183,7 +191,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
       if (v0 + chunk < n) load_ids(v0 + chunk);  // in flight while this step counts
       __syncthreads();
       if (tt < ntiles) {
-        for (int u = 0; u < nv; ++u) {
+        for (int u = phase; u < nv; u += gpt) {
           uint32_t a[8], b[2];
           const uint4 a0 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8]);
           const uint4 a1 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8 + 4]);
@@ -206,8 +214,14 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
               const int32_t j = J0 + tx * 4 + 2 * w;
               if (i < m) {
                 int32_t* dst = dm + int64_t(i) * m + j;
-                if (j < m) dst[0] = (first_flush ? 0 : dst[0]) + int32_t(acc[r][w] & 0xFFFFu);
-                if (j + 1 < m) dst[1] = (first_flush ? 0 : dst[1]) + int32_t(acc[r][w] >> 16);
+                const int32_t lo = int32_t(acc[r][w] & 0xFFFFu), hi = int32_t(acc[r][w] >> 16);
+                if (gpt > 1) {
+                  if (j < m && lo) atomicAdd(dst, lo);
+                  if (j + 1 < m && hi) atomicAdd(dst + 1, hi);
+                } else {
+                  if (j < m) dst[0] = (first_flush ? 0 : dst[0]) + lo;
+                  if (j + 1 < m) dst[1] = (first_flush ? 0 : dst[1]) + hi;
+                }
               }
             }
             acc[r][0] = acc[r][1] = 0u;
@@ -370,6 +384,7 @@ struct schulze_batch {
   int32_t tally_policy = 0;  // 0: each m-bucket's ballots per step; 1: eight everywhere
   int32_t order_policy = 0;  // 0 longest first, 1 the caller's order
   int32_t bucket_chunk[schulze::kBuckets] = {32, 32, 32, 16, 16};
+  int32_t bucket_gpt[schulze::kBuckets] = {1, 1, 1, 1, 1};
   size_t smem = 0;
 };
 
@@ -399,13 +414,17 @@ int32_t job_chunk(const schulze_batch* b, int32_t m) {
   return c;
 }
 
+int32_t job_gpt(const schulze_batch* b, int32_t m) { return b->tally_policy == 1 ? 1 : b->bucket_gpt[bucket_of(m)]; }
+
+bool gpt_valid(int32_t g) { return g == 1 || g == 2 || g == 4; }
+
 void order_jobs(schulze_batch* b) {
   std::vector<Job> js(size_t(b->E));
   for (int32_t e = 0; e < b->E; ++e) js[e] = b->jobs_host[e];
   std::sort(js.begin(), js.end(), [](const Job& x, const Job& y) { return x.e < y.e; });
   if (b->order_policy == 0)
     std::stable_sort(js.begin(), js.end(), [](const Job& x, const Job& y) { return job_cost(x) > job_cost(y); });
-  for (Job& j : js) j.chunk = job_chunk(b, j.m);
+  for (Job& j : js) j.chunk = job_chunk(b, j.m), j.gpt = job_gpt(b, j.m);
   b->jobs_host = js;
 }
 
@@ -567,6 +586,21 @@ int schulze_batch_set_bucket_chunk(schulze_batch* b, int32_t bucket, int32_t chu
   return upload_jobs(b);
 }
 
+int schulze_batch_set_bucket_tiles(schulze_batch* b, int32_t bucket, int32_t groups_per_tile) {
+  if (!b || bucket < 0 || bucket >= kBuckets || !gpt_valid(groups_per_tile)) return SCHULZE_EINVAL;
+  if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SCHULZE_ECUDA;
+  b->bucket_gpt[bucket] = groups_per_tile;
+  order_jobs(b);
+  return upload_jobs(b);
+}
+
+int schulze_batch_bucket_tiles(const schulze_batch* b, int32_t* groups_per_tile) {
+  if (!b || !groups_per_tile) return SCHULZE_EINVAL;
+  for (int q = 0; q < kBuckets; ++q) groups_per_tile[q] = b->bucket_gpt[q];
+  return SCHULZE_OK;
+}
+
 int schulze_batch_bucket_schedule(const schulze_batch* b, int32_t* bucket_max_m, int32_t* chunks,
                                   int32_t* elections) {
   if (!b) return SCHULZE_EINVAL;
@@ -638,29 +672,36 @@ int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* c
     for (const Job& j : b->jobs_host)
       if (bucket_of(j.m) == q) sub.push_back(j), nsum += j.n;
     if (sub.empty()) continue;
+    // the cached value is chunk * 8 + groups per tile
     char key[400];
-    snprintf(key, sizeof(key), "%.100s|s16=%d|bucket<=%d|elections=%zu|mean_n=%lld", prop.name, b->s16 ? 1 : 0,
-             kBucketMax[q], sub.size(), (long long)(nsum / double(sub.size())));
+    snprintf(key, sizeof(key), "%.100s|s16=%d|bucket<=%d|chunk_gpt|elections=%zu|mean_n=%lld", prop.name,
+             b->s16 ? 1 : 0, kBucketMax[q], sub.size(), (long long)(nsum / double(sub.size())));
     clean(key);
-    int best_c = lookup(key);
-    if (best_c < 0 || !chunk_fits(kBucketMax[q], best_c)) {
+    int best_v = lookup(key);
+    if (best_v < 0 || !chunk_fits(kBucketMax[q], best_v / 8) || !gpt_valid(best_v % 8)) {
       // time this bucket's elections alone for every staging size that fits
+      // and every number of groups per tally tile
       float best = 1e30f;
-      best_c = b->bucket_chunk[q];
+      best_v = b->bucket_chunk[q] * 8 + b->bucket_gpt[q];
       for (int c : kChunkChoices) {
         if (!chunk_fits(kBucketMax[q], c)) continue;
-        for (Job& j : sub) j.chunk = c;
-        if (cudaMemcpy(b->jobs_dev, sub.data(), sizeof(Job) * sub.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-          rc = SCHULZE_ECUDA;
-          break;
+        for (int g : kGptChoices) {
+          for (Job& j : sub) j.chunk = c, j.gpt = g;
+          if (cudaMemcpy(b->jobs_dev, sub.data(), sizeof(Job) * sub.size(), cudaMemcpyHostToDevice) !=
+              cudaSuccess) {
+            rc = SCHULZE_ECUDA;
+            break;
+          }
+          float ms = 0.f;
+          if ((rc = time_jobs(int32_t(sub.size()), &ms)) != SCHULZE_OK) break;
+          if (ms < best) best = ms, best_v = c * 8 + g;
         }
-        float ms = 0.f;
-        if ((rc = time_jobs(int32_t(sub.size()), &ms)) != SCHULZE_OK) break;
-        if (ms < best) best = ms, best_c = c;
+        if (rc != SCHULZE_OK) break;
       }
-      fresh.emplace_back(key, best_c);
+      fresh.emplace_back(key, best_v);
     }
-    b->bucket_chunk[q] = best_c;
+    b->bucket_chunk[q] = best_v / 8;
+    b->bucket_gpt[q] = best_v % 8;
   }
   int32_t bo = -1;
   if (rc == SCHULZE_OK) {

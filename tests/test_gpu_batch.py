@@ -145,9 +145,11 @@ def test_batch_autotune_keeps_results_exact(tmp_path):
     for q in used:  # every choice is a staging size that fits the bucket
         mx, ch, _ = sched1[q]
         assert ch in (8, 16, 32, 64) and ch * (-(-mx // 64) * 64) * 6 <= 131584 and ch * mx <= 16384
+    tiles1 = b.bucket_tiles()
+    assert all(g in (1, 2, 4) for g in tiles1)
     b2 = S.SchulzeBatch(bw.n, bw.m, bw.k)
     t2, o2 = b2.autotune(ranks, cache)  # a new plan of the same batch reads the cache
-    assert (t1, o1) == (t2, o2) and b2.bucket_schedule() == sched1
+    assert (t1, o1) == (t2, o2) and b2.bucket_schedule() == sched1 and b2.bucket_tiles() == tiles1
     assert open(cache).read().splitlines() == lines  # nothing re-timed
     outs = _outputs(b)
     b.run(ranks, *outs)
@@ -157,8 +159,9 @@ def test_batch_autotune_keeps_results_exact(tmp_path):
 
 def test_batch_every_bucket_schedule_is_exact():
     """Every ballots-per-step size each m-bucket accepts (8 to 64 where the
-    position rows fit) gives the oracle's results; sizes that do not fit are
-    refused."""
+    position rows fit) and every number of tile groups per tally tile (1, 2,
+    4) gives the oracle's results; sizes that do not fit, and other group
+    counts, are refused."""
     els = _mixed_elections(seed=8) + [(W.mallows(41, 900, 700, 700, 0.9, W.permutation(41, 700)), 700),
                                       (W.impartial(42, 300, 1000, 60), 1000)]
     n, m, k, flat = _pack(els)
@@ -173,6 +176,18 @@ def test_batch_every_bucket_schedule_is_exact():
             else:
                 with pytest.raises(S.SchulzeError):
                     b.set_bucket_chunk(q, chunk)
+        outs = _outputs(b)
+        b.run(ranks, *outs)
+        torch.cuda.synchronize()
+        _check(b, els, outs)
+    for q in range(5):
+        b.set_bucket_chunk(q, 8)
+        with pytest.raises(S.SchulzeError):
+            b.set_bucket_tiles(q, 3)
+    for gpt in (2, 4):
+        for q in range(5):
+            b.set_bucket_tiles(q, gpt)
+        assert b.bucket_tiles() == [gpt] * 5
         outs = _outputs(b)
         b.run(ranks, *outs)
         torch.cuda.synchronize()
