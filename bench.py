@@ -81,8 +81,8 @@ WORKLOADS = {
     "huge_pl": dict(desc="m=16384, n=200000, top-20 Plackett-Luce Zipf(1.1), int32 closure"),
     "batch_mixed": dict(desc="4096 elections, m~U[8,512], n~U[50,5000], full rankings, half Mallows "
                              "(phi~U[0.5,1]) half impartial culture, one persistent launch"),
-    "learned": dict(desc="proposal network trained on 2000 GPU-solved top-k Mallows elections; "
-                         "32 evaluation elections m=8192, n=20000, top-50, phi=0.9"),
+    "learned": dict(desc="proposal network trained on GPU-solved top-k Mallows elections (20000 by "
+                         "default); evaluation elections m=8192, n=20000, top-50, phi=0.9 (256 by default)"),
     "spotify_like": dict(desc="m=18407, n=15553, top-200 Plackett-Luce Zipf(1.1): the shape of the paper's "
                               "largest Spotify profile, synthetic"),
     "iterated_topk": dict(desc="top-10 ranking by iterated winner removal on the m=4096, n=20000, top-50 "
