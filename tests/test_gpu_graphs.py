@@ -189,3 +189,28 @@ def test_host_call_graph_replays():
     S.schulze_run_host(r_pin, m, winners=win, order=order, device=0)
     check(ballots[0], win.numpy(), order.numpy(), "after invalid ballots")
     assert ctx.status() == S.OK
+
+
+def test_run_outputs_are_ordered_on_the_callers_stream():
+    """schulze_run writes p on a side stream of its context and joins it back
+    to the caller's stream: work queued on that stream after the call sees all
+    of p, with no device-wide synchronisation in between. p is filled with -1
+    first; a reduction queued right after the call must find no -1 left, the
+    diagonal zero, and the same p as a call that synchronises the device."""
+    e = W.large_topk()  # 151 listed of 4096: p is mostly the zero rows of unlisted candidates
+    m = e.m
+    dev = torch.device("cuda")
+    r = torch.from_numpy(e.ranks).to(dev)
+    ref = S.schulze_run(r, m)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        out = _outs(m, dev)
+        out["p"].fill_(-1)
+        S.schulze_run(r, m, out=out)
+        low = out["p"].min()
+        diag = out["p"].diagonal().abs().sum()
+        same = torch.equal(out["p"], ref["p"])  # a host read: synchronises s only
+    torch.cuda.synchronize()
+    assert int(low) >= 0 and int(diag) == 0 and same
