@@ -293,6 +293,9 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restric
     h1[o] = fmaxf(s, 0.f);
   }
   float out = p[kOffB3];
+  // four outputs at a time: their sums are independent chains that hide
+  // each other's latency (each sum still runs in the parameters' order)
+#pragma unroll 4
   for (int o = 0; o < kH; ++o) {
     float s = p[kOffB2 + o];
     const float4* w = reinterpret_cast<const float4*>(p + kOffW2 + o * kH);
