@@ -290,6 +290,21 @@ int schulze_batch_layout(const schulze_batch* b, int64_t* ranks_elems, int64_t* 
 int schulze_batch_run(schulze_batch* b, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
                       int32_t* order, int32_t* beaten_by, schulze_stream_t stream);
 
+/* The batch from HOST buffers, end to end: ranks_host in the plan's layout
+ * (page-locked memory gives the copies full speed; any host memory works),
+ * winners_host / order_host (host int32 [vec_elems], either may be NULL)
+ * receive the results. The caller's elections are cut into up to eight
+ * segments of about equal ballot bytes; each segment's ballots are copied on
+ * the plan's own copy stream while the previous segment is computed, and
+ * each segment runs as one launch (its elections longest first, the plan's
+ * schedule). The first call allocates the plan's device copy of the ballots
+ * and its output buffers (ranks_elems + 2 vec_elems int32), kept until
+ * schulze_batch_destroy. Synchronous: returns once the results are on the
+ * host. Bad ballots are reported as SCHULZE_EDATA in the context's status
+ * word. */
+int schulze_batch_run_host(schulze_batch* b, const int32_t* ranks_host, int32_t* winners_host, int32_t* order_host,
+                           schulze_stream_t stream);
+
 /* Schedule knobs: tally_policy 0 stages each election's ballots in steps of
  * its m-bucket's size (schulze_batch_set_bucket_chunk, the autotuner), 1
  * stages eight everywhere; order_policy 0 runs the longest elections first,

@@ -63,6 +63,7 @@ SIGNATURES = [
     ("schulze_batch_set_bucket_chunk", _c.c_int, [_vp, _i32, _i32]),
     ("schulze_batch_bucket_schedule", _c.c_int, [_vp, _vp, _vp, _vp]),
     ("schulze_batch_set_bucket_tiles", _c.c_int, [_vp, _i32, _i32]),
+    ("schulze_batch_run_host", _c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("schulze_batch_bucket_tiles", _c.c_int, [_vp, _vp]),
     ("schulze_batch_autotune", _c.c_int, [_vp, _vp, _c.c_char_p, _c.POINTER(_i32), _c.POINTER(_i32), _vp]),
     ("schulze_features", _c.c_int, [_vp, _vp, _i32, _i64, _vp, _vp]),
@@ -480,6 +481,27 @@ class SchulzeBatch:
                 raise ValueError(f"{name} is smaller than the plan's layout")
         _check(self._lib.schulze_batch_run(self.handle, _ptr(ranks), _ptr(d), _ptr(p), _ptr(winners), _ptr(order),
                                            _ptr(beaten_by), _stream(stream, self.ctx.device)), "schulze_batch_run")
+
+    def run_host(self, ranks, winners=None, order=None, stream=None):
+        """Run every election from host buffers (schulze_batch_run_host): ranks a
+        contiguous int32 CPU tensor or array in the plan's layout (pinned memory
+        copies fastest); winners / order host int32 buffers of vec_elems (made
+        when None). Returns (winners, order) once they are on the host."""
+        def host_ptr(a, name, size):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.int32 or not a.is_contiguous() or a.numel() < size:
+                    raise ValueError(f"{name} must be a contiguous int32 CPU tensor of at least {size} elements")
+                return a.data_ptr()
+            if a.dtype != np.int32 or not a.flags.c_contiguous or a.size < size:
+                raise ValueError(f"{name} must be a contiguous int32 array of at least {size} elements")
+            return a.ctypes.data
+        rptr = host_ptr(ranks, "ranks", self.ranks_elems)
+        winners = np.empty(self.vec_elems, np.int32) if winners is None else winners
+        order = np.empty(self.vec_elems, np.int32) if order is None else order
+        wptr, optr = host_ptr(winners, "winners", self.vec_elems), host_ptr(order, "order", self.vec_elems)
+        _check(self._lib.schulze_batch_run_host(self.handle, _vp(rptr), _vp(wptr), _vp(optr),
+                                                _stream(stream, self.ctx.device)), "schulze_batch_run_host")
+        return winners, order
 
     def set_schedule(self, tally_policy: int, order_policy: int):
         _check(self._lib.schulze_batch_set_schedule(self.handle, tally_policy, order_policy),

@@ -34,6 +34,8 @@ struct Job {
   int64_t ranks_off, mat_off, vec_off;
   int32_t chunk;  // ballots staged per tally step (the schedule of the election's m-bucket)
   int32_t gpt;    // tile groups that share one tally tile, splitting its ballots (1, 2 or 4)
+  int32_t seg;    // schulze_batch_run_host: the segment whose arrival mark the job waits for
+  int32_t pad;
 };
 
 // Elections are grouped by m into buckets, each with its own tally schedule
@@ -64,6 +66,11 @@ struct BatchArgs {
   size_t slot_bytes;  // per CTA: W slot, then a d slot when the caller passes no d
   size_t w_bytes;
   int32_t* status;
+  // schulze_batch_run_host: arrival marks of the ballot segments (set by the
+  // copy stream after each segment's copy; null otherwise) and the bound on
+  // a wait for one, in SM clock cycles
+  const int32_t* seg_flag;
+  long long wait_limit;
 };
 
 // Dynamic shared memory of one batch CTA, reused stage by stage. The tally
@@ -128,7 +135,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
       const int32_t q = q0 + u * lanes;
-      cv[u] = (have && q < k) ? __ldcs(row + q) : -1;
+      cv[u] = (have && q < k) ? __ldcg(row + q) : -1;  // L2 only: see schulze_batch_run_host
     }
   };
   if (gpt > 1)  // the groups of a tile add into d (visible after the first barrier below)
@@ -349,6 +356,27 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
     __syncthreads();
     if (ji >= a.njobs) return;
     const Job jb = a.jobs[ji];
+    if (a.seg_flag) {
+      // the job's ballots may still be on their way: thread 0 waits (bounded)
+      // for its segment's arrival mark, which the copy stream writes after
+      // the segment's copy; the ballots are then read from L2, where the copy
+      // landed (the tally reads them with L2-only loads, so no line cached in
+      // L1 before the mark can be stale)
+      __shared__ int32_t s_arrived;
+      if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        int32_t seen = 0;
+        for (;;) {
+          asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(seen) : "l"(a.seg_flag + jb.seg) : "memory");
+          if (seen || clock64() - t0 > a.wait_limit) break;
+          __nanosleep(200);
+        }
+        if (!seen) set_status(a.status, SCHULZE_ETIMEOUT);
+        s_arrived = seen;
+      }
+      __syncthreads();
+      if (!s_arrived) return;  // this CTA stops; the status word reports the timeout
+    }
     const int32_t* ranks = a.ranks + jb.ranks_off;
     int32_t* dm = a.d ? a.d + jb.mat_off : dslot;
     const int32_t m = jb.m;
@@ -386,6 +414,18 @@ struct schulze_batch {
   int32_t bucket_chunk[schulze::kBuckets] = {32, 32, 32, 16, 16};
   int32_t bucket_gpt[schulze::kBuckets] = {1, 1, 1, 1, 1};
   size_t smem = 0;
+  // schulze_batch_run_host (allocated at its first call): device ballots and
+  // outputs, the caller's elections cut into segments of about equal ballot
+  // bytes with each segment's job table (longest first), the copy stream and
+  // one event per segment
+  int32_t* host_ranks = nullptr;
+  int32_t* host_out = nullptr;  // winners [vec_elems], then order [vec_elems]
+  int32_t* seg_flag = nullptr;  // arrival mark per segment
+  int32_t* host_one = nullptr;  // page-locked 1, copied into a mark
+  schulze::Job* seg_jobs_dev = nullptr;
+  std::vector<int32_t> seg_elec0;  // per segment: its first election
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t flags_clear = nullptr;
 };
 
 namespace schulze {
@@ -440,10 +480,13 @@ int upload_jobs(schulze_batch* b) {
 // subset uploaded by the autotuner), outputs to the per-CTA scratch or the
 // caller's buffers.
 int launch_jobs(schulze_batch* b, int32_t njobs, const int32_t* ranks, int32_t* d, int32_t* p, int32_t* winners,
-                int32_t* order, int32_t* beaten_by, cudaStream_t stream) {
+                int32_t* order, int32_t* beaten_by, cudaStream_t stream, const Job* jobs = nullptr,
+                const int32_t* seg_flag = nullptr) {
   if (cudaMemsetAsync(b->head, 0, 4, stream) != cudaSuccess) return SCHULZE_ECUDA;
   BatchArgs a;
-  a.jobs = b->jobs_dev;
+  a.jobs = jobs ? jobs : b->jobs_dev;
+  a.seg_flag = seg_flag;
+  a.wait_limit = b->ctx->wait_limit_cycles;
   a.njobs = njobs;
   a.head = b->head;
   a.ranks = ranks;
@@ -539,7 +582,101 @@ int schulze_batch_destroy(schulze_batch* b) {
   cudaFree(b->jobs_dev);
   cudaFree(b->head);
   cudaFree(b->scratch);
+  if (b->host_ranks) cudaFree(b->host_ranks);
+  if (b->host_out) cudaFree(b->host_out);
+  if (b->seg_jobs_dev) cudaFree(b->seg_jobs_dev);
+  if (b->seg_flag) cudaFree(b->seg_flag);
+  if (b->host_one) cudaFreeHost(b->host_one);
+  if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
+  if (b->flags_clear) cudaEventDestroy(b->flags_clear);
   delete b;
+  return SCHULZE_OK;
+}
+
+namespace {
+
+// schulze_batch_run_host's state: at the first call the buffers and the
+// segments of the caller's elections (contiguous ballots, about equal ballot
+// bytes); at every call the job table: segment after segment, each one's
+// elections longest first, with the plan's schedule of that moment.
+int host_path_setup(schulze_batch* b) {
+  if (!b->host_out) {
+    constexpr int kSegments = 8;
+    const int nseg = std::max(1, std::min<int>(kSegments, b->E));
+    b->seg_elec0.assign(1, 0);
+    const double per = double(std::max<int64_t>(b->ranks_elems, 1)) / nseg;
+    for (int32_t e = 1; e < b->E && int(b->seg_elec0.size()) < nseg; ++e)
+      if (double(b->ranks_off[e]) >= per * double(b->seg_elec0.size())) b->seg_elec0.push_back(e);
+    b->seg_elec0.push_back(b->E);
+    const size_t ns = b->seg_elec0.size() - 1;
+    if (cudaMalloc(&b->host_ranks, sizeof(int32_t) * size_t(std::max<int64_t>(b->ranks_elems, 1))) != cudaSuccess ||
+        cudaMalloc(&b->host_out, sizeof(int32_t) * 2 * size_t(std::max<int64_t>(b->vec_elems, 1))) != cudaSuccess ||
+        cudaMalloc(&b->seg_jobs_dev, sizeof(Job) * size_t(b->E)) != cudaSuccess ||
+        cudaMalloc(&b->seg_flag, sizeof(int32_t) * ns) != cudaSuccess ||
+        cudaMallocHost(&b->host_one, sizeof(int32_t)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->flags_clear, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return SCHULZE_ENOMEM;  // what was allocated is freed by schulze_batch_destroy
+    }
+    *b->host_one = 1;
+  }
+  std::vector<Job> by_e(size_t(b->E));
+  for (const Job& j : b->jobs_host) by_e[size_t(j.e)] = j;
+  std::vector<Job> table;
+  table.reserve(size_t(b->E));
+  for (size_t s = 0; s + 1 < b->seg_elec0.size(); ++s) {
+    const size_t t0 = table.size();
+    for (int32_t e = b->seg_elec0[s]; e < b->seg_elec0[s + 1]; ++e) {
+      table.push_back(by_e[size_t(e)]);
+      table.back().seg = int32_t(s);
+    }
+    std::stable_sort(table.begin() + int64_t(t0), table.end(),
+                     [](const Job& x, const Job& y) { return job_cost(x) > job_cost(y); });
+  }
+  return cudaMemcpy(b->seg_jobs_dev, table.data(), sizeof(Job) * table.size(), cudaMemcpyHostToDevice) == cudaSuccess
+             ? SCHULZE_OK
+             : SCHULZE_ECUDA;
+}
+
+}  // namespace
+
+int schulze_batch_run_host(schulze_batch* b, const int32_t* ranks_host, int32_t* winners_host, int32_t* order_host,
+                           schulze_stream_t stream) {
+  AbiRange abi_range("schulze_batch_run_host");
+  if (!b || (b->ranks_elems > 0 && !ranks_host)) return SCHULZE_EINVAL;
+  if (cudaSetDevice(b->ctx->device) != cudaSuccess) return SCHULZE_ECUDA;
+  if (b->E == 0) return SCHULZE_OK;
+  if (int rc = host_path_setup(b)) return rc;
+  const size_t ns = b->seg_elec0.size() - 1;
+  int32_t* win = b->host_out;
+  int32_t* ord = b->host_out + b->vec_elems;
+  // the arrival marks cleared on stream, and the copy stream after that:
+  // each segment's ballots, then its mark; meanwhile one launch over every
+  // election on stream, each CTA waiting for the mark of its job's segment
+  if (cudaMemsetAsync(b->seg_flag, 0, sizeof(int32_t) * ns, stream) != cudaSuccess ||
+      cudaEventRecord(b->flags_clear, stream) != cudaSuccess ||
+      cudaStreamWaitEvent(b->copy_stream, b->flags_clear, 0) != cudaSuccess)
+    return SCHULZE_ECUDA;
+  for (size_t s = 0; s < ns; ++s) {
+    const int64_t r0 = b->ranks_off[b->seg_elec0[s]];
+    const int64_t r1 = b->seg_elec0[s + 1] < b->E ? b->ranks_off[b->seg_elec0[s + 1]] : b->ranks_elems;
+    if (r1 > r0 && cudaMemcpyAsync(b->host_ranks + r0, ranks_host + r0, sizeof(int32_t) * size_t(r1 - r0),
+                                   cudaMemcpyHostToDevice, b->copy_stream) != cudaSuccess)
+      return SCHULZE_ECUDA;
+    if (cudaMemcpyAsync(b->seg_flag + s, b->host_one, sizeof(int32_t), cudaMemcpyHostToDevice, b->copy_stream) !=
+        cudaSuccess)
+      return SCHULZE_ECUDA;
+  }
+  if (int rc = launch_jobs(b, b->E, b->host_ranks, nullptr, nullptr, winners_host ? win : nullptr,
+                           order_host ? ord : nullptr, nullptr, stream, b->seg_jobs_dev, b->seg_flag))
+    return rc;
+  const size_t vb = sizeof(int32_t) * size_t(b->vec_elems);
+  if ((winners_host && cudaMemcpyAsync(winners_host, win, vb, cudaMemcpyDeviceToHost, stream) != cudaSuccess) ||
+      (order_host && cudaMemcpyAsync(order_host, ord, vb, cudaMemcpyDeviceToHost, stream) != cudaSuccess))
+    return SCHULZE_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess || cudaStreamSynchronize(b->copy_stream) != cudaSuccess)
+    return SCHULZE_ECUDA;
   return SCHULZE_OK;
 }
 

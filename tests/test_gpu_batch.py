@@ -194,6 +194,26 @@ def test_batch_every_bucket_schedule_is_exact():
         _check(b, els, outs)
 
 
+def test_batch_from_host_buffers_matches_oracle():
+    """schulze_batch_run_host: ballots from host memory (page-locked, and a
+    plain numpy array), copied segment by segment beside the computation;
+    winners and order on the host equal the oracle's, for every election,
+    on two calls in a row and after the schedule changed in between."""
+    els = _mixed_elections(seed=11) + [(W.mallows(51, 700, 300, 300, 0.9, W.permutation(51, 300)), 300)]
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k)
+    pinned = torch.from_numpy(flat).pin_memory() if flat.size else torch.zeros(1, dtype=torch.int32)
+    win1, ord1 = b.run_host(pinned)
+    b.set_schedule(1, 1)  # eight ballots per step, the caller's order
+    win2, ord2 = b.run_host(flat if flat.size else np.zeros(1, np.int32))
+    for e, (r, mm) in enumerate(els):
+        vo = int(b.vec_off[e])
+        _, _, ww, ow, _ = oracle.schulze(r, mm)
+        for win, order, what in ((win1, ord1, "pinned"), (win2, ord2, "pageable")):
+            np.testing.assert_array_equal(win[vo:vo + mm], ww, err_msg=f"{what} winners of election {e}")
+            np.testing.assert_array_equal(order[vo:vo + mm], ow, err_msg=f"{what} order of election {e}")
+
+
 def test_batch_reports_bad_ballots():
     ctx = S.context()
     assert ctx.status() == S.OK
