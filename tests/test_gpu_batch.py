@@ -214,6 +214,33 @@ def test_batch_from_host_buffers_matches_oracle():
             np.testing.assert_array_equal(order[vo:vo + mm], ow, err_msg=f"{what} order of election {e}")
 
 
+def test_batch_host_wait_limit_returns_and_recovers():
+    """schulze_batch_run_host's bounded wait for a segment's arrival mark:
+    with the context's wait limit at one clock cycle (and about 8 MB of
+    ballots per segment, so the first marks come long after the first CTAs
+    look) the call still returns, the status word holds OK or
+    SCHULZE_ETIMEOUT, and the next call at the normal limit is exact."""
+    ctx = S.context()
+    assert ctx.status() == S.OK
+    els = [(W.impartial(300 + e, 4000, 64, 64), 64) for e in range(64)]  # 64 x 1 MB of ballots
+    n, m, k, flat = _pack(els)
+    b = S.SchulzeBatch(n, m, k, ctx=ctx)
+    pinned = torch.from_numpy(flat).pin_memory()
+    try:
+        ctx.set_wait_limit(1)
+        b.run_host(pinned)
+        assert ctx.status() in (S.OK, S.ETIMEOUT)
+    finally:
+        ctx.set_wait_limit(4_000_000_000)
+    win, order = b.run_host(pinned)
+    assert ctx.status() == S.OK
+    for e, (r, mm) in enumerate(els[:8]):
+        vo = int(b.vec_off[e])
+        _, _, ww, ow, _ = oracle.schulze(r, mm)
+        np.testing.assert_array_equal(win[vo:vo + mm], ww, err_msg=f"winners of election {e}")
+        np.testing.assert_array_equal(order[vo:vo + mm], ow, err_msg=f"order of election {e}")
+
+
 def test_batch_reports_bad_ballots():
     ctx = S.context()
     assert ctx.status() == S.OK
