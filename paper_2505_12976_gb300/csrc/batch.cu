@@ -100,7 +100,8 @@ constexpr int kTT = 64;  // tally tile: 64 x 64 counters per group, 8 x 4 per th
 // count them in 16-bit lanes (two columns per word, the row operand
 // duplicated into both halves); the groups of one tile take alternate
 // staged ballots and add their counts into d (zeroed first) with atomics,
-// so an election of one or two tiles still keeps every group busy.
+// so an election of one or two tiles still keeps every group busy (and so
+// does a last round with one or two tiles left, whatever jb.gpt is).
 // Ballots are staged `chunk` at a time as full position rows (unlisted
 // candidates at position k), so one staging serves the four tiles of a
 // round. Counters are added into d every kFlushVoters ballots. Full
@@ -121,7 +122,11 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16) | kGuard2;
   const int32_t mpad = int32_t(align_up(size_t(m), kTT));
   const int chunk = jb.chunk;  // chunk * mpad * 6 <= sizeof(BatchSmem), chunk * k <= kBT * kPrefetch (plan)
-  const int gpt = jb.gpt, tpr = kGroups / gpt, phase = g % gpt;  // tiles per round, this group's ballots
+  const int gpt = jb.gpt, tpr = kGroups / gpt;  // tiles per round
+  // a last round with fewer tiles than groups shares them out: one tile to
+  // all four groups, two tiles to two groups each
+  const int32_t rem_last = ntiles % tpr;
+  const int gpt_last = rem_last == 0 ? gpt : kGroups / (rem_last == 1 ? 1 : rem_last == 2 ? 2 : 4);
   uint32_t* dup = reinterpret_cast<uint32_t*>(sm.raw);                         // [chunk][mpad]
   uint16_t* pos = reinterpret_cast<uint16_t*>(sm.raw + size_t(chunk) * mpad * 4);  // [chunk][mpad]
   // ballot ids of a step: thread tid holds positions q0 + u * lanes of ballot
@@ -138,11 +143,12 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
       cv[u] = (have && q < k) ? __ldcg(row + q) : -1;  // L2 only: see schulze_batch_run_host
     }
   };
-  if (gpt > 1)  // the groups of a tile add into d (visible after the first barrier below)
+  if (gpt > 1 || gpt_last > 1)  // the groups of a tile add into d (visible after the first barrier below)
     for (int64_t t = tid; t < int64_t(m) * m; t += kBT) dm[t] = 0;
   for (int32_t t0 = 0; t0 < ntiles; t0 += tpr) {
-    // this group's tile (bi, bj)
-    const int32_t tt = t0 + g / gpt;
+    // this group's tile (bi, bj) and its share of the staged ballots
+    const int gr = ntiles - t0 < tpr ? gpt_last : gpt, phase = g % gr;
+    const int32_t tt = t0 + g / gr;
     int32_t bi = 0, bj = 0;
     if (tt < ntiles) {
       if (full) {
@@ -198,7 +204,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
       if (v0 + chunk < n) load_ids(v0 + chunk);  // in flight while this step counts
       __syncthreads();
       if (tt < ntiles) {
-        for (int u = phase; u < nv; u += gpt) {
+        for (int u = phase; u < nv; u += gr) {
           uint32_t a[8], b[2];
           const uint4 a0 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8]);
           const uint4 a1 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8 + 4]);
@@ -222,7 +228,7 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
               if (i < m) {
                 int32_t* dst = dm + int64_t(i) * m + j;
                 const int32_t lo = int32_t(acc[r][w] & 0xFFFFu), hi = int32_t(acc[r][w] >> 16);
-                if (gpt > 1) {
+                if (gr > 1) {
                   if (j < m && lo) atomicAdd(dst, lo);
                   if (j + 1 < m && hi) atomicAdd(dst + 1, hi);
                 } else {

@@ -26,11 +26,11 @@ def lib():
 
 
 def _mixed_elections(seed=3):
-    """Uneven elections: tiny to m = 300, n from 0 to 4000, full and top-k,
+    """Uneven elections: tiny to m = 330, n from 0 to 4000, full and top-k,
     Mallows and impartial culture, plus degenerate ones."""
     rs = np.random.Generator(np.random.PCG64(seed))
     out = []
-    sizes = [1, 2, 3, 8, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 257, 300]
+    sizes = [1, 2, 3, 8, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 257, 300, 330]
     for t, m in enumerate(sizes):
         n = int(rs.integers(1, 4000)) if t % 5 else int(rs.integers(1, 60))
         k = [m, max(0, m - 1), max(1, m // 3), 1][t % 4]
