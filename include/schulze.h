@@ -314,7 +314,7 @@ int schulze_batch_set_schedule(schulze_batch* b, int32_t tally_policy, int32_t o
 /* Elections are grouped by m into five buckets (m <= 64, 128, 256, 512,
  * 1024); the tally of an election stages `chunk` ballots per step as position
  * rows in shared memory (8, 16, 32 or 64; a power of two that fits: chunk *
- * ceil64(m) * 6 bytes within the CTA's shared memory and chunk * m <= 16384),
+ * ceil64(m) * 6 bytes within the CTA's shared memory and chunk * m <= 8192),
  * set here per bucket (EINVAL for a size that does not fit the bucket's
  * largest m). Synchronous. */
 int schulze_batch_set_bucket_chunk(schulze_batch* b, int32_t bucket, int32_t chunk);

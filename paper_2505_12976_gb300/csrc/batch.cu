@@ -50,7 +50,9 @@ inline int bucket_of(int32_t m) {
 }
 constexpr int kChunkChoices[4] = {8, 16, 32, 64};
 constexpr int kGptChoices[3] = {1, 2, 4};
-constexpr int kPrefetch = 32;  // ballot ids a thread holds for the next step
+// ballot ids a thread holds for the next step (16: the kernel then fits 128
+// registers without spilling, which outweighs the longer steps that 32 allows)
+constexpr int kPrefetch = 16;
 
 struct BatchArgs {
   const Job* jobs;

@@ -144,7 +144,7 @@ def test_batch_autotune_keeps_results_exact(tmp_path):
     assert sum("bucket<=" in ln for ln in lines) == len(used) and sum("|order|" in ln for ln in lines) == 1
     for q in used:  # every choice is a staging size that fits the bucket
         mx, ch, _ = sched1[q]
-        assert ch in (8, 16, 32, 64) and ch * (-(-mx // 64) * 64) * 6 <= 131584 and ch * mx <= 16384
+        assert ch in (8, 16, 32, 64) and ch * (-(-mx // 64) * 64) * 6 <= 131584 and ch * mx <= 8192
     tiles1 = b.bucket_tiles()
     assert all(g in (1, 2, 4) for g in tiles1)
     b2 = S.SchulzeBatch(bw.n, bw.m, bw.k)
@@ -169,7 +169,7 @@ def test_batch_every_bucket_schedule_is_exact():
     ranks = torch.from_numpy(flat).cuda()
     bucket_max = [mx for mx, _, _ in b.bucket_schedule()]
     for chunk in (8, 16, 32, 64):
-        fits = [c * (-(-mx // 64) * 64) * 6 <= 131584 and c * mx <= 16384 for mx in bucket_max for c in [chunk]]
+        fits = [c * (-(-mx // 64) * 64) * 6 <= 131584 and c * mx <= 8192 for mx in bucket_max for c in [chunk]]
         for q, ok in enumerate(fits):
             if ok:
                 b.set_bucket_chunk(q, chunk)
