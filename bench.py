@@ -778,7 +778,9 @@ def run_kernel_case(args, local):
     times and once timed; `tally_compact` does the same for the m = 4096,
     n = 20000 top-50 election (151 listed candidates: the compact form);
     `batch_sample` runs a 256-election sample of the mixed batch twice and
-    once timed. Prints the timed call's milliseconds."""
+    once timed; `features` computes the 16 per-candidate features of one
+    m = 8192, n = 20000 top-50 election of the learned workload's evaluation
+    set three times and once timed. Prints the timed call's milliseconds."""
     import torch
     import paper_2505_12976_gb300 as S
     import workloads as W
@@ -801,6 +803,13 @@ def run_kernel_case(args, local):
         r = torch.from_numpy(e.ranks).to(dev)
         d = torch.empty((e.m, e.m), dtype=torch.int32, device=dev)
         call = lambda: S.schulze_tally(r, e.m, d=d)
+        reps = 3
+    elif args.kernel_case == "features":
+        lb = W.learned_eval(E=1)
+        e = lb.election(0)
+        d = S.schulze_tally(torch.from_numpy(e.ranks).to(dev), e.m)
+        feat = torch.empty((e.m, 16), dtype=torch.float32, device=dev)
+        call = lambda: S.schulze_features(d, int(lb.n[0]), feat=feat)
         reps = 3
     else:
         bw = W.batch_mixed(E=256, seed=123)
@@ -869,7 +878,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=20, help="training epochs (learned workload)")
     ap.add_argument("--margin", action="store_true", help="margin edge weights instead of winning votes")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["closure_s32", "closure_s16", "tally_grouped", "tally_compact", "batch_sample"],
+                    choices=["closure_s32", "closure_s16", "tally_grouped", "tally_compact", "batch_sample",
+                             "features"],
                     help="run one small single-kernel case for profiling instead of the benchmark")
     ap.add_argument("--shard-voters", action="store_true",
                     help="one election, voters split over the ranks (tally + all-reduce of d; strong scaling)")

@@ -365,7 +365,9 @@ int schulze_batch_autotune(schulze_batch* b, const int32_t* ranks, const char* c
  * winning-votes edge over n; the loser filter of Sect. 4 (1 if the largest
  * incoming edge is heavier); their difference; outgoing and incoming edge
  * sums; smallest and largest margin; largest d[c][j]; the ranks of the row
- * sum and of wins - losses among the candidates (0 = best, over m-1). */
+ * sum and of wins - losses among the candidates (0 = best, over m-1). d is
+ * a tally of n ballots: its entries are counts in [0, n] (sums and ranks
+ * are exact under that bound, not for arbitrary matrices). */
 int schulze_features(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, float* feat, schulze_stream_t stream);
 
 /* score[c] = MLP(feat[c]) for N candidates (device arrays). */

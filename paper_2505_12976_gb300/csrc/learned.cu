@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -58,84 +59,176 @@ __global__ void acc_init_kernel(Acc a, int32_t m) {
   }
 }
 
-__device__ __forceinline__ int32_t warp_sum(int32_t v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
-}
-__device__ __forceinline__ long long warp_sum64(long long v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
-}
 __device__ __forceinline__ int32_t warp_max(int32_t v) {
   for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
   return v;
 }
-__device__ __forceinline__ int32_t warp_min(int32_t v) {
-  for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-  return v;
+
+// Row statistics without per-tile atomics: a CTA takes a strip of kFR rows
+// 32 s .. 32 s + 31 against the columns of one chunk (kFChunks chunks, in
+// the order of features_cta), tile by tile (kFC columns): d[i][j] and the transposed d[j][i]
+// copied into shared memory with cp.async, kFStages - 1 tiles in flight
+// while one is counted. Thread t takes row t / 8 and the eight columns
+// 4 (t % 8) .. +3 and 32 + 4 (t % 8) .. +3 of each tile (16-byte reads of
+// the row tile, one word of the transposed tile per column; both free of
+// bank conflicts), keeping its statistics in registers, its sums as 32-bit
+// partials over a tile (entries of d are counts in [0, n]) added into 64-bit
+// totals after each tile. The eight threads of a row combine them with
+// shuffles at the end and one adds them to the candidate's accumulators
+// (ties follow from wins and losses). Tiles holding no diagonal entry and
+// no padding skip the per-entry checks. Every entry is read twice (as d[i][j]
+// for row i and as d[i][j] for row j's column).
+constexpr int kFR = 32, kFC = 64, kFChunks = 8;
+constexpr int kFXL = kFC + 4;  // row tile stride: 16-byte aligned rows
+constexpr int kFYL = kFR + 1;  // transposed tile stride
+
+__device__ __forceinline__ void cp_async4(int32_t* dst, const int32_t* src, bool ok) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(int32_t* dst, const int32_t* src, bool ok) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Row statistics without per-tile atomics: CTA (s, ch) takes the strip of
-// kFR rows 32 s .. 32 s + 31 against the columns of chunk ch (kFChunks
-// chunks), tile by tile (kFC columns): d[i][j] and the transposed d[j][i]
-// staged in shared memory, thread t accumulating row t / 8's statistics over
-// every eighth column of each tile in registers. The eight threads of a row
-// combine them with shuffles at the end and one adds them to the
-// candidate's accumulators (ties follow from wins and losses). Every entry
-// is read twice (as d[i][j] for row i and as d[i][j] for row j's column).
-constexpr int kFR = 32, kFC = 64, kFChunks = 8;
+// Tiles in flight per CTA: kFStages buffers of both tiles in dynamic shared
+// memory, kFStages - 1 tiles copied ahead of the one being counted.
+#ifndef SCHULZE_FEAT_STAGES
+#define SCHULZE_FEAT_STAGES 3
+#endif
+constexpr int kFStages = SCHULZE_FEAT_STAGES;
+constexpr int kFStageWords = kFR * kFXL + kFC * kFYL;
+constexpr size_t kFSmem = size_t(kFStages) * kFStageWords * 4;
 
-__global__ void __launch_bounds__(256) features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
-  __shared__ int32_t x[kFR][kFC + 1];  // d[i][j]
-  __shared__ int32_t y[kFC][kFR + 1];  // d[j][i]
-  const int32_t I = blockIdx.x * kFR;
+// kVec: rows of d start on 16-byte boundaries (m % 4 == 0, d aligned), so
+// the copies move four entries at a time. kWide: n >= 2^29, where eight
+// entries of a tile could overflow a 32-bit partial sum.
+// The CTA's (strip, chunk) from its place in the launch: strips are grouped
+// by the chunk that holds their rows as columns (2 per strips a group), and
+// the CTAs of (row group g, chunk c) follow right after those of (c, g), so
+// that the transposed tiles one set reads were just read by the other and
+// are still in L2.
+__device__ void features_cta(int32_t nstrips, int32_t per, int32_t* strip, int32_t* chunk) {
+  const int32_t S = 2 * per;
+  int32_t L = blockIdx.x;
+  for (int32_t g = 0; g < kFChunks; ++g)
+    for (int32_t c = g; c < kFChunks; ++c)
+      for (int side = 0; side < (c == g ? 1 : 2); ++side) {
+        const int32_t rg = side ? c : g, ch = side ? g : c;
+        const int32_t cnt = max(0, min(S, nstrips - rg * S));
+        if (L < cnt) {
+          *strip = rg * S + L, *chunk = ch;
+          return;
+        }
+        L -= cnt;
+      }
+  *strip = nstrips, *chunk = 0;  // not reached: the grid has nstrips * kFChunks CTAs
+}
+
+template <bool kVec, bool kWide>
+__global__ void __launch_bounds__(256, 4) features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
+  using Part = typename std::conditional<kWide, unsigned long long, uint32_t>::type;
+  extern __shared__ __align__(16) int32_t fsm[];
+  // stage b: x = d[i][j] (kFR rows of kFXL), then y = d[j][i] (kFC rows: of
+  // kFYL words, or with kVec of 32 words whose 16-byte quads are permuted by
+  // the row, so that both the 16-byte copies and the column reads below
+  // avoid bank conflicts)
+  auto X = [&](int b) { return reinterpret_cast<int32_t(*)[kFXL]>(fsm + b * kFStageWords); };
+  auto Yp = [&](int b) { return fsm + b * kFStageWords + kFR * kFXL; };
+  auto yat = [&](int b, int c, int rr) -> int32_t* {  // &y[c][rr]
+    return kVec ? Yp(b) + c * 32 + ((((rr >> 2) ^ ((c >> 2) & 7)) << 2) | (rr & 3)) : Yp(b) + c * kFYL + rr;
+  };
+  __shared__ int32_t s_place[2];
   const int32_t ntile = (m + kFC - 1) / kFC, per = (ntile + kFChunks - 1) / kFChunks;
-  const int32_t t0 = blockIdx.y * per, t1 = min(ntile, t0 + per);
+  if (threadIdx.x == 0) features_cta((m + kFR - 1) / kFR, per, &s_place[0], &s_place[1]);
+  __syncthreads();
+  const int32_t I = s_place[0] * kFR;
+  const int32_t t0 = s_place[1] * per, t1 = min(ntile, t0 + per);
+  if (I >= m || t0 >= t1) return;
   const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
   const int32_t i = I + r;
   int32_t win = 0, loss = 0, mx_wo = 0, mx_wi = 0, mx_d = 0, mn_mg = INT32_MAX, mx_mg = INT32_MIN;
-  long long s_row = 0, s_col = 0, s_wo = 0, s_wi = 0;
-  // the next tile's entries are loaded into registers while one is counted
-  constexpr int kPer = kFR * kFC / 256;  // entries of each tile per thread
-  int32_t nx[kPer], ny[kPer];
-  auto fetch = [&](int32_t J) {
+  unsigned long long s_row = 0, s_col = 0, s_wo = 0, s_wi = 0;
+  auto issue = [&](int32_t J, int b) {
+    if (kVec) {
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      const int rr = e / kFC, cc = e % kFC;  // x: row rr, column cc
-      nx[u] = (J < m && I + rr < m && J + cc < m) ? d[int64_t(I + rr) * m + J + cc] : 0;
-      const int yr = e / kFR, yc = e % kFR;  // y: row yr (candidate J + yr), column yc (candidate I + yc)
-      ny[u] = (J < m && J + yr < m && I + yc < m) ? d[int64_t(J + yr) * m + I + yc] : 0;
-    }
-  };
-  fetch(t0 * kFC);
-  for (int32_t tile = t0; tile < t1; ++tile) {
-    const int32_t J = tile * kFC;
-    __syncthreads();  // the previous tile is read
+      for (int u = 0; u < 2; ++u) {  // x: 32 rows x 16 quads
+        const int e = threadIdx.x + 256 * u, rr = e >> 4, cc = (e & 15) * 4;
+        const bool ok = I + rr < m && J + cc < m;
+        cp_async16(&X(b)[rr][cc], ok ? d + int64_t(I + rr) * m + J + cc : d, ok);
+      }
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      x[e / kFC][e % kFC] = nx[u];
-      y[e / kFR][e % kFR] = ny[u];
-    }
-    __syncthreads();
-    if (tile + 1 < t1) fetch(J + kFC);
-    if (i < m) {
+      for (int u = 0; u < 2; ++u) {  // y: 64 rows (candidates J + yr) x 8 quads (I + 4 qd ..)
+        const int e = threadIdx.x + 256 * u, yr = e >> 3, qd = e & 7;
+        const bool ok = J + yr < m && I + 4 * qd < m;
+        cp_async16(yat(b, yr, 4 * qd), ok ? d + int64_t(J + yr) * m + I + 4 * qd : d, ok);
+      }
+    } else {
 #pragma unroll
-      for (int u = 0; u < kFC / 8; ++u) {
-        const int c = q + 8 * u;
-        const int32_t j = J + c;
-        if (j >= m || j == i) continue;
-        const int32_t dij = x[r][c], dji = y[c][r];
-        const bool w = dij > dji, l = dji > dij;
-        win += w, loss += l;
-        s_row += dij, s_col += dji;
-        const int32_t wo = w ? dij : 0, wi = l ? dji : 0;
-        s_wo += wo, s_wi += wi;
-        mx_wo = max(mx_wo, wo), mx_wi = max(mx_wi, wi), mx_d = max(mx_d, dij);
-        mn_mg = min(mn_mg, dij - dji), mx_mg = max(mx_mg, dij - dji);
+      for (int u = 0; u < 8; ++u) {  // x: 32 rows x 64 columns
+        const int e = threadIdx.x + 256 * u, rr = e >> 6, cc = e & 63;
+        const bool ok = I + rr < m && J + cc < m;
+        cp_async4(&X(b)[rr][cc], ok ? d + int64_t(I + rr) * m + J + cc : d, ok);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {  // y: 64 rows (candidates J + yr) x 32 columns (I + yc)
+        const int e = threadIdx.x + 256 * u, yr = e >> 5, yc = e & 31;
+        const bool ok = J + yr < m && I + yc < m;
+        cp_async4(yat(b, yr, yc), ok ? d + int64_t(J + yr) * m + I + yc : d, ok);
       }
     }
+    cp_async_commit();
+  };
+  Part p_row = 0, p_col = 0, p_wo = 0, p_wi = 0;
+  auto count = [&](int32_t a_, int32_t b_) {
+    const int32_t diff = a_ - b_;
+    p_row += Part(a_), p_col += Part(b_);
+    mx_d = max(mx_d, a_);
+    mn_mg = min(mn_mg, diff), mx_mg = max(mx_mg, diff);
+    const bool w = diff > 0, l = diff < 0;
+    win += w, loss += l;
+    const int32_t wo = w ? a_ : 0, wi = l ? b_ : 0;
+    p_wo += Part(wo), p_wi += Part(wi);
+    mx_wo = max(mx_wo, wo), mx_wi = max(mx_wi, wi);
+  };
+  for (int st = 0; st < kFStages - 1; ++st) {
+    if (t0 + st < t1) issue((t0 + st) * kFC, st);
+    else cp_async_commit();  // empty groups keep the wait below uniform
+  }
+  for (int32_t tile = t0; tile < t1; ++tile) {
+    const int32_t J = tile * kFC;
+    const int kk = tile - t0, b = kk % kFStages;
+    cp_async_wait<kFStages - 2>();  // this thread's copies of this tile have landed
+    __syncthreads();                // everyone's have, and the previous tile is counted
+    if (tile + kFStages - 1 < t1) issue((tile + kFStages - 1) * kFC, (kk + kFStages - 1) % kFStages);
+    else cp_async_commit();
+    if (i >= m) continue;
+    int32_t dij[8], dji[8];
+    {
+      const int4 lo = *reinterpret_cast<const int4*>(&X(b)[r][4 * q]);
+      const int4 hi = *reinterpret_cast<const int4*>(&X(b)[r][32 + 4 * q]);
+      dij[0] = lo.x, dij[1] = lo.y, dij[2] = lo.z, dij[3] = lo.w;
+      dij[4] = hi.x, dij[5] = hi.y, dij[6] = hi.z, dij[7] = hi.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dji[k] = *yat(b, (k >> 2) * 32 + 4 * q + (k & 3), r);
+    p_row = p_col = p_wo = p_wi = 0;
+    if (J + kFC <= m && (J >= I + kFR || I >= J + kFC)) {  // no diagonal entry, no padding
+#pragma unroll
+      for (int k = 0; k < 8; ++k) count(dij[k], dji[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int32_t j = J + (k >> 2) * 32 + 4 * q + (k & 3);
+        if (j < m && j != i) count(dij[k], dji[k]);
+      }
+    }
+    s_row += p_row, s_col += p_col, s_wo += p_wo, s_wi += p_wi;
   }
 #pragma unroll
   for (int o = 1; o <= 4; o <<= 1) {
@@ -154,10 +247,10 @@ __global__ void __launch_bounds__(256) features_pass_kernel(const int32_t* __res
   if (q == 0 && i < m) {
     if (win) atomicAdd(&a.wins[i], win);
     if (loss) atomicAdd(&a.losses[i], loss);
-    if (s_row) atomicAdd(&a.rowsum[i], (unsigned long long)s_row);
-    if (s_col) atomicAdd(&a.colsum[i], (unsigned long long)s_col);
-    if (s_wo) atomicAdd(&a.sumw_out[i], (unsigned long long)s_wo);
-    if (s_wi) atomicAdd(&a.sumw_in[i], (unsigned long long)s_wi);
+    if (s_row) atomicAdd(&a.rowsum[i], s_row);
+    if (s_col) atomicAdd(&a.colsum[i], s_col);
+    if (s_wo) atomicAdd(&a.sumw_out[i], s_wo);
+    if (s_wi) atomicAdd(&a.sumw_in[i], s_wi);
     if (mx_wo) atomicMax(&a.maxw_out[i], mx_wo);
     if (mx_wi) atomicMax(&a.maxw_in[i], mx_wi);
     if (mx_d) atomicMax(&a.max_drow[i], mx_d);
@@ -168,58 +261,81 @@ __global__ void __launch_bounds__(256) features_pass_kernel(const int32_t* __res
 
 // f[c][0..13] from the accumulators; ranks (14, 15) are counted afterwards.
 __global__ void features_finalize_kernel(Acc a, int32_t m, int64_t n, float* __restrict__ feat) {
+  const double nn = double(n > 0 ? n : 1), mm = double(m > 1 ? m - 1 : 1);
+  const double inv_m = 1.0 / mm, inv_n = 1.0 / nn, inv_nm = 1.0 / (nn * mm);  // FP64 divides are slow
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
     float* f = feat + int64_t(c) * kNF;
-    for (int q = 0; q < kNF; ++q) f[q] = 0.f;
-    if (m < 2) continue;
-    const double nn = double(n > 0 ? n : 1), mm = double(m - 1);
-    f[0] = float(double(a.wins[c]) / mm);
-    f[1] = float(double(a.losses[c]) / mm);
-    f[2] = float(double(int64_t(m - 1) - a.wins[c] - a.losses[c]) / mm);  // every other candidate: win, loss or tie
-    f[3] = float(double(a.rowsum[c]) / (nn * mm));
-    f[4] = float(double(a.colsum[c]) / (nn * mm));
-    f[5] = float(double(a.maxw_out[c]) / nn);
-    f[6] = float(double(a.maxw_in[c]) / nn);
-    f[7] = a.maxw_in[c] > a.maxw_out[c] ? 1.f : 0.f;
-    f[8] = float(double(a.maxw_out[c] - a.maxw_in[c]) / nn);
-    f[9] = float(double(a.sumw_out[c]) / (nn * mm));
-    f[10] = float(double(a.sumw_in[c]) / (nn * mm));
-    f[11] = float(double(a.min_margin[c]) / nn);
-    f[12] = float(double(a.max_margin[c]) / nn);
-    f[13] = float(double(a.max_drow[c]) / nn);
+    if (m < 2) {
+      for (int q = 0; q < kNF; ++q) f[q] = 0.f;
+      continue;
+    }
+    const int32_t wn = a.wins[c], ls = a.losses[c], mo = a.maxw_out[c], mi = a.maxw_in[c];
+    f[0] = float(double(wn) * inv_m);
+    f[1] = float(double(ls) * inv_m);
+    f[2] = float(double(int64_t(m - 1) - wn - ls) * inv_m);  // every other candidate: win, loss or tie
+    f[3] = float(double(a.rowsum[c]) * inv_nm);
+    f[4] = float(double(a.colsum[c]) * inv_nm);
+    f[5] = float(double(mo) * inv_n);
+    f[6] = float(double(mi) * inv_n);
+    f[7] = mi > mo ? 1.f : 0.f;
+    f[8] = float(double(mo - mi) * inv_n);
+    f[9] = float(double(a.sumw_out[c]) * inv_nm);
+    f[10] = float(double(a.sumw_in[c]) * inv_nm);
+    f[11] = float(double(a.min_margin[c]) * inv_n);
+    f[12] = float(double(a.max_margin[c]) * inv_n);
+    f[13] = float(double(a.max_drow[c]) * inv_n);
+    f[14] = f[15] = 0.f;  // the ranks, filled in afterwards
   }
 }
 
 // f[c][14] = #{j: rowsum[j] > rowsum[c]} / (m-1); f[c][15] likewise for
-// wins - losses. 2D grid: (chunks of c, chunks of j); counts added atomically.
-__global__ void __launch_bounds__(256) features_rank_kernel(Acc a, int32_t m, int32_t* __restrict__ cnt14,
-                                                            int32_t* __restrict__ cnt15) {
-  __shared__ unsigned long long rs[256];
-  __shared__ int32_t cp[256];
-  const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int32_t j = blockIdx.y * 256 + threadIdx.x;
-  rs[threadIdx.x] = j < m ? a.rowsum[j] : 0ull;
-  cp[threadIdx.x] = j < m ? a.wins[j] - a.losses[j] : INT32_MIN;
+// wins - losses. CTA (s, cb, z) ranks by the row sums (z = 0) or by wins -
+// losses (z = 1): it maps the keys of candidates kRankChunk s .. + kRankChunk
+// - 1 to unsigned integers in the same order (row sum + 1; wins - losses +
+// 2^31), all above the padding value 0, sorts them into descending order with
+// a bitonic network in shared memory, then counts for each candidate c of
+// block cb the keys of the chunk above its own by binary search; the counts
+// of the chunks are added atomically.
+constexpr int kRankChunk = 1024;
+__global__ void __launch_bounds__(kRankChunk / 2) features_rank_kernel(Acc a, int32_t m, int32_t* __restrict__ cnt14,
+                                                                       int32_t* __restrict__ cnt15) {
+  __shared__ unsigned long long ks[kRankChunk];
+  const bool by_row = blockIdx.z == 0;
+  auto key = [&](int32_t c) -> unsigned long long {
+    return by_row ? a.rowsum[c] + 1ull
+                  : (unsigned long long)(int64_t(a.wins[c]) - a.losses[c] + (int64_t(1) << 31));
+  };
+  const int32_t j0 = blockIdx.x * kRankChunk;
+  for (int t = threadIdx.x; t < kRankChunk; t += blockDim.x) ks[t] = j0 + t < m ? key(j0 + t) : 0ull;
   __syncthreads();
-  if (c >= m) return;
-  const unsigned long long mine = a.rowsum[c];
-  const int32_t mycp = a.wins[c] - a.losses[c];
-  const int lim = min(256, m - int32_t(blockIdx.y) * 256);
-  int32_t k14 = 0, k15 = 0;
-  for (int t = 0; t < lim; ++t) {
-    k14 += rs[t] > mine;
-    k15 += cp[t] > mycp;
+  for (int k = 2; k <= kRankChunk; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int t = threadIdx.x, i = 2 * t - (t & (j - 1)), l = i + j;  // i has bit j clear
+      const unsigned long long x = ks[i], y = ks[l];
+      if ((x < y) == ((i & k) == 0)) ks[i] = y, ks[l] = x;  // descending where bit k of i is clear
+      __syncthreads();
+    }
+  int32_t* cnt = by_row ? cnt14 : cnt15;
+  const int32_t c1 = min(m, int32_t(blockIdx.y + 1) * kRankChunk);
+  for (int32_t c = blockIdx.y * kRankChunk + threadIdx.x; c < c1; c += blockDim.x) {
+    const unsigned long long x = key(c);
+    int lo = 0, hi = kRankChunk;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ks[mid] > x) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo) atomicAdd(&cnt[c], lo);
   }
-  if (k14) atomicAdd(&cnt14[c], k14);
-  if (k15) atomicAdd(&cnt15[c], k15);
 }
 
 __global__ void features_rank_finalize_kernel(const int32_t* __restrict__ cnt14, const int32_t* __restrict__ cnt15,
                                               int32_t m, float* __restrict__ feat) {
+  const double inv_m = 1.0 / double(m > 1 ? m - 1 : 1);
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
     if (m < 2) continue;
-    feat[int64_t(c) * kNF + 14] = float(double(cnt14[c]) / double(m - 1));
-    feat[int64_t(c) * kNF + 15] = float(double(cnt15[c]) / double(m - 1));
+    feat[int64_t(c) * kNF + 14] = float(double(cnt14[c]) * inv_m);
+    feat[int64_t(c) * kNF + 15] = float(double(cnt15[c]) * inv_m);
   }
 }
 
@@ -778,16 +894,22 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
   {
     Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
     acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m);
-    features_pass_kernel<<<dim3(unsigned((m + kFR - 1) / kFR), kFChunks), 256, 0, stream>>>(d, m, w.acc);
-    features_finalize_kernel<<<g, 256, 0, stream>>>(w.acc, m, n, feat);
+    const unsigned grid = unsigned((m + kFR - 1) / kFR) * kFChunks;
+    const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(d) % 16 == 0, wide = n >= (int64_t(1) << 29);
+    auto kern = vec ? (wide ? features_pass_kernel<true, true> : features_pass_kernel<true, false>)
+                    : (wide ? features_pass_kernel<false, true> : features_pass_kernel<false, false>);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
+    kern<<<grid, 256, kFSmem, stream>>>(d, m, w.acc);
+    features_finalize_kernel<<<(m + 63) / 64, 64, 0, stream>>>(w.acc, m, n, feat);
   }
   if (cudaMemsetAsync(w.cnt14, 0, size_t(m) * 4, stream) != cudaSuccess ||
       cudaMemsetAsync(w.cnt15, 0, size_t(m) * 4, stream) != cudaSuccess)
     return SCHULZE_ECUDA;
   {
     Launch L(ctx, stream, "learn_feature_ranks", double(m) * 16.0);
-    features_rank_kernel<<<dim3((m + 255) / 256, (m + 255) / 256), 256, 0, stream>>>(w.acc, m, w.cnt14, w.cnt15);
-    features_rank_finalize_kernel<<<g, 256, 0, stream>>>(w.cnt14, w.cnt15, m, feat);
+    const unsigned nch = unsigned((m + kRankChunk - 1) / kRankChunk);
+    features_rank_kernel<<<dim3(nch, nch, 2), kRankChunk / 2, 0, stream>>>(w.acc, m, w.cnt14, w.cnt15);
+    features_rank_finalize_kernel<<<(m + 63) / 64, 64, 0, stream>>>(w.cnt14, w.cnt15, m, feat);
   }
   return check_launch();
 }

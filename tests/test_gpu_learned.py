@@ -42,12 +42,12 @@ def _elections():
     out.append((np.array([[0]], np.int32), 1))
     out.append((W.impartial(3, 7, 2, 2), 2))
     for t, (m, n, k, phi) in enumerate([(40, 500, 40, 0.9), (150, 2000, 12, 0.85), (300, 900, 30, 1.0),
-                                        (777, 3000, 25, 0.95), (64, 1000, 64, 0.8)]):
+                                        (777, 3000, 25, 0.95), (64, 1000, 64, 0.8), (2052, 2500, 30, 0.9)]):
         out.append((W.mallows(50 + t, n, m, k, phi, W.permutation(50 + t, m)), m))
     return out
 
 
-@pytest.mark.parametrize("case", range(10))
+@pytest.mark.parametrize("case", range(11))
 def test_features_match_oracle(case):
     r, m = _elections()[case]
     d = oracle.tally(r, m)
