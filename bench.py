@@ -206,6 +206,45 @@ def run_learned(args, world, rank, local):
     E = len(rows)
     avg = lambda key: sum(x[key] for x in rows) / E
     closure_ms, mlp_ms, cop_ms = avg("closure_ms"), avg("mlp_ms"), avg("copeland_ms")
+    # per-kernel durations of the MLP path on the library's stream, from a
+    # second, profiled pass over 16 of the evaluation elections: the features
+    # pass dominates (algorithmic bytes: one read of d, m^2 4 B); the
+    # certification's work is its widest-path rounds over the warm square
+    # (two int32 copies of it, read once per round)
+    sample = []
+    for e in range(min(16, ev.E)):
+        sample.append((S.schulze_tally(torch.from_numpy(ev.election(e).ranks).to(dev), int(ev.m[e]), ctx=ctx),
+                       int(ev.n[e])))
+    warm = [int(((d > d.t()).any(dim=1)).sum().item()) for d, _ in sample]
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    rounds = [S.schulze_winners_fast(d, nn, trainer.params, top=4, ctx=ctx)[1][3] for d, nn in sample]
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    del sample
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    mm4 = float(ev.m[0]) * float(ev.m[0]) * 4
+    fst = prof.get("learn_features")
+    roof = None
+    if fst:
+        per = fst["ms"] / max(1, fst["launches"])
+        roof = {"bound": "hbm", "kernel": "learn_features (features pass)", "achieved": mm4 / (per * 1e-3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "frac": mm4 / (per * 1e-3) / 1e9 / hbm_peak,
+                "traffic": profiled_traffic().get(("learn_features", "learned")) if not (args.m or args.n) else None,
+                "bytes_per_launch": mm4, "work": "d read once (m^2 4 B; each entry is read twice, the second "
+                "time mostly from L2)", "per_launch_ms": per, "launches": fst["launches"],
+                "peak_source": hbm_src}
+    cst = prof.get("certify_paths")
+    certify = None
+    if cst:
+        cert_bytes = sum(r * 2.0 * 4.0 * w * w for r, w in zip(rounds, warm))
+        certify = {"per_launch_ms": cst["ms"] / max(1, cst["launches"]), "launches": cst["launches"],
+                   "rounds_mean": sum(rounds) / len(rounds), "warm_mean": sum(warm) / len(warm),
+                   "bytes_per_round": "2 x 4 B x warm^2 (the warm square and its transpose)",
+                   "achieved_GBps": cert_bytes / (cst["ms"] * 1e-3) / 1e9,
+                   "note": "one 1024-thread CTA; the warm square stays in L1/L2, so the rounds are latency-bound"}
+    breakdown = {kname: {"ms_per_election": st["ms"] / max(1, len(rounds)), "launches": st["launches"]}
+                 for kname, st in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     line = {"metric": METRIC + " (learned-proposal workload: elections/sec of exact winner determination)",
             "value": 1e3 / mlp_ms, "unit": "elections/s", "n_gpus": 1, "steps": E, "warmup": 1,
             "ms_per_step": mlp_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -227,7 +266,7 @@ def run_learned(args, world, rank, local):
             "dense_profile": dense_row,
             "train": {"seconds": t_train, "data_seconds": t_data, "loss_first_epoch": hist[0],
                       "loss_last_epoch": hist[-1]},
-            "roofline": None, "cpu_baseline": None,
+            "roofline": roof, "certify": certify, "kernels": breakdown, "cpu_baseline": None,
             "e2e": None, "e2e_note": "timed from a device-resident tally; no host buffers on this path",
             "device_status": ctx.status(), "clocks": clock_info}
     print(json.dumps(line), flush=True)

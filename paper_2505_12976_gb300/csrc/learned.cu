@@ -892,14 +892,20 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
                   cudaStream_t stream) {
   const int g = std::max(1, std::min((m + 255) / 256, 1024));
   {
-    Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
+    Launch L(ctx, stream, "learn_features_init", double(m) * 64.0);
     acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m);
+  }
+  {
+    Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
     const unsigned grid = unsigned((m + kFR - 1) / kFR) * kFChunks;
     const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(d) % 16 == 0, wide = n >= (int64_t(1) << 29);
     auto kern = vec ? (wide ? features_pass_kernel<true, true> : features_pass_kernel<true, false>)
                     : (wide ? features_pass_kernel<false, true> : features_pass_kernel<false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
     kern<<<grid, 256, kFSmem, stream>>>(d, m, w.acc);
+  }
+  {
+    Launch L(ctx, stream, "learn_features_finalize", double(m) * kNF * 4.0);
     features_finalize_kernel<<<(m + 63) / 64, 64, 0, stream>>>(w.acc, m, n, feat);
   }
   if (cudaMemsetAsync(w.cnt14, 0, size_t(m) * 4, stream) != cudaSuccess ||
