@@ -105,9 +105,6 @@ constexpr int kFStages = SCHULZE_FEAT_STAGES;
 constexpr int kFStageWords = kFR * kFXL + kFC * kFYL;
 constexpr size_t kFSmem = size_t(kFStages) * kFStageWords * 4;
 
-// kVec: rows of d start on 16-byte boundaries (m % 4 == 0, d aligned), so
-// the copies move four entries at a time. kWide: n >= 2^29, where eight
-// entries of a tile could overflow a 32-bit partial sum.
 // The CTA's (strip, chunk) from its place in the launch: strips are grouped
 // by the chunk that holds their rows as columns (2 per strips a group), and
 // the CTAs of (row group g, chunk c) follow right after those of (c, g), so
@@ -130,9 +127,33 @@ __device__ void features_cta(int32_t nstrips, int32_t per, int32_t* strip, int32
   *strip = nstrips, *chunk = 0;  // not reached: the grid has nstrips * kFChunks CTAs
 }
 
-template <bool kVec, bool kWide>
+__device__ __forceinline__ uint32_t prmt(uint32_t x, uint32_t y, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(y), "r"(sel));
+  return r;
+}
+
+// Feature statistics modes, by the ballot count n (entries of d lie in [0, n]):
+// kFPacked (n <= 32766): tiles without diagonal entries or padding are
+//   counted two entries per instruction, as 16-bit lanes. With a guard bit
+//   set in each lane, (a | G) - b holds 2^15 + a - b per lane without a
+//   borrow across lanes (a, b < 2^15): its bit 15 is set iff a >= b, and the
+//   biased margins keep their order for unsigned 16-bit min / max. Masks of
+//   the guard bits count wins and losses, and lane sums (two-lane dot
+//   products with weights 1, 1) add entries and masked entries into 32-bit
+//   partials; a mask widened from a lane's sign bit (prmt) selects the
+//   winning edges. Biased lanes lie in [2, 2^16 - 2], so the initial values
+//   2^16 - 1 (minimum) and 0 (maximum) mark "no entry".
+// kFNarrow (n < 2^29): 32-bit partial sums per tile, one entry at a time.
+// kFWide: 64-bit sums per entry (eight entries of a tile could overflow a
+//   32-bit partial).
+// kVec: rows of d start on 16-byte boundaries (m % 4 == 0, d aligned), so
+// the copies move four entries at a time.
+constexpr int kFPacked = 0, kFNarrow = 1, kFWide = 2;
+
+template <bool kVec, int kMode>
 __global__ void __launch_bounds__(256, 4) features_pass_kernel(const int32_t* __restrict__ d, int32_t m, Acc a) {
-  using Part = typename std::conditional<kWide, unsigned long long, uint32_t>::type;
+  using Part = typename std::conditional<kMode == kFWide, unsigned long long, uint32_t>::type;
   extern __shared__ __align__(16) int32_t fsm[];
   // stage b: x = d[i][j] (kFR rows of kFXL), then y = d[j][i] (kFC rows: of
   // kFYL words, or with kVec of 32 words whose 16-byte quads are permuted by
@@ -185,6 +206,10 @@ __global__ void __launch_bounds__(256, 4) features_pass_kernel(const int32_t* __
     cp_async_commit();
   };
   Part p_row = 0, p_col = 0, p_wo = 0, p_wi = 0;
+  // packed lanes (kFPacked): biased margin min / max, largest entry, largest
+  // winning edge out / in, and wins / losses counted in units of 2^15
+  constexpr uint32_t G = 0x80008000u;
+  uint32_t mn2 = 0xFFFFFFFFu, mx2 = 0u, mxd2 = 0u, mxwo2 = 0u, mxwi2 = 0u, wacc = 0u, lacc = 0u;
   auto count = [&](int32_t a_, int32_t b_) {
     const int32_t diff = a_ - b_;
     p_row += Part(a_), p_col += Part(b_);
@@ -219,8 +244,30 @@ __global__ void __launch_bounds__(256, 4) features_pass_kernel(const int32_t* __
     for (int k = 0; k < 8; ++k) dji[k] = *yat(b, (k >> 2) * 32 + 4 * q + (k & 3), r);
     p_row = p_col = p_wo = p_wi = 0;
     if (J + kFC <= m && (J >= I + kFR || I >= J + kFC)) {  // no diagonal entry, no padding
+      if (kMode == kFPacked) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) count(dij[k], dji[k]);
+        for (int k = 0; k < 8; k += 4) {  // two lane pairs at a time (three-input min / max)
+          uint32_t av[2], bv[2], dA[2], wo[2], wi[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            av[h] = prmt(uint32_t(dij[k + 2 * h]), uint32_t(dij[k + 2 * h + 1]), 0x5410u);  // d[i][j], d[i][j+1]
+            bv[h] = prmt(uint32_t(dji[k + 2 * h]), uint32_t(dji[k + 2 * h + 1]), 0x5410u);  // d[j][i], d[j+1][i]
+            dA[h] = (av[h] | G) - bv[h];                    // 2^15 + a - b per lane
+            const uint32_t dB = (bv[h] | G) - av[h];        // 2^15 + b - a
+            const uint32_t wb = ~dB & G, lb = ~dA[h] & G;  // a > b, a < b
+            wacc = __dp2a_lo(wb, 0x0101u, wacc), lacc = __dp2a_lo(lb, 0x0101u, lacc);
+            wo[h] = av[h] & prmt(wb, 0u, 0xBB99u), wi[h] = bv[h] & prmt(lb, 0u, 0xBB99u);
+            p_row = __dp2a_lo(av[h], 0x0101u, p_row), p_col = __dp2a_lo(bv[h], 0x0101u, p_col);
+            p_wo = __dp2a_lo(wo[h], 0x0101u, p_wo), p_wi = __dp2a_lo(wi[h], 0x0101u, p_wi);
+          }
+          mn2 = __vimin3_u16x2(mn2, dA[0], dA[1]), mx2 = __vimax3_u16x2(mx2, dA[0], dA[1]);
+          mxd2 = __vimax3_u16x2(mxd2, av[0], av[1]);
+          mxwo2 = __vimax3_u16x2(mxwo2, wo[0], wo[1]), mxwi2 = __vimax3_u16x2(mxwi2, wi[0], wi[1]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) count(dij[k], dji[k]);
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -229,6 +276,16 @@ __global__ void __launch_bounds__(256, 4) features_pass_kernel(const int32_t* __
       }
     }
     s_row += p_row, s_col += p_col, s_wo += p_wo, s_wi += p_wi;
+  }
+  if (kMode == kFPacked) {  // fold the lanes into the per-entry statistics
+    win += int32_t(wacc >> 15), loss += int32_t(lacc >> 15);
+    const int32_t mnb = min(int32_t(mn2 & 0xFFFFu), int32_t(mn2 >> 16));
+    const int32_t mxb = max(int32_t(mx2 & 0xFFFFu), int32_t(mx2 >> 16));
+    if (mnb != 0xFFFF) mn_mg = min(mn_mg, mnb - 0x8000);
+    if (mxb != 0) mx_mg = max(mx_mg, mxb - 0x8000);
+    mx_d = max(mx_d, max(int32_t(mxd2 & 0xFFFFu), int32_t(mxd2 >> 16)));
+    mx_wo = max(mx_wo, max(int32_t(mxwo2 & 0xFFFFu), int32_t(mxwo2 >> 16)));
+    mx_wi = max(mx_wi, max(int32_t(mxwi2 & 0xFFFFu), int32_t(mxwi2 >> 16)));
   }
 #pragma unroll
   for (int o = 1; o <= 4; o <<= 1) {
@@ -898,9 +955,14 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
   {
     Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
     const unsigned grid = unsigned((m + kFR - 1) / kFR) * kFChunks;
-    const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(d) % 16 == 0, wide = n >= (int64_t(1) << 29);
-    auto kern = vec ? (wide ? features_pass_kernel<true, true> : features_pass_kernel<true, false>)
-                    : (wide ? features_pass_kernel<false, true> : features_pass_kernel<false, false>);
+    const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(d) % 16 == 0;
+    const int mode = n <= 32766 ? kFPacked : n < (int64_t(1) << 29) ? kFNarrow : kFWide;
+    auto kern = vec ? (mode == kFPacked   ? features_pass_kernel<true, kFPacked>
+                       : mode == kFNarrow ? features_pass_kernel<true, kFNarrow>
+                                          : features_pass_kernel<true, kFWide>)
+                    : (mode == kFPacked   ? features_pass_kernel<false, kFPacked>
+                       : mode == kFNarrow ? features_pass_kernel<false, kFNarrow>
+                                          : features_pass_kernel<false, kFWide>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
     kern<<<grid, 256, kFSmem, stream>>>(d, m, w.acc);
   }

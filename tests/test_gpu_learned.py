@@ -55,6 +55,21 @@ def test_features_match_oracle(case):
     np.testing.assert_allclose(f.cpu().numpy(), M.features(d, r.shape[0]), rtol=1e-6, atol=1e-7)
 
 
+@pytest.mark.parametrize("m", [300, 301])
+@pytest.mark.parametrize("scale", [1, 20, 1 << 19])
+def test_features_every_count_width_matches_oracle(m, scale):
+    """The features pass counts two entries per instruction (16-bit lanes)
+    for n <= 32766, one at a time with 32-bit partial sums below 2^29 and
+    with 64-bit sums above; a tally scaled by `scale` (with n scaled alike,
+    so entries stay in [0, n]) takes each of the three, with rows of d
+    16-byte aligned (m = 300) or not (m = 301)."""
+    r = W.mallows(77, 1100, m, 30, 0.9, W.permutation(77, m))
+    d = oracle.tally(r, m).astype(np.int64) * scale
+    n = r.shape[0] * scale
+    f = S.schulze_features(cu(d), n)
+    np.testing.assert_allclose(f.cpu().numpy(), M.features(d, n), rtol=1e-6, atol=1e-7)
+
+
 def test_mlp_forward_matches_oracle():
     rs = np.random.Generator(np.random.PCG64(1))
     theta = W.mlp_init(3)
