@@ -96,6 +96,7 @@ union BatchSmem {
 // ------------------------------------------------------------- tally
 
 constexpr int kTT = 64;  // tally tile: 64 x 64 counters per group, 8 x 4 per thread
+constexpr int kDiagBlocks = 72;  // 8 x 4 blocks of a diagonal tile on or above the diagonal
 
 // The election's d, tile by tile: the four 128-thread groups take tiles of
 // 64 x 64 entries, jb.gpt groups per tile (4 / gpt tiles per round), and
@@ -116,9 +117,15 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   const int32_t n = jb.n, m = jb.m, k = jb.k;
   const bool full = k >= m - 1;
   const int32_t nbt = (m + kTT - 1) / kTT;
-  const int32_t ntiles = full ? nbt * (nbt + 1) / 2 : nbt * nbt;
   const int tid = threadIdx.x, g = tid / tiles::kThreads, lt = tid % tiles::kThreads;
   const int tx = lt % (kTT / 4), ty = lt / (kTT / 4);
+  // Full rankings with one group per tile: the tiles above the diagonal are
+  // tasks of their own, and the 8 x 4 thread blocks of the diagonal tiles on
+  // or above the diagonal (tx >= 2 ty: 72 of 128 per tile) are packed into
+  // tasks of 128 blocks; the blocks below are mirrored with the lower tiles.
+  const bool packdiag = full && jb.gpt == 1;
+  const int32_t noff = nbt * (nbt - 1) / 2;
+  const int32_t ntiles = !full ? nbt * nbt : packdiag ? noff + (nbt * kDiagBlocks + 127) / 128 : nbt * (nbt + 1) / 2;
   // positions are below 2^15 (m <= 1024): the row operand carries the guard
   // bits of count_lt2
   const uint32_t unl = uint32_t(k) & 0xFFFFu, unl2 = unl | (unl << 16) | kGuard2;
@@ -148,20 +155,33 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
   if (gpt > 1 || gpt_last > 1)  // the groups of a tile add into d (visible after the first barrier below)
     for (int64_t t = tid; t < int64_t(m) * m; t += kBT) dm[t] = 0;
   for (int32_t t0 = 0; t0 < ntiles; t0 += tpr) {
-    // this group's tile (bi, bj) and its share of the staged ballots
+    // this group's task and its share of the staged ballots; the thread's
+    // 8 x 4 block of d starts at row R0, column C0 (act: it has one)
     const int gr = ntiles - t0 < tpr ? gpt_last : gpt, phase = g % gr;
     const int32_t tt = t0 + g / gr;
-    int32_t bi = 0, bj = 0;
-    if (tt < ntiles) {
-      if (full) {
-        int32_t rem = tt;
-        while (rem >= nbt - bi) rem -= nbt - bi, ++bi;
-        bj = bi + rem;
+    int32_t R0 = 0, C0 = 0;
+    bool act = tt < ntiles;
+    if (act) {
+      if (packdiag && tt >= noff) {  // packed blocks of the diagonal tiles
+        const int32_t idx = (tt - noff) * 128 + lt;
+        act = idx < nbt * kDiagBlocks;
+        const int32_t dt = idx / kDiagBlocks;
+        int blk = idx % kDiagBlocks, by = 0;
+        while (blk >= kTT / 4 - 2 * by) blk -= kTT / 4 - 2 * by, ++by;  // row group by holds 16 - 2 by blocks
+        R0 = dt * kTT + by * 8, C0 = dt * kTT + (2 * by + blk) * 4;
       } else {
-        bi = tt / nbt, bj = tt % nbt;
+        int32_t bi = 0, bj = 0;
+        if (full) {  // tiles bi <= bj in order (bi < bj when the diagonal is packed)
+          const int32_t dlt = packdiag ? 1 : 0;
+          int32_t rem = tt;
+          while (rem >= nbt - bi - dlt) rem -= nbt - bi - dlt, ++bi;
+          bj = bi + dlt + rem;
+        } else {
+          bi = tt / nbt, bj = tt % nbt;
+        }
+        R0 = bi * kTT + ty * 8, C0 = bj * kTT + tx * 4;
       }
     }
-    const int32_t I0 = bi * kTT, J0 = bj * kTT;
     const bool check = t0 == 0;
     uint32_t acc[8][2];
 #pragma unroll
@@ -205,13 +225,13 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
       }
       if (v0 + chunk < n) load_ids(v0 + chunk);  // in flight while this step counts
       __syncthreads();
-      if (tt < ntiles) {
+      if (act) {
         for (int u = phase; u < nv; u += gr) {
           uint32_t a[8], b[2];
-          const uint4 a0 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8]);
-          const uint4 a1 = *reinterpret_cast<const uint4*>(&dup[u * mpad + I0 + ty * 8 + 4]);
+          const uint4 a0 = *reinterpret_cast<const uint4*>(&dup[u * mpad + R0]);
+          const uint4 a1 = *reinterpret_cast<const uint4*>(&dup[u * mpad + R0 + 4]);
           a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
-          const uint2 bv = *reinterpret_cast<const uint2*>(&pos[u * mpad + J0 + tx * 4]);
+          const uint2 bv = *reinterpret_cast<const uint2*>(&pos[u * mpad + C0]);
           b[0] = bv.x, b[1] = bv.y;
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
@@ -223,10 +243,10 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
         if (last || ((v0 + chunk) % kFlushVoters) == 0) {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
-            const int32_t i = I0 + ty * 8 + r;
+            const int32_t i = R0 + r;
 #pragma unroll
             for (int w = 0; w < 2; ++w) {
-              const int32_t j = J0 + tx * 4 + 2 * w;
+              const int32_t j = C0 + 2 * w;
               if (i < m) {
                 int32_t* dst = dm + int64_t(i) * m + j;
                 const int32_t lo = int32_t(acc[r][w] & 0xFFFFu), hi = int32_t(acc[r][w] >> 16);
@@ -247,10 +267,13 @@ __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t*
     }
   }
   __syncthreads();
-  if (full && nbt > 1) {
+  if (full && (nbt > 1 || packdiag)) {
+    // the tiles below the diagonal and, when packed, the blocks of the
+    // diagonal tiles below it (column block (j % 64) / 4 < 2 (i % 64) / 8)
     for (int64_t t = threadIdx.x; t < int64_t(m) * m; t += kBT) {
       const int32_t i = int32_t(t / m), j = int32_t(t % m);
-      if (i / kTT > j / kTT) dm[t] = n - dm[int64_t(j) * m + i];
+      if (i / kTT > j / kTT || (packdiag && i / kTT == j / kTT && (j % kTT) / 4 < 2 * ((i % kTT) / 8)))
+        dm[t] = n - dm[int64_t(j) * m + i];
     }
   }
   __syncthreads();
