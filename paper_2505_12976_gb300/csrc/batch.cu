@@ -108,8 +108,9 @@ constexpr int kDiagBlocks = 72;  // 8 x 4 blocks of a diagonal tile on or above 
 // Ballots are staged `chunk` at a time as full position rows (unlisted
 // candidates at position k), so one staging serves the four tiles of a
 // round. Counters are added into d every kFlushVoters ballots. Full
-// rankings count only the tiles on and above the diagonal and mirror the
-// rest: d[j][i] = n - d[i][j]. The first round also checks the ballots: an
+// rankings count only the tiles above the diagonal and the thread blocks of
+// the diagonal tiles on or above it, and mirror the rest: d[j][i] = n -
+// d[i][j]. The first round also checks the ballots: an
 // id out of range, or one whose position slot is already taken within the
 // same ballot, is reported as SCHULZE_EDATA.
 __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, BatchSmem& sm,
