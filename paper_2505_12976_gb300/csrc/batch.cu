@@ -109,8 +109,8 @@ constexpr int kDiagBlocks = 72;  // 8 x 4 blocks of a diagonal tile on or above 
 // candidates at position k), so one staging serves the four tiles of a
 // round. Counters are added into d every kFlushVoters ballots. Full
 // rankings count only the tiles above the diagonal and the thread blocks of
-// the diagonal tiles on or above it, and mirror the rest: d[j][i] = n -
-// d[i][j]. The first round also checks the ballots: an
+// the diagonal tiles on or above it (whole diagonal tiles when groups share
+// tiles), and mirror the rest: d[j][i] = n - d[i][j]. The first round also checks the ballots: an
 // id out of range, or one whose position slot is already taken within the
 // same ballot, is reported as SCHULZE_EDATA.
 __device__ void tally(const Job& jb, const int32_t* __restrict__ ranks, int32_t* __restrict__ dm, BatchSmem& sm,
