@@ -49,8 +49,11 @@ struct Acc {  // per-candidate accumulators of the features pass
   int32_t* max_drow;
 };
 
-__global__ void acc_init_kernel(Acc a, int32_t m) {
+// The accumulators of the features pass and the rank counters (one launch
+// instead of a kernel and two memsets).
+__global__ void acc_init_kernel(Acc a, int32_t m, int32_t* __restrict__ cnt14, int32_t* __restrict__ cnt15) {
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    cnt14[c] = cnt15[c] = 0;
     a.wins[c] = a.losses[c] = 0;
     a.rowsum[c] = a.colsum[c] = a.sumw_out[c] = a.sumw_in[c] = 0ull;
     a.maxw_out[c] = a.maxw_in[c] = a.max_drow[c] = 0;
@@ -961,7 +964,7 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
   const int g = std::max(1, std::min((m + 255) / 256, 1024));
   {
     Launch L(ctx, stream, "learn_features_init", double(m) * 64.0);
-    acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m);
+    acc_init_kernel<<<g, 256, 0, stream>>>(w.acc, m, w.cnt14, w.cnt15);
   }
   {
     Launch L(ctx, stream, "learn_features", double(m) * double(m) * 4.0);
@@ -981,9 +984,6 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
     Launch L(ctx, stream, "learn_features_finalize", double(m) * kNF * 4.0);
     features_finalize_kernel<<<(m + 63) / 64, 64, 0, stream>>>(w.acc, m, n, feat);
   }
-  if (cudaMemsetAsync(w.cnt14, 0, size_t(m) * 4, stream) != cudaSuccess ||
-      cudaMemsetAsync(w.cnt15, 0, size_t(m) * 4, stream) != cudaSuccess)
-    return SCHULZE_ECUDA;
   {
     Launch L(ctx, stream, "learn_feature_ranks", double(m) * 16.0);
     const unsigned nch = unsigned((m + kRankChunk - 1) / kRankChunk);
