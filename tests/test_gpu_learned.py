@@ -70,6 +70,20 @@ def test_features_every_count_width_matches_oracle(m, scale):
     np.testing.assert_allclose(f.cpu().numpy(), M.features(d, n), rtol=1e-6, atol=1e-7)
 
 
+def test_features_of_an_unaligned_tally():
+    """d one element past a 16-byte boundary with m a multiple of 4: the
+    features pass copies it element by element and matches the oracle."""
+    m = 300
+    r = W.mallows(78, 900, m, 25, 0.9, W.permutation(78, m))
+    d = oracle.tally(r, m)
+    buf = torch.full((m * m + 1,), -9, dtype=torch.int32, device="cuda")
+    t = buf[1:].view(m, m)
+    assert t.data_ptr() % 16 != 0
+    t.copy_(cu(d))
+    f = S.schulze_features(t, r.shape[0])
+    np.testing.assert_allclose(f.cpu().numpy(), M.features(d, r.shape[0]), rtol=1e-6, atol=1e-7)
+
+
 def test_mlp_forward_matches_oracle():
     rs = np.random.Generator(np.random.PCG64(1))
     theta = W.mlp_init(3)
