@@ -706,8 +706,7 @@ __device__ __forceinline__ void warp_merge(float (&ls)[kMaxProposals], int32_t (
 // The `top` best scores (ties: smaller id first), -1 past the candidates;
 // one CTA: each thread keeps the best `top` of its scores in registers,
 // each warp merges its lanes' lists, warp 0 merges the warps'.
-__global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ score, int32_t m, int32_t top,
-                                                    int32_t* __restrict__ out) {
+__device__ void topk_body(const float* __restrict__ score, int32_t m, int32_t top, int32_t* __restrict__ out) {
   __shared__ float ws[32][kMaxProposals];
   __shared__ int32_t wi[32][kMaxProposals];
   float ls[kMaxProposals];
@@ -753,9 +752,8 @@ __global__ void copeland_score_kernel(Acc a, int32_t m, float* __restrict__ scor
 
 // warm[a] = a-th candidate with an outgoing edge (wins > 0), in id order;
 // slot[c] = its index or -1. One CTA.
-__global__ void __launch_bounds__(1024) warm_list_kernel(const int32_t* __restrict__ wins, int32_t m,
-                                                         int32_t* __restrict__ warm, int32_t* __restrict__ slot,
-                                                         int32_t* __restrict__ nwarm) {
+__device__ void warm_list_body(const int32_t* __restrict__ wins, int32_t m, int32_t* __restrict__ warm,
+                               int32_t* __restrict__ slot, int32_t* __restrict__ nwarm) {
   __shared__ int32_t part[1024];
   const int T = blockDim.x;
   const int per = (m + T - 1) / T;
@@ -780,6 +778,25 @@ __global__ void __launch_bounds__(1024) warm_list_kernel(const int32_t* __restri
     }
   }
   if (threadIdx.x == T - 1) *nwarm = part[T - 1];
+}
+
+__global__ void __launch_bounds__(1024) warm_list_kernel(const int32_t* __restrict__ wins, int32_t m,
+                                                         int32_t* __restrict__ warm, int32_t* __restrict__ slot,
+                                                         int32_t* __restrict__ nwarm) {
+  warm_list_body(wins, m, warm, slot, nwarm);
+}
+
+// The proposals and the warm list in one launch (CTA 0 and CTA 1 side by
+// side): the two single-CTA passes of schulze_winners_fast depend on
+// different inputs (the scores; the wins of the features pass).
+__global__ void __launch_bounds__(1024) propose_kernel(const float* __restrict__ score, int32_t m, int32_t top,
+                                                       int32_t* __restrict__ out, const int32_t* __restrict__ wins,
+                                                       int32_t* __restrict__ warm, int32_t* __restrict__ slot,
+                                                       int32_t* __restrict__ nwarm) {
+  if (blockIdx.x == 0)
+    topk_body(score, m, top, out);
+  else
+    warm_list_body(wins, m, warm, slot, nwarm);
 }
 
 // Ww[a][b] = w(warm[a], warm[b]) and Wt[b][a] = the same (winning votes).
@@ -995,8 +1012,8 @@ int features_into(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t n, floa
 
 int certify_launch(schulze_ctx* ctx, const int32_t* d, int32_t m, const int32_t* cand, int32_t ncand,
                    int32_t* winners, int32_t* res, const LearnedWs& w, int32_t* fwd, int32_t* bwd,
-                   cudaStream_t stream) {
-  {
+                   cudaStream_t stream, bool warm_listed = false) {
+  if (!warm_listed) {
     Launch L(ctx, stream, "certify_warm_list", double(m) * 8.0);
     warm_list_kernel<<<1, 1024, 0, stream>>>(w.acc.wins, m, w.warm, w.slot, w.nwarm);
   }
@@ -1126,10 +1143,12 @@ int schulze_winners_fast(schulze_ctx* ctx, const int32_t* d, int32_t m, int64_t 
       copeland_score_kernel<<<std::max(1, std::min((m + 255) / 256, 1024)), 256, 0, stream>>>(w.acc, m, w.score);
   }
   {
-    Launch L(ctx, stream, "proposal_topk", double(m) * 4.0);
-    topk_kernel<<<1, 1024, 0, stream>>>(w.score, m, std::min(top, m), w.cand);
+    Launch L(ctx, stream, "proposal_topk", double(m) * 4.0);  // and the warm list
+    propose_kernel<<<2, 1024, 0, stream>>>(w.score, m, std::min(top, m), w.cand, w.acc.wins, w.warm, w.slot,
+                                          w.nwarm);
   }
-  if (int rc = certify_launch(ctx, d, m, w.cand, std::min(top, m), winners, w.res, w, fwd, bwd, stream)) return rc;
+  if (int rc = certify_launch(ctx, d, m, w.cand, std::min(top, m), winners, w.res, w, fwd, bwd, stream, true))
+    return rc;
   int32_t res[4] = {0, -1, 0, 0};
   int32_t nwarm = 0;
   if (cudaMemcpyAsync(res, w.res, sizeof(res), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
